@@ -1,0 +1,167 @@
+"""Parameter grid of the 5-D helix voxel space and its shared input tables.
+
+The paper discretises the helix parameter space into voxels (multidimensional intervals,
+Section 3.1).  Here a voxel ("cell") is a box over the five axes
+
+    a = 0: d0      signed transverse distance of the POCA to the origin  [m]
+    a = 1: phi0    azimuth of the helix tangent at the POCA              [rad]
+    a = 2: omega   signed curvature rho = 1/R                            [1/m]
+    a = 3: z0      z of the helix at the POCA                            [m]
+    a = 4: tanl    lambda = tan(dip angle)
+
+Level 0 has bins[a] cells along axis a; every level halves each cell along every axis, so a
+level-L cell index is idx_a in [0, bins[a] * 2**L) and its 32 children are 2 idx_a + bit_a.
+The omega axis is split into two equal halves [-1, -0.15] and [0.15, 1] so that no cell
+straddles omega = 0.
+
+This module only defines the grid: the finest-level cell edges (rounded to nearest once
+here) and a table of outward-rounded enclosures of sin/cos over every phi0 cell of every
+level.  Both are inputs shared by every consumer; none of the voting arithmetic is here.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+AXES = ("d0", "phi0", "omega", "z0", "tanl")
+N_AXES = 5
+KEY_BITS = 10            # bits per axis in a cell key (idx < 1024)
+
+
+@dataclass
+class Grid:
+    bins: np.ndarray        # int32[5], level-0 bins per axis
+    levels: int             # number of bisection levels after level 0
+    topk: int
+    lo_edge: list           # per axis: float64[bins[a] << levels], finest-cell lower edges
+    hi_edge: list           # per axis: float64[bins[a] << levels], finest-cell upper edges
+    sincos: np.ndarray      # float64[sum_L bins[1] << L, 4]: (sin_lo, sin_hi, cos_lo, cos_hi)
+    sincos_offset: np.ndarray   # int64[levels + 1]: first row of level L in `sincos`
+    ranges: tuple = ()
+
+    def n_fine(self, a: int) -> int:
+        return int(self.bins[a]) << self.levels
+
+    def cell_edges(self, level: int, a: int, idx):
+        """Lower and upper edge of cell idx (any array) on axis a at `level`."""
+        sh = self.levels - level
+        idx = np.asarray(idx, np.int64)
+        return self.lo_edge[a][idx << sh], self.hi_edge[a][((idx + 1) << sh) - 1]
+
+    def n_coarse(self) -> int:
+        return int(np.prod(self.bins.astype(np.int64)))
+
+
+def _uniform_edges(lo: float, hi: float, n: int):
+    w = (hi - lo) / n
+    e = lo + np.arange(n + 1, dtype=np.float64) * w
+    return e[:-1].copy(), e[1:].copy()
+
+
+def _widen(x: np.ndarray, k: int, direction: float) -> np.ndarray:
+    for _ in range(k):
+        x = np.nextafter(x, direction)
+    return x
+
+
+def sincos_enclosures(a: np.ndarray, b: np.ndarray, ulps: int = 2):
+    """Outward enclosures of sin and cos over [a_i, b_i]: hull of the end-point values
+    widened by `ulps` ulp each way, joined with +-1 wherever a multiple of pi/2 where sin or
+    cos reaches an extremum may lie inside the cell (tested with a margin), clamped to
+    [-1, 1]."""
+    sa, sb, ca, cb = np.sin(a), np.sin(b), np.cos(a), np.cos(b)
+    s_lo = _widen(np.minimum(sa, sb), ulps, -np.inf)
+    s_hi = _widen(np.maximum(sa, sb), ulps, np.inf)
+    c_lo = _widen(np.minimum(ca, cb), ulps, -np.inf)
+    c_hi = _widen(np.maximum(ca, cb), ulps, np.inf)
+    eps = 1e-12
+    half_pi = np.pi / 2.0
+    k_lo = np.floor((a - eps) / half_pi).astype(np.int64)
+    k_hi = np.ceil((b + eps) / half_pi).astype(np.int64)
+    for i in range(a.shape[0]):
+        for k in range(k_lo[i], k_hi[i] + 1):
+            x = k * half_pi
+            if a[i] - eps <= x <= b[i] + eps:
+                m = k % 4          # 0: cos=1, 1: sin=1, 2: cos=-1, 3: sin=-1
+                if m == 0:
+                    c_hi[i] = 1.0
+                elif m == 1:
+                    s_hi[i] = 1.0
+                elif m == 2:
+                    c_lo[i] = -1.0
+                else:
+                    s_lo[i] = -1.0
+    clip = lambda x: np.clip(x, -1.0, 1.0)
+    return clip(s_lo), clip(s_hi), clip(c_lo), clip(c_hi)
+
+
+def make_grid(bins, levels: int, topk: int,
+              d0=(-0.01, 0.01), phi0=(0.0, 2.0 * np.pi), omega_abs=(0.15, 1.0),
+              z0=(-0.10, 0.10), tanl=(-0.8, 0.8)) -> Grid:
+    bins = np.asarray(bins, np.int32)
+    assert bins.shape == (5,) and bins[2] % 2 == 0, "omega bins are split evenly per sign"
+    assert all(int(b) << levels <= (1 << KEY_BITS) for b in bins)
+    lo_e, hi_e = [], []
+    for a, rng in enumerate((d0, phi0, None, z0, tanl)):
+        n = int(bins[a]) << levels
+        if a == 2:
+            h = n // 2
+            nlo, nhi = _uniform_edges(-omega_abs[1], -omega_abs[0], h)
+            plo, phi_ = _uniform_edges(omega_abs[0], omega_abs[1], h)
+            lo_e.append(np.concatenate([nlo, plo]))
+            hi_e.append(np.concatenate([nhi, phi_]))
+        else:
+            l_, h_ = _uniform_edges(rng[0], rng[1], n)
+            lo_e.append(l_)
+            hi_e.append(h_)
+    g = Grid(bins=bins, levels=levels, topk=topk, lo_edge=lo_e, hi_edge=hi_e,
+             sincos=np.zeros((0, 4)), sincos_offset=np.zeros(levels + 1, np.int64),
+             ranges=(d0, phi0, omega_abs, z0, tanl))
+    rows, offs, parent = [], [], None
+    off = 0
+    for L in range(levels + 1):
+        n = int(bins[1]) << L
+        a, b = g.cell_edges(L, 1, np.arange(n))
+        s_lo, s_hi, c_lo, c_hi = sincos_enclosures(a, b)
+        if parent is not None:   # a child's enclosure never exceeds its parent's
+            p = parent[np.arange(n) >> 1]
+            s_lo = np.maximum(s_lo, p[:, 0])
+            s_hi = np.minimum(s_hi, p[:, 1])
+            c_lo = np.maximum(c_lo, p[:, 2])
+            c_hi = np.minimum(c_hi, p[:, 3])
+        tab = np.stack([s_lo, s_hi, c_lo, c_hi], axis=1)
+        rows.append(tab)
+        offs.append(off)
+        off += n
+        parent = tab
+    g.sincos = np.ascontiguousarray(np.concatenate(rows, axis=0))
+    g.sincos_offset = np.asarray(offs, np.int64)
+    return g
+
+
+def cell_key(idx5) -> np.ndarray:
+    """Packed uint64 key sum_a idx_a << (10 a); idx5 has shape (..., 5)."""
+    idx5 = np.asarray(idx5, np.uint64)
+    k = np.zeros(idx5.shape[:-1], np.uint64)
+    for a in range(N_AXES):
+        k |= idx5[..., a] << np.uint64(KEY_BITS * a)
+    return k
+
+
+def key_indices(keys) -> np.ndarray:
+    keys = np.asarray(keys, np.uint64)
+    m = np.uint64((1 << KEY_BITS) - 1)
+    return np.stack([(keys >> np.uint64(KEY_BITS * a)) & m for a in range(N_AXES)],
+                    axis=-1).astype(np.int64)
+
+
+def coarse_index_to_idx5(lin, bins) -> np.ndarray:
+    """Level-0 linear index (d0 fastest, tanl slowest) -> per-axis indices.  This order
+    is the key order, so sorting by linear index sorts by key."""
+    lin = np.asarray(lin, np.int64)
+    out = []
+    for a in range(N_AXES):
+        out.append(lin % int(bins[a]))
+        lin = lin // int(bins[a])
+    return np.stack(out, axis=-1)

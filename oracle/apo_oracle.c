@@ -1,0 +1,329 @@
+/* Plain CPU oracle of interval-arithmetic Apollonius voting over the 5-D helix parameter
+ * space (arXiv:2401.04576, Sections 3.1 and 3.3, Appendix A).
+ *
+ * TEST INFRASTRUCTURE.  Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline /
+ * reference leg load this library.  It shares no code with the CUDA path.
+ *
+ * It is slow on purpose: every cell is evaluated against every hit with the full interval
+ * program of vote_program.inc, one directed operation at a time, under fesetround
+ * (FE_DOWNWARD, upward results by exact negation).  OpenMP only splits the loop over
+ * cells; it changes no result.
+ *
+ * Build: cc -O1 -frounding-math -ffp-contract=off -fno-fast-math -fopenmp -shared -fPIC
+ * (no FMA contraction: every product and sum is rounded on its own).
+ */
+#include <fenv.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#pragma STDC FENV_ACCESS ON
+
+#define REAL double
+#define SFX _d
+#define SQRT sqrt
+#define NEXTUP(x) nextafter((x), INFINITY)
+#include "vote_program.inc"
+#undef REAL
+#undef SFX
+#undef SQRT
+#undef NEXTUP
+
+#define REAL float
+#define SFX _f
+#define SQRT sqrtf
+#define NEXTUP(x) nextafterf((x), INFINITY)
+#include "vote_program.inc"
+#undef REAL
+#undef SFX
+#undef SQRT
+#undef NEXTUP
+
+/* ------------------------------------------------------------------------------------ */
+/* Inputs                                                                                */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+    int32_t n_wires;
+    const double *x0, *y0, *sin_phis, *cos_phis, *tan_tau, *sphi_t, *cphi_t, *t2;
+} or_wires;
+
+typedef struct {
+    int32_t bins[5];
+    int32_t levels;
+    int32_t topk;
+    const double *lo_edge[5];     /* finest-level cell edges, bins[a] << levels each */
+    const double *hi_edge[5];
+    const double *sincos;         /* rows of (sin lo, sin hi, cos lo, cos hi) */
+    const int64_t *sincos_offset; /* first row of level L */
+} or_grid;
+
+/* One cell of `level` as 6 FP64 intervals: D, S0, C0, W, Z, L (lo, hi each). */
+static void cell_intervals(const or_grid *g, int level, const int32_t idx[5], double c[12]) {
+    int sh = g->levels - level;
+    double lo[5], hi[5];
+    for (int a = 0; a < 5; a++) {
+        int64_t i = idx[a];
+        lo[a] = g->lo_edge[a][i << sh];
+        hi[a] = g->hi_edge[a][((i + 1) << sh) - 1];
+    }
+    const double *sc = g->sincos + 4 * (g->sincos_offset[level] + idx[1]);
+    c[0] = lo[0]; c[1] = hi[0];
+    c[2] = sc[0]; c[3] = sc[1];
+    c[4] = sc[2]; c[5] = sc[3];
+    c[6] = lo[2]; c[7] = hi[2];
+    c[8] = lo[3]; c[9] = hi[3];
+    c[10] = lo[4]; c[11] = hi[4];
+}
+
+static void hit_constants(const or_wires *w, int32_t wid, double drift, double h[9]) {
+    h[0] = w->x0[wid]; h[1] = w->y0[wid]; h[2] = w->sin_phis[wid]; h[3] = w->cos_phis[wid];
+    h[4] = w->tan_tau[wid]; h[5] = w->sphi_t[wid]; h[6] = w->cphi_t[wid]; h[7] = w->t2[wid];
+    h[8] = drift;
+}
+
+/* FP32 inputs: each FP64 end point rounded outward (lo down, hi up). */
+static float rd32(double x) { volatile float r = (float)x; return r; }   /* FE_DOWNWARD */
+static float ru32(double x) { volatile float r = (float)(-x); return -r; }
+
+/* The vote of one (cell, hit) pair.  prec 0: FP64 intervals, 1: FP32 intervals. */
+static int vote_pair(const double c[12], const double h[9], int prec, double *out) {
+    if (prec == 0) {
+        iv_d C[6], H[9];
+        for (int i = 0; i < 6; i++) C[i] = mk_d(c[2 * i], c[2 * i + 1]);
+        for (int i = 0; i < 9; i++) H[i] = mk_d(h[i], h[i]);
+        return vote_program_d(C[0], C[1], C[2], C[3], C[4], C[5], H[0], H[1], H[2], H[3],
+                              H[4], H[5], H[6], H[7], H[8], out);
+    } else {
+        iv_f C[6], H[9];
+        for (int i = 0; i < 6; i++) C[i] = mk_f(rd32(c[2 * i]), ru32(c[2 * i + 1]));
+        for (int i = 0; i < 9; i++) H[i] = mk_f(rd32(h[i]), ru32(h[i]));
+        return vote_program_f(C[0], C[1], C[2], C[3], C[4], C[5], H[0], H[1], H[2], H[3],
+                              H[4], H[5], H[6], H[7], H[8], out);
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Exported: one pair                                                                    */
+/* ------------------------------------------------------------------------------------ */
+int or_vote_pair(const double cell[12], const double hit[9], int prec, double out[5]) {
+    int old = fegetround();
+    fesetround(FE_DOWNWARD);
+    int v = vote_pair(cell, hit, prec, out);
+    fesetround(old);
+    return v;
+}
+
+
+/* ------------------------------------------------------------------------------------ */
+/* Cell keys                                                                             */
+/* ------------------------------------------------------------------------------------ */
+static void key_to_idx(uint64_t key, int32_t idx[5]) {
+    for (int a = 0; a < 5; a++) idx[a] = (int32_t)((key >> (10 * a)) & 1023u);
+}
+static uint64_t idx_to_key(const int32_t idx[5]) {
+    uint64_t k = 0;
+    for (int a = 0; a < 5; a++) k |= (uint64_t)idx[a] << (10 * a);
+    return k;
+}
+
+/* votes of n cells of `level` (given by key) for one event's hits: Eq. (ApoVote) summed
+ * over hits, one vote per (cell, hit) whichever drift sign passes (Section 3.1). */
+void or_vote_cells(const or_grid *g, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
+                   const double *drift, int32_t level, int32_t prec, const uint64_t *keys,
+                   int64_t n, int32_t *votes) {
+    #pragma omp parallel
+    {
+        int old = fegetround();
+        fesetround(FE_DOWNWARD);
+        #pragma omp for schedule(dynamic, 256)
+        for (int64_t j = 0; j < n; j++) {
+            int32_t idx[5];
+            double c[12], h[9];
+            key_to_idx(keys[j], idx);
+            cell_intervals(g, level, idx, c);
+            int32_t v = 0;
+            for (int32_t i = 0; i < n_hits; i++) {
+                hit_constants(w, wire_id[i], drift[i], h);
+                v += vote_pair(c, h, prec, NULL);
+            }
+            votes[j] = v;
+        }
+        fesetround(old);
+    }
+}
+
+/* keys of all level-0 cells in linear order (d0 fastest, tanl slowest = key order) */
+static void coarse_keys(const or_grid *g, uint64_t *keys) {
+    int64_t n = 1;
+    for (int a = 0; a < 5; a++) n *= g->bins[a];
+    for (int64_t j = 0; j < n; j++) {
+        int64_t r = j;
+        int32_t idx[5];
+        for (int a = 0; a < 5; a++) { idx[a] = (int32_t)(r % g->bins[a]); r /= g->bins[a]; }
+        keys[j] = idx_to_key(idx);
+    }
+}
+
+void or_coarse_keys(const or_grid *g, uint64_t *keys) { coarse_keys(g, keys); }
+
+/* ------------------------------------------------------------------------------------ */
+/* Top-K and bisection                                                                   */
+/* ------------------------------------------------------------------------------------ */
+typedef struct { uint64_t key; int32_t votes; } kv;
+
+/* votes descending, then key ascending (deterministic tie-break) */
+static int kv_cmp(const void *pa, const void *pb) {
+    const kv *a = (const kv *)pa, *b = (const kv *)pb;
+    if (a->votes != b->votes) return a->votes > b->votes ? -1 : 1;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return 0;
+}
+
+/* The K best cells by (votes desc, key asc); returns how many were written (min(K, n)). */
+int64_t or_topk(const uint64_t *keys, const int32_t *votes, int64_t n, int32_t K,
+                uint64_t *out_keys, int32_t *out_votes) {
+    kv *a = (kv *)malloc(sizeof(kv) * (size_t)(n > 0 ? n : 1));
+    for (int64_t j = 0; j < n; j++) { a[j].key = keys[j]; a[j].votes = votes[j]; }
+    qsort(a, (size_t)n, sizeof(kv), kv_cmp);
+    int64_t m = n < K ? n : K;
+    for (int64_t j = 0; j < m; j++) { out_keys[j] = a[j].key; out_votes[j] = a[j].votes; }
+    free(a);
+    return m;
+}
+
+/* each cell -> its 32 children (index 2 idx_a + bit_a, bit_a = bit a of the child number) */
+void or_children(const uint64_t *keys, int64_t n, uint64_t *children) {
+    for (int64_t j = 0; j < n; j++) {
+        int32_t idx[5], c[5];
+        key_to_idx(keys[j], idx);
+        for (int b = 0; b < 32; b++) {
+            for (int a = 0; a < 5; a++) c[a] = 2 * idx[a] + ((b >> a) & 1);
+            children[32 * j + b] = idx_to_key(c);
+        }
+    }
+}
+
+/* Final estimate (Section 3.3: values and errors from the centres and sizes of the
+ * maximum-vote voxels): over the cells whose votes equal the maximum, in ascending key
+ * order, value = mean of the cell centres (lo + hi) / 2 and error = (max hi - min lo) / 2
+ * per axis, all in round-to-nearest. */
+static void estimate(const or_grid *g, int level, const uint64_t *keys, const int32_t *votes,
+                     int64_t n, double p[5], double werr[5], int32_t *best) {
+    int32_t vmax = -1;
+    for (int64_t j = 0; j < n; j++) if (votes[j] > vmax) vmax = votes[j];
+    kv *a = (kv *)malloc(sizeof(kv) * (size_t)(n > 0 ? n : 1));
+    int64_t m = 0;
+    for (int64_t j = 0; j < n; j++)
+        if (votes[j] == vmax) { a[m].key = keys[j]; a[m].votes = votes[j]; m++; }
+    qsort(a, (size_t)m, sizeof(kv), kv_cmp);
+    int sh = g->levels - level;
+    for (int ax = 0; ax < 5; ax++) {
+        double sum = 0, lo_min = INFINITY, hi_max = -INFINITY;
+        for (int64_t j = 0; j < m; j++) {
+            int32_t idx[5];
+            key_to_idx(a[j].key, idx);
+            double lo = g->lo_edge[ax][(int64_t)idx[ax] << sh];
+            double hi = g->hi_edge[ax][(((int64_t)idx[ax] + 1) << sh) - 1];
+            sum += (lo + hi) / 2;
+            if (lo < lo_min) lo_min = lo;
+            if (hi > hi_max) hi_max = hi;
+        }
+        p[ax] = sum / (double)m;
+        werr[ax] = (hi_max - lo_min) / 2;
+    }
+    *best = vmax;
+    free(a);
+}
+
+/* Whole coarse-to-fine search for one event (configuration of the grid: bins, levels,
+ * top-K).  Level 0 is the full grid; at each level the K best cells survive and are
+ * bisected along every axis; the last level's maximum-vote cells give the estimate.
+ * prec[L] selects FP64 (0) or FP32 (1) intervals at level L.
+ * Trace outputs (may be NULL): frontier keys / votes kept after level L, K per level,
+ * and the last level's votes (K * 32). */
+int or_solve_event(const or_grid *g, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
+                   const double *drift, const int32_t *prec, double p[5], double werr[5],
+                   int32_t *best_votes, uint64_t *trace_keys, int32_t *trace_votes,
+                   uint64_t *last_keys, int32_t *last_votes) {
+    int64_t n0 = 1;
+    for (int a = 0; a < 5; a++) n0 *= g->bins[a];
+    int32_t K = g->topk;
+    uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n0);
+    int32_t *votes = (int32_t *)malloc(sizeof(int32_t) * (size_t)n0);
+    coarse_keys(g, keys);
+    or_vote_cells(g, w, n_hits, wire_id, drift, 0, prec[0], keys, n0, votes);
+    uint64_t *fk = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)K);
+    int32_t *fv = (int32_t *)malloc(sizeof(int32_t) * (size_t)K);
+    uint64_t *ck = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)K * 32);
+    int32_t *cv = (int32_t *)malloc(sizeof(int32_t) * (size_t)K * 32);
+    int64_t m = or_topk(keys, votes, n0, K, fk, fv);
+    if (trace_keys) { memcpy(trace_keys, fk, sizeof(uint64_t) * (size_t)m); memcpy(trace_votes, fv, sizeof(int32_t) * (size_t)m); }
+    for (int L = 1; L <= g->levels; L++) {
+        or_children(fk, m, ck);
+        or_vote_cells(g, w, n_hits, wire_id, drift, L, prec[L], ck, m * 32, cv);
+        if (L == g->levels) {
+            estimate(g, L, ck, cv, m * 32, p, werr, best_votes);
+            if (last_keys) { memcpy(last_keys, ck, sizeof(uint64_t) * (size_t)m * 32); memcpy(last_votes, cv, sizeof(int32_t) * (size_t)m * 32); }
+            break;
+        }
+        m = or_topk(ck, cv, m * 32, K, fk, fv);
+        if (trace_keys) {
+            memcpy(trace_keys + (size_t)L * K, fk, sizeof(uint64_t) * (size_t)m);
+            memcpy(trace_votes + (size_t)L * K, fv, sizeof(int32_t) * (size_t)m);
+        }
+    }
+    if (g->levels == 0) estimate(g, 0, keys, votes, n0, p, werr, best_votes);
+    free(keys); free(votes); free(fk); free(fv); free(ck); free(cv);
+    return 0;
+}
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void or_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Exported for the pin tests: the transcendental enclosures on their own.               */
+/* ------------------------------------------------------------------------------------ */
+void or_atan_iv(double lo, double hi, int prec, double out[2]) {
+    int old = fegetround();
+    fesetround(FE_DOWNWARD);
+    if (prec == 0) {
+        iv_d r = atan_iv_d(mk_d(lo, hi));
+        out[0] = r.lo; out[1] = r.hi;
+    } else {
+        iv_f r = atan_iv_f(mk_f(rd32(lo), ru32(hi)));
+        out[0] = r.lo; out[1] = r.hi;
+    }
+    fesetround(old);
+}
+
+void or_sincos_iv(double lo, double hi, int prec, double out[4]) {
+    int old = fegetround();
+    fesetround(FE_DOWNWARD);
+    if (prec == 0) {
+        iv_d s, c;
+        sincos_iv_d(mk_d(lo, hi), &s, &c);
+        out[0] = s.lo; out[1] = s.hi; out[2] = c.lo; out[3] = c.hi;
+    } else {
+        iv_f s, c;
+        sincos_iv_f(mk_f(rd32(lo), ru32(hi)), &s, &c);
+        out[0] = s.lo; out[1] = s.hi; out[2] = c.lo; out[3] = c.hi;
+    }
+    fesetround(old);
+}
