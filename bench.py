@@ -1,0 +1,385 @@
+"""Benchmark of the interval-voting hot path on GB300.
+
+One step = apo_solve_batch over a batch of synthetic single-track events of the toy
+stereo chamber: coarse 16^5-cell voting, top-64, six rounds of bisection + voting + top-64,
+and the max-vote estimate (arXiv:2401.04576, Sections 3.1 and 3.3), FP64 intervals.
+The metric is (cell, hit) interval evaluations decided per second (coarse cells x hits +
+bisected cells x hits, summed over events), with events per second beside it.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl apo|reference]
+Under torchrun (N > 1) every rank runs its own batch on its own GPU (weak scaling); the
+step time is the maximum over ranks.  --impl reference times the CPU oracle instead (rank
+0 only) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("cell-hit interval evals/s and events/s at 1 GB300 (FP32-bulk vs plain FP64); "
+          "p50/p99 ms")
+WORKLOAD = dict(name="1024 single-track events, 16^5 coarse cells, top-64, 6 bisection levels, "
+                     "FP64 intervals", n_events=1024, seed=2, bins=16, levels=6, topk=64)
+
+# Directed floating-point operations of one evaluation of the vote program, by phase:
+# per (cell, hit) without tan(lambda), tan(lambda)-dependent part, both drift signs.
+# Counted by the oracle's instrumented interval operations (2 per rounding interval
+# operation); tests/test_bench_host.py checks these against it.
+OPS_PREFIX, OPS_LPART, OPS_SIGNS, OPS_CELL = 188, 147, 60, 2
+OPS_FULL = OPS_CELL + OPS_PREFIX + OPS_LPART + OPS_SIGNS
+OPS_TAIL = OPS_LPART + OPS_SIGNS
+
+
+def coarse_kernel_ops(n_parent: int, n_prefix: int, n_tail: int) -> int:
+    """Algorithmic directed FP operations of the coarse vote kernel from its work counters:
+    parent-cell tests are full evaluations, each (cell, hit) prefix and each tan(lambda)
+    tail as counted."""
+    return n_parent * OPS_FULL + n_prefix * OPS_PREFIX + n_tail * OPS_TAIL
+
+
+def pairs_decided(n_hits: np.ndarray, n_coarse: int, levels: int, topk: int) -> float:
+    """(cell, hit) pairs whose vote one step decides: all coarse cells and the topk * 32
+    children of every bisection level, times the hits of each event."""
+    return float(np.sum(n_hits.astype(np.float64)) * (n_coarse + levels * topk * 32))
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(value: float, world: int) -> float:
+    """Maximum of a per-rank number over ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def make_inputs(seed_offset: int = 0):
+    from gen import chamber, grid as G
+    w = chamber.make_wires()
+    g = G.make_grid([WORKLOAD["bins"]] * 5, WORKLOAD["levels"], WORKLOAD["topk"])
+    ev = chamber.single_track_events(WORKLOAD["n_events"], seed=WORKLOAD["seed"] + seed_offset,
+                                     w=w)
+    return w, g, ev
+
+
+def cpu_baseline(w, g, ev, n_sample: int) -> dict:
+    """The oracle as it stands, on the host cores, over the first n_sample events (full
+    coarse-to-fine search each)."""
+    from oracle import oracle as O
+    tab = O.Tables(g, w)
+    nh = np.diff(ev.offsets)[:n_sample]
+    t0 = time.perf_counter()
+    for e in range(n_sample):
+        a, b = ev.offsets[e], ev.offsets[e + 1]
+        O.solve_event(tab, ev.wire_id[a:b], ev.drift[a:b])
+    dt = time.perf_counter() - t0
+    pairs = pairs_decided(nh, g.n_coarse(), g.levels, g.topk)
+    return {"value": pairs / dt, "unit": "evals/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{n_sample} of the {ev.n_events} events, full search each "
+                      f"({pairs:.3g} pair evaluations, {dt:.1f} s wall)",
+            "events_per_s": n_sample / dt}
+
+
+def run_reference(args) -> None:
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    w, g, ev = make_inputs()
+    from oracle import oracle as O
+    tab = O.Tables(g, w)
+    n_sample = 1
+    times = []
+    for i in range(args.warmup + args.steps):
+        e = i % ev.n_events
+        a, b = ev.offsets[e], ev.offsets[e + 1]
+        t0 = time.perf_counter()
+        O.solve_event(tab, ev.wire_id[a:b], ev.drift[a:b])
+        if i >= args.warmup:
+            times.append((time.perf_counter() - t0, b - a))
+    dt = sum(t for t, _ in times)
+    pairs = sum(pairs_decided(np.array([n]), g.n_coarse(), g.levels, g.topk) for _, n in times)
+    val = pairs / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "evals/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"],
+                   "sample": f"{n_sample} event per step (of {WORKLOAD['n_events']})"},
+        "events_per_s": len(times) / dt,
+        "cpu_baseline": {"value": val, "unit": "evals/s", "cores": O.num_threads(),
+                         "kind": "oracle", "sample": f"{n_sample} event per step"},
+        "e2e": {"value": val, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_apo(args) -> None:
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2401_04576_gb300 import apo
+
+    w, g, ev = make_inputs(seed_offset=rank)
+    nh = np.diff(ev.offsets)
+    geom = apo.Geometry(g, w)
+    hits = apo.DeviceHits.from_events(ev)
+    ws = geom.workspace(ev.n_events)
+    lv = g.levels
+    opts64 = apo.solve_opts(precision=[apo.F64] * (lv + 1))
+    opts32 = apo.solve_opts(precision=[apo.F32] * 5 + [apo.F64] * (lv + 1 - 5))
+    tracks = torch.zeros(ev.n_events * apo.TRACK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    ntr = torch.zeros(ev.n_events, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step(o):
+        apo.solve_batch(geom, hits, o, tracks=tracks, n_tracks=ntr, workspace=ws, stream=stream)
+
+    def timed(o, steps, warmup):
+        for _ in range(warmup):
+            step(o)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            step(o)
+            s1.record(stream)
+            s1.synchronize()
+            ms.append(s0.elapsed_time(s1))
+        torch.cuda.synchronize()
+        barrier(world)
+        return ms
+
+    with ClockSampler(local) as clk:
+        ms64 = timed(opts64, args.steps, args.warmup)
+    clocks = clk.summary()
+    t_step = reduce_max(sum(ms64) / len(ms64), world)
+    pairs = pairs_decided(nh, geom.n_coarse, lv, g.topk)
+    value = pairs * world / (t_step * 1e-3)
+
+    # FP32-bulk precision form on the same events (FP32 coarse + levels 1-4, FP64 5-6)
+    ms32 = timed(opts32, max(2, args.steps), 1)
+    t32 = reduce_max(sum(ms32) / len(ms32), world)
+
+    # roofline of the dominant kernel (coarse vote): counted work / live launch time
+    votes = torch.empty((ev.n_events, geom.n_coarse), dtype=torch.int32, device="cuda")
+    counts = torch.zeros(4, dtype=torch.int64, device="cuda")
+    L = apo.lib()
+    hc = hits.c()
+    import ctypes as C
+    rc = L.apo_diag_vote_coarse_counts(geom.handle, C.byref(hc), apo.F64, apo._ptr(votes),
+                                       apo._ptr(counts), apo._ptr(ws), ws.numel(),
+                                       apo._stream_ptr(stream))
+    apo._check(rc)
+    n_par, n_pre, n_tail, n_launch = (int(x) for x in counts.cpu().tolist())
+    ops_launch = coarse_kernel_ops(n_par, n_pre, n_tail) / max(n_launch, 1)
+    kms = []
+    for _ in range(max(2, args.steps)):
+        flush.fill_(1)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        apo.vote(geom, hits, precision=apo.F64, out=votes, workspace=ws, stream=stream)
+        s1.record(stream)
+        s1.synchronize()
+        kms.append(s0.elapsed_time(s1) / n_launch)
+    k_ms = statistics.mean(kms)
+    peak = apo.pipe_peak(apo.F64)
+    achieved = ops_launch / (k_ms * 1e-3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "kernel": "k_vote_coarse<double>",
+                "peak_source": "measured: libapo directed-rounding FP64 add/mul microbenchmark "
+                               "(apo_diag_pipe_peak) on this GPU, this run",
+                "ops_per_launch": ops_launch, "launch_ms": k_ms}
+
+    # end to end through the host-buffer entry point (pinned host inputs, tracks back)
+    off_h = torch.from_numpy(np.ascontiguousarray(ev.offsets, np.int32)).pin_memory()
+    wid_h = torch.from_numpy(np.ascontiguousarray(ev.wire_id, np.int32)).pin_memory()
+    dr_h = torch.from_numpy(np.ascontiguousarray(ev.drift, np.float64)).pin_memory()
+    wsh = torch.empty(apo.host_workspace_bytes(geom, ev.n_events, int(ev.offsets[-1])),
+                      dtype=torch.uint8, device="cuda")
+    out_h = np.zeros((ev.n_events, 1), apo.TRACK_DTYPE)
+    e2e_ms = []
+    for i in range(1 + max(2, args.steps)):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        apo.solve_batch_host(geom, off_h.numpy(), wid_h.numpy(), dr_h.numpy(), opts64,
+                             workspace=wsh, out=out_h, stream=stream)
+        if i > 0:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    t_e2e = reduce_max(statistics.mean(e2e_ms), world)
+    h2d = 4 * (ev.n_events + 1) + 12 * int(ev.offsets[-1])
+    d2h = apo.TRACK_DTYPE.itemsize * ev.n_events + 4 * ev.n_events
+
+    launches = apo.solve_launches(geom, ev.n_events)
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "n_events": ev.n_events,
+                   "coarse_cells": geom.n_coarse, "topk": g.topk, "levels": lv,
+                   "hits_per_event_mean": float(nh.mean()),
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "events_per_s": ev.n_events * world / (t_step * 1e-3),
+        "fp32_bulk": {"ms_per_step": t32, "value": pairs * world / (t32 * 1e-3),
+                      "unit": "evals/s", "events_per_s": ev.n_events * world / (t32 * 1e-3),
+                      "precision": "FP32 levels 0-4, FP64 levels 5-6"},
+        "step_ms_p50": float(np.percentile(ms64, 50)), "step_ms_p99": float(np.percentile(ms64, 99)),
+        "e2e": {"value": pairs * world / (t_e2e * 1e-3), "unit": "evals/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e},
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks,
+        "roofline": roofline,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, g, ev, args.cpu_sample)
+    if rank == 0:
+        print(json.dumps(line))
+    geom.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_case(args) -> None:
+    """Small profiling case: one warm-up and one measured call of a single kernel family on
+    the first --events events of the workload (for ncu captures of one launch)."""
+    import torch
+    from paper_2401_04576_gb300 import apo
+    w, g, ev = make_inputs()
+    ev = ev.subset(range(args.events))
+    geom = apo.Geometry(g, w)
+    hits = apo.DeviceHits.from_events(ev)
+    ws = geom.workspace(ev.n_events)
+    prec = apo.F64 if args.case.endswith("f64") else apo.F32
+    if args.case.startswith("coarse"):
+        votes = torch.empty((ev.n_events, geom.n_coarse), dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            apo.vote(geom, hits, precision=prec, out=votes, workspace=ws)
+    else:
+        o = apo.solve_opts(precision=[prec] * (g.levels + 1))
+        for _ in range(2):
+            apo.solve_batch(geom, hits, o, workspace=ws)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "events": ev.n_events, "ok": True}))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="apo", choices=["apo", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default=None,
+                    choices=["coarse-f64", "coarse-f32", "solve-f64", "solve-f32"],
+                    help="run one small profiling case instead of the benchmark")
+    ap.add_argument("--events", type=int, default=64)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.case:
+        run_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_apo(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/* apo: interval-arithmetic Apollonius voting for a full-stereo drift chamber on one GPU.
+ *
+ * C ABI of libapo.so.  Method: arXiv:2401.04576 (da Silva, Lebrun, Angelique, Del Buono).
+ * Every hit (a stereo wire and its drift distance) votes, with both drift signs, for every
+ * cell of a 5-D helix parameter grid whose outward-rounded interval extension of the
+ * Apollonius tangency condition contains zero (Section 3.1, Eq. ApoVote, with d^Ax of
+ * Eq. defdiAX_b and Phi of Eqs. ApproxPhi_a-d, Appendix A).  The best cells are kept and
+ * bisected, coarse to fine; the final cells with the most votes give the helix and its
+ * errors (Section 3.3).
+ *
+ * Conventions of every entry point:
+ *  - returns an apo_status; never aborts the process;
+ *  - the caller owns every buffer it passes; the library owns only its handles;
+ *  - "device" pointers are CUDA global memory on the current device; "host" pointers are
+ *    ordinary host memory; all device work is queued on the caller's stream (a
+ *    cudaStream_t passed as void*; NULL = legacy default stream) and is asynchronous
+ *    unless stated otherwise;
+ *  - there is no CPU fallback: without a usable CUDA device calls return APO_ECUDA.
+ *
+ * Parameter cell axes (index a): 0 d0 [m] (signed POCA distance to the origin along
+ * (-sin phi0, cos phi0)), 1 phi0 [rad] (tangent azimuth at the POCA), 2 omega [1/m]
+ * (signed curvature; helix centre (-(R+d0) sin phi0, (R+d0) cos phi0), R = 1/omega),
+ * 3 z0 [m] (z at the POCA), 4 tanl = tan(dip angle).  A level-L cell index idx_a is in
+ * [0, bins[a] << L); its key is sum_a idx_a << (10 a); its 32 children are 2 idx_a + bit_a.
+ */
+#ifndef APO_H
+#define APO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+typedef enum {
+    APO_OK = 0,
+    APO_EINVAL = -1,   /* bad argument or malformed input                          */
+    APO_ENOMEM = -2,   /* workspace too small / device allocation failed           */
+    APO_ECUDA = -3,    /* a CUDA call failed (message: apo_last_error())           */
+    APO_ETIMEOUT = -4, /* a device wait hit its iteration limit                    */
+    APO_EBUSY = -5     /* serving queue full: retry later                          */
+} apo_status;
+
+/* interval precision of one level */
+enum { APO_F64 = 0, APO_F32 = 1 };
+
+#define APO_HIT_CAP 256      /* hits per event */
+#define APO_MAX_LEVELS 8     /* bisection levels after the coarse level */
+#define APO_MAX_TRACKS 8     /* tracks per event in multi-track extraction */
+
+typedef struct apo_geometry apo_geometry;
+
+/* Wire table (paper Appendix A, Eqs. wirePar_a,b): wire i passes through (x0, y0, 0) with
+ * direction (sin phi_s tan tau, -cos phi_s tan tau, 1).  Host arrays of n_wires doubles,
+ * copied by apo_geometry_create; sphi_t, cphi_t, t2 are the products sin(phi_s) tan(tau),
+ * cos(phi_s) tan(tau), tan(tau)^2 rounded once by the caller and used as given. */
+typedef struct {
+    int32_t n_wires;
+    const double *x0, *y0, *sin_phis, *cos_phis, *tan_tau, *sphi_t, *cphi_t, *t2;
+} apo_wires;
+
+/* Parameter grid (the voxel discretisation of Section 3.1, extended to five axes).
+ * lo_edge[a] / hi_edge[a]: host arrays of bins[a] << levels finest-level cell edges; a
+ * level-L cell idx spans [lo_edge[idx << (levels-L)], hi_edge[((idx+1) << (levels-L)) - 1]].
+ * No omega cell may contain 0.  sincos: host array of rows (sin lo, sin hi, cos lo,
+ * cos hi), outward enclosures of sin/cos over each phi0 cell, level by level (level L
+ * starts at row sum_{l<L} bins[1] << l).  All copied.  Limits: bins[a] << levels <= 1024,
+ * levels <= APO_MAX_LEVELS, 1 <= topk, topk * 32 <= 4096, topk <= number of level-0 cells. */
+typedef struct {
+    int32_t bins[5];
+    int32_t levels;
+    int32_t topk;
+    const double *lo_edge[5];
+    const double *hi_edge[5];
+    const double *sincos;
+} apo_grid;
+
+/* A batch of events in CSR form; DEVICE arrays owned by the caller.  Event e owns hits
+ * offsets[e] .. offsets[e+1]-1 (at most APO_HIT_CAP); wire_id in [0, n_wires); drift >= 0
+ * and finite.  A malformed event does not stop the batch: its track gets votes =
+ * APO_EINVAL. */
+typedef struct {
+    int32_t n_events;
+    const int32_t *offsets;
+    const int32_t *wire_id;
+    const double *drift;
+} apo_hits;
+
+/* One reconstructed helix (Section 3.3): p = mean centre of the final maximum-vote cells,
+ * w = half-extent of their union, votes = their vote count (< 0: status of a malformed
+ * event), n_hits = hits of the event. */
+typedef struct {
+    double p[5];
+    double w[5];
+    int32_t votes;
+    int32_t n_hits;
+} apo_track;
+
+/* Options of apo_solve_batch.  precision[L] selects FP64 or FP32 intervals at level L
+ * (L = 0 is the coarse grid); FP32 end points are rounded outward, so an FP32 vote set
+ * contains the FP64 one cell by cell.  trace_keys / trace_votes (device, may be NULL):
+ * n_events x (levels + 1) x topk, the cells kept after each level (the last row holds the
+ * best topk final cells). */
+typedef struct {
+    int32_t precision[APO_MAX_LEVELS + 1];
+    int32_t max_tracks;      /* 1 = single track per event */
+    int32_t min_votes;       /* multi-track: stop when the best track has fewer votes */
+    double mask_sigma;       /* multi-track: drift resolution used to mask found hits */
+    uint64_t *trace_keys;
+    int32_t *trace_votes;
+} apo_solve_opts;
+
+/* Fills *opts with: all levels FP64, one track, min_votes 6, mask_sigma 150e-6, no trace. */
+void apo_solve_opts_default(apo_solve_opts *opts);
+
+/* Text of the last error on this thread ("" if none). */
+const char *apo_last_error(void);
+
+/* Copies the wire table and grid to the current device and prepares the series constants
+ * used by the transcendental enclosures.  The geometry is immutable afterwards and may be
+ * used from any stream.  Synchronous.  APO_EINVAL on limits above, APO_ECUDA on failure. */
+int apo_geometry_create(const apo_wires *wires, const apo_grid *grid, apo_geometry **out);
+void apo_geometry_destroy(apo_geometry *geom);
+
+/* Number of level-0 cells (product of bins). */
+int64_t apo_coarse_cells(const apo_geometry *geom);
+
+/* Device workspace needed by apo_vote / apo_refine / apo_solve_batch for n_events events
+ * (opts may be NULL for the first two).  The caller allocates it (any device allocator,
+ * 256-byte aligned) and passes it back; it may be reused across calls on one stream. */
+int apo_workspace_bytes(const apo_geometry *geom, int32_t n_events, const apo_solve_opts *opts,
+                        size_t *bytes);
+
+/* Eq. (ApoVote) summed over each event's hits for a set of cells at `level` (Section 3.1:
+ * one vote per hit when either drift sign passes).  cell_keys: device, n_events x
+ * n_cells_per_event keys; NULL = the full level-0 grid in linear order (d0 fastest,
+ * tanl slowest; then level must be 0 and n_cells_per_event = apo_coarse_cells).
+ * votes_out: device int32, n_events x n_cells_per_event. */
+int apo_vote(const apo_geometry *geom, const apo_hits *hits, const uint64_t *cell_keys,
+             int64_t n_cells_per_event, int32_t level, int32_t precision, int32_t *votes_out,
+             void *workspace, size_t workspace_bytes, void *stream);
+
+/* One coarse-to-fine step: per event, keeps the topk cells of (keys_in, votes_in) by
+ * (votes descending, key ascending) and writes them to kept_keys / kept_votes (device,
+ * n_events x topk, may be NULL) and their 32 children each (level + 1) to children_out
+ * (device, n_events x topk x 32).  keys_in NULL = the full level-0 grid in linear order. */
+int apo_refine(const apo_geometry *geom, const apo_hits *hits, const uint64_t *keys_in,
+               const int32_t *votes_in, int64_t n_in_per_event, int32_t level,
+               uint64_t *kept_keys, int32_t *kept_votes, uint64_t *children_out,
+               void *workspace, size_t workspace_bytes, void *stream);
+
+/* Whole search for every event: level-0 voting, top-K, `levels` rounds of bisection,
+ * voting and top-K, and the estimate of Section 3.3.  tracks_out: device,
+ * n_events x opts->max_tracks records; n_tracks_out: device int32 per event (may be NULL).
+ * Multi-track (max_tracks > 1): after each track, the hits that vote for its final
+ * maximum-vote cells with the drift widened by +-3 mask_sigma are removed and the event is
+ * searched again, until max_tracks or a best vote count below min_votes. */
+int apo_solve_batch(const apo_geometry *geom, const apo_hits *hits, const apo_solve_opts *opts,
+                    apo_track *tracks_out, int32_t *n_tracks_out, void *workspace,
+                    size_t workspace_bytes, void *stream);
+
+/* As apo_solve_batch with HOST inputs and outputs: copies offsets / wire_id / drift to
+ * the workspace, runs, copies the tracks back and synchronises the stream.  The hits
+ * arrays must hold offsets[n_events] entries; workspace from apo_workspace_bytes with
+ * apo_host_extra_bytes(n_hits) added. */
+size_t apo_host_extra_bytes(int32_t n_events, int64_t n_hits);
+int apo_solve_batch_host(const apo_geometry *geom, int32_t n_events, const int32_t *offsets,
+                         const int32_t *wire_id, const double *drift, const apo_solve_opts *opts,
+                         apo_track *tracks_out, int32_t *n_tracks_out, void *workspace,
+                         size_t workspace_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APO_H */

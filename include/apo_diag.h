@@ -1,0 +1,37 @@
+/* apo diagnostics: measurement entry points of libapo.so used by the benchmark.  They are
+ * not part of the method (the paper has no counterpart); they make the roofline figures
+ * reproducible.  Conventions as in apo.h. */
+#ifndef APO_DIAG_H
+#define APO_DIAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "apo.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* apo_vote on the full level-0 grid that also counts the work the coarse kernel does:
+ * counts_out (device, 4 x uint64, zeroed by the call) receives the number of parent-cell
+ * evaluations, per-(cell, hit) prefix evaluations and tan(lambda) tail evaluations, and
+ * the number of coarse-kernel launches. */
+int apo_diag_vote_coarse_counts(const apo_geometry *geom, const apo_hits *hits, int32_t precision,
+                                int32_t *votes_out, unsigned long long *counts_out,
+                                void *workspace, size_t workspace_bytes, void *stream);
+
+/* Number of coarse-kernel launches apo_vote / apo_solve_batch make for n_events events. */
+int32_t apo_diag_coarse_launches(const apo_geometry *geom, int32_t n_events);
+
+/* Throughput microbenchmark of one directed-rounding operation on the current device:
+ * precision APO_F64 / APO_F32, op 0 = add (__dadd_rd), 1 = mul (__dmul_rd), 2 = an
+ * alternating add/mul chain.  Many independent chains per thread, every SM busy.
+ * *ops_per_s = operations per second.  Synchronous, about 0.1 s. */
+int apo_diag_pipe_peak(int32_t precision, int32_t op, double *ops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APO_DIAG_H */

@@ -297,6 +297,17 @@ void or_set_num_threads(int n) {
 #endif
 }
 
+/* Directed operations of one full evaluation of the vote program, by phase (per cell,
+ * per (cell, hit) without tan(lambda), tan(lambda)-dependent, both drift signs). */
+void or_op_counts(const double cell[12], const double hit[9], int prec, unsigned long long out[4]) {
+    int old = fegetround();
+    fesetround(FE_DOWNWARD);
+    for (int i = 0; i < 4; i++) { opcnt_d[i] = 0; opcnt_f[i] = 0; }
+    vote_pair(cell, hit, prec, NULL);
+    for (int i = 0; i < 4; i++) out[i] = prec == 0 ? opcnt_d[i] : opcnt_f[i];
+    fesetround(old);
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* Exported for the pin tests: the transcendental enclosures on their own.               */
 /* ------------------------------------------------------------------------------------ */

@@ -45,6 +45,7 @@ def lib():
         L.or_solve_event.restype = C.c_int
         L.or_atan_iv.argtypes = [C.c_double, C.c_double, C.c_int, dp]
         L.or_sincos_iv.argtypes = [C.c_double, C.c_double, C.c_int, dp]
+        L.or_op_counts.argtypes = [dp, dp, C.c_int, C.POINTER(C.c_ulonglong)]
         L.or_num_threads.restype = C.c_int
         L.or_set_num_threads.argtypes = [C.c_int]
         _lib = L
@@ -101,6 +102,16 @@ def vote_pair(cell12, hit9, prec: int = 0):
     out = np.zeros(5)
     v = lib().or_vote_pair(_p(c, C.c_double), _p(h, C.c_double), int(prec), _p(out, C.c_double))
     return int(v), out
+
+
+def op_counts(cell12, hit9, prec: int = 0) -> np.ndarray:
+    """Directed operations of one evaluation of the vote program by phase: per cell, per
+    (cell, hit) without tan(lambda), tan(lambda)-dependent part, both drift signs."""
+    c = np.ascontiguousarray(cell12, np.float64)
+    h = np.ascontiguousarray(hit9, np.float64)
+    out = (C.c_ulonglong * 4)()
+    lib().or_op_counts(_p(c, C.c_double), _p(h, C.c_double), int(prec), out)
+    return np.array(list(out), np.int64)
 
 
 def atan_iv(lo: float, hi: float, prec: int = 0) -> np.ndarray:

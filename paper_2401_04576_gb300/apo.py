@@ -1,0 +1,303 @@
+"""Thin ctypes binding of libapo.so (include/apo.h): argument marshalling only.
+
+Device memory and streams come from PyTorch; every step of the hot path runs in the
+library's CUDA kernels.  There is no CPU fallback: loading fails loudly when the library
+is missing, and calls raise when CUDA is unusable.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+APO_OK, APO_EINVAL, APO_ENOMEM, APO_ECUDA, APO_ETIMEOUT, APO_EBUSY = 0, -1, -2, -3, -4, -5
+F64, F32 = 0, 1
+HIT_CAP = 256
+MAX_LEVELS = 8
+MAX_TRACKS = 8
+
+TRACK_DTYPE = np.dtype([("p", "<f8", (5,)), ("w", "<f8", (5,)), ("votes", "<i4"),
+                        ("n_hits", "<i4")])
+assert TRACK_DTYPE.itemsize == 88
+
+_dp = C.POINTER(C.c_double)
+
+
+class ApoWires(C.Structure):
+    _fields_ = [("n_wires", C.c_int32)] + [(n, _dp) for n in
+                ("x0", "y0", "sin_phis", "cos_phis", "tan_tau", "sphi_t", "cphi_t", "t2")]
+
+
+class ApoGrid(C.Structure):
+    _fields_ = [("bins", C.c_int32 * 5), ("levels", C.c_int32), ("topk", C.c_int32),
+                ("lo_edge", _dp * 5), ("hi_edge", _dp * 5), ("sincos", _dp)]
+
+
+class ApoHits(C.Structure):
+    _fields_ = [("n_events", C.c_int32), ("offsets", C.c_void_p), ("wire_id", C.c_void_p),
+                ("drift", C.c_void_p)]
+
+
+class ApoSolveOpts(C.Structure):
+    _fields_ = [("precision", C.c_int32 * (MAX_LEVELS + 1)), ("max_tracks", C.c_int32),
+                ("min_votes", C.c_int32), ("mask_sigma", C.c_double),
+                ("trace_keys", C.c_void_p), ("trace_votes", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads (building if needed) the in-tree libapo.so."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            path = _build.build()
+        L = C.CDLL(path)
+        vp, i32, i64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+        L.apo_last_error.restype = C.c_char_p
+        L.apo_solve_opts_default.argtypes = [C.POINTER(ApoSolveOpts)]
+        L.apo_geometry_create.argtypes = [C.POINTER(ApoWires), C.POINTER(ApoGrid), C.POINTER(vp)]
+        L.apo_geometry_destroy.argtypes = [vp]
+        L.apo_coarse_cells.argtypes = [vp]
+        L.apo_coarse_cells.restype = i64
+        L.apo_workspace_bytes.argtypes = [vp, i32, C.POINTER(ApoSolveOpts), C.POINTER(sz)]
+        L.apo_vote.argtypes = [vp, C.POINTER(ApoHits), vp, i64, i32, i32, vp, vp, sz, vp]
+        L.apo_refine.argtypes = [vp, C.POINTER(ApoHits), vp, vp, i64, i32, vp, vp, vp, vp, sz, vp]
+        L.apo_solve_batch.argtypes = [vp, C.POINTER(ApoHits), C.POINTER(ApoSolveOpts), vp, vp, vp,
+                                      sz, vp]
+        L.apo_host_extra_bytes.argtypes = [i32, i64]
+        L.apo_host_extra_bytes.restype = sz
+        L.apo_solve_batch_host.argtypes = [vp, i32, vp, vp, vp, C.POINTER(ApoSolveOpts), vp, vp,
+                                           vp, sz, vp]
+        L.apo_diag_vote_coarse_counts.argtypes = [vp, C.POINTER(ApoHits), i32, vp, vp, vp, sz, vp]
+        L.apo_diag_coarse_launches.argtypes = [vp, i32]
+        L.apo_diag_coarse_launches.restype = i32
+        L.apo_diag_pipe_peak.argtypes = [i32, i32, C.POINTER(C.c_double)]
+        _lib = L
+    return _lib
+
+
+class ApoError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"apo error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc):
+    if rc != APO_OK:
+        raise ApoError(rc, lib().apo_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else int(t.data_ptr()))
+
+
+class Geometry:
+    """Device copy of a wire table (gen.chamber.Wires-like) and grid (gen.grid.Grid-like)."""
+
+    def __init__(self, grid, wires):
+        self.grid, self.wires = grid, wires
+        keep = []
+
+        def dp(a):
+            a = np.ascontiguousarray(a, np.float64)
+            keep.append(a)
+            return a.ctypes.data_as(_dp)
+
+        w = ApoWires()
+        w.n_wires = int(wires.n)
+        for name in ("x0", "y0", "sin_phis", "cos_phis", "tan_tau", "sphi_t", "cphi_t", "t2"):
+            setattr(w, name, dp(getattr(wires, name)))
+        g = ApoGrid()
+        for a in range(5):
+            g.bins[a] = int(grid.bins[a])
+            g.lo_edge[a] = dp(grid.lo_edge[a])
+            g.hi_edge[a] = dp(grid.hi_edge[a])
+        g.levels = int(grid.levels)
+        g.topk = int(grid.topk)
+        g.sincos = dp(grid.sincos)
+        h = C.c_void_p()
+        _check(lib().apo_geometry_create(C.byref(w), C.byref(g), C.byref(h)))
+        self.handle = h
+        self.n_coarse = int(lib().apo_coarse_cells(h))
+        self.levels, self.topk = int(grid.levels), int(grid.topk)
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().apo_geometry_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self, n_events: int, opts: ApoSolveOpts | None = None) -> int:
+        n = C.c_size_t()
+        _check(lib().apo_workspace_bytes(self.handle, int(n_events),
+                                         None if opts is None else C.byref(opts), C.byref(n)))
+        return int(n.value)
+
+    def workspace(self, n_events: int, extra: int = 0):
+        torch = _torch()
+        return torch.empty(self.workspace_bytes(n_events) + extra, dtype=torch.uint8,
+                           device="cuda")
+
+
+class DeviceHits:
+    """CSR hits on the device (torch tensors)."""
+
+    def __init__(self, offsets, wire_id, drift):
+        self.offsets, self.wire_id, self.drift = offsets, wire_id, drift
+        self.n_events = int(offsets.shape[0] - 1)
+
+    @classmethod
+    def from_events(cls, ev, device="cuda"):
+        torch = _torch()
+        return cls(torch.as_tensor(np.asarray(ev.offsets, np.int32), device=device),
+                   torch.as_tensor(np.asarray(ev.wire_id, np.int32), device=device),
+                   torch.as_tensor(np.asarray(ev.drift, np.float64), device=device))
+
+    def c(self) -> ApoHits:
+        h = ApoHits()
+        h.n_events = self.n_events
+        h.offsets, h.wire_id, h.drift = _ptr(self.offsets), _ptr(self.wire_id), _ptr(self.drift)
+        return h
+
+
+def solve_opts(precision=None, levels: int = 0, max_tracks: int = 1, min_votes: int = 6,
+               mask_sigma: float = 150e-6, trace_keys=None, trace_votes=None) -> ApoSolveOpts:
+    o = ApoSolveOpts()
+    lib().apo_solve_opts_default(C.byref(o))
+    if precision is not None:
+        for i, p in enumerate(precision):
+            o.precision[i] = int(p)
+    o.max_tracks, o.min_votes, o.mask_sigma = int(max_tracks), int(min_votes), float(mask_sigma)
+    o.trace_keys = _ptr(trace_keys).value
+    o.trace_votes = _ptr(trace_votes).value
+    return o
+
+
+def vote(geom: Geometry, hits: DeviceHits, keys=None, level: int = 0, precision: int = F64,
+         n_per_event: int | None = None, out=None, workspace=None, stream=None):
+    """apo_vote: votes (int32, n_events x n_cells) of the given keys or the full coarse grid."""
+    torch = _torch()
+    n = geom.n_coarse if keys is None else int(n_per_event if n_per_event is not None
+                                                 else keys.shape[-1])
+    if out is None:
+        out = torch.empty((hits.n_events, n), dtype=torch.int32, device="cuda")
+    ws = geom.workspace(hits.n_events) if workspace is None else workspace
+    hc = hits.c()
+    _check(lib().apo_vote(geom.handle, C.byref(hc), _ptr(keys), n, int(level), int(precision),
+                          _ptr(out), _ptr(ws), ws.numel(), _stream_ptr(stream)))
+    return out
+
+
+def refine(geom: Geometry, hits: DeviceHits, votes, keys=None, level: int = 0, workspace=None,
+           stream=None):
+    """apo_refine: (kept_keys, kept_votes, children) per event."""
+    torch = _torch()
+    ne, K = hits.n_events, geom.topk
+    n_in = geom.n_coarse if keys is None else int(keys.shape[-1])
+    kk = torch.empty((ne, K), dtype=torch.int64, device="cuda")
+    kv = torch.empty((ne, K), dtype=torch.int32, device="cuda")
+    ch = torch.empty((ne, K * 32), dtype=torch.int64, device="cuda")
+    ws = geom.workspace(ne) if workspace is None else workspace
+    hc = hits.c()
+    _check(lib().apo_refine(geom.handle, C.byref(hc), _ptr(keys), _ptr(votes), n_in, int(level),
+                            _ptr(kk), _ptr(kv), _ptr(ch), _ptr(ws), ws.numel(),
+                            _stream_ptr(stream)))
+    return kk, kv, ch
+
+
+def solve_batch(geom: Geometry, hits: DeviceHits, opts: ApoSolveOpts | None = None,
+                tracks=None, n_tracks=None, workspace=None, stream=None):
+    """apo_solve_batch: device tracks (uint8 tensor of apo_track records) and per-event
+    track counts."""
+    torch = _torch()
+    o = opts if opts is not None else solve_opts()
+    mt = int(o.max_tracks)
+    if tracks is None:
+        tracks = torch.zeros(hits.n_events * mt * TRACK_DTYPE.itemsize, dtype=torch.uint8,
+                             device="cuda")
+    if n_tracks is None:
+        n_tracks = torch.zeros(hits.n_events, dtype=torch.int32, device="cuda")
+    ws = geom.workspace(hits.n_events) if workspace is None else workspace
+    hc = hits.c()
+    _check(lib().apo_solve_batch(geom.handle, C.byref(hc), C.byref(o), _ptr(tracks),
+                                 _ptr(n_tracks), _ptr(ws), ws.numel(), _stream_ptr(stream)))
+    return tracks, n_tracks
+
+
+def tracks_to_numpy(tracks, n_events: int, max_tracks: int = 1) -> np.ndarray:
+    a = tracks.cpu().numpy() if hasattr(tracks, "cpu") else np.asarray(tracks)
+    return a.view(TRACK_DTYPE).reshape(n_events, max_tracks)
+
+
+def host_workspace_bytes(geom: Geometry, n_events: int, n_hits: int) -> int:
+    return geom.workspace_bytes(n_events) + int(lib().apo_host_extra_bytes(int(n_events), int(n_hits)))
+
+
+def solve_batch_host(geom: Geometry, offsets: np.ndarray, wire_id: np.ndarray, drift: np.ndarray,
+                     opts: ApoSolveOpts | None = None, workspace=None, out=None, stream=None):
+    """apo_solve_batch_host: host arrays in, host tracks out (synchronous)."""
+    o = opts if opts is not None else solve_opts()
+    offsets = np.ascontiguousarray(offsets, np.int32)
+    wire_id = np.ascontiguousarray(wire_id, np.int32)
+    drift = np.ascontiguousarray(drift, np.float64)
+    n_ev = int(offsets.shape[0] - 1)
+    ws = workspace
+    if ws is None:
+        torch = _torch()
+        ws = torch.empty(host_workspace_bytes(geom, n_ev, int(offsets[-1])), dtype=torch.uint8,
+                         device="cuda")
+    if out is None:
+        out = np.zeros((n_ev, int(o.max_tracks)), TRACK_DTYPE)
+    nt = np.zeros(n_ev, np.int32)
+
+    def hp(a):
+        return C.c_void_p(a.ctypes.data)
+
+    _check(lib().apo_solve_batch_host(geom.handle, n_ev, hp(offsets), hp(wire_id), hp(drift),
+                                      C.byref(o), hp(out), hp(nt), _ptr(ws), ws.numel(),
+                                      _stream_ptr(stream)))
+    return out, nt
+
+
+def pipe_peak(precision: int = F64) -> float:
+    """Measured directed-rounding add / mul throughput of the current GPU (operations per
+    second, the best of add, mul and an alternating chain)."""
+    best = 0.0
+    for op in (0, 1, 2):
+        r = C.c_double()
+        _check(lib().apo_diag_pipe_peak(int(precision), op, C.byref(r)))
+        best = max(best, r.value)
+    return best
+
+
+def coarse_launches(geom: Geometry, n_events: int) -> int:
+    return int(lib().apo_diag_coarse_launches(geom.handle, int(n_events)))
+
+
+def solve_launches(geom: Geometry, n_events: int) -> int:
+    """Kernel launches of one single-track apo_solve_batch: staging, then per chunk of
+    events the coarse vote, the coarse selection, per level the child vote and top-K,
+    and the estimate."""
+    return 1 + coarse_launches(geom, n_events) * (3 + 2 * geom.levels)

@@ -1,0 +1,471 @@
+// Host side of the C ABI declared in include/apo.h: geometry upload, workspace layout and
+// the coarse-to-fine pipeline (arXiv:2401.04576, Sections 3.1 and 3.3) queued on the
+// caller's stream.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/apo.h"
+#include "../../include/apo_diag.h"
+#include "kernels.cuh"
+
+using namespace apo;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(APO_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                      \
+    } while (0)
+
+int check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(APO_ECUDA, "%s launch: %s", what, cudaGetErrorString(e));
+    return APO_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct apo_geometry {
+    DevGeom dg;
+    int device;
+    long long n_coarse;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+// Workspace regions for a batch of n_events.
+struct Layout {
+    size_t status, n_hits, hd, hf, votes, hist, fk, fv, ck, cv, mask, end;
+    int chunk;
+};
+
+Layout layout(const apo_geometry *g, int n_events) {
+    Layout L;
+    const int K = g->dg.topk;
+    long long chunk = (1LL << 28) / (g->n_coarse > 0 ? g->n_coarse : 1);
+    if (chunk < 1) chunk = 1;
+    if (chunk > n_events) chunk = n_events > 0 ? n_events : 1;
+    L.chunk = (int)chunk;
+    size_t o = 0;
+    L.status = o; o += 256;
+    L.n_hits = o; o = align256(o + sizeof(int32_t) * (size_t)n_events);
+    L.hd = o; o = align256(o + sizeof(HitRecD) * (size_t)n_events * kHitCap);
+    L.hf = o; o = align256(o + sizeof(HitRecF) * (size_t)n_events * kHitCap);
+    L.votes = o; o = align256(o + sizeof(int32_t) * (size_t)chunk * (size_t)g->n_coarse);
+    L.hist = o; o = align256(o + sizeof(uint32_t) * (size_t)chunk * kHistBins);
+    L.fk = o; o = align256(o + sizeof(uint64_t) * (size_t)n_events * K);
+    L.fv = o; o = align256(o + sizeof(int32_t) * (size_t)n_events * K);
+    L.ck = o; o = align256(o + sizeof(uint64_t) * (size_t)n_events * K * 32);
+    L.cv = o; o = align256(o + sizeof(int32_t) * (size_t)n_events * K * 32);
+    L.mask = o; o = align256(o + sizeof(uint32_t) * (size_t)n_events * (kHitCap / 32));
+    L.end = o;
+    return L;
+}
+
+template <typename P> P *at(void *ws, size_t off) {
+    return reinterpret_cast<P *>(static_cast<unsigned char *>(ws) + off);
+}
+
+int check_geom(const apo_geometry *g) {
+    if (!g) return fail(APO_EINVAL, "geometry is NULL");
+    int dev = -1;
+    CU(cudaGetDevice(&dev));
+    if (dev != g->device)
+        return fail(APO_EINVAL, "geometry lives on device %d, current device is %d", g->device, dev);
+    return APO_OK;
+}
+
+int check_hits(const apo_hits *h) {
+    if (!h) return fail(APO_EINVAL, "hits is NULL");
+    if (h->n_events < 0) return fail(APO_EINVAL, "n_events < 0");
+    if (h->n_events > 0 && (!h->offsets || !h->wire_id || !h->drift))
+        return fail(APO_EINVAL, "hits arrays must be non-NULL");
+    return APO_OK;
+}
+
+int check_ws(const apo_geometry *g, int n_events, void *ws, size_t bytes, Layout &L) {
+    L = layout(g, n_events);
+    if (!ws) return fail(APO_EINVAL, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % 256)
+        return fail(APO_EINVAL, "workspace must be 256-byte aligned");
+    if (bytes < L.end)
+        return fail(APO_ENOMEM, "workspace too small: %zu < %zu bytes", bytes, L.end);
+    return APO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *apo_last_error(void) { return g_err; }
+
+void apo_solve_opts_default(apo_solve_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    for (int i = 0; i <= APO_MAX_LEVELS; i++) o->precision[i] = APO_F64;
+    o->max_tracks = 1;
+    o->min_votes = 6;
+    o->mask_sigma = 150e-6;
+}
+
+int apo_geometry_create(const apo_wires *w, const apo_grid *gr, apo_geometry **out) {
+    if (!out) return fail(APO_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!w || !gr) return fail(APO_EINVAL, "wires / grid is NULL");
+    if (w->n_wires <= 0) return fail(APO_EINVAL, "n_wires must be > 0");
+    const double *wa[8] = {w->x0, w->y0, w->sin_phis, w->cos_phis, w->tan_tau, w->sphi_t, w->cphi_t, w->t2};
+    for (int i = 0; i < 8; i++)
+        if (!wa[i]) return fail(APO_EINVAL, "wire array %d is NULL", i);
+    if (gr->levels < 0 || gr->levels > APO_MAX_LEVELS) return fail(APO_EINVAL, "levels out of range");
+    if (gr->topk < 1 || gr->topk * 32 > 4096) return fail(APO_EINVAL, "topk must be in [1, 128]");
+    long long n0 = 1;
+    for (int a = 0; a < 5; a++) {
+        if (gr->bins[a] < 1 || ((long long)gr->bins[a] << gr->levels) > 1024)
+            return fail(APO_EINVAL, "bins[%d] << levels must be in [1, 1024]", a);
+        if (!gr->lo_edge[a] || !gr->hi_edge[a]) return fail(APO_EINVAL, "edge table %d is NULL", a);
+        n0 *= gr->bins[a];
+    }
+    if (!gr->sincos) return fail(APO_EINVAL, "sincos table is NULL");
+    if (gr->bins[0] * gr->bins[3] > 256)
+        return fail(APO_EINVAL, "bins[0] * bins[3] must be <= 256 (one thread each in a block)");
+    if (n0 < gr->topk) return fail(APO_EINVAL, "fewer level-0 cells than topk");
+    // omega cells must not contain 0
+    {
+        int nf = gr->bins[2] << gr->levels;
+        for (int i = 0; i < nf; i++)
+            if (!(gr->hi_edge[2][i] < 0.0 || gr->lo_edge[2][i] > 0.0))
+                return fail(APO_EINVAL, "omega cell %d contains 0", i);
+    }
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    apo_geometry *g = new apo_geometry();
+    g->device = dev;
+    g->n_coarse = n0;
+    DevGeom &d = g->dg;
+    std::memset(&d, 0, sizeof(d));
+    for (int a = 0; a < 5; a++) d.bins[a] = gr->bins[a];
+    d.levels = gr->levels;
+    d.topk = gr->topk;
+    d.n_wires = w->n_wires;
+    auto upload = [&](const double *src, size_t n, const double **dst) -> int {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, n * sizeof(double));
+        if (e != cudaSuccess) return fail(APO_ECUDA, "cudaMalloc: %s", cudaGetErrorString(e));
+        g->allocs.push_back(p);
+        e = cudaMemcpy(p, src, n * sizeof(double), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(APO_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+        *dst = static_cast<const double *>(p);
+        return APO_OK;
+    };
+    int rc = APO_OK;
+    for (int i = 0; i < 8 && rc == APO_OK; i++) rc = upload(wa[i], (size_t)w->n_wires, &d.wire[i]);
+    for (int a = 0; a < 5 && rc == APO_OK; a++) {
+        size_t nf = (size_t)gr->bins[a] << gr->levels;
+        rc = upload(gr->lo_edge[a], nf, &d.lo_edge[a]);
+        if (rc == APO_OK) rc = upload(gr->hi_edge[a], nf, &d.hi_edge[a]);
+    }
+    long long rows = 0;
+    for (int L = 0; L <= gr->levels; L++) {
+        d.sincos_off[L] = rows;
+        rows += (long long)gr->bins[1] << L;
+    }
+    if (rc == APO_OK) rc = upload(gr->sincos, (size_t)rows * 4, &d.sincos);
+    if (rc == APO_OK) {
+        SeriesConsts *dk = nullptr;
+        cudaError_t e = cudaMalloc(&dk, sizeof(SeriesConsts));
+        if (e == cudaSuccess) {
+            launch_series_consts(dk, 0);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpy(&d.k, dk, sizeof(SeriesConsts), cudaMemcpyDeviceToHost);
+            cudaFree(dk);
+        }
+        if (e != cudaSuccess) rc = fail(APO_ECUDA, "series constants: %s", cudaGetErrorString(e));
+    }
+    if (rc != APO_OK) {
+        apo_geometry_destroy(g);
+        return rc;
+    }
+    *out = g;
+    return APO_OK;
+}
+
+void apo_geometry_destroy(apo_geometry *g) {
+    if (!g) return;
+    for (void *p : g->allocs) cudaFree(p);
+    delete g;
+}
+
+int64_t apo_coarse_cells(const apo_geometry *g) { return g ? g->n_coarse : 0; }
+
+int apo_workspace_bytes(const apo_geometry *g, int32_t n_events, const apo_solve_opts *, size_t *bytes) {
+    if (!g || !bytes) return fail(APO_EINVAL, "NULL argument");
+    if (n_events < 0) return fail(APO_EINVAL, "n_events < 0");
+    *bytes = layout(g, n_events).end;
+    return APO_OK;
+}
+
+size_t apo_host_extra_bytes(int32_t n_events, int64_t n_hits) {
+    return align256(sizeof(int32_t) * (size_t)(n_events + 1)) + align256(sizeof(int32_t) * (size_t)n_hits) +
+           align256(sizeof(double) * (size_t)n_hits) + align256(sizeof(apo_track) * (size_t)n_events * APO_MAX_TRACKS) +
+           align256(sizeof(int32_t) * (size_t)n_events) + 256;
+}
+
+int apo_vote(const apo_geometry *g, const apo_hits *hits, const uint64_t *cell_keys,
+             int64_t n_cells_per_event, int32_t level, int32_t precision, int32_t *votes_out,
+             void *ws, size_t ws_bytes, void *stream) {
+    int rc;
+    if ((rc = check_geom(g)) || (rc = check_hits(hits))) return rc;
+    if (precision != APO_F64 && precision != APO_F32) return fail(APO_EINVAL, "bad precision");
+    if (level < 0 || level > g->dg.levels) return fail(APO_EINVAL, "level out of range");
+    if (!votes_out) return fail(APO_EINVAL, "votes_out is NULL");
+    if (!cell_keys && (level != 0 || n_cells_per_event != g->n_coarse))
+        return fail(APO_EINVAL, "full-grid voting needs level 0 and n_cells = apo_coarse_cells");
+    if (n_cells_per_event < 0) return fail(APO_EINVAL, "n_cells < 0");
+    Layout L;
+    if ((rc = check_ws(g, hits->n_events, ws, ws_bytes, L))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int ne = hits->n_events;
+    if (ne == 0 || n_cells_per_event == 0) return APO_OK;
+    unsigned *status = at<unsigned>(ws, L.status);
+    int32_t *nh = at<int32_t>(ws, L.n_hits);
+    HitRecD *hd = at<HitRecD>(ws, L.hd);
+    HitRecF *hf = at<HitRecF>(ws, L.hf);
+    CU(cudaMemsetAsync(status, 0, 256, s));
+    launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, status, s);
+    if ((rc = check_launch("stage"))) return rc;
+    if (!cell_keys) {
+        uint32_t *hist = at<uint32_t>(ws, L.hist);
+        for (int e0 = 0; e0 < ne; e0 += L.chunk) {
+            int n = ne - e0 < L.chunk ? ne - e0 : L.chunk;
+            CU(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)n * kHistBins, s));
+            launch_vote_coarse(g->dg, precision, e0, n, hd, hf, nh, votes_out + (size_t)e0 * g->n_coarse,
+                               hist, status, s);
+            if ((rc = check_launch("vote_coarse"))) return rc;
+        }
+    } else {
+        launch_vote_keys(g->dg, precision, ne, hd, hf, nh, level, cell_keys, n_cells_per_event,
+                         votes_out, s);
+        if ((rc = check_launch("vote_keys"))) return rc;
+    }
+    return APO_OK;
+}
+
+int apo_refine(const apo_geometry *g, const apo_hits *hits, const uint64_t *keys_in,
+               const int32_t *votes_in, int64_t n_in, int32_t level, uint64_t *kept_keys,
+               int32_t *kept_votes, uint64_t *children_out, void *ws, size_t ws_bytes, void *stream) {
+    int rc;
+    if ((rc = check_geom(g)) || (rc = check_hits(hits))) return rc;
+    if (level < 0 || level >= g->dg.levels) return fail(APO_EINVAL, "level must be in [0, levels)");
+    if (!votes_in || !children_out) return fail(APO_EINVAL, "votes_in / children_out is NULL");
+    if (!keys_in && (level != 0 || n_in != g->n_coarse))
+        return fail(APO_EINVAL, "implicit keys need level 0 and n_in = apo_coarse_cells");
+    if (keys_in && (n_in < 1 || n_in > 4096)) return fail(APO_EINVAL, "n_in must be in [1, 4096]");
+    Layout L;
+    if ((rc = check_ws(g, hits->n_events, ws, ws_bytes, L))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int ne = hits->n_events, K = g->dg.topk;
+    if (ne == 0) return APO_OK;
+    uint64_t *fk = at<uint64_t>(ws, L.fk);
+    int32_t *fv = at<int32_t>(ws, L.fv);
+    if (!keys_in) {
+        uint32_t *hist = at<uint32_t>(ws, L.hist);
+        for (int e0 = 0; e0 < ne; e0 += L.chunk) {
+            int n = ne - e0 < L.chunk ? ne - e0 : L.chunk;
+            CU(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)n * kHistBins, s));
+            launch_hist(n, votes_in + (size_t)e0 * g->n_coarse, g->n_coarse, hist, s);
+            launch_select_coarse(g->dg, e0, n, votes_in + (size_t)e0 * g->n_coarse, hist, K, fk, fv, s);
+            if ((rc = check_launch("select_coarse"))) return rc;
+        }
+    } else {
+        launch_topk(ne, keys_in, votes_in, (int)n_in, K, fk, fv, s);
+        if ((rc = check_launch("topk"))) return rc;
+    }
+    if (kept_keys) CU(cudaMemcpyAsync(kept_keys, fk, sizeof(uint64_t) * (size_t)ne * K, cudaMemcpyDeviceToDevice, s));
+    if (kept_votes) CU(cudaMemcpyAsync(kept_votes, fv, sizeof(int32_t) * (size_t)ne * K, cudaMemcpyDeviceToDevice, s));
+    launch_children(fk, (long long)ne * K, children_out, s);
+    return check_launch("children");
+}
+
+static int trace_copy(const apo_solve_opts *o, const apo_geometry *g, int e0, int n, int level,
+                      const uint64_t *keys, const int32_t *votes, cudaStream_t s) {
+    if (!o->trace_keys && !o->trace_votes) return APO_OK;
+    const int K = g->dg.topk, lv = g->dg.levels;
+    if (o->trace_keys)
+        CU(cudaMemcpy2DAsync(o->trace_keys + ((size_t)e0 * (lv + 1) + level) * K, sizeof(uint64_t) * K * (lv + 1),
+                             keys, sizeof(uint64_t) * K, sizeof(uint64_t) * K, n, cudaMemcpyDeviceToDevice, s));
+    if (o->trace_votes)
+        CU(cudaMemcpy2DAsync(o->trace_votes + ((size_t)e0 * (lv + 1) + level) * K, sizeof(int32_t) * K * (lv + 1),
+                             votes, sizeof(int32_t) * K, sizeof(int32_t) * K, n, cudaMemcpyDeviceToDevice, s));
+    return APO_OK;
+}
+
+int apo_solve_batch(const apo_geometry *g, const apo_hits *hits, const apo_solve_opts *opts,
+                    apo_track *tracks_out, int32_t *n_tracks_out, void *ws, size_t ws_bytes, void *stream) {
+    int rc;
+    if ((rc = check_geom(g)) || (rc = check_hits(hits))) return rc;
+    apo_solve_opts def;
+    apo_solve_opts_default(&def);
+    const apo_solve_opts *o = opts ? opts : &def;
+    const int lv = g->dg.levels, K = g->dg.topk;
+    for (int i = 0; i <= lv; i++)
+        if (o->precision[i] != APO_F64 && o->precision[i] != APO_F32) return fail(APO_EINVAL, "bad precision[%d]", i);
+    if (o->max_tracks != 1) return fail(APO_EINVAL, "max_tracks > 1 is not supported by this build");
+    if (!tracks_out && hits->n_events > 0) return fail(APO_EINVAL, "tracks_out is NULL");
+    Layout L;
+    if ((rc = check_ws(g, hits->n_events, ws, ws_bytes, L))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int ne = hits->n_events;
+    if (ne == 0) return APO_OK;
+    unsigned *status = at<unsigned>(ws, L.status);
+    int32_t *nh = at<int32_t>(ws, L.n_hits);
+    HitRecD *hd = at<HitRecD>(ws, L.hd);
+    HitRecF *hf = at<HitRecF>(ws, L.hf);
+    int32_t *votes = at<int32_t>(ws, L.votes);
+    uint32_t *hist = at<uint32_t>(ws, L.hist);
+    uint64_t *fk = at<uint64_t>(ws, L.fk);
+    int32_t *fv = at<int32_t>(ws, L.fv);
+    uint64_t *ck = at<uint64_t>(ws, L.ck);
+    int32_t *cv = at<int32_t>(ws, L.cv);
+    CU(cudaMemsetAsync(status, 0, 256, s));
+    launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, status, s);
+    if ((rc = check_launch("stage"))) return rc;
+    for (int e0 = 0; e0 < ne; e0 += L.chunk) {
+        const int n = ne - e0 < L.chunk ? ne - e0 : L.chunk;
+        CU(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)n * kHistBins, s));
+        launch_vote_coarse(g->dg, o->precision[0], e0, n, hd, hf, nh, votes, hist, status, s);
+        if ((rc = check_launch("vote_coarse"))) return rc;
+        launch_select_coarse(g->dg, e0, n, votes, hist, K, fk, fv, s);
+        if ((rc = check_launch("select_coarse"))) return rc;
+        uint64_t *fke = fk + (size_t)e0 * K;
+        int32_t *fve = fv + (size_t)e0 * K;
+        uint64_t *cke = ck + (size_t)e0 * K * 32;
+        int32_t *cve = cv + (size_t)e0 * K * 32;
+        const HitRecD *hde = hd + (size_t)e0 * kHitCap;
+        const HitRecF *hfe = hf + (size_t)e0 * kHitCap;
+        const int32_t *nhe = nh + e0;
+        if ((rc = trace_copy(o, g, e0, n, 0, fke, fve, s))) return rc;
+        for (int lev = 1; lev <= lv; lev++) {
+            launch_vote_children(g->dg, o->precision[lev], n, hde, hfe, nhe, lev, fke, K, cke, cve, s);
+            if ((rc = check_launch("vote_children"))) return rc;
+            launch_topk(n, cke, cve, K * 32, K, fke, fve, s);
+            if ((rc = check_launch("topk"))) return rc;
+            if ((rc = trace_copy(o, g, e0, n, lev, fke, fve, s))) return rc;
+            if (lev == lv) {
+                launch_estimate_tracks(g->dg, n, cke, cve, K * 32, lev, nhe, tracks_out + (size_t)e0 * o->max_tracks,
+                                       o->max_tracks, n_tracks_out ? n_tracks_out + e0 : nullptr, s);
+                if ((rc = check_launch("estimate"))) return rc;
+            }
+        }
+        if (lv == 0) return fail(APO_EINVAL, "levels = 0 is not supported by apo_solve_batch");
+    }
+    return APO_OK;
+}
+
+int apo_diag_vote_coarse_counts(const apo_geometry *g, const apo_hits *hits, int32_t precision,
+                                int32_t *votes_out, unsigned long long *counts, void *ws,
+                                size_t ws_bytes, void *stream) {
+    int rc;
+    if ((rc = check_geom(g)) || (rc = check_hits(hits))) return rc;
+    if (!votes_out || !counts) return fail(APO_EINVAL, "votes_out / counts_out is NULL");
+    if (precision != APO_F64 && precision != APO_F32) return fail(APO_EINVAL, "bad precision");
+    Layout L;
+    if ((rc = check_ws(g, hits->n_events, ws, ws_bytes, L))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int ne = hits->n_events;
+    CU(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), s));
+    if (ne == 0) return APO_OK;
+    unsigned *status = at<unsigned>(ws, L.status);
+    int32_t *nh = at<int32_t>(ws, L.n_hits);
+    HitRecD *hd = at<HitRecD>(ws, L.hd);
+    HitRecF *hf = at<HitRecF>(ws, L.hf);
+    uint32_t *hist = at<uint32_t>(ws, L.hist);
+    CU(cudaMemsetAsync(status, 0, 256, s));
+    launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, status, s);
+    unsigned long long launches = 0;
+    for (int e0 = 0; e0 < ne; e0 += L.chunk) {
+        int n = ne - e0 < L.chunk ? ne - e0 : L.chunk;
+        CU(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)n * kHistBins, s));
+        launch_vote_coarse(g->dg, precision, e0, n, hd, hf, nh, votes_out + (size_t)e0 * g->n_coarse,
+                           hist, status, s, counts);
+        if ((rc = check_launch("vote_coarse"))) return rc;
+        launches++;
+    }
+    CU(cudaMemcpyAsync(counts + 3, &launches, sizeof(launches), cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));
+    return APO_OK;
+}
+
+int32_t apo_diag_coarse_launches(const apo_geometry *g, int32_t n_events) {
+    if (!g || n_events <= 0) return 0;
+    Layout L = layout(g, n_events);
+    return (n_events + L.chunk - 1) / L.chunk;
+}
+
+int apo_diag_pipe_peak(int32_t precision, int32_t op, double *ops_per_s) {
+    if (!ops_per_s) return fail(APO_EINVAL, "ops_per_s is NULL");
+    if (precision != APO_F64 && precision != APO_F32) return fail(APO_EINVAL, "bad precision");
+    double r = pipe_peak(precision, op);
+    if (r <= 0) return fail(APO_ECUDA, "pipe microbenchmark failed");
+    *ops_per_s = r;
+    return APO_OK;
+}
+
+int apo_solve_batch_host(const apo_geometry *g, int32_t n_events, const int32_t *offsets,
+                         const int32_t *wire_id, const double *drift, const apo_solve_opts *opts,
+                         apo_track *tracks_out, int32_t *n_tracks_out, void *ws, size_t ws_bytes,
+                         void *stream) {
+    int rc;
+    if ((rc = check_geom(g))) return rc;
+    if (n_events < 0 || (n_events > 0 && (!offsets || !tracks_out))) return fail(APO_EINVAL, "bad arguments");
+    const int64_t n_hits = n_events > 0 ? offsets[n_events] : 0;
+    if (n_hits < 0) return fail(APO_EINVAL, "offsets[n_events] < 0");
+    if (n_hits > 0 && (!wire_id || !drift)) return fail(APO_EINVAL, "hit arrays are NULL");
+    Layout L = layout(g, n_events);
+    const size_t need = L.end + apo_host_extra_bytes(n_events, n_hits);
+    if (!ws || ws_bytes < need) return fail(APO_ENOMEM, "workspace too small: %zu < %zu", ws_bytes, need);
+    apo_solve_opts def;
+    apo_solve_opts_default(&def);
+    const apo_solve_opts *o = opts ? opts : &def;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    size_t off = L.end;
+    int32_t *d_off = at<int32_t>(ws, off); off += align256(sizeof(int32_t) * (size_t)(n_events + 1));
+    int32_t *d_wid = at<int32_t>(ws, off); off += align256(sizeof(int32_t) * (size_t)n_hits);
+    double *d_dr = at<double>(ws, off); off += align256(sizeof(double) * (size_t)n_hits);
+    apo_track *d_tr = at<apo_track>(ws, off); off += align256(sizeof(apo_track) * (size_t)n_events * APO_MAX_TRACKS);
+    int32_t *d_nt = at<int32_t>(ws, off);
+    CU(cudaMemcpyAsync(d_off, offsets, sizeof(int32_t) * (size_t)(n_events + 1), cudaMemcpyHostToDevice, s));
+    if (n_hits > 0) {
+        CU(cudaMemcpyAsync(d_wid, wire_id, sizeof(int32_t) * (size_t)n_hits, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(d_dr, drift, sizeof(double) * (size_t)n_hits, cudaMemcpyHostToDevice, s));
+    }
+    apo_hits h{n_events, d_off, d_wid, d_dr};
+    if ((rc = apo_solve_batch(g, &h, o, d_tr, d_nt, ws, L.end, stream))) return rc;
+    CU(cudaMemcpyAsync(tracks_out, d_tr, sizeof(apo_track) * (size_t)n_events * o->max_tracks,
+                       cudaMemcpyDeviceToHost, s));
+    if (n_tracks_out)
+        CU(cudaMemcpyAsync(n_tracks_out, d_nt, sizeof(int32_t) * (size_t)n_events, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return APO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// Directed-rounding pipe microbenchmark (roofline denominators for the ALU-bound vote
+// kernels): independent dependency chains per thread, grid covering every SM.
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace apo {
+
+constexpr int kChains = 8;
+constexpr int kIters = 2048;
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(256) k_pipe(T seed, T *sink) {
+    T x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; c++) x[c] = seed + T(c) * T(1e-3) + T(threadIdx.x) * T(1e-6);
+    const T a = T(1e-7), m = T(0.9999999);
+#pragma unroll 4
+    for (int i = 0; i < kIters; i++) {
+#pragma unroll
+        for (int c = 0; c < kChains; c++) {
+            if (OP == 0) x[c] = rd_add(x[c], a);
+            else if (OP == 1) x[c] = rd_mul(x[c], m);
+            else x[c] = (i & 1) ? rd_mul(x[c], m) : ru_add(x[c], a);
+        }
+    }
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < kChains; c++) s += x[c];
+    if (s == T(-12345)) *sink = s;   // keeps the chains alive
+}
+
+template <typename T, int OP> static double run_pipe() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    T *sink = nullptr;
+    if (cudaMalloc(&sink, sizeof(T)) != cudaSuccess) return -1.0;
+    const int blocks = sms * 8, threads = 256;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_pipe<T, OP><<<blocks, threads>>>(T(1), sink);   // warm-up
+    cudaEventRecord(e0);
+    const int reps = 3;
+    for (int r = 0; r < reps; r++) k_pipe<T, OP><<<blocks, threads>>>(T(1), sink);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (cudaGetLastError() != cudaSuccess || ms <= 0.f) return -1.0;
+    double ops = (double)reps * blocks * threads * kIters * kChains;
+    return ops / (ms * 1e-3);
+}
+
+double pipe_peak(int precision, int op) {
+    if (precision == 0) {
+        if (op == 0) return run_pipe<double, 0>();
+        if (op == 1) return run_pipe<double, 1>();
+        return run_pipe<double, 2>();
+    }
+    if (op == 0) return run_pipe<float, 0>();
+    if (op == 1) return run_pipe<float, 1>();
+    return run_pipe<float, 2>();
+}
+
+}  // namespace apo

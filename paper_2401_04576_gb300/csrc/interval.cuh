@@ -1,0 +1,125 @@
+// Outward-rounded interval arithmetic on the GPU, FP64 and FP32.
+//
+// Each interval operation returns [rd(exact minimum), ru(exact maximum)] of the operation
+// over its operand intervals, using the directed-rounding intrinsics (__dadd_rd, __fmul_ru,
+// __dsqrt_rd, ...), which are never contracted into FMAs.  Products and quotients pick
+// the end points by sign cases; since rd/ru are monotone this equals the min/max over all
+// four end-point products or quotients.
+#pragma once
+#include <cstdint>
+
+namespace apo {
+
+template <typename T> struct IV { T lo, hi; };
+
+// ---- directed scalar operations, overloaded on the precision ----
+__device__ __forceinline__ double rd_add(double a, double b) { return __dadd_rd(a, b); }
+__device__ __forceinline__ double ru_add(double a, double b) { return __dadd_ru(a, b); }
+__device__ __forceinline__ double rd_sub(double a, double b) { return __dsub_rd(a, b); }
+__device__ __forceinline__ double ru_sub(double a, double b) { return __dsub_ru(a, b); }
+__device__ __forceinline__ double rd_mul(double a, double b) { return __dmul_rd(a, b); }
+__device__ __forceinline__ double ru_mul(double a, double b) { return __dmul_ru(a, b); }
+__device__ __forceinline__ double rd_div(double a, double b) { return __ddiv_rd(a, b); }
+__device__ __forceinline__ double ru_div(double a, double b) { return __ddiv_ru(a, b); }
+__device__ __forceinline__ double rd_rcp(double a) { return __drcp_rd(a); }
+__device__ __forceinline__ double ru_rcp(double a) { return __drcp_ru(a); }
+__device__ __forceinline__ double rd_sqrt(double a) { return __dsqrt_rd(a); }
+__device__ __forceinline__ double ru_sqrt(double a) { return __dsqrt_ru(a); }
+
+__device__ __forceinline__ float rd_add(float a, float b) { return __fadd_rd(a, b); }
+__device__ __forceinline__ float ru_add(float a, float b) { return __fadd_ru(a, b); }
+__device__ __forceinline__ float rd_sub(float a, float b) { return __fsub_rd(a, b); }
+__device__ __forceinline__ float ru_sub(float a, float b) { return __fsub_ru(a, b); }
+__device__ __forceinline__ float rd_mul(float a, float b) { return __fmul_rd(a, b); }
+__device__ __forceinline__ float ru_mul(float a, float b) { return __fmul_ru(a, b); }
+__device__ __forceinline__ float rd_div(float a, float b) { return __fdiv_rd(a, b); }
+__device__ __forceinline__ float ru_div(float a, float b) { return __fdiv_ru(a, b); }
+__device__ __forceinline__ float rd_rcp(float a) { return __frcp_rd(a); }
+__device__ __forceinline__ float ru_rcp(float a) { return __frcp_ru(a); }
+__device__ __forceinline__ float rd_sqrt(float a) { return __fsqrt_rd(a); }
+__device__ __forceinline__ float ru_sqrt(float a) { return __fsqrt_ru(a); }
+
+template <typename T> __device__ __forceinline__ T mn(T a, T b) { return a < b ? a : b; }
+template <typename T> __device__ __forceinline__ T mx(T a, T b) { return a > b ? a : b; }
+
+template <typename T> __device__ __forceinline__ IV<T> mk(T lo, T hi) { return IV<T>{lo, hi}; }
+template <typename T> __device__ __forceinline__ IV<T> add(IV<T> a, IV<T> b) {
+    return {rd_add(a.lo, b.lo), ru_add(a.hi, b.hi)};
+}
+template <typename T> __device__ __forceinline__ IV<T> sub(IV<T> a, IV<T> b) {
+    return {rd_sub(a.lo, b.hi), ru_sub(a.hi, b.lo)};
+}
+template <typename T> __device__ __forceinline__ IV<T> neg(IV<T> a) { return {-a.hi, -a.lo}; }
+
+template <typename T> __device__ __forceinline__ IV<T> mul(IV<T> a, IV<T> b) {
+    if (a.lo >= T(0)) {
+        if (b.lo >= T(0)) return {rd_mul(a.lo, b.lo), ru_mul(a.hi, b.hi)};
+        if (b.hi <= T(0)) return {rd_mul(a.hi, b.lo), ru_mul(a.lo, b.hi)};
+        return {rd_mul(a.hi, b.lo), ru_mul(a.hi, b.hi)};
+    }
+    if (a.hi <= T(0)) {
+        if (b.lo >= T(0)) return {rd_mul(a.lo, b.hi), ru_mul(a.hi, b.lo)};
+        if (b.hi <= T(0)) return {rd_mul(a.hi, b.hi), ru_mul(a.lo, b.lo)};
+        return {rd_mul(a.lo, b.hi), ru_mul(a.lo, b.lo)};
+    }
+    if (b.lo >= T(0)) return {rd_mul(a.lo, b.hi), ru_mul(a.hi, b.hi)};
+    if (b.hi <= T(0)) return {rd_mul(a.hi, b.lo), ru_mul(a.lo, b.lo)};
+    return {mn(rd_mul(a.lo, b.hi), rd_mul(a.hi, b.lo)), mx(ru_mul(a.lo, b.lo), ru_mul(a.hi, b.hi))};
+}
+
+// a / b with 0 not in b
+template <typename T> __device__ __forceinline__ IV<T> divi(IV<T> a, IV<T> b) {
+    if (b.lo > T(0)) {
+        T l = a.lo >= T(0) ? rd_div(a.lo, b.hi) : rd_div(a.lo, b.lo);
+        T h = a.hi >= T(0) ? ru_div(a.hi, b.lo) : ru_div(a.hi, b.hi);
+        return {l, h};
+    }
+    T l = a.hi >= T(0) ? rd_div(a.hi, b.hi) : rd_div(a.hi, b.lo);
+    T h = a.lo >= T(0) ? ru_div(a.lo, b.lo) : ru_div(a.lo, b.hi);
+    return {l, h};
+}
+
+// 1 / b with 0 not in b
+template <typename T> __device__ __forceinline__ IV<T> recip(IV<T> b) {
+    return {rd_rcp(b.hi), ru_rcp(b.lo)};
+}
+
+template <typename T> __device__ __forceinline__ IV<T> sqr(IV<T> a) {
+    if (a.lo >= T(0)) return {rd_mul(a.lo, a.lo), ru_mul(a.hi, a.hi)};
+    if (a.hi <= T(0)) return {rd_mul(a.hi, a.hi), ru_mul(a.lo, a.lo)};
+    return {T(0), mx(ru_mul(a.lo, a.lo), ru_mul(a.hi, a.hi))};
+}
+
+// square root, lower end clamped at 0 (caller guarantees hi >= 0)
+template <typename T> __device__ __forceinline__ IV<T> sqrti(IV<T> a) {
+    return {a.lo > T(0) ? rd_sqrt(a.lo) : T(0), ru_sqrt(a.hi)};
+}
+
+template <typename T> __device__ __forceinline__ IV<T> scale2(IV<T> a) { return {a.lo * T(2), a.hi * T(2)}; }
+template <typename T> __device__ __forceinline__ IV<T> half(IV<T> a) { return {a.lo * T(0.5), a.hi * T(0.5)}; }
+template <typename T> __device__ __forceinline__ IV<T> clamp1(IV<T> a) {
+    return {mx(a.lo, T(-1)), mn(a.hi, T(1))};
+}
+template <typename T> __device__ __forceinline__ IV<T> hull(IV<T> a, IV<T> b) {
+    return {mn(a.lo, b.lo), mx(a.hi, b.hi)};
+}
+template <typename T> __device__ __forceinline__ T mag(IV<T> a) { return mx(-a.lo, a.hi); }
+template <typename T> __device__ __forceinline__ bool contains0(IV<T> a) {
+    return a.lo <= T(0) && a.hi >= T(0);
+}
+template <typename T> __device__ __forceinline__ IV<T> pm(T r) { return {-r, r}; }
+
+// [rd(1/k), ru(1/k)] for an integer k > 0
+template <typename T> __device__ __forceinline__ IV<T> inv_int(int k) {
+    return {rd_rcp(T(k)), ru_rcp(T(k))};
+}
+
+// ru(m^n), m >= 0, by repeated upward products
+template <typename T> __device__ __forceinline__ T ru_pow(T m, int n) {
+    T r = T(1);
+#pragma unroll
+    for (int i = 0; i < n; i++) r = ru_mul(r, m);
+    return r;
+}
+
+}  // namespace apo

@@ -1,0 +1,116 @@
+// Device-side data layout shared by the kernels and the C-ABI host code.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/apo.h"
+#include "vote_program.cuh"
+
+namespace apo {
+
+constexpr int kHitCap = 256;        // hits per event
+constexpr int kMaxLevels = 8;
+constexpr int kHistBins = kHitCap + 1;
+
+// Read-only device tables of one geometry, passed to kernels by value.
+struct DevGeom {
+    int bins[5];
+    int levels;
+    int topk;
+    int n_wires;
+    const double *lo_edge[5];       // finest-level cell edges per axis
+    const double *hi_edge[5];
+    const double *sincos;           // (sin lo, sin hi, cos lo, cos hi) per phi0 cell per level
+    long long sincos_off[kMaxLevels + 1];
+    const double *wire[8];          // x0, y0, sin phis, cos phis, tan tau, sphi*t, cphi*t, t^2
+    SeriesConsts k;
+};
+
+// One hit as staged for the vote kernels: 80 bytes, a multiple of 16 so an event's hits
+// form one contiguous, 16-byte aligned block for a bulk (TMA) copy into shared memory.
+struct alignas(16) HitRecD { double v[9]; double pad; };          // x0 y0 sph cph t spt cpt t2 d
+struct alignas(16) HitRecF { float lo[9]; float hi[9]; float pad[2]; };
+static_assert(sizeof(HitRecD) == 80 && sizeof(HitRecF) == 80, "hit record size");
+
+// Cell edges on axis a for index i at `level`.
+__device__ __forceinline__ IV<double> edge(const DevGeom &g, int a, int level, int i) {
+    int sh = g.levels - level;
+    return {g.lo_edge[a][(long long)i << sh], g.hi_edge[a][(((long long)i + 1) << sh) - 1]};
+}
+__device__ __forceinline__ IV<double> sin_phi0(const DevGeom &g, int level, int i) {
+    const double *r = g.sincos + 4 * (g.sincos_off[level] + i);
+    return {r[0], r[1]};
+}
+__device__ __forceinline__ IV<double> cos_phi0(const DevGeom &g, int level, int i) {
+    const double *r = g.sincos + 4 * (g.sincos_off[level] + i);
+    return {r[2], r[3]};
+}
+
+// Conversion of an FP64 interval to the working precision (outward for FP32).
+template <typename T> __device__ __forceinline__ IV<T> to_prec(IV<double> a);
+template <> __device__ __forceinline__ IV<double> to_prec<double>(IV<double> a) { return a; }
+template <> __device__ __forceinline__ IV<float> to_prec<float>(IV<double> a) {
+    return {__double2float_rd(a.lo), __double2float_ru(a.hi)};
+}
+
+template <typename T> __device__ __forceinline__ Hit<T> load_hit(const void *rec);
+template <> __device__ __forceinline__ Hit<double> load_hit<double>(const void *rec) {
+    const HitRecD &r = *reinterpret_cast<const HitRecD *>(rec);
+    Hit<double> h;
+    IV<double> *f = &h.x0;
+#pragma unroll
+    for (int i = 0; i < 9; i++) f[i] = {r.v[i], r.v[i]};
+    return h;
+}
+template <> __device__ __forceinline__ Hit<float> load_hit<float>(const void *rec) {
+    const HitRecF &r = *reinterpret_cast<const HitRecF *>(rec);
+    Hit<float> h;
+    IV<float> *f = &h.x0;
+#pragma unroll
+    for (int i = 0; i < 9; i++) f[i] = {r.lo[i], r.hi[i]};
+    return h;
+}
+
+__device__ __forceinline__ uint64_t pack_key(const int idx[5]) {
+    uint64_t k = 0;
+#pragma unroll
+    for (int a = 0; a < 5; a++) k |= (uint64_t)idx[a] << (10 * a);
+    return k;
+}
+__device__ __forceinline__ void unpack_key(uint64_t k, int idx[5]) {
+#pragma unroll
+    for (int a = 0; a < 5; a++) idx[a] = (int)((k >> (10 * a)) & 1023u);
+}
+
+// Status words written by kernels (bit flags, OR-ed into a device word).
+enum : unsigned { ST_TIMEOUT = 1u, ST_BADHIT = 2u, ST_TOOMANY = 4u, ST_BADOFFS = 8u };
+
+// ---- launch wrappers (kernels.cu) ----
+void launch_stage(const DevGeom &g, int n_events, const int32_t *offsets, const int32_t *wire_id,
+                  const double *drift, HitRecD *hd, HitRecF *hf, int32_t *n_hits,
+                  unsigned *status, cudaStream_t s);
+void launch_vote_coarse(const DevGeom &g, int prec, int ev0, int n_ev, const HitRecD *hd,
+                        const HitRecF *hf, const int32_t *n_hits, int32_t *votes, uint32_t *hist,
+                        unsigned *status, cudaStream_t s, unsigned long long *ctr = nullptr);
+void launch_vote_keys(const DevGeom &g, int prec, int n_ev, const HitRecD *hd, const HitRecF *hf,
+                      const int32_t *n_hits, int level, const uint64_t *keys, long long n_per_ev,
+                      int32_t *votes, cudaStream_t s);
+void launch_vote_children(const DevGeom &g, int prec, int n_ev, const HitRecD *hd,
+                          const HitRecF *hf, const int32_t *n_hits, int child_level,
+                          const uint64_t *parents, int n_par, uint64_t *child_keys,
+                          int32_t *child_votes, cudaStream_t s);
+void launch_select_coarse(const DevGeom &g, int ev0, int n_ev, const int32_t *votes,
+                          const uint32_t *hist, int K, uint64_t *out_keys, int32_t *out_votes,
+                          cudaStream_t s);
+void launch_topk(int n_ev, const uint64_t *keys, const int32_t *votes, int n_in, int K,
+                 uint64_t *out_keys, int32_t *out_votes, cudaStream_t s);
+void launch_estimate_tracks(const DevGeom &g, int n_ev, const uint64_t *keys, const int32_t *votes,
+                            int n_in, int level, const int32_t *n_hits, apo_track *out, int stride,
+                            int32_t *n_tracks, cudaStream_t s);
+void launch_series_consts(SeriesConsts *dev_out, cudaStream_t s);
+double pipe_peak(int precision, int op);   // diag.cu: directed operations per second
+void launch_hist(int n_ev, const int32_t *votes, long long n, uint32_t *hist, cudaStream_t s);
+void launch_children(const uint64_t *keys, long long n, uint64_t *out, cudaStream_t s);
+
+}  // namespace apo
