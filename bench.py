@@ -255,7 +255,7 @@ def run_apo(args) -> None:
 
     # roofline of the dominant kernel (coarse vote): counted work / live launch time
     votes = torch.empty((ev.n_events, geom.n_coarse), dtype=torch.int32, device="cuda")
-    counts = torch.zeros(4, dtype=torch.int64, device="cuda")
+    counts = torch.zeros(8, dtype=torch.int64, device="cuda")
     L = apo.lib()
     hc = hits.c()
     import ctypes as C
@@ -263,8 +263,9 @@ def run_apo(args) -> None:
                                        apo._ptr(counts), apo._ptr(ws), ws.numel(),
                                        apo._stream_ptr(stream))
     apo._check(rc)
-    n_par, n_pre, n_tail, n_launch = (int(x) for x in counts.cpu().tolist())
+    n_par, n_pre, n_tail, n_launch, p32, q32, t32c, _ = (int(x) for x in counts.cpu().tolist())
     ops_launch = coarse_kernel_ops(n_par, n_pre, n_tail) / max(n_launch, 1)
+    ops32_launch = coarse_kernel_ops(p32, q32, t32c) / max(n_launch, 1)
     kms = []
     for _ in range(max(2, args.steps)):
         flush.fill_(1)
@@ -282,7 +283,12 @@ def run_apo(args) -> None:
                 "kernel": "k_vote_coarse<double>",
                 "peak_source": "measured: libapo directed-rounding FP64 add/mul microbenchmark "
                                "(apo_diag_pipe_peak) on this GPU, this run",
-                "ops_per_launch": ops_launch, "launch_ms": k_ms}
+                "ops_per_launch": ops_launch, "launch_ms": k_ms,
+                "fp32_filter_ops_per_launch": ops32_launch,
+                "fp32_filter_tflops": ops32_launch / (k_ms * 1e-3) / 1e12,
+                "work": {"fp64_parent": n_par, "fp64_prefix": n_pre, "fp64_tail": n_tail,
+                         "fp32_parent": p32, "fp32_prefix": q32, "fp32_tail": t32c,
+                         "launches": n_launch}}
 
     # end to end through the host-buffer entry point (pinned host inputs, tracks back)
     off_h = torch.from_numpy(np.ascontiguousarray(ev.offsets, np.int32)).pin_memory()

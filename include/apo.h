@@ -43,8 +43,11 @@ typedef enum {
     APO_EBUSY = -5     /* serving queue full: retry later                          */
 } apo_status;
 
-/* interval precision of one level */
-enum { APO_F64 = 0, APO_F32 = 1 };
+/* interval precision of one level.  APO_F64: FP64 intervals.  APO_F32: FP32 intervals.
+ * APO_F64_FILTERED: FP64 intervals evaluated only where the FP32 program votes first (FP32
+ * intervals contain the FP64 ones, so the votes are exactly APO_F64's; it pays only where
+ * most FP32 votes are "no"). */
+enum { APO_F64 = 0, APO_F32 = 1, APO_F64_FILTERED = 2 };
 
 #define APO_HIT_CAP 256      /* hits per event */
 #define APO_MAX_LEVELS 8     /* bisection levels after the coarse level */

@@ -14,9 +14,9 @@ extern "C" {
 #endif
 
 /* apo_vote on the full level-0 grid that also counts the work the coarse kernel does:
- * counts_out (device, 4 x uint64, zeroed by the call) receives the number of parent-cell
- * evaluations, per-(cell, hit) prefix evaluations and tan(lambda) tail evaluations, and
- * the number of coarse-kernel launches. */
+ * counts_out (device, 8 x uint64, zeroed by the call) receives FP64 parent-cell
+ * evaluations, FP64 per-(cell, hit) prefix evaluations, FP64 tan(lambda) tail evaluations,
+ * the number of coarse-kernel launches, then the same three FP32 counts. */
 int apo_diag_vote_coarse_counts(const apo_geometry *geom, const apo_hits *hits, int32_t precision,
                                 int32_t *votes_out, unsigned long long *counts_out,
                                 void *workspace, size_t workspace_bytes, void *stream);

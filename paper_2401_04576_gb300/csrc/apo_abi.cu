@@ -235,7 +235,8 @@ int apo_vote(const apo_geometry *g, const apo_hits *hits, const uint64_t *cell_k
              void *ws, size_t ws_bytes, void *stream) {
     int rc;
     if ((rc = check_geom(g)) || (rc = check_hits(hits))) return rc;
-    if (precision != APO_F64 && precision != APO_F32) return fail(APO_EINVAL, "bad precision");
+    if (precision != APO_F64 && precision != APO_F32 && precision != APO_F64_FILTERED)
+        return fail(APO_EINVAL, "bad precision");
     if (level < 0 || level > g->dg.levels) return fail(APO_EINVAL, "level out of range");
     if (!votes_out) return fail(APO_EINVAL, "votes_out is NULL");
     if (!cell_keys && (level != 0 || n_cells_per_event != g->n_coarse))
@@ -328,7 +329,8 @@ int apo_solve_batch(const apo_geometry *g, const apo_hits *hits, const apo_solve
     const apo_solve_opts *o = opts ? opts : &def;
     const int lv = g->dg.levels, K = g->dg.topk;
     for (int i = 0; i <= lv; i++)
-        if (o->precision[i] != APO_F64 && o->precision[i] != APO_F32) return fail(APO_EINVAL, "bad precision[%d]", i);
+        if (o->precision[i] != APO_F64 && o->precision[i] != APO_F32 && o->precision[i] != APO_F64_FILTERED)
+            return fail(APO_EINVAL, "bad precision[%d]", i);
     if (o->max_tracks != 1) return fail(APO_EINVAL, "max_tracks > 1 is not supported by this build");
     if (!tracks_out && hits->n_events > 0) return fail(APO_EINVAL, "tracks_out is NULL");
     Layout L;
@@ -387,12 +389,13 @@ int apo_diag_vote_coarse_counts(const apo_geometry *g, const apo_hits *hits, int
     int rc;
     if ((rc = check_geom(g)) || (rc = check_hits(hits))) return rc;
     if (!votes_out || !counts) return fail(APO_EINVAL, "votes_out / counts_out is NULL");
-    if (precision != APO_F64 && precision != APO_F32) return fail(APO_EINVAL, "bad precision");
+    if (precision != APO_F64 && precision != APO_F32 && precision != APO_F64_FILTERED)
+        return fail(APO_EINVAL, "bad precision");
     Layout L;
     if ((rc = check_ws(g, hits->n_events, ws, ws_bytes, L))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int ne = hits->n_events;
-    CU(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), s));
+    CU(cudaMemsetAsync(counts, 0, 8 * sizeof(unsigned long long), s));
     if (ne == 0) return APO_OK;
     unsigned *status = at<unsigned>(ws, L.status);
     int32_t *nh = at<int32_t>(ws, L.n_hits);

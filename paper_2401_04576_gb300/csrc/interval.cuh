@@ -39,8 +39,38 @@ __device__ __forceinline__ float ru_rcp(float a) { return __frcp_ru(a); }
 __device__ __forceinline__ float rd_sqrt(float a) { return __fsqrt_rd(a); }
 __device__ __forceinline__ float ru_sqrt(float a) { return __fsqrt_ru(a); }
 
-template <typename T> __device__ __forceinline__ T mn(T a, T b) { return a < b ? a : b; }
-template <typename T> __device__ __forceinline__ T mx(T a, T b) { return a > b ? a : b; }
+// ---- value tests and min / max ----
+// FP64 comparisons would run on the (narrow) FP64 pipe; they are done on the integer pipe
+// through the bit pattern instead (operands are never NaN here).  For x != NaN the signed
+// 64-bit pattern b satisfies: x > 0 <=> b > 0, x <= 0 <=> b <= 0, and the sign bit is set
+// for every x in (-inf, -0].  okey() maps doubles to signed integers in value order.
+// Sign-case selection (nonneg_lo / nonpos_hi) may route an end point of -0 through the
+// mixed-sign formula; every formula used is valid for the intervals it is chosen for, so
+// the end points equal the min / max over the end-point products in every case.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ long long okey(double x) {
+    long long b = dbits(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool gt0(double x) { return dbits(x) > 0; }
+__device__ __forceinline__ bool le0(double x) { return dbits(x) <= 0; }
+__device__ __forceinline__ bool lt0(double x) { return okey(x) < -1; }     // -0 has key -1
+__device__ __forceinline__ bool ge0(double x) { return okey(x) >= -1; }
+__device__ __forceinline__ bool nonneg_lo(double x) { return dbits(x) >= 0; }   // in [+0, inf]
+__device__ __forceinline__ bool nonpos_hi(double x) { return dbits(x) < 0; }    // in [-inf, -0]
+__device__ __forceinline__ bool le(double a, double b) { return okey(a) <= okey(b); }
+__device__ __forceinline__ double mn(double a, double b) { return okey(a) < okey(b) ? a : b; }
+__device__ __forceinline__ double mx(double a, double b) { return okey(a) > okey(b) ? a : b; }
+
+__device__ __forceinline__ bool gt0(float x) { return x > 0.f; }
+__device__ __forceinline__ bool le0(float x) { return x <= 0.f; }
+__device__ __forceinline__ bool lt0(float x) { return x < 0.f; }
+__device__ __forceinline__ bool ge0(float x) { return x >= 0.f; }
+__device__ __forceinline__ bool nonneg_lo(float x) { return x >= 0.f; }
+__device__ __forceinline__ bool nonpos_hi(float x) { return x <= 0.f; }
+__device__ __forceinline__ bool le(float a, float b) { return a <= b; }
+__device__ __forceinline__ float mn(float a, float b) { return a < b ? a : b; }
+__device__ __forceinline__ float mx(float a, float b) { return a > b ? a : b; }
 
 template <typename T> __device__ __forceinline__ IV<T> mk(T lo, T hi) { return IV<T>{lo, hi}; }
 template <typename T> __device__ __forceinline__ IV<T> add(IV<T> a, IV<T> b) {
@@ -52,30 +82,30 @@ template <typename T> __device__ __forceinline__ IV<T> sub(IV<T> a, IV<T> b) {
 template <typename T> __device__ __forceinline__ IV<T> neg(IV<T> a) { return {-a.hi, -a.lo}; }
 
 template <typename T> __device__ __forceinline__ IV<T> mul(IV<T> a, IV<T> b) {
-    if (a.lo >= T(0)) {
-        if (b.lo >= T(0)) return {rd_mul(a.lo, b.lo), ru_mul(a.hi, b.hi)};
-        if (b.hi <= T(0)) return {rd_mul(a.hi, b.lo), ru_mul(a.lo, b.hi)};
+    if (nonneg_lo(a.lo)) {
+        if (nonneg_lo(b.lo)) return {rd_mul(a.lo, b.lo), ru_mul(a.hi, b.hi)};
+        if (nonpos_hi(b.hi)) return {rd_mul(a.hi, b.lo), ru_mul(a.lo, b.hi)};
         return {rd_mul(a.hi, b.lo), ru_mul(a.hi, b.hi)};
     }
-    if (a.hi <= T(0)) {
-        if (b.lo >= T(0)) return {rd_mul(a.lo, b.hi), ru_mul(a.hi, b.lo)};
-        if (b.hi <= T(0)) return {rd_mul(a.hi, b.hi), ru_mul(a.lo, b.lo)};
+    if (nonpos_hi(a.hi)) {
+        if (nonneg_lo(b.lo)) return {rd_mul(a.lo, b.hi), ru_mul(a.hi, b.lo)};
+        if (nonpos_hi(b.hi)) return {rd_mul(a.hi, b.hi), ru_mul(a.lo, b.lo)};
         return {rd_mul(a.lo, b.hi), ru_mul(a.lo, b.lo)};
     }
-    if (b.lo >= T(0)) return {rd_mul(a.lo, b.hi), ru_mul(a.hi, b.hi)};
-    if (b.hi <= T(0)) return {rd_mul(a.hi, b.lo), ru_mul(a.lo, b.lo)};
+    if (nonneg_lo(b.lo)) return {rd_mul(a.lo, b.hi), ru_mul(a.hi, b.hi)};
+    if (nonpos_hi(b.hi)) return {rd_mul(a.hi, b.lo), ru_mul(a.lo, b.lo)};
     return {mn(rd_mul(a.lo, b.hi), rd_mul(a.hi, b.lo)), mx(ru_mul(a.lo, b.lo), ru_mul(a.hi, b.hi))};
 }
 
 // a / b with 0 not in b
 template <typename T> __device__ __forceinline__ IV<T> divi(IV<T> a, IV<T> b) {
-    if (b.lo > T(0)) {
-        T l = a.lo >= T(0) ? rd_div(a.lo, b.hi) : rd_div(a.lo, b.lo);
-        T h = a.hi >= T(0) ? ru_div(a.hi, b.lo) : ru_div(a.hi, b.hi);
+    if (gt0(b.lo)) {
+        T l = nonneg_lo(a.lo) ? rd_div(a.lo, b.hi) : rd_div(a.lo, b.lo);
+        T h = nonneg_lo(a.hi) ? ru_div(a.hi, b.lo) : ru_div(a.hi, b.hi);
         return {l, h};
     }
-    T l = a.hi >= T(0) ? rd_div(a.hi, b.hi) : rd_div(a.hi, b.lo);
-    T h = a.lo >= T(0) ? ru_div(a.lo, b.lo) : ru_div(a.lo, b.hi);
+    T l = nonneg_lo(a.hi) ? rd_div(a.hi, b.hi) : rd_div(a.hi, b.lo);
+    T h = nonneg_lo(a.lo) ? ru_div(a.lo, b.lo) : ru_div(a.lo, b.hi);
     return {l, h};
 }
 
@@ -85,14 +115,14 @@ template <typename T> __device__ __forceinline__ IV<T> recip(IV<T> b) {
 }
 
 template <typename T> __device__ __forceinline__ IV<T> sqr(IV<T> a) {
-    if (a.lo >= T(0)) return {rd_mul(a.lo, a.lo), ru_mul(a.hi, a.hi)};
-    if (a.hi <= T(0)) return {rd_mul(a.hi, a.hi), ru_mul(a.lo, a.lo)};
+    if (nonneg_lo(a.lo)) return {rd_mul(a.lo, a.lo), ru_mul(a.hi, a.hi)};
+    if (nonpos_hi(a.hi)) return {rd_mul(a.hi, a.hi), ru_mul(a.lo, a.lo)};
     return {T(0), mx(ru_mul(a.lo, a.lo), ru_mul(a.hi, a.hi))};
 }
 
 // square root, lower end clamped at 0 (caller guarantees hi >= 0)
 template <typename T> __device__ __forceinline__ IV<T> sqrti(IV<T> a) {
-    return {a.lo > T(0) ? rd_sqrt(a.lo) : T(0), ru_sqrt(a.hi)};
+    return {gt0(a.lo) ? rd_sqrt(a.lo) : T(0), ru_sqrt(a.hi)};
 }
 
 template <typename T> __device__ __forceinline__ IV<T> scale2(IV<T> a) { return {a.lo * T(2), a.hi * T(2)}; }
@@ -105,7 +135,7 @@ template <typename T> __device__ __forceinline__ IV<T> hull(IV<T> a, IV<T> b) {
 }
 template <typename T> __device__ __forceinline__ T mag(IV<T> a) { return mx(-a.lo, a.hi); }
 template <typename T> __device__ __forceinline__ bool contains0(IV<T> a) {
-    return a.lo <= T(0) && a.hi >= T(0);
+    return le0(a.lo) && ge0(a.hi);
 }
 template <typename T> __device__ __forceinline__ IV<T> pm(T r) { return {-r, r}; }
 

@@ -39,27 +39,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
 }
 constexpr long kWaitLimit = 1L << 22;
 
-// Copies `bytes` (multiple of 16, 16-byte aligned ends) of an event's hit records into
-// shared memory.  Returns false (and flags ST_TIMEOUT) if the copy did not complete within
-// the wait limit; the caller then skips the block's work.
-__device__ bool stage_to_smem(void *dst, const void *src, unsigned bytes, uint64_t *bar,
-                              unsigned *status) {
+// Copies up to two blocks (bytes0 / bytes1: multiples of 16, 16-byte aligned ends) of an
+// event's hit records into shared memory with one mbarrier.  Returns false (and flags
+// ST_TIMEOUT) if the copies did not complete within the wait limit; the caller then skips
+// the block's work.
+__device__ bool stage_to_smem(void *dst0, const void *src0, unsigned bytes0, void *dst1,
+                              const void *src1, unsigned bytes1, uint64_t *bar, unsigned *status) {
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    if (bytes == 0) return true;
+    if (bytes0 + bytes1 == 0) return true;
     if (threadIdx.x == 0) {
-        mbar_expect_tx(bar, bytes);
-        bulk_g2s(dst, src, bytes, bar);
+        mbar_expect_tx(bar, bytes0 + bytes1);
+        if (bytes0) bulk_g2s(dst0, src0, bytes0, bar);
+        if (bytes1) bulk_g2s(dst1, src1, bytes1, bar);
     }
     long it = 0;
     while (!mbar_try_wait(bar, 0)) {
         if (++it > kWaitLimit) {
             atomicOr(status, ST_TIMEOUT);
-            // give the copy in flight a second bounded chance before leaving the smem
+            // give the copies in flight a second bounded chance before leaving the smem
             for (long j = 0; j < kWaitLimit && !mbar_try_wait(bar, 0); j++) {
             }
             return false;
@@ -140,14 +142,6 @@ void launch_stage(const DevGeom &g, int n_events, const int32_t *offsets, const 
     k_stage<<<n_events, 128, 0, s>>>(g, n_events, offsets, wire_id, drift, hd, hf, n_hits, status);
 }
 
-template <typename T> __device__ __forceinline__ const void *hit_base(const HitRecD *hd, const HitRecF *hf, int ev);
-template <> __device__ __forceinline__ const void *hit_base<double>(const HitRecD *hd, const HitRecF *, int ev) {
-    return hd + (long long)ev * kHitCap;
-}
-template <> __device__ __forceinline__ const void *hit_base<float>(const HitRecD *, const HitRecF *hf, int ev) {
-    return hf + (long long)ev * kHitCap;
-}
-
 // ---------------------------------------------------------------------------------------
 // Coarse-grid voting.  Block = (event, phi0 bin p, omega bin w); thread = (d0 bin, z0 bin);
 // each thread loops over the tan(lambda) bins, reusing the tan(lambda)-free prefix of the
@@ -155,88 +149,137 @@ template <> __device__ __forceinline__ const void *hit_base<float>(const HitRecD
 // tan(lambda) bins joined): interval operations are inclusion-isotonic and the guards only
 // fire on a parent when they fire on a child, so a hit that fails there fails on every
 // child cell; skipping it leaves every vote unchanged.
+// Modes: FP32 intervals; FP64 intervals; FP64 intervals evaluated only where the FP32
+// program votes (FP32 intervals contain the FP64 ones, so an FP32 "no" is an FP64 "no":
+// the votes are those of the plain FP64 program).
 // Writes votes[e][lin], lin = d + Bd (p + Bp (w + Bw (z + Bz l))), and the per-event
 // histogram of vote counts.
 // ---------------------------------------------------------------------------------------
-template <typename T>
+enum : int { kModeF32 = 0, kModeF64 = 1, kModeF64Filtered = 2 };
+
+template <int MODE> struct CoarseSmem {
+    static constexpr bool k64 = MODE != kModeF32, k32 = MODE != kModeF64;
+    static constexpr size_t hits64 = 0;
+    static constexpr size_t hits32 = k64 ? kHitCap * 80 : 0;
+    static constexpr size_t hist = hits32 + (k32 ? kHitCap * 80 : 0);
+    static constexpr size_t mask = hist + kHistBins * 4 + 12;
+    static constexpr size_t bar = mask + 32;
+    static constexpr size_t L64 = bar + 8;
+    __host__ __device__ static size_t L32(int Bl) { return L64 + 16 * Bl; }
+    __host__ __device__ static size_t cnt(int Bl) { return L32(Bl) + 8 * Bl; }
+    __host__ __device__ static size_t total(int Bl, int nthr) { return cnt(Bl) + 4 * Bl * nthr + 16; }
+};
+
+template <int MODE>
 __global__ void __launch_bounds__(256)
 k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
               int32_t *votes, uint32_t *hist, unsigned *status, unsigned long long *ctr) {
+    using S = CoarseSmem<MODE>;
+    constexpr bool k64 = S::k64, k32 = S::k32;
     extern __shared__ __align__(16) unsigned char smem[];
     const int Bd = g.bins[0], Bp = g.bins[1], Bw = g.bins[2], Bz = g.bins[3], Bl = g.bins[4];
     const int nthr = Bd * Bz;
     const int e = blockIdx.y, ev = ev0 + e;
     const int p = blockIdx.x % Bp, w = blockIdx.x / Bp;
     const int tid = threadIdx.x;
-    unsigned char *hits_s = smem;                                        // kHitCap * 80
-    uint32_t *hist_s = reinterpret_cast<uint32_t *>(smem + kHitCap * 80);    // kHistBins
-    uint32_t *mask_s = hist_s + kHistBins + 3;                            // 8 words
-    uint64_t *bar = reinterpret_cast<uint64_t *>(mask_s + 8);
-    IV<T> *Ls = reinterpret_cast<IV<T> *>(bar + 1);                       // Bl
-    int32_t *cnt = reinterpret_cast<int32_t *>(Ls + Bl);                  // Bl * nthr
+    unsigned char *h64s = smem + S::hits64;
+    unsigned char *h32s = smem + S::hits32;
+    uint32_t *hist_s = reinterpret_cast<uint32_t *>(smem + S::hist);
+    uint32_t *mask_s = reinterpret_cast<uint32_t *>(smem + S::mask);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S::bar);
+    IV<double> *L64 = reinterpret_cast<IV<double> *>(smem + S::L64);
+    IV<float> *L32 = reinterpret_cast<IV<float> *>(smem + S::L32(Bl));
+    int32_t *cnt = reinterpret_cast<int32_t *>(smem + S::cnt(Bl));
 
     int nh = n_hits[ev];
     if (nh < 0) nh = 0;
     for (int i = tid; i < kHistBins; i += nthr) hist_s[i] = 0;
     if (tid < 8) mask_s[tid] = 0;
-    for (int l = tid; l < Bl; l += nthr) Ls[l] = to_prec<T>(edge(g, 4, 0, l));
+    for (int l = tid; l < Bl; l += nthr) {
+        IV<double> el = edge(g, 4, 0, l);
+        L64[l] = el;
+        L32[l] = to_prec<float>(el);
+    }
     for (int i = tid; i < Bl * nthr; i += nthr) cnt[i] = 0;
-    bool ok = stage_to_smem(hits_s, hit_base<T>(hd, hf, ev), (unsigned)nh * 80u, bar, status);
+    const unsigned bytes = (unsigned)nh * 80u;
+    bool ok = stage_to_smem(h64s, hd + (long long)ev * kHitCap, k64 ? bytes : 0u, h32s,
+                            hf + (long long)ev * kHitCap, k32 ? bytes : 0u, bar, status);
     __syncthreads();
     if (!ok) nh = 0;
 
     const SeriesConsts &k = g.k;
-    const IV<T> S0 = to_prec<T>(sin_phi0(g, 0, p)), C0 = to_prec<T>(cos_phi0(g, 0, p));
-    const IV<T> W = to_prec<T>(edge(g, 2, 0, w));
+    const IV<double> S0 = sin_phi0(g, 0, p), C0 = cos_phi0(g, 0, p), W = edge(g, 2, 0, w);
+    unsigned n_par32 = 0, n_pre32 = 0, n_tail32 = 0, n_par64 = 0, n_pre64 = 0, n_tail64 = 0;
     // parent cell test, one hit per thread
     {
         IV<double> D0 = edge(g, 0, 0, 0), D1 = edge(g, 0, 0, Bd - 1);
         IV<double> Z0 = edge(g, 3, 0, 0), Z1 = edge(g, 3, 0, Bz - 1);
         IV<double> L0 = edge(g, 4, 0, 0), L1 = edge(g, 4, 0, Bl - 1);
-        Cell<T> par;
-        par.D = to_prec<T>(IV<double>{D0.lo, D1.hi});
-        par.S0 = S0;
-        par.C0 = C0;
-        par.W = W;
-        par.Z = to_prec<T>(IV<double>{Z0.lo, Z1.hi});
-        par.L = to_prec<T>(IV<double>{L0.lo, L1.hi});
+        Cell<double> par{{D0.lo, D1.hi}, S0, C0, W, {Z0.lo, Z1.hi}, {L0.lo, L1.hi}};
+        Cell<float> par32{to_prec<float>(par.D), to_prec<float>(S0), to_prec<float>(C0),
+                          to_prec<float>(W), to_prec<float>(par.Z), to_prec<float>(par.L)};
         for (int h = tid; h < nh; h += nthr) {
-            Hit<T> hh = load_hit<T>(hits_s + h * 80);
-            if (vote_pair<T>(par, hh, k)) atomicOr(&mask_s[h >> 5], 1u << (h & 31));
+            bool v = true;
+            if (k32) { v = vote_pair<float>(par32, load_hit<float>(h32s + h * 80), k); n_par32++; }
+            if (k64 && v) { v = vote_pair<double>(par, load_hit<double>(h64s + h * 80), k); n_par64++; }
+            if (v) atomicOr(&mask_s[h >> 5], 1u << (h & 31));
         }
     }
     __syncthreads();
 
     const int d = tid % Bd, z = tid / Bd;
-    Cell<T> c;
-    c.D = to_prec<T>(edge(g, 0, 0, d));
-    c.S0 = S0;
-    c.C0 = C0;
-    c.W = W;
-    c.Z = to_prec<T>(edge(g, 3, 0, z));
-    c.L = Ls[0];
+    Cell<double> c{edge(g, 0, 0, d), S0, C0, W, edge(g, 3, 0, z), L64[0]};
+    Cell<float> c32{to_prec<float>(c.D), to_prec<float>(S0), to_prec<float>(C0), to_prec<float>(W),
+                    to_prec<float>(c.Z), L32[0]};
     const bool mir = mirror_cell(c);
-    const bool wguard = !(c.W.lo > T(0));
-    const IV<T> R = recip(c.W);
-    unsigned n_pre = 0, n_tail = 0;     // work counters (diagnostics only)
+    mirror_cell(c32);
+    const bool wguard = !gt0(c.W.lo) || !gt0(c32.W.lo);
+    const IV<double> R = recip(c.W);
+    const IV<float> R32 = recip(c32.W);
+    const unsigned all = Bl >= 32 ? 0xffffffffu : ((1u << Bl) - 1u);
     for (int wd = 0; wd < 8; wd++) {
         uint32_t m = mask_s[wd];
         while (m) {
             int h = wd * 32 + __ffs(m) - 1;
             m &= m - 1;
-            Hit<T> hh = load_hit<T>(hits_s + h * 80);
-            if (mir) mirror_hit(hh);
-            Pre<T> pre;
-            if (!wguard) pre = prefix<T>(c, hh, k);
-            n_pre++;
-            if (wguard || pre.guard) {
+            if (wguard) {
                 for (int l = 0; l < Bl; l++) cnt[l * nthr + tid]++;
                 continue;
             }
-            n_tail += Bl;
+            // tan(lambda) bins still in question after the FP32 program
+            unsigned lm = all;
+            if (k32) {
+                Hit<float> h32 = load_hit<float>(h32s + h * 80);
+                if (mir) mirror_hit(h32);
+                Pre<float> p32 = prefix<float>(c32, h32, k);
+                n_pre32++;
+                if (!p32.guard) {
+                    lm = 0;
+                    n_tail32 += Bl;
 #pragma unroll 1
-            for (int l = 0; l < Bl; l++)
-                if (tail<T>(pre, Ls[l], hh, R, c.W, k)) cnt[l * nthr + tid]++;
+                    for (int l = 0; l < Bl; l++)
+                        if (tail<float>(p32, L32[l], h32, R32, c32.W, k)) lm |= 1u << l;
+                }
+                if (!k64) {
+                    for (int l = 0; l < Bl; l++) cnt[l * nthr + tid] += (lm >> l) & 1u;
+                    continue;
+                }
+            }
+            if (!lm) continue;
+            Hit<double> h64 = load_hit<double>(h64s + h * 80);
+            if (mir) mirror_hit(h64);
+            Pre<double> p64 = prefix<double>(c, h64, k);
+            n_pre64++;
+            if (p64.guard) {
+                for (int l = 0; l < Bl; l++) cnt[l * nthr + tid]++;
+                continue;
+            }
+            while (lm) {
+                int l = __ffs(lm) - 1;
+                lm &= lm - 1;
+                n_tail64++;
+                if (tail<double>(p64, L64[l], h64, R, c.W, k)) cnt[l * nthr + tid]++;
+            }
         }
     }
     const long long ncell = (long long)Bd * Bp * Bw * Bz * Bl;
@@ -250,34 +293,39 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
     __syncthreads();
     for (int i = tid; i < kHistBins; i += nthr)
         if (hist_s[i]) atomicAdd(&hist[(long long)e * kHistBins + i], hist_s[i]);
-    if (ctr) {
-        if (tid == 0) atomicAdd(&ctr[0], (unsigned long long)nh);     // parent evaluations
-        atomicAdd(&ctr[1], (unsigned long long)n_pre);                // prefix evaluations
-        atomicAdd(&ctr[2], (unsigned long long)n_tail);               // tail evaluations
+    if (ctr) {   // work counters (diagnostics): FP64 parent / prefix / tail, -, FP32 ones
+        unsigned long long v[6] = {n_par64, n_pre64, n_tail64, n_par32, n_pre32, n_tail32};
+        const int slot[6] = {0, 1, 2, 4, 5, 6};
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+            unsigned long long x = v[i];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if ((tid & 31) == 0 && x) atomicAdd(&ctr[slot[i]], x);
+        }
     }
 }
 
-template <typename T> static size_t coarse_smem(const DevGeom &g) {
+template <int MODE> static void launch_coarse_mode(const DevGeom &g, int ev0, int n_ev, const HitRecD *hd,
+                                                  const HitRecF *hf, const int32_t *n_hits, int32_t *votes,
+                                                  uint32_t *hist, unsigned *status, cudaStream_t s,
+                                                  unsigned long long *ctr) {
+    dim3 grid(g.bins[1] * g.bins[2], n_ev);
     int nthr = g.bins[0] * g.bins[3];
-    return kHitCap * 80 + (kHistBins + 3 + 8) * 4 + 8 + sizeof(IV<T>) * g.bins[4] +
-           sizeof(int32_t) * g.bins[4] * nthr + 16;
+    size_t sm = CoarseSmem<MODE>::total(g.bins[4], nthr);
+    cudaFuncSetAttribute(k_vote_coarse<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_vote_coarse<MODE><<<grid, nthr, sm, s>>>(g, ev0, hd, hf, n_hits, votes, hist, status, ctr);
 }
 
 void launch_vote_coarse(const DevGeom &g, int prec, int ev0, int n_ev, const HitRecD *hd,
                         const HitRecF *hf, const int32_t *n_hits, int32_t *votes, uint32_t *hist,
                         unsigned *status, cudaStream_t s, unsigned long long *ctr) {
     if (n_ev <= 0) return;
-    dim3 grid(g.bins[1] * g.bins[2], n_ev);
-    int nthr = g.bins[0] * g.bins[3];
-    if (prec == APO_F64) {
-        size_t sm = coarse_smem<double>(g);
-        cudaFuncSetAttribute(k_vote_coarse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_vote_coarse<double><<<grid, nthr, sm, s>>>(g, ev0, hd, hf, n_hits, votes, hist, status, ctr);
-    } else {
-        size_t sm = coarse_smem<float>(g);
-        cudaFuncSetAttribute(k_vote_coarse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_vote_coarse<float><<<grid, nthr, sm, s>>>(g, ev0, hd, hf, n_hits, votes, hist, status, ctr);
-    }
+    if (prec == APO_F32)
+        launch_coarse_mode<kModeF32>(g, ev0, n_ev, hd, hf, n_hits, votes, hist, status, s, ctr);
+    else if (prec == APO_F64_FILTERED)
+        launch_coarse_mode<kModeF64Filtered>(g, ev0, n_ev, hd, hf, n_hits, votes, hist, status, s, ctr);
+    else
+        launch_coarse_mode<kModeF64>(g, ev0, n_ev, hd, hf, n_hits, votes, hist, status, s, ctr);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -285,18 +333,22 @@ void launch_vote_coarse(const DevGeom &g, int prec, int ev0, int n_ev, const Hit
 // 32 children of each parent key (parents != nullptr).  Thread = one cell, looping over
 // all hits of its event; child keys are written out when parents are given.
 // ---------------------------------------------------------------------------------------
-template <typename T>
+template <int MODE>
 __global__ void __launch_bounds__(256)
 k_vote_cells(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits, int level,
              const uint64_t *keys, const uint64_t *parents, long long n_per_ev, uint64_t *out_keys,
              int32_t *out_votes, unsigned *status) {
+    constexpr bool k64 = MODE != kModeF32, k32 = MODE != kModeF64;
     extern __shared__ __align__(16) unsigned char smem[];
-    unsigned char *hits_s = smem;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kHitCap * 80);
+    unsigned char *h64s = smem;
+    unsigned char *h32s = smem + (k64 ? kHitCap * 80 : 0);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (k64 ? kHitCap * 80 : 0) + (k32 ? kHitCap * 80 : 0));
     const int ev = blockIdx.y;
     int nh = n_hits[ev];
     if (nh < 0) nh = 0;
-    bool ok = stage_to_smem(hits_s, hit_base<T>(hd, hf, ev), (unsigned)nh * 80u, bar, status);
+    const unsigned bytes = (unsigned)nh * 80u;
+    bool ok = stage_to_smem(h64s, hd + (long long)ev * kHitCap, k64 ? bytes : 0u, h32s,
+                            hf + (long long)ev * kHitCap, k32 ? bytes : 0u, bar, status);
     __syncthreads();
     if (!ok) nh = 0;
     long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -323,44 +375,54 @@ k_vote_cells(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_h
         if (out_keys) out_keys[o] = key;
         return;
     }
-    Cell<T> c;
-    c.D = to_prec<T>(edge(g, 0, level, idx[0]));
-    c.S0 = to_prec<T>(sin_phi0(g, level, idx[1]));
-    c.C0 = to_prec<T>(cos_phi0(g, level, idx[1]));
-    c.W = to_prec<T>(edge(g, 2, level, idx[2]));
-    c.Z = to_prec<T>(edge(g, 3, level, idx[3]));
-    c.L = to_prec<T>(edge(g, 4, level, idx[4]));
+    Cell<double> c{edge(g, 0, level, idx[0]), sin_phi0(g, level, idx[1]), cos_phi0(g, level, idx[1]),
+                   edge(g, 2, level, idx[2]), edge(g, 3, level, idx[3]), edge(g, 4, level, idx[4])};
+    Cell<float> c32{to_prec<float>(c.D), to_prec<float>(c.S0), to_prec<float>(c.C0),
+                    to_prec<float>(c.W), to_prec<float>(c.Z), to_prec<float>(c.L)};
     const SeriesConsts &k = g.k;
     int v = 0;
     for (int h = 0; h < nh; h++) {
-        Hit<T> hh = load_hit<T>(hits_s + h * 80);
-        v += vote_pair<T>(c, hh, k) ? 1 : 0;
+        bool vt = true;
+        if (k32) vt = vote_pair<float>(c32, load_hit<float>(h32s + h * 80), k);
+        if (k64 && vt) vt = vote_pair<double>(c, load_hit<double>(h64s + h * 80), k);
+        v += vt ? 1 : 0;
     }
     out_votes[o] = v;
     if (out_keys) out_keys[o] = key;
 }
 
-template <typename T>
-static void launch_cells(const DevGeom &g, int n_ev, const HitRecD *hd, const HitRecF *hf,
+template <int MODE>
+static void launch_cells_mode(const DevGeom &g, int n_ev, const HitRecD *hd, const HitRecF *hf,
+                              const int32_t *n_hits, int level, const uint64_t *keys,
+                              const uint64_t *parents, long long n_per_ev, uint64_t *out_keys,
+                              int32_t *out_votes, unsigned *status, cudaStream_t s) {
+    size_t sm = (MODE != kModeF32 ? kHitCap * 80 : 0) + (MODE != kModeF64 ? kHitCap * 80 : 0) + 16;
+    cudaFuncSetAttribute(k_vote_cells<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dim3 grid((unsigned)((n_per_ev + 255) / 256), n_ev);
+    k_vote_cells<MODE><<<grid, 256, sm, s>>>(g, hd, hf, n_hits, level, keys, parents, n_per_ev,
+                                              out_keys, out_votes, status);
+}
+
+static void launch_cells(const DevGeom &g, int prec, int n_ev, const HitRecD *hd, const HitRecF *hf,
                          const int32_t *n_hits, int level, const uint64_t *keys,
                          const uint64_t *parents, long long n_per_ev, uint64_t *out_keys,
                          int32_t *out_votes, unsigned *status, cudaStream_t s) {
-    size_t sm = kHitCap * 80 + 16;
-    dim3 grid((unsigned)((n_per_ev + 255) / 256), n_ev);
-    k_vote_cells<T><<<grid, 256, sm, s>>>(g, hd, hf, n_hits, level, keys, parents, n_per_ev,
-                                           out_keys, out_votes, status);
+    if (prec == APO_F32)
+        launch_cells_mode<kModeF32>(g, n_ev, hd, hf, n_hits, level, keys, parents, n_per_ev, out_keys,
+                                    out_votes, status, s);
+    else if (prec == APO_F64_FILTERED)
+        launch_cells_mode<kModeF64Filtered>(g, n_ev, hd, hf, n_hits, level, keys, parents, n_per_ev,
+                                            out_keys, out_votes, status, s);
+    else
+        launch_cells_mode<kModeF64>(g, n_ev, hd, hf, n_hits, level, keys, parents, n_per_ev, out_keys,
+                                    out_votes, status, s);
 }
 
 void launch_vote_keys(const DevGeom &g, int prec, int n_ev, const HitRecD *hd, const HitRecF *hf,
                       const int32_t *n_hits, int level, const uint64_t *keys, long long n_per_ev,
                       int32_t *votes, cudaStream_t s) {
     if (n_ev <= 0 || n_per_ev <= 0) return;
-    if (prec == APO_F64)
-        launch_cells<double>(g, n_ev, hd, hf, n_hits, level, keys, nullptr, n_per_ev, nullptr, votes,
-                             nullptr, s);
-    else
-        launch_cells<float>(g, n_ev, hd, hf, n_hits, level, keys, nullptr, n_per_ev, nullptr, votes,
-                            nullptr, s);
+    launch_cells(g, prec, n_ev, hd, hf, n_hits, level, keys, nullptr, n_per_ev, nullptr, votes, nullptr, s);
 }
 
 void launch_vote_children(const DevGeom &g, int prec, int n_ev, const HitRecD *hd,
@@ -368,13 +430,8 @@ void launch_vote_children(const DevGeom &g, int prec, int n_ev, const HitRecD *h
                           const uint64_t *parents, int n_par, uint64_t *child_keys,
                           int32_t *child_votes, cudaStream_t s) {
     if (n_ev <= 0 || n_par <= 0) return;
-    long long n = (long long)n_par * 32;
-    if (prec == APO_F64)
-        launch_cells<double>(g, n_ev, hd, hf, n_hits, child_level, nullptr, parents, n, child_keys,
-                             child_votes, nullptr, s);
-    else
-        launch_cells<float>(g, n_ev, hd, hf, n_hits, child_level, nullptr, parents, n, child_keys,
-                            child_votes, nullptr, s);
+    launch_cells(g, prec, n_ev, hd, hf, n_hits, child_level, nullptr, parents, (long long)n_par * 32,
+                 child_keys, child_votes, nullptr, s);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -43,7 +43,7 @@ template <typename T> struct Hit { IV<T> x0, y0, sph, cph, t, spt, cpt, t2, d; }
 // written with (sin phi_s, -cos phi_s)); afterwards omega > 0 and the R > 0 formulas of the
 // paper's appendix apply.  The drift sign is tried both ways, so it needs no flip.
 template <typename T> __device__ __forceinline__ bool mirror_cell(Cell<T> &c) {
-    if (c.W.hi < T(0)) {
+    if (lt0(c.W.hi)) {
         c.D = neg(c.D); c.S0 = neg(c.S0); c.W = neg(c.W);
         return true;
     }
@@ -75,7 +75,7 @@ template <typename T>
 __device__ __forceinline__ void sincos_iv(IV<T> d, IV<T> &s, IV<T> &c, const SeriesConsts &k) {
     const IV<T> one{T(1), T(1)};
     T m = mag(d);
-    if (!(m <= T(1))) { s = {T(-1), T(1)}; c = {T(-1), T(1)}; return; }
+    if (!le(m, T(1))) { s = {T(-1), T(1)}; c = {T(-1), T(1)}; return; }
     IV<T> y = sqr(d);
     IV<T> hs = cst<T>(k, C_SIN7);
     hs = sub(cst<T>(k, C_SIN5), mul(y, hs));
@@ -115,12 +115,12 @@ __device__ __forceinline__ Pre<T> prefix(const Cell<T> &c, const Hit<T> &h, cons
     IV<T> Xt = mul(c.W, wt);
     IV<T> Xn = sub(mul(c.W, V), one);
     p.N = sqrti(add(sqr(Xt), sqr(Xn)));
-    if (p.N.lo <= T(0)) { p.guard = true; return p; }
+    if (le0(p.N.lo)) { p.guard = true; return p; }
     // rho ((R_i^Ax)^2 - R^2)
     p.G0 = add(mul(c.W, sqr(wt)), mul(V, sub(Xn, one)));
     // turning angle psi = phi_i^Ax - phi0 from tan(psi/2) = Xt / (N - Xn)
     IV<T> den = sub(p.N, Xn);
-    if (den.lo <= T(0)) { p.guard = true; return p; }
+    if (le0(den.lo)) { p.guard = true; return p; }
     p.psi = scale2(atan_iv(divi(Xt, den), k));
     // rho s_i^Ax, rho c_i^Ax (Eq. defEQApo1)
     IV<T> E1 = add(mul(c.C0, h.cph), mul(c.S0, h.sph));
@@ -168,7 +168,7 @@ __device__ __forceinline__ bool tail(const Pre<T> &p, IV<T> L, const Hit<T> &h, 
     IV<T> cP = clamp1(sub(mul(p.cPA, cd), mul(p.sPA, sd)));
     // u_d^2 (Eq. normudi)
     IV<T> u2 = add(add(add(one, mul(scale2(h.t), mul(L, sP))), mul(L2, h.t2)), mul(sqr(cP), h.t2));
-    if (u2.lo <= T(0)) return true;
+    if (le0(u2.lo)) return true;
     IV<T> Q = mul(h.d, recip(sqrti(u2)));
     IV<T> Qct = mul(Q, mul(cP, h.t));
     IV<T> LQ = mul(L, Q);
@@ -197,7 +197,7 @@ __device__ __forceinline__ bool tail(const Pre<T> &p, IV<T> L, const Hit<T> &h, 
 template <typename T>
 __device__ __forceinline__ bool vote_pair(Cell<T> c, Hit<T> h, const SeriesConsts &k) {
     if (mirror_cell(c)) mirror_hit(h);
-    if (c.W.lo <= T(0)) return true;
+    if (le0(c.W.lo)) return true;
     IV<T> R = recip(c.W);
     Pre<T> p = prefix(c, h, k);
     if (p.guard) return true;

@@ -46,19 +46,20 @@ def _hits(ev):
     return apo.DeviceHits.from_events(ev)
 
 
-@pytest.mark.parametrize("prec", [apo.F64, apo.F32])
+@pytest.mark.parametrize("prec", [apo.F64, apo.F32, apo.F64_FILTERED])
 def test_coarse_votes_bit_exact(wires, grid1, ev1, prec):
     geom = apo.Geometry(grid1, wires)
     sub = ev1.subset(range(3))
     got = apo.vote(geom, _hits(sub), precision=prec).cpu().numpy()
     tab = O.Tables(grid1, wires)
+    oprec = 1 if prec == apo.F32 else 0
     for e in range(sub.n_events):
         a, b = sub.offsets[e], sub.offsets[e + 1]
-        ref = O.vote_coarse(tab, sub.wire_id[a:b], sub.drift[a:b], prec)
+        ref = O.vote_coarse(tab, sub.wire_id[a:b], sub.drift[a:b], oprec)
         np.testing.assert_array_equal(got[e], ref)
 
 
-@pytest.mark.parametrize("prec", [apo.F64, apo.F32])
+@pytest.mark.parametrize("prec", [apo.F64, apo.F32, apo.F64_FILTERED])
 def test_cell_votes_every_level_bit_exact(wires, grid2, ev2, prec):
     """Random cells and cells around the true helix at every level 0..6."""
     geom = apo.Geometry(grid2, wires)
@@ -80,7 +81,8 @@ def test_cell_votes_every_level_bit_exact(wires, grid2, ev2, prec):
         got = apo.vote(geom, _hits(sub), keys=kt, level=L, precision=prec).cpu().numpy()
         for e in range(sub.n_events):
             a, b = sub.offsets[e], sub.offsets[e + 1]
-            ref = O.vote_cells(tab, sub.wire_id[a:b], sub.drift[a:b], L, keys[e], prec)
+            ref = O.vote_cells(tab, sub.wire_id[a:b], sub.drift[a:b], L, keys[e],
+                               1 if prec == apo.F32 else 0)
             np.testing.assert_array_equal(got[e], ref, err_msg=f"level {L} event {e}")
 
 
@@ -148,12 +150,16 @@ def test_full_size_batch_sampled_events(wires, grid2, ev2):
 
 
 def test_fp32_votes_contain_fp64_votes(wires, grid2, ev2):
+    """Full-grid votes of 8 config-2 events: FP32 >= FP64 cell by cell, and the filtered
+    and unfiltered FP64 kernels agree exactly."""
     geom = apo.Geometry(grid2, wires)
     sub = ev2.subset(range(8))
     h = _hits(sub)
     v64 = apo.vote(geom, h, precision=apo.F64)
+    v64u = apo.vote(geom, h, precision=apo.F64_FILTERED)
     v32 = apo.vote(geom, h, precision=apo.F32)
     assert bool(torch.all(v32 >= v64))
+    assert bool(torch.equal(v64, v64u))
 
 
 def test_edge_cases(wires, grid1):
