@@ -42,6 +42,13 @@ OPS_FULL = OPS_CELL + OPS_PREFIX + OPS_LPART + OPS_SIGNS
 OPS_TAIL = OPS_LPART + OPS_SIGNS
 
 
+# DRAM bytes (read + write) of one k_vote_coarse<FP64> launch per event, from the ncu
+# capture summarised in profiles/k_vote_coarse_f64_64events.md (64 events: 4.81 MB read +
+# 214.43 MB written), scaled by events to the benchmark's launch.  Must be re-captured (or
+# set to None) whenever that kernel changes.
+COARSE_F64_DRAM_BYTES_PER_EVENT = (4.809472e6 + 214.434816e6) / 64
+
+
 def coarse_kernel_ops(n_parent: int, n_prefix: int, n_tail: int) -> int:
     """Algorithmic directed FP operations of the coarse vote kernel from its work counters:
     parent-cell tests are full evaluations, each (cell, hit) prefix and each tan(lambda)
@@ -278,8 +285,13 @@ def run_apo(args) -> None:
     k_ms = statistics.mean(kms)
     peak = apo.pipe_peak(apo.F64)
     achieved = ops_launch / (k_ms * 1e-3)
+    ev_per_launch = ev.n_events / max(n_launch, 1)
+    traffic = (None if COARSE_F64_DRAM_BYTES_PER_EVENT is None
+               else COARSE_F64_DRAM_BYTES_PER_EVENT * ev_per_launch)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read+write of a 64-event launch, scaled by "
+                                  "events to this launch",
                 "kernel": "k_vote_coarse<double>",
                 "peak_source": "measured: libapo directed-rounding FP64 add/mul microbenchmark "
                                "(apo_diag_pipe_peak) on this GPU, this run",
