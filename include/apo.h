@@ -174,6 +174,24 @@ int apo_solve_batch_host(const apo_geometry *geom, int32_t n_events, const int32
                          apo_track *tracks_out, int32_t *n_tracks_out, void *workspace,
                          size_t workspace_bytes, void *stream);
 
+/* Full level-0 voting (as apo_vote with cell_keys = NULL) that allocates nothing and takes
+ * no workspace.  The paper has no counterpart: this is a library service.  It is for
+ * callers that may not allocate device memory while they vote, e.g. a process whose
+ * framework allocator owns the whole device budget, or a latency-bound loop in which
+ * cudaMalloc / cudaFree, which can synchronise the device, are not allowed after start-up.
+ * They still pass their inputs (hits, device) and the output votes_out (device int32,
+ * n_events x apo_coarse_cells).  The scratch (staged hits, hit counts, status, vote
+ * histograms: about 2.7 MB) is one fixed array compiled into libapo.so, held on every
+ * device that loads the library until the process exits; hence at most
+ * APO_NOALLOC_MAX_EVENTS events per call (more: APO_EINVAL, see apo_last_error()).
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress)
+ * and caches it; make that first call before any stream capture.  Every call reuses the
+ * same array and clears what must start at zero; calls whose work overlaps on the GPU
+ * (other streams, other threads) race on it and must be serialised by the caller. */
+#define APO_NOALLOC_MAX_EVENTS 64
+int apo_vote_coarse_noalloc(const apo_geometry *geom, const apo_hits *hits, int32_t precision,
+                            int32_t *votes_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -115,6 +115,14 @@ int check_ws(const apo_geometry *g, int n_events, void *ws, size_t bytes, Layout
 
 }  // namespace
 
+namespace apo {
+const DevGeom *geometry_device_tables(const apo_geometry *g, int *device) {
+    if (device) *device = g ? g->device : -1;
+    return g ? &g->dg : nullptr;
+}
+void set_last_error(const char *msg) { std::snprintf(g_err, sizeof(g_err), "%s", msg); }
+}  // namespace apo
+
 extern "C" {
 
 const char *apo_last_error(void) { return g_err; }

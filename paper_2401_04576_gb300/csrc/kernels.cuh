@@ -110,6 +110,11 @@ void launch_estimate_tracks(const DevGeom &g, int n_ev, const uint64_t *keys, co
                             int32_t *n_tracks, cudaStream_t s);
 void launch_series_consts(SeriesConsts *dev_out, cudaStream_t s);
 double pipe_peak(int precision, int op);   // diag.cu: directed operations per second
+
+// apo_abi.cu: the device tables and device ordinal of a geometry handle, and the message
+// returned by apo_last_error() on this thread.
+const DevGeom *geometry_device_tables(const apo_geometry *g, int *device);
+void set_last_error(const char *msg);
 void launch_hist(int n_ev, const int32_t *votes, long long n, uint32_t *hist, cudaStream_t s);
 void launch_children(const uint64_t *keys, long long n, uint64_t *out, cudaStream_t s);
 
