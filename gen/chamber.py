@@ -145,21 +145,30 @@ def simulate_track(tr: Track, w: Wires, rng: np.random.Generator | None,
     ns = 301
     s_grid = np.linspace(0.0, s_max, ns)
     P, _, _ = _helix(tr, s_grid)
-    # squared distance of every sample to every wire line
-    W0 = np.stack([w.x0, w.y0, np.zeros(w.n)], axis=-1)
-    D = np.stack([w.sphi_t, -w.cphi_t, np.ones(w.n)], axis=-1)
-    D2 = 1.0 + w.t2
+    # A wire can only be hit if its waist point lies within half a cell plus its largest
+    # transverse stereo shift (|z| <= z_half_len) of the helix's circle: the 3-D distance
+    # is at least the transverse one.  The rest need no distance computation.
+    R = 1.0 / tr.omega
+    xc, yc = -(R + tr.d0) * np.sin(tr.phi0), (R + tr.d0) * np.cos(tr.phi0)
+    d_circ = np.abs(np.hypot(w.x0 - xc, w.y0 - yc) - abs(R))
+    near = np.nonzero(d_circ <= w.half_cell + w.z_half_len * np.abs(w.tan_tau) + 1e-3)[0]
+    # squared distance of every sample to every remaining wire line
+    W0 = np.stack([w.x0[near], w.y0[near], np.zeros(near.size)], axis=-1)
+    D = np.stack([w.sphi_t[near], -w.cphi_t[near], np.ones(near.size)], axis=-1)
+    D2 = 1.0 + w.t2[near]
     v = P[None, :, :] - W0[:, None, :]
     vd = np.einsum('wsk,wk->ws', v, D)
     dist2 = np.einsum('wsk,wsk->ws', v, v) - vd * vd / D2[:, None]
     kmin = np.argmin(dist2, axis=1)
-    dmin = np.sqrt(np.maximum(dist2[np.arange(w.n), kmin], 0.0))
+    dmin = np.sqrt(np.maximum(dist2[np.arange(near.size), kmin], 0.0))
     step = s_grid[1] - s_grid[0]
-    cand = np.nonzero(dmin < w.half_cell + step)[0]
+    sel = np.nonzero(dmin < w.half_cell[near] + step)[0]
+    cand = near[sel]
+    kmin = kmin[sel]
     hits: list[Hit] = []
     if cand.size == 0:
         return hits
-    k = kmin[cand]
+    k = kmin
     lo = s_grid[np.maximum(k - 1, 0)]
     hi = s_grid[np.minimum(k + 1, ns - 1)]
     W0c, Dc = _wire_dirs(w, cand)
@@ -177,7 +186,7 @@ def simulate_track(tr: Track, w: Wires, rng: np.random.Generator | None,
     c_ = b_ - g * (b_ - a_)
     d_ = a_ + g * (b_ - a_)
     fc, fd = f(c_), f(d_)
-    for _ in range(60):
+    for _ in range(24):
         left = fc < fd
         b_ = np.where(left, d_, b_)
         a_ = np.where(left, a_, c_)

@@ -108,14 +108,14 @@ typedef struct {
  * best topk final cells). */
 typedef struct {
     int32_t precision[APO_MAX_LEVELS + 1];
-    int32_t max_tracks;      /* 1 = single track per event */
-    int32_t min_votes;       /* multi-track: stop when the best track has fewer votes */
-    double mask_sigma;       /* multi-track: drift resolution used to mask found hits */
+    int32_t max_tracks;      /* tracks per event, 1 .. APO_MAX_TRACKS */
+    int32_t min_votes;       /* stop when the best final vote count is below this */
+    double mask_sigma;       /* drift resolution: found hits are masked with d +- 3 sigma */
     uint64_t *trace_keys;
     int32_t *trace_votes;
 } apo_solve_opts;
 
-/* Fills *opts with: all levels FP64, one track, min_votes 6, mask_sigma 150e-6, no trace. */
+/* Fills *opts with: all levels FP64, one track, min_votes 0, mask_sigma 150e-6, no trace. */
 void apo_solve_opts_default(apo_solve_opts *opts);
 
 /* Text of the last error on this thread ("" if none). */
@@ -155,11 +155,14 @@ int apo_refine(const apo_geometry *geom, const apo_hits *hits, const uint64_t *k
                void *workspace, size_t workspace_bytes, void *stream);
 
 /* Whole search for every event: level-0 voting, top-K, `levels` rounds of bisection,
- * voting and top-K, and the estimate of Section 3.3.  tracks_out: device,
- * n_events x opts->max_tracks records; n_tracks_out: device int32 per event (may be NULL).
- * Multi-track (max_tracks > 1): after each track, the hits that vote for its final
- * maximum-vote cells with the drift widened by +-3 mask_sigma are removed and the event is
- * searched again, until max_tracks or a best vote count below min_votes. */
+ * voting and top-K, and the estimate of Section 3.3, repeated per track: after each track,
+ * every remaining hit that votes (FP64) for one of its final maximum-vote cells with the
+ * drift widened to [d - 3 mask_sigma, d + 3 mask_sigma] is removed (the hit finding of
+ * Section 3.3 with a widened box) and the event is searched again.  An event stops at
+ * max_tracks tracks, when no hit is left, or when the best final vote count is below
+ * min_votes (that search gives no track).  tracks_out: device, n_events x
+ * opts->max_tracks records (unused records zeroed); n_tracks_out: device int32 per event
+ * (may be NULL).  No host synchronisation: the call only queues work on the stream. */
 int apo_solve_batch(const apo_geometry *geom, const apo_hits *hits, const apo_solve_opts *opts,
                     apo_track *tracks_out, int32_t *n_tracks_out, void *workspace,
                     size_t workspace_bytes, void *stream);

@@ -281,6 +281,72 @@ int or_solve_event(const or_grid *g, const or_wires *w, int32_t n_hits, const in
     return 0;
 }
 
+/* The vote of one (cell, hit) pair with the drift widened to the interval [d_lo, d_hi]
+ * (FP64): used to find the hits of a found track. */
+static int vote_pair_drift_iv(const double c[12], const double h[9], double d_lo, double d_hi) {
+    iv_d C[6], H[9];
+    for (int i = 0; i < 6; i++) C[i] = mk_d(c[2 * i], c[2 * i + 1]);
+    for (int i = 0; i < 8; i++) H[i] = mk_d(h[i], h[i]);
+    H[8] = mk_d(d_lo, d_hi);
+    return vote_program_d(C[0], C[1], C[2], C[3], C[4], C[5], H[0], H[1], H[2], H[3], H[4],
+                          H[5], H[6], H[7], H[8], NULL);
+}
+
+/* Multi-track extraction (the paper's hit finding of Section 3.3, applied to several
+ * tracks): search the event's active hits; if the best final vote count is below
+ * min_votes or no hit is active, stop; otherwise record the track and deactivate every
+ * active hit that votes (FP64) for at least one of the final maximum-vote cells with its
+ * drift widened to [max(d - 3 sigma, 0), d + 3 sigma]; repeat up to max_tracks times.
+ * 3 sigma is 3.0 * mask_sigma in round-to-nearest; the widened end points are rounded
+ * outward.  Outputs per track: p / werr (5 each), votes; *n_found; hit_track[i] = index
+ * of the track that masked hit i, or -1. */
+int or_solve_event_multi(const or_grid *g, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
+                         const double *drift, const int32_t *prec, int32_t max_tracks,
+                         int32_t min_votes, double mask_sigma, double *p, double *werr,
+                         int32_t *votes, int32_t *n_found, int32_t *hit_track) {
+    const double width = 3.0 * mask_sigma;
+    const int32_t K = g->topk;
+    int32_t *wa = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_hits > 0 ? n_hits : 1));
+    double *da = (double *)malloc(sizeof(double) * (size_t)(n_hits > 0 ? n_hits : 1));
+    int32_t *ia = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_hits > 0 ? n_hits : 1));
+    uint64_t *lk = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)K * 32);
+    int32_t *lv = (int32_t *)malloc(sizeof(int32_t) * (size_t)K * 32);
+    for (int32_t i = 0; i < n_hits; i++) hit_track[i] = -1;
+    *n_found = 0;
+    for (int32_t t = 0; t < max_tracks; t++) {
+        int32_t na = 0;
+        for (int32_t i = 0; i < n_hits; i++)
+            if (hit_track[i] < 0) { wa[na] = wire_id[i]; da[na] = drift[i]; ia[na] = i; na++; }
+        if (na == 0) break;
+        int32_t best = 0;
+        or_solve_event(g, w, na, wa, da, prec, p + 5 * t, werr + 5 * t, &best, NULL, NULL, lk, lv);
+        if (best < min_votes) break;
+        votes[t] = best;
+        *n_found = t + 1;
+        int old = fegetround();
+        fesetround(FE_DOWNWARD);
+        for (int64_t j = 0; j < (int64_t)K * 32; j++) {
+            if (lv[j] != best) continue;
+            int32_t idx[5];
+            double c[12], h[9];
+            key_to_idx(lk[j], idx);
+            cell_intervals(g, g->levels, idx, c);
+            for (int32_t q = 0; q < na; q++) {
+                int32_t i = ia[q];
+                if (hit_track[i] >= 0) continue;
+                hit_constants(w, wire_id[i], drift[i], h);
+                volatile double lo = drift[i] - width;              /* rounded down */
+                volatile double hi = -((-drift[i]) - width);        /* rounded up */
+                double dlo = lo > 0 ? lo : 0.0;
+                if (vote_pair_drift_iv(c, h, dlo, hi)) hit_track[i] = t;
+            }
+        }
+        fesetround(old);
+    }
+    free(wa); free(da); free(ia); free(lk); free(lv);
+    return 0;
+}
+
 int or_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -43,6 +43,9 @@ def lib():
         L.or_solve_event.argtypes = [C.POINTER(OrGrid), C.POINTER(OrWires), C.c_int32, ip, dp,
                                      ip, dp, dp, ip, up, ip, up, ip]
         L.or_solve_event.restype = C.c_int
+        L.or_solve_event_multi.argtypes = [C.POINTER(OrGrid), C.POINTER(OrWires), C.c_int32, ip, dp,
+                                           ip, C.c_int32, C.c_int32, C.c_double, dp, dp, ip, ip, ip]
+        L.or_solve_event_multi.restype = C.c_int
         L.or_atan_iv.argtypes = [C.c_double, C.c_double, C.c_int, dp]
         L.or_sincos_iv.argtypes = [C.c_double, C.c_double, C.c_int, dp]
         L.or_op_counts.argtypes = [dp, dp, C.c_int, C.POINTER(C.c_ulonglong)]
@@ -202,3 +205,29 @@ def solve_event(tab: Tables, wire_id, drift, prec_per_level=None):
                          _p(tv, C.c_int32), _p(lk, C.c_uint64), _p(lvv, C.c_int32))
     return dict(p=p, w=werr, votes=int(best[0]), trace_keys=tk.reshape(lv + 1, K),
                 trace_votes=tv.reshape(lv + 1, K), last_keys=lk, last_votes=lvv)
+
+
+def solve_event_multi(tab: Tables, wire_id, drift, max_tracks: int, min_votes: int,
+                      mask_sigma: float = 150e-6, prec_per_level=None):
+    """Multi-track extraction of one event (see or_solve_event_multi).  Returns dict with
+    per-track estimates / errors / votes, the number of tracks and, per hit, the index of
+    the track that masked it (-1: none)."""
+    g = tab.grid
+    prec = np.zeros(g.levels + 1, np.int32) if prec_per_level is None else \
+        np.ascontiguousarray(prec_per_level, np.int32)
+    wid = np.ascontiguousarray(wire_id, np.int32)
+    dr = np.ascontiguousarray(drift, np.float64)
+    n = wid.shape[0]
+    p = np.zeros(5 * max_tracks)
+    werr = np.zeros(5 * max_tracks)
+    votes = np.zeros(max_tracks, np.int32)
+    nf = np.zeros(1, np.int32)
+    ht = np.zeros(max(n, 1), np.int32)
+    lib().or_solve_event_multi(C.byref(tab.cg), C.byref(tab.cw), int(n), _p(wid, C.c_int32),
+                               _p(dr, C.c_double), _p(prec, C.c_int32), int(max_tracks),
+                               int(min_votes), float(mask_sigma), _p(p, C.c_double),
+                               _p(werr, C.c_double), _p(votes, C.c_int32), _p(nf, C.c_int32),
+                               _p(ht, C.c_int32))
+    k = int(nf[0])
+    return dict(n_tracks=k, p=p.reshape(max_tracks, 5)[:k], w=werr.reshape(max_tracks, 5)[:k],
+                votes=votes[:k], hit_track=ht[:n])

@@ -182,7 +182,7 @@ class DeviceHits:
         return h
 
 
-def solve_opts(precision=None, levels: int = 0, max_tracks: int = 1, min_votes: int = 6,
+def solve_opts(precision=None, levels: int = 0, max_tracks: int = 1, min_votes: int = 0,
                mask_sigma: float = 150e-6, trace_keys=None, trace_votes=None) -> ApoSolveOpts:
     o = ApoSolveOpts()
     lib().apo_solve_opts_default(C.byref(o))

@@ -55,7 +55,7 @@ namespace {
 
 // Workspace regions for a batch of n_events.
 struct Layout {
-    size_t status, n_hits, hd, hf, votes, hist, fk, fv, ck, cv, mask, end;
+    size_t status, n_hits, hd, hf, votes, hist, fk, fv, ck, cv, mask, done, ntr, end;
     int chunk;
 };
 
@@ -78,6 +78,8 @@ Layout layout(const apo_geometry *g, int n_events) {
     L.ck = o; o = align256(o + sizeof(uint64_t) * (size_t)n_events * K * 32);
     L.cv = o; o = align256(o + sizeof(int32_t) * (size_t)n_events * K * 32);
     L.mask = o; o = align256(o + sizeof(uint32_t) * (size_t)n_events * (kHitCap / 32));
+    L.done = o; o = align256(o + sizeof(int32_t) * (size_t)n_events);
+    L.ntr = o; o = align256(o + sizeof(int32_t) * (size_t)n_events);
     L.end = o;
     return L;
 }
@@ -132,7 +134,7 @@ void apo_solve_opts_default(apo_solve_opts *o) {
     std::memset(o, 0, sizeof(*o));
     for (int i = 0; i <= APO_MAX_LEVELS; i++) o->precision[i] = APO_F64;
     o->max_tracks = 1;
-    o->min_votes = 6;
+    o->min_votes = 0;
     o->mask_sigma = 150e-6;
 }
 
@@ -260,7 +262,8 @@ int apo_vote(const apo_geometry *g, const apo_hits *hits, const uint64_t *cell_k
     HitRecD *hd = at<HitRecD>(ws, L.hd);
     HitRecF *hf = at<HitRecF>(ws, L.hf);
     CU(cudaMemsetAsync(status, 0, 256, s));
-    launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, status, s);
+    launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh,
+                 at<uint32_t>(ws, L.mask), at<int32_t>(ws, L.done), status, s);
     if ((rc = check_launch("stage"))) return rc;
     if (!cell_keys) {
         uint32_t *hist = at<uint32_t>(ws, L.hist);
@@ -336,10 +339,13 @@ int apo_solve_batch(const apo_geometry *g, const apo_hits *hits, const apo_solve
     apo_solve_opts_default(&def);
     const apo_solve_opts *o = opts ? opts : &def;
     const int lv = g->dg.levels, K = g->dg.topk;
+    if (lv < 1) return fail(APO_EINVAL, "apo_solve_batch needs levels >= 1");
     for (int i = 0; i <= lv; i++)
         if (o->precision[i] != APO_F64 && o->precision[i] != APO_F32 && o->precision[i] != APO_F64_FILTERED)
             return fail(APO_EINVAL, "bad precision[%d]", i);
-    if (o->max_tracks != 1) return fail(APO_EINVAL, "max_tracks > 1 is not supported by this build");
+    if (o->max_tracks < 1 || o->max_tracks > APO_MAX_TRACKS)
+        return fail(APO_EINVAL, "max_tracks must be in [1, %d]", APO_MAX_TRACKS);
+    if (!(o->mask_sigma >= 0.0 && o->mask_sigma < 1.0)) return fail(APO_EINVAL, "mask_sigma out of range");
     if (!tracks_out && hits->n_events > 0) return fail(APO_EINVAL, "tracks_out is NULL");
     Layout L;
     if ((rc = check_ws(g, hits->n_events, ws, ws_bytes, L))) return rc;
@@ -356,16 +362,15 @@ int apo_solve_batch(const apo_geometry *g, const apo_hits *hits, const apo_solve
     int32_t *fv = at<int32_t>(ws, L.fv);
     uint64_t *ck = at<uint64_t>(ws, L.ck);
     int32_t *cv = at<int32_t>(ws, L.cv);
+    uint32_t *active = at<uint32_t>(ws, L.mask);
+    int32_t *done = at<int32_t>(ws, L.done);
+    int32_t *ntr = n_tracks_out ? n_tracks_out : at<int32_t>(ws, L.ntr);
+    const double width = 3.0 * o->mask_sigma;   // round-to-nearest, as the oracle
     CU(cudaMemsetAsync(status, 0, 256, s));
-    launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, status, s);
+    launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, active, done, status, s);
     if ((rc = check_launch("stage"))) return rc;
     for (int e0 = 0; e0 < ne; e0 += L.chunk) {
         const int n = ne - e0 < L.chunk ? ne - e0 : L.chunk;
-        CU(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)n * kHistBins, s));
-        launch_vote_coarse(g->dg, o->precision[0], e0, n, hd, hf, nh, votes, hist, status, s);
-        if ((rc = check_launch("vote_coarse"))) return rc;
-        launch_select_coarse(g->dg, e0, n, votes, hist, K, fk, fv, s);
-        if ((rc = check_launch("select_coarse"))) return rc;
         uint64_t *fke = fk + (size_t)e0 * K;
         int32_t *fve = fv + (size_t)e0 * K;
         uint64_t *cke = ck + (size_t)e0 * K * 32;
@@ -373,20 +378,28 @@ int apo_solve_batch(const apo_geometry *g, const apo_hits *hits, const apo_solve
         const HitRecD *hde = hd + (size_t)e0 * kHitCap;
         const HitRecF *hfe = hf + (size_t)e0 * kHitCap;
         const int32_t *nhe = nh + e0;
-        if ((rc = trace_copy(o, g, e0, n, 0, fke, fve, s))) return rc;
-        for (int lev = 1; lev <= lv; lev++) {
-            launch_vote_children(g->dg, o->precision[lev], n, hde, hfe, nhe, lev, fke, K, cke, cve, s);
-            if ((rc = check_launch("vote_children"))) return rc;
-            launch_topk(n, cke, cve, K * 32, K, fke, fve, s);
-            if ((rc = check_launch("topk"))) return rc;
-            if ((rc = trace_copy(o, g, e0, n, lev, fke, fve, s))) return rc;
-            if (lev == lv) {
-                launch_estimate_tracks(g->dg, n, cke, cve, K * 32, lev, nhe, tracks_out + (size_t)e0 * o->max_tracks,
-                                       o->max_tracks, n_tracks_out ? n_tracks_out + e0 : nullptr, s);
-                if ((rc = check_launch("estimate"))) return rc;
+        uint32_t *acte = active + (size_t)e0 * 8;
+        // one round per track: search the active hits, record, mask the track's hits
+        for (int round = 0; round < o->max_tracks; round++) {
+            CU(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)n * kHistBins, s));
+            launch_vote_coarse(g->dg, o->precision[0], e0, n, hd, hf, nh, votes, hist, status, s, nullptr,
+                               active);
+            if ((rc = check_launch("vote_coarse"))) return rc;
+            launch_select_coarse(g->dg, e0, n, votes, hist, K, fk, fv, s);
+            if ((rc = check_launch("select_coarse"))) return rc;
+            if (round == 0 && (rc = trace_copy(o, g, e0, n, 0, fke, fve, s))) return rc;
+            for (int lev = 1; lev <= lv; lev++) {
+                launch_vote_children(g->dg, o->precision[lev], n, hde, hfe, nhe, lev, fke, K, cke, cve, s, acte);
+                if ((rc = check_launch("vote_children"))) return rc;
+                launch_topk(n, cke, cve, K * 32, K, fke, fve, s);
+                if ((rc = check_launch("topk"))) return rc;
+                if (round == 0 && (rc = trace_copy(o, g, e0, n, lev, fke, fve, s))) return rc;
             }
+            launch_estimate_mask(g->dg, n, cke, cve, K * 32, lv, nhe, acte, done + e0, hde, round,
+                                 o->max_tracks, o->min_votes, width,
+                                 tracks_out + (size_t)e0 * o->max_tracks, ntr + e0, s);
+            if ((rc = check_launch("estimate_mask"))) return rc;
         }
-        if (lv == 0) return fail(APO_EINVAL, "levels = 0 is not supported by apo_solve_batch");
     }
     return APO_OK;
 }
@@ -411,7 +424,8 @@ int apo_diag_vote_coarse_counts(const apo_geometry *g, const apo_hits *hits, int
     HitRecF *hf = at<HitRecF>(ws, L.hf);
     uint32_t *hist = at<uint32_t>(ws, L.hist);
     CU(cudaMemsetAsync(status, 0, 256, s));
-    launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, status, s);
+    launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh,
+                 at<uint32_t>(ws, L.mask), at<int32_t>(ws, L.done), status, s);
     unsigned long long launches = 0;
     for (int e0 = 0; e0 < ne; e0 += L.chunk) {
         int n = ne - e0 < L.chunk ? ne - e0 : L.chunk;

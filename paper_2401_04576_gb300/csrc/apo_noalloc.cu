@@ -27,7 +27,9 @@ constexpr size_t kOffNHits = 256;
 constexpr size_t kOffHD = kOffNHits + al256(sizeof(int32_t) * kMaxEv);
 constexpr size_t kOffHF = kOffHD + al256(sizeof(HitRecD) * kMaxEv * kHitCap);
 constexpr size_t kOffHist = kOffHF + al256(sizeof(HitRecF) * kMaxEv * kHitCap);
-constexpr size_t kScratchBytes = kOffHist + al256(sizeof(uint32_t) * kMaxEv * kHistBins);
+constexpr size_t kOffActive = kOffHist + al256(sizeof(uint32_t) * kMaxEv * kHistBins);
+constexpr size_t kOffDone = kOffActive + al256(sizeof(uint32_t) * kMaxEv * 8);
+constexpr size_t kScratchBytes = kOffDone + al256(sizeof(int32_t) * kMaxEv);
 
 // The scratch itself: one copy per device that loads this library, kept until the process
 // exits.  In host code this name is only a stand-in for the symbol; the device address
@@ -94,11 +96,13 @@ extern "C" int apo_vote_coarse_noalloc(const apo_geometry *g, const apo_hits *hi
     HitRecD *hd = reinterpret_cast<HitRecD *>(b + kOffHD);
     HitRecF *hf = reinterpret_cast<HitRecF *>(b + kOffHF);
     uint32_t *hist = reinterpret_cast<uint32_t *>(b + kOffHist);
+    uint32_t *active = reinterpret_cast<uint32_t *>(b + kOffActive);
+    int32_t *done = reinterpret_cast<int32_t *>(b + kOffDone);
     // the array keeps the previous call's contents: clear what the kernels accumulate into
     cudaError_t e = cudaMemsetAsync(status, 0, 256, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)ne * kHistBins, s);
     if (e != cudaSuccess) return err(APO_ECUDA, cudaGetErrorString(e));
-    launch_stage(*dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, status, s);
+    launch_stage(*dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, active, done, status, s);
     launch_vote_coarse(*dg, precision, 0, ne, hd, hf, nh, votes_out, hist, status, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return err(APO_ECUDA, cudaGetErrorString(e));

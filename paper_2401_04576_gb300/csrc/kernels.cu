@@ -94,7 +94,7 @@ void launch_series_consts(SeriesConsts *dev_out, cudaStream_t s) {
 // ---------------------------------------------------------------------------------------
 __global__ void k_stage(DevGeom g, int n_events, const int32_t *offsets, const int32_t *wire_id,
                         const double *drift, HitRecD *hd, HitRecF *hf, int32_t *n_hits,
-                        unsigned *status) {
+                        uint32_t *active, int32_t *done, unsigned *status) {
     int e = blockIdx.x;
     if (e >= n_events) return;
     __shared__ int bad;
@@ -102,12 +102,13 @@ __global__ void k_stage(DevGeom g, int n_events, const int32_t *offsets, const i
     __syncthreads();
     int a = offsets[e], b = offsets[e + 1];
     int n = b - a;
-    if (n < 0 || a < 0) {
-        if (threadIdx.x == 0) { n_hits[e] = APO_EINVAL; atomicOr(status, ST_BADOFFS); }
-        return;
-    }
-    if (n > kHitCap) {
-        if (threadIdx.x == 0) { n_hits[e] = APO_EINVAL; atomicOr(status, ST_TOOMANY); }
+    if (n < 0 || a < 0 || n > kHitCap) {
+        if (threadIdx.x < 8) active[(long long)e * 8 + threadIdx.x] = 0u;
+        if (threadIdx.x == 0) {
+            n_hits[e] = APO_EINVAL;
+            done[e] = 0;
+            atomicOr(status, n > kHitCap ? ST_TOOMANY : ST_BADOFFS);
+        }
         return;
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -129,17 +130,24 @@ __global__ void k_stage(DevGeom g, int n_events, const int32_t *offsets, const i
         hf[(long long)e * kHitCap + i] = rf;
     }
     __syncthreads();
+    if (threadIdx.x < 8) {   // every valid hit starts active
+        int lo = 32 * threadIdx.x;
+        uint32_t m = bad ? 0u : (n >= lo + 32 ? 0xffffffffu : (n > lo ? (1u << (n - lo)) - 1u : 0u));
+        active[(long long)e * 8 + threadIdx.x] = m;
+    }
     if (threadIdx.x == 0) {
+        done[e] = 0;
         if (bad) { n_hits[e] = APO_EINVAL; atomicOr(status, ST_BADHIT); }
         else n_hits[e] = n;
     }
 }
 
 void launch_stage(const DevGeom &g, int n_events, const int32_t *offsets, const int32_t *wire_id,
-                  const double *drift, HitRecD *hd, HitRecF *hf, int32_t *n_hits, unsigned *status,
-                  cudaStream_t s) {
+                  const double *drift, HitRecD *hd, HitRecF *hf, int32_t *n_hits, uint32_t *active,
+                  int32_t *done, unsigned *status, cudaStream_t s) {
     if (n_events <= 0) return;
-    k_stage<<<n_events, 128, 0, s>>>(g, n_events, offsets, wire_id, drift, hd, hf, n_hits, status);
+    k_stage<<<n_events, 128, 0, s>>>(g, n_events, offsets, wire_id, drift, hd, hf, n_hits, active,
+                                      done, status);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -173,7 +181,8 @@ template <int MODE> struct CoarseSmem {
 template <int MODE>
 __global__ void __launch_bounds__(256)
 k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
-              int32_t *votes, uint32_t *hist, unsigned *status, unsigned long long *ctr) {
+              const uint32_t *active, int32_t *votes, uint32_t *hist, unsigned *status,
+              unsigned long long *ctr) {
     using S = CoarseSmem<MODE>;
     constexpr bool k64 = S::k64, k32 = S::k32;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -218,11 +227,24 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
         Cell<double> par{{D0.lo, D1.hi}, S0, C0, W, {Z0.lo, Z1.hi}, {L0.lo, L1.hi}};
         Cell<float> par32{to_prec<float>(par.D), to_prec<float>(S0), to_prec<float>(C0),
                           to_prec<float>(W), to_prec<float>(par.Z), to_prec<float>(par.L)};
-        for (int h = tid; h < nh; h += nthr) {
+        const uint32_t *act = active ? active + (long long)ev * 8 : nullptr;
+        auto parent_vote = [&](int h) -> bool {
+            if (h >= nh || (act && !((act[h >> 5] >> (h & 31)) & 1u))) return false;
             bool v = true;
             if (k32) { v = vote_pair<float>(par32, load_hit<float>(h32s + h * 80), k); n_par32++; }
             if (k64 && v) { v = vote_pair<double>(par, load_hit<double>(h64s + h * 80), k); n_par64++; }
-            if (v) atomicOr(&mask_s[h >> 5], 1u << (h & 31));
+            return v;
+        };
+        const int lane = tid & 31, warp = tid >> 5, nfull = nthr >> 5;
+        if (nfull > 0) {   // full warps take 32 hits each; the warp ballot is the mask word
+            if (warp < nfull)
+                for (int base = warp * 32; base < nh; base += nfull * 32) {
+                    unsigned m = __ballot_sync(0xffffffffu, parent_vote(base + lane));
+                    if (lane == 0) mask_s[base >> 5] = m;
+                }
+        } else {
+            for (int h = tid; h < nh; h += nthr)
+                if (parent_vote(h)) atomicOr(&mask_s[h >> 5], 1u << (h & 31));
         }
     }
     __syncthreads();
@@ -305,27 +327,39 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
     }
 }
 
+// Raises the dynamic shared-memory limit of a kernel once per process (the attribute is a
+// property of the function; setting it outside any stream capture keeps captures clean).
+template <typename K> static void smem_limit_once(K kernel, bool &flag) {
+    if (!flag) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        flag = true;
+    }
+}
+
 template <int MODE> static void launch_coarse_mode(const DevGeom &g, int ev0, int n_ev, const HitRecD *hd,
-                                                  const HitRecF *hf, const int32_t *n_hits, int32_t *votes,
+                                                  const HitRecF *hf, const int32_t *n_hits,
+                                                  const uint32_t *active, int32_t *votes,
                                                   uint32_t *hist, unsigned *status, cudaStream_t s,
                                                   unsigned long long *ctr) {
+    static bool attr = false;
+    smem_limit_once(k_vote_coarse<MODE>, attr);
     dim3 grid(g.bins[1] * g.bins[2], n_ev);
     int nthr = g.bins[0] * g.bins[3];
     size_t sm = CoarseSmem<MODE>::total(g.bins[4], nthr);
-    cudaFuncSetAttribute(k_vote_coarse<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_vote_coarse<MODE><<<grid, nthr, sm, s>>>(g, ev0, hd, hf, n_hits, votes, hist, status, ctr);
+    k_vote_coarse<MODE><<<grid, nthr, sm, s>>>(g, ev0, hd, hf, n_hits, active, votes, hist, status, ctr);
 }
 
 void launch_vote_coarse(const DevGeom &g, int prec, int ev0, int n_ev, const HitRecD *hd,
                         const HitRecF *hf, const int32_t *n_hits, int32_t *votes, uint32_t *hist,
-                        unsigned *status, cudaStream_t s, unsigned long long *ctr) {
+                        unsigned *status, cudaStream_t s, unsigned long long *ctr,
+                        const uint32_t *active) {
     if (n_ev <= 0) return;
     if (prec == APO_F32)
-        launch_coarse_mode<kModeF32>(g, ev0, n_ev, hd, hf, n_hits, votes, hist, status, s, ctr);
+        launch_coarse_mode<kModeF32>(g, ev0, n_ev, hd, hf, n_hits, active, votes, hist, status, s, ctr);
     else if (prec == APO_F64_FILTERED)
-        launch_coarse_mode<kModeF64Filtered>(g, ev0, n_ev, hd, hf, n_hits, votes, hist, status, s, ctr);
+        launch_coarse_mode<kModeF64Filtered>(g, ev0, n_ev, hd, hf, n_hits, active, votes, hist, status, s, ctr);
     else
-        launch_coarse_mode<kModeF64>(g, ev0, n_ev, hd, hf, n_hits, votes, hist, status, s, ctr);
+        launch_coarse_mode<kModeF64>(g, ev0, n_ev, hd, hf, n_hits, active, votes, hist, status, s, ctr);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -335,9 +369,9 @@ void launch_vote_coarse(const DevGeom &g, int prec, int ev0, int n_ev, const Hit
 // ---------------------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(256)
-k_vote_cells(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits, int level,
-             const uint64_t *keys, const uint64_t *parents, long long n_per_ev, uint64_t *out_keys,
-             int32_t *out_votes, unsigned *status) {
+k_vote_cells(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
+             const uint32_t *active, int level, const uint64_t *keys, const uint64_t *parents,
+             long long n_per_ev, uint64_t *out_keys, int32_t *out_votes, unsigned *status) {
     constexpr bool k64 = MODE != kModeF32, k32 = MODE != kModeF64;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *h64s = smem;
@@ -380,8 +414,10 @@ k_vote_cells(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_h
     Cell<float> c32{to_prec<float>(c.D), to_prec<float>(c.S0), to_prec<float>(c.C0),
                     to_prec<float>(c.W), to_prec<float>(c.Z), to_prec<float>(c.L)};
     const SeriesConsts &k = g.k;
+    const uint32_t *act = active ? active + (long long)ev * 8 : nullptr;
     int v = 0;
     for (int h = 0; h < nh; h++) {
+        if (act && !((act[h >> 5] >> (h & 31)) & 1u)) continue;
         bool vt = true;
         if (k32) vt = vote_pair<float>(c32, load_hit<float>(h32s + h * 80), k);
         if (k64 && vt) vt = vote_pair<double>(c, load_hit<double>(h64s + h * 80), k);
@@ -393,45 +429,47 @@ k_vote_cells(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_h
 
 template <int MODE>
 static void launch_cells_mode(const DevGeom &g, int n_ev, const HitRecD *hd, const HitRecF *hf,
-                              const int32_t *n_hits, int level, const uint64_t *keys,
-                              const uint64_t *parents, long long n_per_ev, uint64_t *out_keys,
-                              int32_t *out_votes, unsigned *status, cudaStream_t s) {
+                              const int32_t *n_hits, const uint32_t *active, int level,
+                              const uint64_t *keys, const uint64_t *parents, long long n_per_ev,
+                              uint64_t *out_keys, int32_t *out_votes, unsigned *status, cudaStream_t s) {
+    static bool attr = false;
+    smem_limit_once(k_vote_cells<MODE>, attr);
     size_t sm = (MODE != kModeF32 ? kHitCap * 80 : 0) + (MODE != kModeF64 ? kHitCap * 80 : 0) + 16;
-    cudaFuncSetAttribute(k_vote_cells<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 grid((unsigned)((n_per_ev + 255) / 256), n_ev);
-    k_vote_cells<MODE><<<grid, 256, sm, s>>>(g, hd, hf, n_hits, level, keys, parents, n_per_ev,
+    k_vote_cells<MODE><<<grid, 256, sm, s>>>(g, hd, hf, n_hits, active, level, keys, parents, n_per_ev,
                                               out_keys, out_votes, status);
 }
 
 static void launch_cells(const DevGeom &g, int prec, int n_ev, const HitRecD *hd, const HitRecF *hf,
-                         const int32_t *n_hits, int level, const uint64_t *keys,
-                         const uint64_t *parents, long long n_per_ev, uint64_t *out_keys,
-                         int32_t *out_votes, unsigned *status, cudaStream_t s) {
+                         const int32_t *n_hits, const uint32_t *active, int level,
+                         const uint64_t *keys, const uint64_t *parents, long long n_per_ev,
+                         uint64_t *out_keys, int32_t *out_votes, unsigned *status, cudaStream_t s) {
     if (prec == APO_F32)
-        launch_cells_mode<kModeF32>(g, n_ev, hd, hf, n_hits, level, keys, parents, n_per_ev, out_keys,
-                                    out_votes, status, s);
+        launch_cells_mode<kModeF32>(g, n_ev, hd, hf, n_hits, active, level, keys, parents, n_per_ev,
+                                    out_keys, out_votes, status, s);
     else if (prec == APO_F64_FILTERED)
-        launch_cells_mode<kModeF64Filtered>(g, n_ev, hd, hf, n_hits, level, keys, parents, n_per_ev,
-                                            out_keys, out_votes, status, s);
+        launch_cells_mode<kModeF64Filtered>(g, n_ev, hd, hf, n_hits, active, level, keys, parents,
+                                            n_per_ev, out_keys, out_votes, status, s);
     else
-        launch_cells_mode<kModeF64>(g, n_ev, hd, hf, n_hits, level, keys, parents, n_per_ev, out_keys,
-                                    out_votes, status, s);
+        launch_cells_mode<kModeF64>(g, n_ev, hd, hf, n_hits, active, level, keys, parents, n_per_ev,
+                                    out_keys, out_votes, status, s);
 }
 
 void launch_vote_keys(const DevGeom &g, int prec, int n_ev, const HitRecD *hd, const HitRecF *hf,
                       const int32_t *n_hits, int level, const uint64_t *keys, long long n_per_ev,
                       int32_t *votes, cudaStream_t s) {
     if (n_ev <= 0 || n_per_ev <= 0) return;
-    launch_cells(g, prec, n_ev, hd, hf, n_hits, level, keys, nullptr, n_per_ev, nullptr, votes, nullptr, s);
+    launch_cells(g, prec, n_ev, hd, hf, n_hits, nullptr, level, keys, nullptr, n_per_ev, nullptr, votes,
+                 nullptr, s);
 }
 
 void launch_vote_children(const DevGeom &g, int prec, int n_ev, const HitRecD *hd,
                           const HitRecF *hf, const int32_t *n_hits, int child_level,
                           const uint64_t *parents, int n_par, uint64_t *child_keys,
-                          int32_t *child_votes, cudaStream_t s) {
+                          int32_t *child_votes, cudaStream_t s, const uint32_t *active) {
     if (n_ev <= 0 || n_par <= 0) return;
-    launch_cells(g, prec, n_ev, hd, hf, n_hits, child_level, nullptr, parents, (long long)n_par * 32,
-                 child_keys, child_votes, nullptr, s);
+    launch_cells(g, prec, n_ev, hd, hf, n_hits, active, child_level, nullptr, parents,
+                 (long long)n_par * 32, child_keys, child_votes, nullptr, s);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -559,53 +597,117 @@ void launch_topk(int n_ev, const uint64_t *keys, const int32_t *votes, int n_in,
 }
 
 // ---------------------------------------------------------------------------------------
-// Final estimate (Section 3.3): over the maximum-vote cells in ascending key order, the
-// mean of the cell centres and the half-extent of their union per axis, in
-// round-to-nearest; written into apo_track records (stride tracks per event).
+// Final estimate (Section 3.3) and, for multi-track extraction, hit masking.  Per event
+// (one block) in round `round`: stop (done) if no hit is active or the best final vote
+// count is below min_votes; otherwise write track `round`: over the maximum-vote cells in
+// ascending key order, the mean of the cell centres and the half-extent of their union per
+// axis, in round-to-nearest.  Then deactivate every active hit that votes (FP64) for at
+// least one maximum-vote cell with its drift widened to [max(rd(d - width), 0),
+// ru(d + width)] (the paper's hit finding with a widened box, Section 3.3).
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024)
-k_estimate(DevGeom g, const uint64_t *keys, const int32_t *votes, int n_in, int level,
-           const int32_t *n_hits, apo_track *out, int stride, int32_t *n_tracks) {
+__global__ void __launch_bounds__(256)
+k_estimate_mask(DevGeom g, const uint64_t *keys, const int32_t *votes, int n_in, int level,
+                const int32_t *n_hits, uint32_t *active, int32_t *done, const HitRecD *hd,
+                int round, int max_tracks, int min_votes, double width, apo_track *out,
+                int32_t *n_tracks) {
     __shared__ uint64_t s[kSortMax];
-    const int e = blockIdx.x;
-    int np2 = pow2_ge(n_in);
-    load_sorted(s, keys + (long long)e * n_in, votes + (long long)e * n_in, n_in, np2);
-    if (threadIdx.x != 0) return;
-    apo_track &t = out[(long long)e * stride];
-    int nh = n_hits[e];
+    __shared__ uint32_t act0[8], act1[8];
+    __shared__ int s_vmax, s_m;
+    const int e = blockIdx.x, tid = threadIdx.x;
+    if (done[e]) return;
+    const int nh = n_hits[e];
+    apo_track *te = out + (long long)e * max_tracks;
+    if (round == 0) {
+        if (tid < max_tracks) {
+            for (int a = 0; a < 5; a++) { te[tid].p[a] = 0.0; te[tid].w[a] = 0.0; }
+            te[tid].votes = (tid == 0 && nh < 0) ? nh : 0;
+            te[tid].n_hits = nh < 0 ? 0 : nh;
+        }
+        if (tid == 0) n_tracks[e] = 0;
+    }
     if (nh < 0) {
-        for (int a = 0; a < 5; a++) { t.p[a] = 0.0; t.w[a] = 0.0; }
-        t.votes = nh;
-        t.n_hits = 0;
-        if (n_tracks) n_tracks[e] = 0;
+        __syncthreads();
+        if (tid == 0) done[e] = 1;
         return;
     }
-    int vmax = 1023 - (int)(s[0] >> 50);
-    int m = 0;
-    while (m < n_in && 1023 - (int)(s[m] >> 50) == vmax) m++;
-    for (int a = 0; a < 5; a++) {
-        double sum = 0.0, lo_min = 1e300, hi_max = -1e300;
-        for (int j = 0; j < m; j++) {
-            int idx[5];
-            unpack_key(s[j] & kKeyMask, idx);
-            IV<double> ed = edge(g, a, level, idx[a]);
-            sum = __dadd_rn(sum, __dmul_rn(__dadd_rn(ed.lo, ed.hi), 0.5));
-            lo_min = ed.lo < lo_min ? ed.lo : lo_min;
-            hi_max = ed.hi > hi_max ? ed.hi : hi_max;
-        }
-        t.p[a] = __ddiv_rn(sum, (double)m);
-        t.w[a] = __dmul_rn(__dsub_rn(hi_max, lo_min), 0.5);
+    if (tid < 8) act0[tid] = act1[tid] = active[(long long)e * 8 + tid];
+    __syncthreads();
+    int na = 0;
+    for (int i = 0; i < 8; i++) na += __popc(act0[i]);
+    if (na == 0) {
+        if (tid == 0) done[e] = 1;
+        return;
     }
-    t.votes = vmax;
-    t.n_hits = nh;
-    if (n_tracks) n_tracks[e] = 1;
+    int np2 = pow2_ge(n_in);
+    load_sorted(s, keys + (long long)e * n_in, votes + (long long)e * n_in, n_in, np2);
+    if (tid == 0) {
+        int vmax = 1023 - (int)(s[0] >> 50);
+        int m = 0;
+        while (m < n_in && 1023 - (int)(s[m] >> 50) == vmax) m++;
+        s_vmax = vmax;
+        s_m = m;
+    }
+    __syncthreads();
+    const int vmax = s_vmax, m = s_m;
+    if (vmax < min_votes) {
+        if (tid == 0) done[e] = 1;
+        return;
+    }
+    if (tid == 0) {
+        apo_track &t = te[round];
+        for (int a = 0; a < 5; a++) {
+            double sum = 0.0, lo_min = 1e300, hi_max = -1e300;
+            for (int j = 0; j < m; j++) {
+                int idx[5];
+                unpack_key(s[j] & kKeyMask, idx);
+                IV<double> ed = edge(g, a, level, idx[a]);
+                sum = __dadd_rn(sum, __dmul_rn(__dadd_rn(ed.lo, ed.hi), 0.5));
+                lo_min = ed.lo < lo_min ? ed.lo : lo_min;
+                hi_max = ed.hi > hi_max ? ed.hi : hi_max;
+            }
+            t.p[a] = __ddiv_rn(sum, (double)m);
+            t.w[a] = __dmul_rn(__dsub_rn(hi_max, lo_min), 0.5);
+        }
+        t.votes = vmax;
+        t.n_hits = nh;
+        n_tracks[e] = round + 1;
+    }
+    if (round + 1 >= max_tracks) {
+        if (tid == 0) done[e] = 1;
+        return;
+    }
+    const SeriesConsts &k = g.k;
+    const long long pairs = (long long)m * nh;
+    for (long long q = tid; q < pairs; q += blockDim.x) {
+        const int j = (int)(q / nh), i = (int)(q % nh);
+        if (!((act0[i >> 5] >> (i & 31)) & 1u)) continue;
+        if (!((act1[i >> 5] >> (i & 31)) & 1u)) continue;   // already masked by another cell
+        int idx[5];
+        unpack_key(s[j] & kKeyMask, idx);
+        Cell<double> c{edge(g, 0, level, idx[0]), sin_phi0(g, level, idx[1]), cos_phi0(g, level, idx[1]),
+                       edge(g, 2, level, idx[2]), edge(g, 3, level, idx[3]), edge(g, 4, level, idx[4])};
+        Hit<double> h = load_hit<double>(hd + (long long)e * kHitCap + i);
+        const double d = h.d.lo;
+        const double dlo = __dsub_rd(d, width);
+        h.d = {gt0(dlo) ? dlo : 0.0, __dadd_ru(d, width)};
+        if (vote_pair<double>(c, h, k)) atomicAnd(&act1[i >> 5], ~(1u << (i & 31)));
+    }
+    __syncthreads();
+    if (tid < 8) active[(long long)e * 8 + tid] = act1[tid];
+    if (tid == 0) {
+        int left = 0;
+        for (int i = 0; i < 8; i++) left += __popc(act1[i]);
+        if (left == 0) done[e] = 1;
+    }
 }
 
-void launch_estimate_tracks(const DevGeom &g, int n_ev, const uint64_t *keys, const int32_t *votes,
-                            int n_in, int level, const int32_t *n_hits, apo_track *out, int stride,
-                            int32_t *n_tracks, cudaStream_t s) {
+void launch_estimate_mask(const DevGeom &g, int n_ev, const uint64_t *keys, const int32_t *votes,
+                          int n_in, int level, const int32_t *n_hits, uint32_t *active, int32_t *done,
+                          const HitRecD *hd, int round, int max_tracks, int min_votes, double width,
+                          apo_track *out, int32_t *n_tracks, cudaStream_t s) {
     if (n_ev <= 0) return;
-    k_estimate<<<n_ev, 1024, 0, s>>>(g, keys, votes, n_in, level, n_hits, out, stride, n_tracks);
+    k_estimate_mask<<<n_ev, 256, 0, s>>>(g, keys, votes, n_in, level, n_hits, active, done, hd, round,
+                                          max_tracks, min_votes, width, out, n_tracks);
 }
 
 }  // namespace apo

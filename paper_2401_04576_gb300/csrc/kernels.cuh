@@ -89,25 +89,28 @@ enum : unsigned { ST_TIMEOUT = 1u, ST_BADHIT = 2u, ST_TOOMANY = 4u, ST_BADOFFS =
 // ---- launch wrappers (kernels.cu) ----
 void launch_stage(const DevGeom &g, int n_events, const int32_t *offsets, const int32_t *wire_id,
                   const double *drift, HitRecD *hd, HitRecF *hf, int32_t *n_hits,
-                  unsigned *status, cudaStream_t s);
+                  uint32_t *active, int32_t *done, unsigned *status, cudaStream_t s);
+// active: per event 8 words of hit-activity bits (nullptr: every hit active)
 void launch_vote_coarse(const DevGeom &g, int prec, int ev0, int n_ev, const HitRecD *hd,
                         const HitRecF *hf, const int32_t *n_hits, int32_t *votes, uint32_t *hist,
-                        unsigned *status, cudaStream_t s, unsigned long long *ctr = nullptr);
+                        unsigned *status, cudaStream_t s, unsigned long long *ctr = nullptr,
+                        const uint32_t *active = nullptr);
 void launch_vote_keys(const DevGeom &g, int prec, int n_ev, const HitRecD *hd, const HitRecF *hf,
                       const int32_t *n_hits, int level, const uint64_t *keys, long long n_per_ev,
                       int32_t *votes, cudaStream_t s);
 void launch_vote_children(const DevGeom &g, int prec, int n_ev, const HitRecD *hd,
                           const HitRecF *hf, const int32_t *n_hits, int child_level,
                           const uint64_t *parents, int n_par, uint64_t *child_keys,
-                          int32_t *child_votes, cudaStream_t s);
+                          int32_t *child_votes, cudaStream_t s, const uint32_t *active = nullptr);
 void launch_select_coarse(const DevGeom &g, int ev0, int n_ev, const int32_t *votes,
                           const uint32_t *hist, int K, uint64_t *out_keys, int32_t *out_votes,
                           cudaStream_t s);
 void launch_topk(int n_ev, const uint64_t *keys, const int32_t *votes, int n_in, int K,
                  uint64_t *out_keys, int32_t *out_votes, cudaStream_t s);
-void launch_estimate_tracks(const DevGeom &g, int n_ev, const uint64_t *keys, const int32_t *votes,
-                            int n_in, int level, const int32_t *n_hits, apo_track *out, int stride,
-                            int32_t *n_tracks, cudaStream_t s);
+void launch_estimate_mask(const DevGeom &g, int n_ev, const uint64_t *keys, const int32_t *votes,
+                          int n_in, int level, const int32_t *n_hits, uint32_t *active, int32_t *done,
+                          const HitRecD *hd, int round, int max_tracks, int min_votes, double width,
+                          apo_track *out, int32_t *n_tracks, cudaStream_t s);
 void launch_series_consts(SeriesConsts *dev_out, cudaStream_t s);
 double pipe_peak(int precision, int op);   // diag.cu: directed operations per second
 

@@ -26,7 +26,7 @@ def test_library_exports_every_declared_symbol():
 def test_opts_default_and_errors_without_gpu():
     from paper_2401_04576_gb300 import apo
     o = apo.solve_opts()
-    assert o.max_tracks == 1 and o.min_votes == 6 and abs(o.mask_sigma - 150e-6) < 1e-18
+    assert o.max_tracks == 1 and o.min_votes == 0 and abs(o.mask_sigma - 150e-6) < 1e-18
     assert all(o.precision[i] == apo.F64 for i in range(apo.MAX_LEVELS + 1))
     L = apo.lib()
     assert L.apo_geometry_create(None, None, None) == apo.APO_EINVAL

@@ -193,7 +193,8 @@ def test_edge_cases(wires, grid1):
     nt = nt.cpu().numpy()
     for i in (2, 3, 4, 5):
         assert t[i]["votes"] == apo.APO_EINVAL and nt[i] == 0, i
-    for i in (0, 1, 6):
+    assert nt[0] == 0 and t[0]["votes"] == 0            # no hit: no track
+    for i in (1, 6):
         a, b = offs[i], offs[i + 1]
         r = O.solve_event(tab, ev.wire_id[a:b], ev.drift[a:b])
         assert t[i]["votes"] == r["votes"] and nt[i] == 1, i
@@ -225,3 +226,50 @@ def test_refine_matches_oracle(wires, grid1, ev1):
         assert sorted(zip(kk[e].view(np.uint64).tolist(), kv[e].tolist())) == \
             sorted(zip(rk.tolist(), rv.tolist()))
         np.testing.assert_array_equal(np.sort(ch[e].view(np.uint64)), np.sort(O.children(rk)))
+
+
+def _multi(geom, ev, grid, precision, max_tracks, min_votes):
+    o = apo.solve_opts(precision=precision, max_tracks=max_tracks, min_votes=min_votes)
+    tracks, nt = apo.solve_batch(geom, _hits(ev), o)
+    torch.cuda.synchronize()
+    return apo.tracks_to_numpy(tracks, ev.n_events, max_tracks), nt.cpu().numpy()
+
+
+def _compare_multi(tab, ev, e, t, nt, precision, max_tracks, min_votes):
+    a, b = ev.offsets[e], ev.offsets[e + 1]
+    r = O.solve_event_multi(tab, ev.wire_id[a:b], ev.drift[a:b], max_tracks, min_votes,
+                            prec_per_level=precision)
+    assert nt[e] == r["n_tracks"], (e, nt[e], r["n_tracks"])
+    for k in range(r["n_tracks"]):
+        assert t[e, k]["votes"] == r["votes"][k], (e, k)
+        assert np.array_equal(t[e, k]["p"], r["p"][k]) and np.array_equal(t[e, k]["w"], r["w"][k])
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_multi_track_small_grid_bit_exact(wires, mixed):
+    """Multi-track extraction with hit masking (1-5 helices + noise per event): number of
+    tracks, every track's estimate and votes against the oracle."""
+    g = G.make_grid([8] * 5, 3, 16)
+    geom = apo.Geometry(g, wires)
+    ev = chamber.multi_track_events(6, seed=41, w=wires)
+    precision = ([apo.F32] * 2 + [apo.F64] * 2) if mixed else [apo.F64] * 4
+    t, nt = _multi(geom, ev, g, precision, 5, 6)
+    tab = O.Tables(g, wires)
+    for e in range(ev.n_events):
+        _compare_multi(tab, ev, e, t, nt, precision, 5, 6)
+    assert nt.sum() > ev.n_events
+
+
+def test_multi_track_full_size_sampled(wires):
+    """4096 uneven events (1-5 tracks + 10-30 % noise, up to 200 hits), 10^5 coarse cells,
+    top-64, 6 levels, FP32 levels 0-4 and FP64 levels 5-6, at most 5 tracks: two sampled
+    events recomputed whole by the oracle."""
+    g = G.make_grid([10] * 5, 6, 64)
+    geom = apo.Geometry(g, wires)
+    ev = chamber.multi_track_events(4096, seed=4, w=wires)
+    precision = [apo.F32] * 5 + [apo.F64] * 2
+    t, nt = _multi(geom, ev, g, precision, 5, 6)
+    tab = O.Tables(g, wires)
+    for e in (7, 3000):
+        _compare_multi(tab, ev, e, t, nt, precision, 5, 6)
+    assert np.all((nt >= 0) & (nt <= 5))
