@@ -101,6 +101,17 @@ typedef struct {
     int32_t n_hits;
 } apo_track;
 
+/* Execution knobs of apo_solve_batch.  None of them changes any result (every setting
+ * evaluates the same interval program cell by cell); apo_autotune picks them by timing.
+ * Zero means the default. */
+typedef struct {
+    int32_t coarse_filter;   /* 1: on the level-0 grid, evaluate FP64 levels only where the
+                                FP32 program votes (as APO_F64_FILTERED) */
+    int32_t cells_filter;    /* 1: the same for the bisected cells of levels >= 1 */
+    int32_t cells_block;     /* threads per block of the cell-voting kernel: 128 or 256 */
+    int32_t chunk_events;    /* events per level-0 launch (at most the workspace's chunk) */
+} apo_tune;
+
 /* Options of apo_solve_batch.  precision[L] selects FP64 or FP32 intervals at level L
  * (L = 0 is the coarse grid); FP32 end points are rounded outward, so an FP32 vote set
  * contains the FP64 one cell by cell.  trace_keys / trace_votes (device, may be NULL):
@@ -113,6 +124,9 @@ typedef struct {
     double mask_sigma;       /* drift resolution: found hits are masked with d +- 3 sigma */
     uint64_t *trace_keys;
     int32_t *trace_votes;
+    apo_tune tune;
+    int32_t use_graph;       /* 1: record the whole search as a CUDA graph on the first call
+                                with these arguments, and replay it on later calls */
 } apo_solve_opts;
 
 /* Fills *opts with: all levels FP64, one track, min_votes 0, mask_sigma 150e-6, no trace. */
@@ -166,6 +180,14 @@ int apo_refine(const apo_geometry *geom, const apo_hits *hits, const uint64_t *k
 int apo_solve_batch(const apo_geometry *geom, const apo_hits *hits, const apo_solve_opts *opts,
                     apo_track *tracks_out, int32_t *n_tracks_out, void *workspace,
                     size_t workspace_bytes, void *stream);
+
+/* Times apo_solve_batch on `hits` (typically a sample of the batch to come) for every
+ * combination of the apo_tune knobs and writes the fastest to *best (its time to *best_ms,
+ * may be NULL).  opts: as for apo_solve_batch (its tune and use_graph are ignored).
+ * Workspace as for apo_solve_batch.  Synchronous. */
+int apo_autotune(const apo_geometry *geom, const apo_hits *hits, const apo_solve_opts *opts,
+                 void *workspace, size_t workspace_bytes, void *stream, apo_tune *best,
+                 float *best_ms);
 
 /* As apo_solve_batch with HOST inputs and outputs: copies offsets / wire_id / drift to
  * the workspace, runs, copies the tracks back and synchronises the stream.  The hits

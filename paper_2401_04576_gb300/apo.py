@@ -41,10 +41,19 @@ class ApoHits(C.Structure):
                 ("drift", C.c_void_p)]
 
 
+class ApoTune(C.Structure):
+    _fields_ = [("coarse_filter", C.c_int32), ("cells_filter", C.c_int32),
+                ("cells_block", C.c_int32), ("chunk_events", C.c_int32)]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
 class ApoSolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int32 * (MAX_LEVELS + 1)), ("max_tracks", C.c_int32),
                 ("min_votes", C.c_int32), ("mask_sigma", C.c_double),
-                ("trace_keys", C.c_void_p), ("trace_votes", C.c_void_p)]
+                ("trace_keys", C.c_void_p), ("trace_votes", C.c_void_p),
+                ("tune", ApoTune), ("use_graph", C.c_int32)]
 
 
 _lib = None
@@ -74,6 +83,8 @@ def lib():
         L.apo_host_extra_bytes.restype = sz
         L.apo_solve_batch_host.argtypes = [vp, i32, vp, vp, vp, C.POINTER(ApoSolveOpts), vp, vp,
                                            vp, sz, vp]
+        L.apo_autotune.argtypes = [vp, C.POINTER(ApoHits), C.POINTER(ApoSolveOpts), vp, sz, vp,
+                                   C.POINTER(ApoTune), C.POINTER(C.c_float)]
         L.apo_diag_vote_coarse_counts.argtypes = [vp, C.POINTER(ApoHits), i32, vp, vp, vp, sz, vp]
         L.apo_diag_coarse_launches.argtypes = [vp, i32]
         L.apo_diag_coarse_launches.restype = i32
@@ -183,9 +194,13 @@ class DeviceHits:
 
 
 def solve_opts(precision=None, levels: int = 0, max_tracks: int = 1, min_votes: int = 0,
-               mask_sigma: float = 150e-6, trace_keys=None, trace_votes=None) -> ApoSolveOpts:
+               mask_sigma: float = 150e-6, trace_keys=None, trace_votes=None, tune=None,
+               use_graph: bool = False) -> ApoSolveOpts:
     o = ApoSolveOpts()
     lib().apo_solve_opts_default(C.byref(o))
+    if tune is not None:
+        o.tune = tune
+    o.use_graph = 1 if use_graph else 0
     if precision is not None:
         for i, p in enumerate(precision):
             o.precision[i] = int(p)
@@ -244,6 +259,19 @@ def solve_batch(geom: Geometry, hits: DeviceHits, opts: ApoSolveOpts | None = No
     _check(lib().apo_solve_batch(geom.handle, C.byref(hc), C.byref(o), _ptr(tracks),
                                  _ptr(n_tracks), _ptr(ws), ws.numel(), _stream_ptr(stream)))
     return tracks, n_tracks
+
+
+def autotune(geom: Geometry, hits: DeviceHits, opts: ApoSolveOpts | None = None, workspace=None,
+             stream=None):
+    """apo_autotune: the fastest execution knobs for this batch (results never change)."""
+    o = opts if opts is not None else solve_opts()
+    ws = geom.workspace(hits.n_events) if workspace is None else workspace
+    best = ApoTune()
+    ms = C.c_float()
+    hc = hits.c()
+    _check(lib().apo_autotune(geom.handle, C.byref(hc), C.byref(o), _ptr(ws), ws.numel(),
+                              _stream_ptr(stream), C.byref(best), C.byref(ms)))
+    return best, float(ms.value)
 
 
 def tracks_to_numpy(tracks, n_events: int, max_tracks: int = 1) -> np.ndarray:

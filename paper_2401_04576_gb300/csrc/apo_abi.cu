@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "../../include/apo.h"
@@ -44,18 +45,28 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+// A recorded search: replayed when apo_solve_batch is called again with the same key.
+struct GraphEntry {
+    unsigned char key[256];
+    size_t key_len;
+    cudaGraphExec_t exec;
+};
+
 struct apo_geometry {
     DevGeom dg;
     int device;
     long long n_coarse;
     std::vector<void *> allocs;
+    std::mutex graph_mu;                 // guards the two members below
+    std::vector<GraphEntry> graphs;
+    cudaStream_t capture_stream = nullptr;
 };
 
 namespace {
 
 // Workspace regions for a batch of n_events.
 struct Layout {
-    size_t status, n_hits, hd, hf, votes, hist, fk, fv, ck, cv, mask, done, ntr, end;
+    size_t status, n_hits, hd, hf, votes, hist, fk, fv, ck, cv, mask, done, ntr, tune_tracks, end;
     int chunk;
 };
 
@@ -80,6 +91,7 @@ Layout layout(const apo_geometry *g, int n_events) {
     L.mask = o; o = align256(o + sizeof(uint32_t) * (size_t)n_events * (kHitCap / 32));
     L.done = o; o = align256(o + sizeof(int32_t) * (size_t)n_events);
     L.ntr = o; o = align256(o + sizeof(int32_t) * (size_t)n_events);
+    L.tune_tracks = o; o = align256(o + sizeof(apo_track) * (size_t)n_events * APO_MAX_TRACKS);
     L.end = o;
     return L;
 }
@@ -168,6 +180,7 @@ int apo_geometry_create(const apo_wires *w, const apo_grid *gr, apo_geometry **o
     }
     int dev = 0;
     CU(cudaGetDevice(&dev));
+    init_kernel_attributes();
     apo_geometry *g = new apo_geometry();
     g->device = dev;
     g->n_coarse = n0;
@@ -221,6 +234,8 @@ int apo_geometry_create(const apo_wires *w, const apo_grid *gr, apo_geometry **o
 
 void apo_geometry_destroy(apo_geometry *g) {
     if (!g) return;
+    for (GraphEntry &e : g->graphs) cudaGraphExecDestroy(e.exec);
+    if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
     for (void *p : g->allocs) cudaFree(p);
     delete g;
 }
@@ -331,14 +346,15 @@ static int trace_copy(const apo_solve_opts *o, const apo_geometry *g, int e0, in
     return APO_OK;
 }
 
-int apo_solve_batch(const apo_geometry *g, const apo_hits *hits, const apo_solve_opts *opts,
-                    apo_track *tracks_out, int32_t *n_tracks_out, void *ws, size_t ws_bytes, void *stream) {
+}  // extern "C"
+
+namespace {
+
+int validate_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_opts *o,
+                   const apo_track *tracks_out, void *ws, size_t ws_bytes, Layout &L) {
     int rc;
     if ((rc = check_geom(g)) || (rc = check_hits(hits))) return rc;
-    apo_solve_opts def;
-    apo_solve_opts_default(&def);
-    const apo_solve_opts *o = opts ? opts : &def;
-    const int lv = g->dg.levels, K = g->dg.topk;
+    const int lv = g->dg.levels;
     if (lv < 1) return fail(APO_EINVAL, "apo_solve_batch needs levels >= 1");
     for (int i = 0; i <= lv; i++)
         if (o->precision[i] != APO_F64 && o->precision[i] != APO_F32 && o->precision[i] != APO_F64_FILTERED)
@@ -346,10 +362,19 @@ int apo_solve_batch(const apo_geometry *g, const apo_hits *hits, const apo_solve
     if (o->max_tracks < 1 || o->max_tracks > APO_MAX_TRACKS)
         return fail(APO_EINVAL, "max_tracks must be in [1, %d]", APO_MAX_TRACKS);
     if (!(o->mask_sigma >= 0.0 && o->mask_sigma < 1.0)) return fail(APO_EINVAL, "mask_sigma out of range");
+    if (o->tune.cells_block != 0 && o->tune.cells_block != 128 && o->tune.cells_block != 256)
+        return fail(APO_EINVAL, "tune.cells_block must be 0, 128 or 256");
+    if (o->tune.chunk_events < 0) return fail(APO_EINVAL, "tune.chunk_events < 0");
     if (!tracks_out && hits->n_events > 0) return fail(APO_EINVAL, "tracks_out is NULL");
-    Layout L;
-    if ((rc = check_ws(g, hits->n_events, ws, ws_bytes, L))) return rc;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return check_ws(g, hits->n_events, ws, ws_bytes, L);
+}
+
+// Queues the whole search on stream s (no host synchronisation, capturable).
+int enqueue_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_opts *o,
+                  apo_track *tracks_out, int32_t *n_tracks_out, void *ws, const Layout &L,
+                  cudaStream_t s) {
+    int rc;
+    const int lv = g->dg.levels, K = g->dg.topk;
     const int ne = hits->n_events;
     if (ne == 0) return APO_OK;
     unsigned *status = at<unsigned>(ws, L.status);
@@ -366,11 +391,18 @@ int apo_solve_batch(const apo_geometry *g, const apo_hits *hits, const apo_solve
     int32_t *done = at<int32_t>(ws, L.done);
     int32_t *ntr = n_tracks_out ? n_tracks_out : at<int32_t>(ws, L.ntr);
     const double width = 3.0 * o->mask_sigma;   // round-to-nearest, as the oracle
+    const int chunk = (o->tune.chunk_events > 0 && o->tune.chunk_events < L.chunk) ? o->tune.chunk_events : L.chunk;
+    const int block = o->tune.cells_block ? o->tune.cells_block : 256;
+    auto prec_at = [&](int lev) {
+        int p = o->precision[lev];
+        bool filt = lev == 0 ? o->tune.coarse_filter != 0 : o->tune.cells_filter != 0;
+        return (p == APO_F64 && filt) ? (int)APO_F64_FILTERED : p;
+    };
     CU(cudaMemsetAsync(status, 0, 256, s));
     launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, active, done, status, s);
     if ((rc = check_launch("stage"))) return rc;
-    for (int e0 = 0; e0 < ne; e0 += L.chunk) {
-        const int n = ne - e0 < L.chunk ? ne - e0 : L.chunk;
+    for (int e0 = 0; e0 < ne; e0 += chunk) {
+        const int n = ne - e0 < chunk ? ne - e0 : chunk;
         uint64_t *fke = fk + (size_t)e0 * K;
         int32_t *fve = fv + (size_t)e0 * K;
         uint64_t *cke = ck + (size_t)e0 * K * 32;
@@ -382,14 +414,14 @@ int apo_solve_batch(const apo_geometry *g, const apo_hits *hits, const apo_solve
         // one round per track: search the active hits, record, mask the track's hits
         for (int round = 0; round < o->max_tracks; round++) {
             CU(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)n * kHistBins, s));
-            launch_vote_coarse(g->dg, o->precision[0], e0, n, hd, hf, nh, votes, hist, status, s, nullptr,
-                               active);
+            launch_vote_coarse(g->dg, prec_at(0), e0, n, hd, hf, nh, votes, hist, status, s, nullptr, active);
             if ((rc = check_launch("vote_coarse"))) return rc;
             launch_select_coarse(g->dg, e0, n, votes, hist, K, fk, fv, s);
             if ((rc = check_launch("select_coarse"))) return rc;
             if (round == 0 && (rc = trace_copy(o, g, e0, n, 0, fke, fve, s))) return rc;
             for (int lev = 1; lev <= lv; lev++) {
-                launch_vote_children(g->dg, o->precision[lev], n, hde, hfe, nhe, lev, fke, K, cke, cve, s, acte);
+                launch_vote_children(g->dg, prec_at(lev), n, hde, hfe, nhe, lev, fke, K, cke, cve, s, acte,
+                                     block);
                 if ((rc = check_launch("vote_children"))) return rc;
                 launch_topk(n, cke, cve, K * 32, K, fke, fve, s);
                 if ((rc = check_launch("topk"))) return rc;
@@ -401,6 +433,117 @@ int apo_solve_batch(const apo_geometry *g, const apo_hits *hits, const apo_solve
             if ((rc = check_launch("estimate_mask"))) return rc;
         }
     }
+    return APO_OK;
+}
+
+// Key of a recorded search: every argument that the queued work depends on.
+size_t graph_key(unsigned char *k, const apo_hits *h, const apo_solve_opts *o, const apo_track *t,
+                 const int32_t *nt, const void *ws, size_t ws_bytes) {
+    size_t n = 0;
+    auto put = [&](const void *p, size_t b) { std::memcpy(k + n, p, b); n += b; };
+    put(h, sizeof(*h));
+    apo_solve_opts oc = *o;
+    oc.use_graph = 0;
+    put(&oc, sizeof(oc));
+    put(&t, sizeof(t));
+    put(&nt, sizeof(nt));
+    put(&ws, sizeof(ws));
+    put(&ws_bytes, sizeof(ws_bytes));
+    return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int apo_solve_batch(const apo_geometry *g, const apo_hits *hits, const apo_solve_opts *opts,
+                    apo_track *tracks_out, int32_t *n_tracks_out, void *ws, size_t ws_bytes, void *stream) {
+    apo_solve_opts def;
+    apo_solve_opts_default(&def);
+    const apo_solve_opts *o = opts ? opts : &def;
+    Layout L;
+    int rc = validate_solve(g, hits, o, tracks_out, ws, ws_bytes, L);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!o->use_graph || hits->n_events == 0)
+        return enqueue_solve(g, hits, o, tracks_out, n_tracks_out, ws, L, s);
+    static_assert(sizeof(apo_hits) + sizeof(apo_solve_opts) + 4 * sizeof(void *) <= sizeof(GraphEntry::key),
+                  "graph key size");
+    apo_geometry *gm = const_cast<apo_geometry *>(g);
+    GraphEntry ent;
+    ent.key_len = graph_key(ent.key, hits, o, tracks_out, n_tracks_out, ws, ws_bytes);
+    std::lock_guard<std::mutex> lk(gm->graph_mu);
+    for (GraphEntry &e : gm->graphs)
+        if (e.key_len == ent.key_len && std::memcmp(e.key, ent.key, ent.key_len) == 0) {
+            CU(cudaGraphLaunch(e.exec, s));
+            return APO_OK;
+        }
+    if (!gm->capture_stream) CU(cudaStreamCreateWithFlags(&gm->capture_stream, cudaStreamNonBlocking));
+    cudaStream_t cap = gm->capture_stream;
+    CU(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue_solve(g, hits, o, tracks_out, n_tracks_out, ws, L, cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+    if (rc != APO_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ce != cudaSuccess) return fail(APO_ECUDA, "stream capture: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&ent.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(APO_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    gm->graphs.push_back(ent);
+    CU(cudaGraphLaunch(ent.exec, s));
+    return APO_OK;
+}
+
+int apo_autotune(const apo_geometry *g, const apo_hits *hits, const apo_solve_opts *opts, void *ws,
+                 size_t ws_bytes, void *stream, apo_tune *best, float *best_ms) {
+    if (!best) return fail(APO_EINVAL, "best is NULL");
+    apo_solve_opts def;
+    apo_solve_opts_default(&def);
+    apo_solve_opts o = opts ? *opts : def;
+    o.use_graph = 0;
+    o.trace_keys = nullptr;
+    o.trace_votes = nullptr;
+    std::memset(&o.tune, 0, sizeof(o.tune));
+    Layout L;
+    apo_track *tt = nullptr;
+    int rc = check_ws(g, hits ? hits->n_events : 0, ws, ws_bytes, L);
+    if (rc) return rc;
+    tt = at<apo_track>(ws, L.tune_tracks);
+    if ((rc = validate_solve(g, hits, &o, tt, ws, ws_bytes, L))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    *best = o.tune;
+    float best_t = 1e30f;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    const int chunks[2] = {0, L.chunk > 4 ? L.chunk / 4 : 0};
+    for (int cf = 0; cf < 2; cf++)
+        for (int lf = 0; lf < 2; lf++)
+            for (int bs = 0; bs < 2; bs++)
+                for (int ch = 0; ch < 2; ch++) {
+                    if (ch == 1 && chunks[1] == 0) continue;
+                    apo_tune t{cf, lf, bs ? 128 : 256, chunks[ch]};
+                    o.tune = t;
+                    float ms = 0.f;
+                    for (int rep = 0; rep < 2 && rc == APO_OK; rep++) {   // warm-up, then timed
+                        if (rep == 1) cudaEventRecord(e0, s);
+                        rc = enqueue_solve(g, hits, &o, tt, nullptr, ws, L, s);
+                        if (rep == 1) cudaEventRecord(e1, s);
+                    }
+                    if (rc != APO_OK) break;
+                    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                        rc = fail(APO_ECUDA, "autotune timing failed");
+                        break;
+                    }
+                    if (ms < best_t) { best_t = ms; *best = t; }
+                }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != APO_OK) return rc;
+    if (best_ms) *best_ms = best_t;
     return APO_OK;
 }
 

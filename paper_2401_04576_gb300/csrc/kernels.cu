@@ -329,6 +329,8 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
 
 // Raises the dynamic shared-memory limit of a kernel once per process (the attribute is a
 // property of the function; setting it outside any stream capture keeps captures clean).
+static bool g_attr_coarse[3] = {false, false, false}, g_attr_cells[3] = {false, false, false};
+
 template <typename K> static void smem_limit_once(K kernel, bool &flag) {
     if (!flag) {
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
@@ -341,8 +343,7 @@ template <int MODE> static void launch_coarse_mode(const DevGeom &g, int ev0, in
                                                   const uint32_t *active, int32_t *votes,
                                                   uint32_t *hist, unsigned *status, cudaStream_t s,
                                                   unsigned long long *ctr) {
-    static bool attr = false;
-    smem_limit_once(k_vote_coarse<MODE>, attr);
+    smem_limit_once(k_vote_coarse<MODE>, g_attr_coarse[MODE]);
     dim3 grid(g.bins[1] * g.bins[2], n_ev);
     int nthr = g.bins[0] * g.bins[3];
     size_t sm = CoarseSmem<MODE>::total(g.bins[4], nthr);
@@ -431,28 +432,30 @@ template <int MODE>
 static void launch_cells_mode(const DevGeom &g, int n_ev, const HitRecD *hd, const HitRecF *hf,
                               const int32_t *n_hits, const uint32_t *active, int level,
                               const uint64_t *keys, const uint64_t *parents, long long n_per_ev,
-                              uint64_t *out_keys, int32_t *out_votes, unsigned *status, cudaStream_t s) {
-    static bool attr = false;
-    smem_limit_once(k_vote_cells<MODE>, attr);
+                              uint64_t *out_keys, int32_t *out_votes, unsigned *status, cudaStream_t s,
+                              int block) {
+    smem_limit_once(k_vote_cells<MODE>, g_attr_cells[MODE]);
     size_t sm = (MODE != kModeF32 ? kHitCap * 80 : 0) + (MODE != kModeF64 ? kHitCap * 80 : 0) + 16;
-    dim3 grid((unsigned)((n_per_ev + 255) / 256), n_ev);
-    k_vote_cells<MODE><<<grid, 256, sm, s>>>(g, hd, hf, n_hits, active, level, keys, parents, n_per_ev,
-                                              out_keys, out_votes, status);
+    dim3 grid((unsigned)((n_per_ev + block - 1) / block), n_ev);
+    k_vote_cells<MODE><<<grid, block, sm, s>>>(g, hd, hf, n_hits, active, level, keys, parents, n_per_ev,
+                                                out_keys, out_votes, status);
 }
 
 static void launch_cells(const DevGeom &g, int prec, int n_ev, const HitRecD *hd, const HitRecF *hf,
                          const int32_t *n_hits, const uint32_t *active, int level,
                          const uint64_t *keys, const uint64_t *parents, long long n_per_ev,
-                         uint64_t *out_keys, int32_t *out_votes, unsigned *status, cudaStream_t s) {
+                         uint64_t *out_keys, int32_t *out_votes, unsigned *status, cudaStream_t s,
+                         int block = 256) {
+    if (block != 128) block = 256;
     if (prec == APO_F32)
         launch_cells_mode<kModeF32>(g, n_ev, hd, hf, n_hits, active, level, keys, parents, n_per_ev,
-                                    out_keys, out_votes, status, s);
+                                    out_keys, out_votes, status, s, block);
     else if (prec == APO_F64_FILTERED)
         launch_cells_mode<kModeF64Filtered>(g, n_ev, hd, hf, n_hits, active, level, keys, parents,
-                                            n_per_ev, out_keys, out_votes, status, s);
+                                            n_per_ev, out_keys, out_votes, status, s, block);
     else
         launch_cells_mode<kModeF64>(g, n_ev, hd, hf, n_hits, active, level, keys, parents, n_per_ev,
-                                    out_keys, out_votes, status, s);
+                                    out_keys, out_votes, status, s, block);
 }
 
 void launch_vote_keys(const DevGeom &g, int prec, int n_ev, const HitRecD *hd, const HitRecF *hf,
@@ -466,10 +469,22 @@ void launch_vote_keys(const DevGeom &g, int prec, int n_ev, const HitRecD *hd, c
 void launch_vote_children(const DevGeom &g, int prec, int n_ev, const HitRecD *hd,
                           const HitRecF *hf, const int32_t *n_hits, int child_level,
                           const uint64_t *parents, int n_par, uint64_t *child_keys,
-                          int32_t *child_votes, cudaStream_t s, const uint32_t *active) {
+                          int32_t *child_votes, cudaStream_t s, const uint32_t *active, int block) {
     if (n_ev <= 0 || n_par <= 0) return;
     launch_cells(g, prec, n_ev, hd, hf, n_hits, active, child_level, nullptr, parents,
-                 (long long)n_par * 32, child_keys, child_votes, nullptr, s);
+                 (long long)n_par * 32, child_keys, child_votes, nullptr, s, block);
+}
+
+// Sets every vote kernel's dynamic shared-memory limit now, outside any stream capture.
+void init_kernel_attributes() {
+    const int lim = 96 * 1024;   // on the current device, every time a geometry is created there
+    cudaFuncSetAttribute(k_vote_coarse<kModeF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_coarse<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_coarse<kModeF64Filtered>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_cells<kModeF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_cells<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_cells<kModeF64Filtered>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    for (int i = 0; i < 3; i++) g_attr_coarse[i] = g_attr_cells[i] = true;
 }
 
 // ---------------------------------------------------------------------------------------

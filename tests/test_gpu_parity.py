@@ -273,3 +273,49 @@ def test_multi_track_full_size_sampled(wires):
     for e in (7, 3000):
         _compare_multi(tab, ev, e, t, nt, precision, 5, 6)
     assert np.all((nt >= 0) & (nt <= 5))
+
+
+def test_graph_replay_and_tuning_knobs_do_not_change_results(wires):
+    """Recording the search as a CUDA graph and replaying it, and every execution knob the
+    autotuner chooses from, give the same tracks bit for bit; a replay sees new contents
+    of the same input buffers."""
+    g = G.make_grid([8] * 5, 3, 16)
+    geom = apo.Geometry(g, wires)
+    ev = chamber.multi_track_events(40, seed=43, w=wires)
+    hits = _hits(ev)
+    ws = geom.workspace(ev.n_events)
+    prec = [apo.F32, apo.F32, apo.F64, apo.F64]
+
+    def run(**kw):
+        o = apo.solve_opts(precision=prec, max_tracks=4, min_votes=6, **kw)
+        tr, nt = apo.solve_batch(geom, hits, o, workspace=ws)
+        torch.cuda.synchronize()
+        return tr.cpu().numpy().copy(), nt.cpu().numpy().copy()
+
+    ref_t, ref_n = run()
+    assert ref_n.sum() > ev.n_events
+    for cf in (0, 1):
+        for lf in (0, 1):
+            for bs in (128, 256):
+                for ch in (0, 7):
+                    t, n = run(tune=apo.ApoTune(cf, lf, bs, ch))
+                    assert np.array_equal(t, ref_t) and np.array_equal(n, ref_n), (cf, lf, bs, ch)
+    o = apo.solve_opts(precision=prec, max_tracks=4, min_votes=6, use_graph=True)
+    tracks = torch.zeros(ev.n_events * 4 * apo.TRACK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    ntr = torch.zeros(ev.n_events, dtype=torch.int32, device="cuda")
+    for _ in range(2):                        # first call records, second replays
+        tracks.zero_()
+        apo.solve_batch(geom, hits, o, tracks=tracks, n_tracks=ntr, workspace=ws)
+        torch.cuda.synchronize()
+        assert np.array_equal(tracks.cpu().numpy(), ref_t) and np.array_equal(ntr.cpu().numpy(), ref_n)
+    # new drift values in the same buffer: the replay must follow them
+    hits.drift.mul_(0.5)
+    apo.solve_batch(geom, hits, o, tracks=tracks, n_tracks=ntr, workspace=ws)
+    t_g = tracks.cpu().numpy().copy()
+    apo.solve_batch(geom, hits, apo.solve_opts(precision=prec, max_tracks=4, min_votes=6),
+                    tracks=tracks, n_tracks=ntr, workspace=ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(t_g, tracks.cpu().numpy())
+    best, ms = apo.autotune(geom, hits, apo.solve_opts(precision=prec, max_tracks=4, min_votes=6),
+                            workspace=ws)
+    assert ms > 0 and best.cells_block in (128, 256)
