@@ -199,6 +199,62 @@ int apo_solve_batch_host(const apo_geometry *geom, int32_t n_events, const int32
                          apo_track *tracks_out, int32_t *n_tracks_out, void *workspace,
                          size_t workspace_bytes, void *stream);
 
+/* ---- Serving: continuous batching of events as they arrive ----
+ * A server owns a fixed set of batch slots on the geometry's device, each with its own
+ * stream, device workspace and pinned host staging, all allocated at creation and kept
+ * resident.  A background host thread moves submitted events into a free slot as soon as
+ * one frees up (up to batch_events per slot), queues the whole search for that batch, and
+ * collects finished batches; batches in different slots run concurrently on the device,
+ * and requests arriving meanwhile wait only for the next free slot.  Every event's search
+ * is independent of the others in its batch, so its result is the same alone and in any
+ * mix.  The paper has no counterpart (it processes one track at a time, Section 3.3). */
+typedef struct apo_server apo_server;
+
+typedef struct {
+    apo_solve_opts solve;        /* search options for every event (trace / graph ignored) */
+    int32_t batch_events;        /* events per batch slot (>= 1) */
+    int32_t max_slots;           /* upper bound on slots; the memory budget may allow fewer */
+    size_t device_bytes;         /* device memory budget for all slots (0: one slot) */
+    int32_t max_pending;         /* submitted events waiting for a slot before APO_EBUSY */
+    int32_t inject_error_after;  /* > 0: fail the n-th batch as a CUDA error would (tests) */
+} apo_serve_opts;
+
+/* Defaults: default search, 64 events per slot, 4 slots, budget 0, 4096 pending, no
+ * injection. */
+void apo_serve_opts_default(apo_serve_opts *opts);
+
+/* Device bytes of one batch slot for these options (workspace + staged inputs / outputs):
+ * the unit of the memory budget device_bytes.  0 on bad arguments. */
+size_t apo_serve_slot_bytes(const apo_geometry *geom, const apo_serve_opts *opts);
+
+/* Creates the slots (as many as max_slots and device_bytes allow, at least one) and starts
+ * the scheduling thread.  APO_ENOMEM if even one slot does not fit. */
+int apo_serve_create(const apo_geometry *geom, const apo_serve_opts *opts, apo_server **out);
+
+/* Number of batch slots the server created. */
+int32_t apo_serve_slots(const apo_server *srv);
+
+/* Submits one event (host arrays of n_hits wire ids and drifts, copied).  APO_EBUSY when
+ * max_pending events are already waiting (back-pressure: retry later), APO_EINVAL for
+ * n_hits outside [0, APO_HIT_CAP], APO_ECUDA once the server has failed. */
+int apo_serve_submit(apo_server *srv, const int32_t *wire_id, const double *drift, int32_t n_hits,
+                     uint64_t request_id);
+
+/* Moves up to max finished events into host arrays: tracks (max x solve.max_tracks
+ * records), n_tracks and request_id (max each); *n_done = how many.  Non-blocking.
+ * Returns APO_ECUDA (with the message in apo_last_error) if a batch failed. */
+int apo_serve_poll(apo_server *srv, apo_track *tracks, int32_t *n_tracks, uint64_t *request_id,
+                   int32_t max, int32_t *n_done);
+
+/* Waits until every submitted event has finished (or timeout_ms passes: APO_ETIMEOUT). */
+int apo_serve_drain(apo_server *srv, int32_t timeout_ms);
+
+/* Batches launched so far and the largest number of slots that were in flight at once. */
+int apo_serve_stats(const apo_server *srv, int32_t *batches, int32_t *max_busy_slots);
+
+/* Stops the scheduling thread after the batches in flight and frees the slots. */
+void apo_serve_destroy(apo_server *srv);
+
 /* Full level-0 voting (as apo_vote with cell_keys = NULL) that allocates nothing and takes
  * no workspace.  The paper has no counterpart: this is a library service.  It is for
  * callers that may not allocate device memory while they vote, e.g. a process whose

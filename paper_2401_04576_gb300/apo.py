@@ -56,6 +56,12 @@ class ApoSolveOpts(C.Structure):
                 ("tune", ApoTune), ("use_graph", C.c_int32)]
 
 
+class ApoServeOpts(C.Structure):
+    _fields_ = [("solve", ApoSolveOpts), ("batch_events", C.c_int32), ("max_slots", C.c_int32),
+                ("device_bytes", C.c_size_t), ("max_pending", C.c_int32),
+                ("inject_error_after", C.c_int32)]
+
+
 _lib = None
 
 
@@ -83,6 +89,17 @@ def lib():
         L.apo_host_extra_bytes.restype = sz
         L.apo_solve_batch_host.argtypes = [vp, i32, vp, vp, vp, C.POINTER(ApoSolveOpts), vp, vp,
                                            vp, sz, vp]
+        L.apo_serve_opts_default.argtypes = [C.POINTER(ApoServeOpts)]
+        L.apo_serve_create.argtypes = [vp, C.POINTER(ApoServeOpts), C.POINTER(vp)]
+        L.apo_serve_slot_bytes.argtypes = [vp, C.POINTER(ApoServeOpts)]
+        L.apo_serve_slot_bytes.restype = sz
+        L.apo_serve_slots.argtypes = [vp]
+        L.apo_serve_slots.restype = i32
+        L.apo_serve_submit.argtypes = [vp, vp, vp, i32, C.c_uint64]
+        L.apo_serve_poll.argtypes = [vp, vp, vp, vp, i32, C.POINTER(i32)]
+        L.apo_serve_drain.argtypes = [vp, i32]
+        L.apo_serve_stats.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+        L.apo_serve_destroy.argtypes = [vp]
         L.apo_autotune.argtypes = [vp, C.POINTER(ApoHits), C.POINTER(ApoSolveOpts), vp, sz, vp,
                                    C.POINTER(ApoTune), C.POINTER(C.c_float)]
         L.apo_diag_vote_coarse_counts.argtypes = [vp, C.POINTER(ApoHits), i32, vp, vp, vp, sz, vp]
@@ -329,3 +346,65 @@ def solve_launches(geom: Geometry, n_events: int) -> int:
     events the coarse vote, the coarse selection, per level the child vote and top-K,
     and the estimate."""
     return 1 + coarse_launches(geom, n_events) * (3 + 2 * geom.levels)
+
+
+class Server:
+    """apo_serve_*: continuous batching of events submitted one by one (host arrays)."""
+
+    def __init__(self, geom: Geometry, solve: ApoSolveOpts | None = None, batch_events: int = 64,
+                 max_slots: int = 4, device_bytes: int = 0, max_pending: int = 4096,
+                 inject_error_after: int = 0):
+        o = ApoServeOpts()
+        lib().apo_serve_opts_default(C.byref(o))
+        if solve is not None:
+            o.solve = solve
+        o.batch_events, o.max_slots, o.device_bytes = int(batch_events), int(max_slots), int(device_bytes)
+        o.max_pending, o.inject_error_after = int(max_pending), int(inject_error_after)
+        self.max_tracks = int(o.solve.max_tracks)
+        self.geom = geom
+        self.slot_bytes = int(lib().apo_serve_slot_bytes(geom.handle, C.byref(o)))
+        h = C.c_void_p()
+        _check(lib().apo_serve_create(geom.handle, C.byref(o), C.byref(h)))
+        self.handle = h
+        self.slots = int(lib().apo_serve_slots(h))
+
+    def submit(self, wire_id, drift, request_id: int) -> int:
+        """Returns the status (APO_OK, or APO_EBUSY when the queue is full)."""
+        w = np.ascontiguousarray(wire_id, np.int32)
+        d = np.ascontiguousarray(drift, np.float64)
+        rc = lib().apo_serve_submit(self.handle, C.c_void_p(w.ctypes.data), C.c_void_p(d.ctypes.data),
+                                    int(w.shape[0]), int(request_id))
+        if rc not in (APO_OK, APO_EBUSY):
+            _check(rc)
+        return rc
+
+    def poll(self, max_items: int = 1024):
+        """[(request_id, tracks[max_tracks] (TRACK_DTYPE), n_tracks)] of finished events."""
+        tr = np.zeros(max_items * self.max_tracks, TRACK_DTYPE)
+        nt = np.zeros(max_items, np.int32)
+        ids = np.zeros(max_items, np.uint64)
+        n = C.c_int32()
+        _check(lib().apo_serve_poll(self.handle, C.c_void_p(tr.ctypes.data), C.c_void_p(nt.ctypes.data),
+                                    C.c_void_p(ids.ctypes.data), int(max_items), C.byref(n)))
+        k = int(n.value)
+        tr = tr.reshape(max_items, self.max_tracks)
+        return [(int(ids[i]), tr[i].copy(), int(nt[i])) for i in range(k)]
+
+    def drain(self, timeout_ms: int = 60000) -> int:
+        return int(lib().apo_serve_drain(self.handle, int(timeout_ms)))
+
+    def stats(self):
+        b, m = C.c_int32(), C.c_int32()
+        _check(lib().apo_serve_stats(self.handle, C.byref(b), C.byref(m)))
+        return int(b.value), int(m.value)
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().apo_serve_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
