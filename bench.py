@@ -37,16 +37,16 @@ WORKLOAD = dict(name="1024 single-track events, 16^5 coarse cells, top-64, 6 bis
 # per (cell, hit) without tan(lambda), tan(lambda)-dependent part, both drift signs.
 # Counted by the oracle's instrumented interval operations (2 per rounding interval
 # operation); tests/test_bench_host.py checks these against it.
-OPS_PREFIX, OPS_LPART, OPS_SIGNS, OPS_CELL = 188, 147, 60, 2
+OPS_PREFIX, OPS_LPART, OPS_SIGNS, OPS_CELL = 176, 117, 60, 2
 OPS_FULL = OPS_CELL + OPS_PREFIX + OPS_LPART + OPS_SIGNS
 OPS_TAIL = OPS_LPART + OPS_SIGNS
 
 
 # DRAM bytes (read + write) of one k_vote_coarse<FP64> launch per event, from the ncu
-# capture summarised in profiles/k_vote_coarse_f64_64events.md (64 events: 4.81 MB read +
-# 214.43 MB written), scaled by events to the benchmark's launch.  Must be re-captured (or
+# capture summarised in profiles/k_vote_coarse_f64_64events.md (64 events: 4.44 MB read +
+# 214.26 MB written), scaled by events to the benchmark's launch.  Must be re-captured (or
 # set to None) whenever that kernel changes.
-COARSE_F64_DRAM_BYTES_PER_EVENT = (4.809472e6 + 214.434816e6) / 64
+COARSE_F64_DRAM_BYTES_PER_EVENT = (4.439296e6 + 214.2592e6) / 64
 
 
 def coarse_kernel_ops(n_parent: int, n_prefix: int, n_tail: int) -> int:
@@ -150,6 +150,66 @@ def make_inputs(seed_offset: int = 0):
     ev = chamber.single_track_events(WORKLOAD["n_events"], seed=WORKLOAD["seed"] + seed_offset,
                                      w=w)
     return w, g, ev
+
+
+def serve_sweep(geom, ev, rates, seconds: float, batch_events: int = 64, max_slots: int = 4,
+                max_pending: int = 4096) -> list:
+    """Poisson arrivals at each offered rate (events/s) into the continuous-batching server
+    (FP32 levels 0-4, FP64 levels 5-6), cycling through the batch's events; per rate:
+    sustained completions/s, p50 / p99 latency from arrival to completion, rejected
+    submissions (queue full)."""
+    import threading
+    from paper_2401_04576_gb300 import apo
+    lv = geom.levels
+    solve = apo.solve_opts(precision=[apo.F32] * 5 + [apo.F64] * (lv + 1 - 5))
+    evs = [(np.ascontiguousarray(ev.wire_id[ev.offsets[e]:ev.offsets[e + 1]], np.int32),
+            np.ascontiguousarray(ev.drift[ev.offsets[e]:ev.offsets[e + 1]], np.float64))
+           for e in range(ev.n_events)]
+    out = []
+    rng = np.random.default_rng(5)
+    for rate in rates:
+        srv = apo.Server(geom, solve, batch_events=batch_events, max_slots=max_slots,
+                         max_pending=max_pending)
+        n = max(64, int(rate * seconds))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
+        t_arr = {}
+        t_done = {}
+        stop = threading.Event()
+
+        def poller():
+            while not stop.is_set() or len(t_done) < len(t_arr):
+                for rid, _, _ in srv.poll(4096):
+                    t_done[rid] = time.perf_counter()
+                if stop.is_set() and srv.drain(0) == apo.APO_OK and len(t_done) >= len(t_arr):
+                    break
+                time.sleep(0.0002)
+
+        th = threading.Thread(target=poller)
+        th.start()
+        rejected = 0
+        t0 = time.perf_counter()
+        for i in range(n):
+            due = t0 + arrivals[i]
+            while time.perf_counter() < due:
+                pass
+            w, d = evs[i % len(evs)]
+            if srv.submit(w, d, i) == apo.APO_OK:
+                t_arr[i] = due
+            else:
+                rejected += 1
+        srv.drain(120000)
+        stop.set()
+        th.join(timeout=120)
+        lat = np.array([1e3 * (t_done[i] - t_arr[i]) for i in t_arr if i in t_done])
+        t_end = max(t_done.values()) if t_done else t0
+        batches, max_busy = srv.stats()
+        srv.close()
+        out.append({"offered_per_s": rate, "completed": int(lat.size), "rejected": rejected,
+                    "sustained_per_s": lat.size / max(t_end - t0, 1e-9),
+                    "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+                    "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+                    "batches": batches, "max_slots_in_flight": max_busy})
+    return out
 
 
 def cpu_baseline(w, g, ev, n_sample: int) -> dict:
@@ -256,9 +316,16 @@ def run_apo(args) -> None:
     pairs = pairs_decided(nh, geom.n_coarse, lv, g.topk)
     value = pairs * world / (t_step * 1e-3)
 
+    tracks64 = apo.tracks_to_numpy(tracks, ev.n_events).copy()
     # FP32-bulk precision form on the same events (FP32 coarse + levels 1-4, FP64 5-6)
     ms32 = timed(opts32, max(2, args.steps), 1)
     t32 = reduce_max(sum(ms32) / len(ms32), world)
+    tracks32 = apo.tracks_to_numpy(tracks, ev.n_events).copy()
+    # its two correctness figures: final helix within one final cell width of the FP64
+    # result (per axis), and FP32 coarse votes >= FP64 coarse votes cell by cell
+    fine_w = np.array([g.hi_edge[a][0] - g.lo_edge[a][0] for a in range(5)])
+    dp = np.abs(tracks32["p"][:, 0, :] - tracks64["p"][:, 0, :])
+    agree = float(np.mean(np.all(dp <= fine_w[None, :] * (1 + 1e-9), axis=1)))
 
     # roofline of the dominant kernel (coarse vote): counted work / live launch time
     votes = torch.empty((ev.n_events, geom.n_coarse), dtype=torch.int32, device="cuda")
@@ -271,6 +338,10 @@ def run_apo(args) -> None:
                                        apo._stream_ptr(stream))
     apo._check(rc)
     n_par, n_pre, n_tail, n_launch, p32, q32, t32c, _ = (int(x) for x in counts.cpu().tolist())
+    votes32 = apo.vote(geom, hits, precision=apo.F32, workspace=ws, stream=stream)
+    superset_violations = int((votes32 < votes).sum().item())
+    n_cells_cmp = int(votes.numel())
+    del votes32
     ops_launch = coarse_kernel_ops(n_par, n_pre, n_tail) / max(n_launch, 1)
     ops32_launch = coarse_kernel_ops(p32, q32, t32c) / max(n_launch, 1)
     kms = []
@@ -335,7 +406,10 @@ def run_apo(args) -> None:
         "events_per_s": ev.n_events * world / (t_step * 1e-3),
         "fp32_bulk": {"ms_per_step": t32, "value": pairs * world / (t32 * 1e-3),
                       "unit": "evals/s", "events_per_s": ev.n_events * world / (t32 * 1e-3),
-                      "precision": "FP32 levels 0-4, FP64 levels 5-6"},
+                      "precision": "FP32 levels 0-4, FP64 levels 5-6",
+                      "final_within_one_cell_of_fp64": agree,
+                      "coarse_superset_violations": superset_violations,
+                      "coarse_cells_compared": n_cells_cmp},
         "step_ms_p50": float(np.percentile(ms64, 50)), "step_ms_p99": float(np.percentile(ms64, 99)),
         "e2e": {"value": pairs * world / (t_e2e * 1e-3), "unit": "evals/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e},
@@ -343,6 +417,16 @@ def run_apo(args) -> None:
         "clocks": clocks,
         "roofline": roofline,
     }
+    if not args.no_serve:
+        sweep = serve_sweep(geom, ev, [1000, 2000, 5000, 10000, 20000, 50000], args.serve_seconds)
+        line["serving"] = {"workload": "Poisson arrivals of the batch's events into apo_serve "
+                                       "(64-event slots, 4 slots), FP32 levels 0-4 / FP64 5-6",
+                           "loads": sweep}
+        below = [x for x in sweep if x["rejected"] == 0 and x["p50_ms"] is not None]
+        if below:
+            line["p50_ms"] = below[-1]["p50_ms"]
+            line["p99_ms"] = below[-1]["p99_ms"]
+            line["p50_p99_at_offered_per_s"] = below[-1]["offered_per_s"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, g, ev, args.cpu_sample)
     if rank == 0:
@@ -384,6 +468,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="apo", choices=["apo", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--case", default=None,
                     choices=["coarse-f64", "coarse-f32", "solve-f64", "solve-f32"],
                     help="run one small profiling case instead of the benchmark")

@@ -70,6 +70,7 @@ typedef struct {
  * No omega cell may contain 0.  sincos: host array of rows (sin lo, sin hi, cos lo,
  * cos hi), outward enclosures of sin/cos over each phi0 cell, level by level (level L
  * starts at row sum_{l<L} bins[1] << l).  All copied.  Limits: bins[a] << levels <= 1024,
+ * bins[0] * bins[3] <= 256, bins[4] <= 32,
  * levels <= APO_MAX_LEVELS, 1 <= topk, topk * 32 <= 4096, topk <= number of level-0 cells. */
 typedef struct {
     int32_t bins[5];
@@ -129,7 +130,8 @@ typedef struct {
                                 with these arguments, and replay it on later calls */
 } apo_solve_opts;
 
-/* Fills *opts with: all levels FP64, one track, min_votes 0, mask_sigma 150e-6, no trace. */
+/* Fills *opts with: all levels FP64, one track, min_votes 0, mask_sigma 150e-6, no trace,
+ * tune = {coarse_filter 0, cells_filter 1, cells_block 256, chunk 0}, no graph. */
 void apo_solve_opts_default(apo_solve_opts *opts);
 
 /* Text of the last error on this thread ("" if none). */

@@ -120,6 +120,33 @@ template <typename T> __device__ __forceinline__ IV<T> sqr(IV<T> a) {
     return {T(0), mx(ru_mul(a.lo, a.lo), ru_mul(a.hi, a.hi))};
 }
 
+// FP32: branch-free forms.  FP32 products are cheap, so the min / max over all four
+// end-point products (the definition) beats sign-case branching, which costs branch
+// instructions, divergence and code size.  Values are identical to the sign-case forms.
+template <> __device__ __forceinline__ IV<float> mul<float>(IV<float> a, IV<float> b) {
+    float l = fminf(fminf(__fmul_rd(a.lo, b.lo), __fmul_rd(a.lo, b.hi)),
+                    fminf(__fmul_rd(a.hi, b.lo), __fmul_rd(a.hi, b.hi)));
+    float h = fmaxf(fmaxf(__fmul_ru(a.lo, b.lo), __fmul_ru(a.lo, b.hi)),
+                    fmaxf(__fmul_ru(a.hi, b.lo), __fmul_ru(a.hi, b.hi)));
+    return {l, h};
+}
+template <> __device__ __forceinline__ IV<float> sqr<float>(IV<float> a) {
+    float ll = __fmul_rd(a.lo, a.lo), hh = __fmul_rd(a.hi, a.hi);
+    float LL = __fmul_ru(a.lo, a.lo), HH = __fmul_ru(a.hi, a.hi);
+    float l = a.lo >= 0.f ? ll : (a.hi <= 0.f ? hh : 0.f);
+    float h = a.lo >= 0.f ? HH : (a.hi <= 0.f ? LL : fmaxf(LL, HH));
+    return {l, h};
+}
+template <> __device__ __forceinline__ IV<float> divi<float>(IV<float> a, IV<float> b) {
+    // b > 0: lo from a.lo, hi from a.hi; b < 0: lo from a.hi, hi from a.lo.  Either way the
+    // numerator's sign picks the divisor end: lo uses b.hi if the numerator is >= 0.
+    const bool bp = b.lo > 0.f;
+    const float nl = bp ? a.lo : a.hi, nh = bp ? a.hi : a.lo;
+    const float dl = nl >= 0.f ? b.hi : b.lo;
+    const float dh = nh >= 0.f ? b.lo : b.hi;
+    return {__fdiv_rd(nl, dl), __fdiv_ru(nh, dh)};
+}
+
 // square root, lower end clamped at 0 (caller guarantees hi >= 0)
 template <typename T> __device__ __forceinline__ IV<T> sqrti(IV<T> a) {
     return {gt0(a.lo) ? rd_sqrt(a.lo) : T(0), ru_sqrt(a.hi)};
@@ -142,14 +169,6 @@ template <typename T> __device__ __forceinline__ IV<T> pm(T r) { return {-r, r};
 // [rd(1/k), ru(1/k)] for an integer k > 0
 template <typename T> __device__ __forceinline__ IV<T> inv_int(int k) {
     return {rd_rcp(T(k)), ru_rcp(T(k))};
-}
-
-// ru(m^n), m >= 0, by repeated upward products
-template <typename T> __device__ __forceinline__ T ru_pow(T m, int n) {
-    T r = T(1);
-#pragma unroll
-    for (int i = 0; i < n; i++) r = ru_mul(r, m);
-    return r;
 }
 
 }  // namespace apo

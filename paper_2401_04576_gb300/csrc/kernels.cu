@@ -174,12 +174,17 @@ template <int MODE> struct CoarseSmem {
     static constexpr size_t bar = mask + 32;
     static constexpr size_t L64 = bar + 8;
     __host__ __device__ static size_t L32(int Bl) { return L64 + 16 * Bl; }
-    __host__ __device__ static size_t cnt(int Bl) { return L32(Bl) + 8 * Bl; }
-    __host__ __device__ static size_t total(int Bl, int nthr) { return cnt(Bl) + 4 * Bl * nthr + 16; }
+    __host__ __device__ static size_t total(int Bl, int) { return L32(Bl) + 8 * Bl + 16; }
 };
 
+// Resident 256-thread blocks per SM asked of the compiler for the FP32 coarse kernel (it
+// caps registers at 64K / (256 x this)); the FP64 kernels are bound by the FP64 pipe.
+#ifndef APO_F32_COARSE_MIN_BLOCKS
+#define APO_F32_COARSE_MIN_BLOCKS 3
+#endif
+
 template <int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, MODE == kModeF32 ? APO_F32_COARSE_MIN_BLOCKS : 1)
 k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
               const uint32_t *active, int32_t *votes, uint32_t *hist, unsigned *status,
               unsigned long long *ctr) {
@@ -198,7 +203,6 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S::bar);
     IV<double> *L64 = reinterpret_cast<IV<double> *>(smem + S::L64);
     IV<float> *L32 = reinterpret_cast<IV<float> *>(smem + S::L32(Bl));
-    int32_t *cnt = reinterpret_cast<int32_t *>(smem + S::cnt(Bl));
 
     int nh = n_hits[ev];
     if (nh < 0) nh = 0;
@@ -209,7 +213,6 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
         L64[l] = el;
         L32[l] = to_prec<float>(el);
     }
-    for (int i = tid; i < Bl * nthr; i += nthr) cnt[i] = 0;
     const unsigned bytes = (unsigned)nh * 80u;
     bool ok = stage_to_smem(h64s, hd + (long long)ev * kHitCap, k64 ? bytes : 0u, h32s,
                             hf + (long long)ev * kHitCap, k32 ? bytes : 0u, bar, status);
@@ -259,13 +262,26 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
     const IV<double> R = recip(c.W);
     const IV<float> R32 = recip(c32.W);
     const unsigned all = Bl >= 32 ? 0xffffffffu : ((1u << Bl) - 1u);
+    // The Bl vote counters of this thread, bit-sliced: bit l of plane k is bit k of counter
+    // l (counts <= 256 need 9 planes).  Adding a mask of votes is a ripple-carry add.
+    uint32_t pl[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) pl[q] = 0u;
+    auto add_votes = [&](uint32_t m) {
+#pragma unroll
+        for (int q = 0; q < 9; q++) {
+            const uint32_t c = pl[q] & m;
+            pl[q] ^= m;
+            m = c;
+        }
+    };
     for (int wd = 0; wd < 8; wd++) {
         uint32_t m = mask_s[wd];
         while (m) {
             int h = wd * 32 + __ffs(m) - 1;
             m &= m - 1;
             if (wguard) {
-                for (int l = 0; l < Bl; l++) cnt[l * nthr + tid]++;
+                add_votes(all);
                 continue;
             }
             // tan(lambda) bins still in question after the FP32 program
@@ -283,7 +299,7 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
                         if (tail<float>(p32, L32[l], h32, R32, c32.W, k)) lm |= 1u << l;
                 }
                 if (!k64) {
-                    for (int l = 0; l < Bl; l++) cnt[l * nthr + tid] += (lm >> l) & 1u;
+                    add_votes(lm);
                     continue;
                 }
             }
@@ -293,21 +309,25 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
             Pre<double> p64 = prefix<double>(c, h64, k);
             n_pre64++;
             if (p64.guard) {
-                for (int l = 0; l < Bl; l++) cnt[l * nthr + tid]++;
+                add_votes(all);
                 continue;
             }
+            uint32_t v64 = 0;
             while (lm) {
                 int l = __ffs(lm) - 1;
                 lm &= lm - 1;
                 n_tail64++;
-                if (tail<double>(p64, L64[l], h64, R, c.W, k)) cnt[l * nthr + tid]++;
+                if (tail<double>(p64, L64[l], h64, R, c.W, k)) v64 |= 1u << l;
             }
+            add_votes(v64);
         }
     }
     const long long ncell = (long long)Bd * Bp * Bw * Bz * Bl;
     int32_t *vo = votes + (long long)e * ncell;
     for (int l = 0; l < Bl; l++) {
-        int v = cnt[l * nthr + tid];
+        int v = 0;
+#pragma unroll
+        for (int q = 0; q < 9; q++) v |= (int)((pl[q] >> l) & 1u) << q;
         long long lin = d + (long long)Bd * (p + (long long)Bp * (w + (long long)Bw * (z + (long long)Bz * l)));
         vo[lin] = v;
         atomicAdd(&hist_s[v], 1u);

@@ -16,7 +16,7 @@
 namespace apo {
 
 // Reciprocals of the series' integer divisors, [rd(1/k), ru(1/k)], computed on the device
-// once per geometry (1/k for k = 1, 3, ..., 17 and 6, 120, 5040, 24, 720, 9!, 8!).
+// once per geometry (1/k for k = 1, 3, ..., 17 and 6, 120, 24; the last entries unused).
 struct SeriesConsts {
     double d_lo[16], d_hi[16];
     float f_lo[16], f_hi[16];
@@ -53,6 +53,12 @@ template <typename T> __device__ __forceinline__ void mirror_hit(Hit<T> &h) {
     h.y0 = neg(h.y0); h.cph = neg(h.cph); h.cpt = neg(h.cpt);
 }
 
+// ru(m^17) for m >= 0 by repeated squaring: m^2, m^4, m^8, m^16, then m^16 m.
+template <typename T> __device__ __forceinline__ T ru_pow17(T m) {
+    T m2 = ru_mul(m, m), m4 = ru_mul(m2, m2), m8 = ru_mul(m4, m4), m16 = ru_mul(m8, m8);
+    return ru_mul(m16, m);
+}
+
 // atan over an interval: two half-angle reductions atan(x) = 2 atan(x/(1 + sqrt(1 + x^2))),
 // the alternating series through x^15 in Horner form on x^2, remainder |x|^17/17, times 4.
 template <typename T> __device__ __forceinline__ IV<T> atan_iv(IV<T> x, const SeriesConsts &k) {
@@ -64,29 +70,24 @@ template <typename T> __device__ __forceinline__ IV<T> atan_iv(IV<T> x, const Se
 #pragma unroll
     for (int j = 6; j >= 0; j--) h = sub(cst<T>(k, C_ATAN0 + j), mul(y, h));
     IV<T> a = mul(x, h);
-    T rem = ru_mul(ru_pow(mag(x), 17), cst<T>(k, C_ATAN0 + 8).hi);
+    T rem = ru_mul(ru_pow17(mag(x)), cst<T>(k, C_ATAN0 + 8).hi);
     a = add(a, pm(rem));
     return {a.lo * T(4), a.hi * T(4)};
 }
 
-// sin and cos over an interval d with |d| <= 1: Taylor through d^7 / d^6 in Horner form on
-// d^2 with Lagrange remainders |d|^9/9!, |d|^8/8!; [-1, 1] when |d| > 1.
+// sin and cos over an interval d with |d| <= 1 (d is the small stereo correction of the
+// phase): sin d = d (1 - d^2/6) + [-1, 1] |d|^5/5!, cos d = 1 - d^2/2 + [-1, 1] |d|^4/4!
+// (Taylor with Lagrange remainders); [-1, 1] when |d| > 1.
 template <typename T>
 __device__ __forceinline__ void sincos_iv(IV<T> d, IV<T> &s, IV<T> &c, const SeriesConsts &k) {
     const IV<T> one{T(1), T(1)};
     T m = mag(d);
     if (!le(m, T(1))) { s = {T(-1), T(1)}; c = {T(-1), T(1)}; return; }
     IV<T> y = sqr(d);
-    IV<T> hs = cst<T>(k, C_SIN7);
-    hs = sub(cst<T>(k, C_SIN5), mul(y, hs));
-    hs = sub(cst<T>(k, C_SIN3), mul(y, hs));
-    IV<T> S = sub(one, mul(y, hs));
-    IV<T> sv = add(mul(d, S), pm(ru_mul(ru_pow(m, 9), cst<T>(k, C_REM9).hi)));
-    IV<T> hc = cst<T>(k, C_COS6);
-    hc = sub(cst<T>(k, C_COS4), mul(y, hc));
-    hc = sub(IV<T>{T(0.5), T(0.5)}, mul(y, hc));
-    IV<T> C = sub(one, mul(y, hc));
-    IV<T> cv = add(C, pm(ru_mul(ru_pow(m, 8), cst<T>(k, C_REM8).hi)));
+    IV<T> S = sub(one, mul(y, cst<T>(k, C_SIN3)));
+    T m2 = ru_mul(m, m), m4 = ru_mul(m2, m2);
+    IV<T> sv = add(mul(d, S), pm(ru_mul(ru_mul(m4, m), cst<T>(k, C_SIN5).hi)));
+    IV<T> cv = add(sub(one, half(y)), pm(ru_mul(m4, cst<T>(k, C_COS4).hi)));
     s = clamp1(sv);
     c = clamp1(cv);
 }
