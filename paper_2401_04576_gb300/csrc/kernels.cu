@@ -60,7 +60,7 @@ __device__ bool stage_to_smem(void *dst0, const void *src0, unsigned bytes0, voi
     long it = 0;
     while (!mbar_try_wait(bar, 0)) {
         if (++it > kWaitLimit) {
-            atomicOr(status, ST_TIMEOUT);
+            if (status) atomicOr(status, ST_TIMEOUT);
             // give the copies in flight a second bounded chance before leaving the smem
             for (long j = 0; j < kWaitLimit && !mbar_try_wait(bar, 0); j++) {
             }
@@ -349,7 +349,8 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
 
 // Raises the dynamic shared-memory limit of a kernel once per process (the attribute is a
 // property of the function; setting it outside any stream capture keeps captures clean).
-static bool g_attr_coarse[3] = {false, false, false}, g_attr_cells[3] = {false, false, false};
+static bool g_attr_coarse[3] = {false, false, false}, g_attr_cells[3] = {false, false, false},
+            g_attr_children[3] = {false, false, false};
 
 template <typename K> static void smem_limit_once(K kernel, bool &flag) {
     if (!flag) {
@@ -448,6 +449,82 @@ k_vote_cells(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_h
     if (out_keys) out_keys[o] = key;
 }
 
+// Children of kept cells, two per thread: the children 2 idx + bit of a parent that differ
+// only in the tan(lambda) bit share every tan(lambda)-free step of the program, so one
+// prefix per hit serves both tails (same operations as evaluating them apart).
+template <int MODE>
+__global__ void __launch_bounds__(256)
+k_vote_children(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
+                const uint32_t *active, int level, const uint64_t *parents, int n_par,
+                uint64_t *out_keys, int32_t *out_votes, unsigned *status) {
+    constexpr bool k64 = MODE != kModeF32, k32 = MODE != kModeF64;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char *h64s = smem;
+    unsigned char *h32s = smem + (k64 ? kHitCap * 80 : 0);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (k64 ? kHitCap * 80 : 0) + (k32 ? kHitCap * 80 : 0));
+    const int ev = blockIdx.y;
+    int nh = n_hits[ev];
+    if (nh < 0) nh = 0;
+    const unsigned bytes = (unsigned)nh * 80u;
+    bool ok = stage_to_smem(h64s, hd + (long long)ev * kHitCap, k64 ? bytes : 0u, h32s,
+                            hf + (long long)ev * kHitCap, k32 ? bytes : 0u, bar, status);
+    __syncthreads();
+    if (!ok) nh = 0;
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= (long long)n_par * 16) return;
+    const int b = (int)(j % 16);
+    int idx[5];
+    unpack_key(parents[(long long)ev * n_par + j / 16], idx);
+#pragma unroll
+    for (int a = 0; a < 4; a++) idx[a] = 2 * idx[a] + ((b >> a) & 1);
+    const int l0 = 2 * idx[4];                    // tan(lambda) bit 0 / 1 of the pair
+    idx[4] = l0;
+    const uint64_t key0 = pack_key(idx);
+    const uint64_t key1 = key0 + (1ULL << 40);
+    Cell<double> c{edge(g, 0, level, idx[0]), sin_phi0(g, level, idx[1]), cos_phi0(g, level, idx[1]),
+                   edge(g, 2, level, idx[2]), edge(g, 3, level, idx[3]), edge(g, 4, level, l0)};
+    const IV<double> L1 = edge(g, 4, level, l0 + 1);
+    Cell<float> c32{to_prec<float>(c.D), to_prec<float>(c.S0), to_prec<float>(c.C0),
+                    to_prec<float>(c.W), to_prec<float>(c.Z), to_prec<float>(c.L)};
+    const IV<float> L1f = to_prec<float>(L1);
+    const bool mir = mirror_cell(c);
+    mirror_cell(c32);
+    const bool wguard = !gt0(c.W.lo) || !gt0(c32.W.lo);
+    const IV<double> R = recip(c.W);
+    const IV<float> R32 = recip(c32.W);
+    const SeriesConsts &k = g.k;
+    const uint32_t *act = active ? active + (long long)ev * 8 : nullptr;
+    int v0 = 0, v1 = 0;
+    for (int h = 0; h < nh; h++) {
+        if (act && !((act[h >> 5] >> (h & 31)) & 1u)) continue;
+        if (wguard) { v0++; v1++; continue; }
+        unsigned lm = 3u;
+        if (k32) {
+            Hit<float> h32 = load_hit<float>(h32s + h * 80);
+            if (mir) mirror_hit(h32);
+            Pre<float> p32 = prefix<float>(c32, h32, k);
+            if (!p32.guard) {
+                lm = (tail<float>(p32, c32.L, h32, R32, c32.W, k) ? 1u : 0u) |
+                     (tail<float>(p32, L1f, h32, R32, c32.W, k) ? 2u : 0u);
+            }
+            if (!k64) { v0 += lm & 1u; v1 += lm >> 1; continue; }
+            if (!lm) continue;
+        }
+        Hit<double> h64 = load_hit<double>(h64s + h * 80);
+        if (mir) mirror_hit(h64);
+        Pre<double> p64 = prefix<double>(c, h64, k);
+        if (p64.guard) { v0++; v1++; continue; }
+        if ((lm & 1u) && tail<double>(p64, c.L, h64, R, c.W, k)) v0++;
+        if ((lm & 2u) && tail<double>(p64, L1, h64, R, c.W, k)) v1++;
+    }
+    // output order: child b at 32 j' + b, child b + 16 at 32 j' + b + 16 (j' = parent)
+    const long long o = (long long)ev * n_par * 32 + (j / 16) * 32 + b;
+    out_keys[o] = key0;
+    out_votes[o] = v0;
+    out_keys[o + 16] = key1;
+    out_votes[o + 16] = v1;
+}
+
 template <int MODE>
 static void launch_cells_mode(const DevGeom &g, int n_ev, const HitRecD *hd, const HitRecF *hf,
                               const int32_t *n_hits, const uint32_t *active, int level,
@@ -486,13 +563,33 @@ void launch_vote_keys(const DevGeom &g, int prec, int n_ev, const HitRecD *hd, c
                  nullptr, s);
 }
 
+template <int MODE>
+static void launch_children_mode(const DevGeom &g, int n_ev, const HitRecD *hd, const HitRecF *hf,
+                                 const int32_t *n_hits, const uint32_t *active, int level,
+                                 const uint64_t *parents, int n_par, uint64_t *out_keys,
+                                 int32_t *out_votes, cudaStream_t s, int block) {
+    size_t sm = (MODE != kModeF32 ? kHitCap * 80 : 0) + (MODE != kModeF64 ? kHitCap * 80 : 0) + 16;
+    smem_limit_once(k_vote_children<MODE>, g_attr_children[MODE]);
+    dim3 grid((unsigned)(((long long)n_par * 16 + block - 1) / block), n_ev);
+    k_vote_children<MODE><<<grid, block, sm, s>>>(g, hd, hf, n_hits, active, level, parents, n_par,
+                                                   out_keys, out_votes, nullptr);
+}
+
 void launch_vote_children(const DevGeom &g, int prec, int n_ev, const HitRecD *hd,
                           const HitRecF *hf, const int32_t *n_hits, int child_level,
                           const uint64_t *parents, int n_par, uint64_t *child_keys,
                           int32_t *child_votes, cudaStream_t s, const uint32_t *active, int block) {
     if (n_ev <= 0 || n_par <= 0) return;
-    launch_cells(g, prec, n_ev, hd, hf, n_hits, active, child_level, nullptr, parents,
-                 (long long)n_par * 32, child_keys, child_votes, nullptr, s, block);
+    if (block != 128) block = 256;
+    if (prec == APO_F32)
+        launch_children_mode<kModeF32>(g, n_ev, hd, hf, n_hits, active, child_level, parents, n_par,
+                                       child_keys, child_votes, s, block);
+    else if (prec == APO_F64_FILTERED)
+        launch_children_mode<kModeF64Filtered>(g, n_ev, hd, hf, n_hits, active, child_level, parents, n_par,
+                                               child_keys, child_votes, s, block);
+    else
+        launch_children_mode<kModeF64>(g, n_ev, hd, hf, n_hits, active, child_level, parents, n_par,
+                                       child_keys, child_votes, s, block);
 }
 
 // Sets every vote kernel's dynamic shared-memory limit now, outside any stream capture.
@@ -504,7 +601,10 @@ void init_kernel_attributes() {
     cudaFuncSetAttribute(k_vote_cells<kModeF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_vote_cells<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_vote_cells<kModeF64Filtered>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    for (int i = 0; i < 3; i++) g_attr_coarse[i] = g_attr_cells[i] = true;
+    cudaFuncSetAttribute(k_vote_children<kModeF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_children<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_children<kModeF64Filtered>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    for (int i = 0; i < 3; i++) g_attr_coarse[i] = g_attr_cells[i] = g_attr_children[i] = true;
 }
 
 // ---------------------------------------------------------------------------------------
