@@ -30,6 +30,18 @@ int32_t apo_diag_coarse_launches(const apo_geometry *geom, int32_t n_events);
  * *ops_per_s = operations per second.  Synchronous, about 0.1 s. */
 int apo_diag_pipe_peak(int32_t precision, int32_t op, double *ops_per_s);
 
+/* Exercises the device-side wait limit: one kernel waits on a barrier that nothing
+ * completes, for at most `limit_polls` polls, then records a timeout in a status word and
+ * ends normally.  Returns APO_ETIMEOUT when the status word shows it (the expected
+ * outcome), APO_OK if it did not, APO_ECUDA on a CUDA failure.  Synchronous; the device
+ * stays usable afterwards. */
+int apo_diag_wait_timeout(int32_t limit_polls);
+
+/* Reads the status word of a workspace after the work queued on it (synchronises
+ * `stream`): APO_ETIMEOUT if a device wait ran out, APO_OK otherwise. */
+int apo_workspace_status(const apo_geometry *geom, int32_t n_events, const void *workspace,
+                         void *stream);
+
 #ifdef __cplusplus
 }
 #endif

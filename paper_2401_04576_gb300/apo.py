@@ -106,6 +106,8 @@ def lib():
         L.apo_diag_coarse_launches.argtypes = [vp, i32]
         L.apo_diag_coarse_launches.restype = i32
         L.apo_diag_pipe_peak.argtypes = [i32, i32, C.POINTER(C.c_double)]
+        L.apo_diag_wait_timeout.argtypes = [i32]
+        L.apo_workspace_status.argtypes = [vp, i32, vp, vp]
         _lib = L
     return _lib
 
@@ -324,6 +326,17 @@ def solve_batch_host(geom: Geometry, offsets: np.ndarray, wire_id: np.ndarray, d
                                       C.byref(o), hp(out), hp(nt), _ptr(ws), ws.numel(),
                                       _stream_ptr(stream)))
     return out, nt
+
+
+def wait_timeout_test(limit_polls: int = 1000) -> int:
+    """apo_diag_wait_timeout: status of a device wait on a barrier nothing completes
+    (APO_ETIMEOUT expected)."""
+    return int(lib().apo_diag_wait_timeout(int(limit_polls)))
+
+
+def workspace_status(geom: Geometry, n_events: int, workspace, stream=None) -> int:
+    return int(lib().apo_workspace_status(geom.handle, int(n_events), _ptr(workspace),
+                                          _stream_ptr(stream)))
 
 
 def pipe_peak(precision: int = F64) -> float:

@@ -9,6 +9,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/apo.h"
 #include "../../include/apo_diag.h"
 #include "kernels.cuh"
@@ -371,6 +373,12 @@ int validate_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_
     return check_ws(g, hits->n_events, ws, ws_bytes, L);
 }
 
+// NVTX range for the host-side queueing of one phase (visible in Nsight timelines).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 // Queues the whole search on stream s (no host synchronisation, capturable).
 int enqueue_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_opts *o,
                   apo_track *tracks_out, int32_t *n_tracks_out, void *ws, const Layout &L,
@@ -415,6 +423,7 @@ int enqueue_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_o
         uint32_t *acte = active + (size_t)e0 * 8;
         // one round per track: search the active hits, record, mask the track's hits
         for (int round = 0; round < o->max_tracks; round++) {
+            NvtxRange range_round("apo search round");
             CU(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)n * kHistBins, s));
             launch_vote_coarse(g->dg, prec_at(0), e0, n, hd, hf, nh, votes, hist, status, s, nullptr, active);
             if ((rc = check_launch("vote_coarse"))) return rc;
@@ -591,6 +600,36 @@ int32_t apo_diag_coarse_launches(const apo_geometry *g, int32_t n_events) {
     return (n_events + L.chunk - 1) / L.chunk;
 }
 
+int apo_diag_wait_timeout(int32_t limit_polls) {
+    unsigned *st = nullptr;
+    CU(cudaMalloc(&st, sizeof(unsigned)));
+    unsigned h = 0;
+    cudaError_t e = cudaMemset(st, 0, sizeof(unsigned));
+    if (e == cudaSuccess) {
+        launch_wait_never(limit_polls > 0 ? limit_polls : 1, st, 0);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, st, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    cudaFree(st);
+    if (e != cudaSuccess) return fail(APO_ECUDA, "wait test: %s", cudaGetErrorString(e));
+    if (h & ST_TIMEOUT) return fail(APO_ETIMEOUT, "device wait ran out of its poll limit");
+    return APO_OK;
+}
+
+int apo_workspace_status(const apo_geometry *g, int32_t n_events, const void *ws, void *stream) {
+    int rc;
+    if ((rc = check_geom(g))) return rc;
+    if (!ws) return fail(APO_EINVAL, "workspace is NULL");
+    Layout L = layout(g, n_events);
+    unsigned h = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CU(cudaMemcpyAsync(&h, static_cast<const unsigned char *>(ws) + L.status, sizeof(unsigned),
+                       cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (h & ST_TIMEOUT) return fail(APO_ETIMEOUT, "a device wait ran out of its poll limit");
+    return APO_OK;
+}
+
 int apo_diag_pipe_peak(int32_t precision, int32_t op, double *ops_per_s) {
     if (!ops_per_s) return fail(APO_EINVAL, "ops_per_s is NULL");
     if (precision != APO_F64 && precision != APO_F32) return fail(APO_EINVAL, "bad precision");
@@ -635,6 +674,9 @@ int apo_solve_batch_host(const apo_geometry *g, int32_t n_events, const int32_t 
     if (n_tracks_out)
         CU(cudaMemcpyAsync(n_tracks_out, d_nt, sizeof(int32_t) * (size_t)n_events, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    unsigned st = 0;
+    CU(cudaMemcpy(&st, at<unsigned>(ws, L.status), sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (st & ST_TIMEOUT) return fail(APO_ETIMEOUT, "a device wait ran out of its poll limit");
     return APO_OK;
 }
 

@@ -50,6 +50,7 @@ struct Slot {
     int32_t *h_off = nullptr, *h_wid = nullptr, *h_nt = nullptr;
     double *h_dr = nullptr;
     apo_track *h_tr = nullptr;
+    unsigned *h_status = nullptr;     // the workspace's status word, copied back per batch
     std::vector<uint64_t> ids;
     bool busy = false;
 };
@@ -84,7 +85,7 @@ int fail_msg(int code, const char *m) {
 size_t slot_io_bytes(int B, int max_tracks) {
     return a256(sizeof(int32_t) * (B + 1)) + a256(sizeof(int32_t) * (size_t)B * APO_HIT_CAP) +
            a256(sizeof(double) * (size_t)B * APO_HIT_CAP) +
-           a256(sizeof(apo_track) * (size_t)B * max_tracks) + a256(sizeof(int32_t) * B);
+           a256(sizeof(apo_track) * (size_t)B * max_tracks) + a256(sizeof(int32_t) * B) + 256;
 }
 
 template <typename P> void carve(unsigned char *&p, P *&out, size_t bytes) {
@@ -135,6 +136,8 @@ int launch_slot(apo_server *sv, Slot &s) {
     if (rc != APO_OK) return rc;
     e = cudaMemcpyAsync(s.h_tr, s.d_tr, sizeof(apo_track) * (size_t)n * mt, cudaMemcpyDeviceToHost, s.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_nt, s.d_nt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s.stream);
+    // the search's status word is the first word of the workspace
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_status, s.dev, sizeof(unsigned), cudaMemcpyDeviceToHost, s.stream);
     if (e == cudaSuccess) e = cudaEventRecord(s.finished, s.stream);
     if (e != cudaSuccess) return fail_msg(APO_ECUDA, cudaGetErrorString(e));
     s.busy = true;
@@ -156,6 +159,12 @@ void worker_loop(apo_server *sv) {
             if (q != cudaSuccess) {
                 sv->error = APO_ECUDA;
                 sv->msg = cudaGetErrorString(q);
+                continue;
+            }
+            if (*s.h_status & ST_TIMEOUT) {
+                sv->error = APO_ETIMEOUT;
+                sv->msg = "apo_serve: a device wait ran out of its poll limit";
+                sv->cv_done.notify_all();
                 continue;
             }
             for (size_t i = 0; i < s.ids.size(); i++) {
@@ -268,6 +277,7 @@ int apo_serve_create(const apo_geometry *g, const apo_serve_opts *opts, apo_serv
         carve(q, s.h_dr, sizeof(double) * (size_t)B * APO_HIT_CAP);
         carve(q, s.h_tr, sizeof(apo_track) * (size_t)B * mt);
         carve(q, s.h_nt, sizeof(int32_t) * B);
+        carve(q, s.h_status, sizeof(unsigned));
     }
     sv->worker = std::thread(worker_loop, sv);
     *out = sv;

@@ -39,6 +39,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
 }
 constexpr long kWaitLimit = 1L << 22;
 
+// Waits for phase `parity` of an mbarrier for at most `limit` polls.  On running out it sets
+// ST_TIMEOUT in *status (if given) and returns false; the caller then leaves the barrier's
+// work undone and the kernel ends normally, so the context stays usable.
+__device__ bool bounded_wait(uint64_t *bar, unsigned parity, long limit, unsigned *status) {
+    for (long it = 0; it < limit; it++)
+        if (mbar_try_wait(bar, parity)) return true;
+    if (status) atomicOr(status, ST_TIMEOUT);
+    return false;
+}
+
 // Copies up to two blocks (bytes0 / bytes1: multiples of 16, 16-byte aligned ends) of an
 // event's hit records into shared memory with one mbarrier.  Returns false (and flags
 // ST_TIMEOUT) if the copies did not complete within the wait limit; the caller then skips
@@ -57,17 +67,28 @@ __device__ bool stage_to_smem(void *dst0, const void *src0, unsigned bytes0, voi
         if (bytes0) bulk_g2s(dst0, src0, bytes0, bar);
         if (bytes1) bulk_g2s(dst1, src1, bytes1, bar);
     }
-    long it = 0;
-    while (!mbar_try_wait(bar, 0)) {
-        if (++it > kWaitLimit) {
-            if (status) atomicOr(status, ST_TIMEOUT);
-            // give the copies in flight a second bounded chance before leaving the smem
-            for (long j = 0; j < kWaitLimit && !mbar_try_wait(bar, 0); j++) {
-            }
-            return false;
-        }
+    if (bounded_wait(bar, 0, kWaitLimit, status)) return true;
+    // give the copies in flight a second bounded chance before leaving the shared memory
+    bounded_wait(bar, 0, kWaitLimit, nullptr);
+    return false;
+}
+
+// Diagnostic: every thread waits on an mbarrier whose expected bytes never arrive (no copy
+// is issued, so nothing is in flight), with a short limit.  The wait must run out and
+// report ST_TIMEOUT; used to test the timeout path without any device fault.
+__global__ void k_wait_never(long limit, unsigned *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect_tx(&bar, 16);
     }
-    return true;
+    __syncthreads();
+    bounded_wait(&bar, 0, limit, status);
+}
+
+void launch_wait_never(long limit, unsigned *status, cudaStream_t s) {
+    k_wait_never<<<1, 32, 0, s>>>(limit, status);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -182,9 +203,12 @@ template <int MODE> struct CoarseSmem {
 #ifndef APO_F32_COARSE_MIN_BLOCKS
 #define APO_F32_COARSE_MIN_BLOCKS 3
 #endif
+#ifndef APO_F64_COARSE_MIN_BLOCKS
+#define APO_F64_COARSE_MIN_BLOCKS 1
+#endif
 
 template <int MODE>
-__global__ void __launch_bounds__(256, MODE == kModeF32 ? APO_F32_COARSE_MIN_BLOCKS : 1)
+__global__ void __launch_bounds__(256, MODE == kModeF32 ? APO_F32_COARSE_MIN_BLOCKS : APO_F64_COARSE_MIN_BLOCKS)
 k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
               const uint32_t *active, int32_t *votes, uint32_t *hist, unsigned *status,
               unsigned long long *ctr) {

@@ -104,6 +104,7 @@ void launch_vote_children(const DevGeom &g, int prec, int n_ev, const HitRecD *h
                           int32_t *child_votes, cudaStream_t s, const uint32_t *active = nullptr,
                           int block = 256);
 void init_kernel_attributes();
+void launch_wait_never(long limit, unsigned *status, cudaStream_t s);
 void launch_select_coarse(const DevGeom &g, int ev0, int n_ev, const int32_t *votes,
                           const uint32_t *hist, int K, uint64_t *out_keys, int32_t *out_votes,
                           cudaStream_t s);
