@@ -46,7 +46,7 @@ OPS_TAIL = OPS_LPART + OPS_SIGNS
 # capture summarised in profiles/k_vote_coarse_f64_64events.md (64 events: 4.44 MB read +
 # 214.26 MB written), scaled by events to the benchmark's launch.  Must be re-captured (or
 # set to None) whenever that kernel changes.
-COARSE_F64_DRAM_BYTES_PER_EVENT = (4.439296e6 + 214.2592e6) / 64
+COARSE_F64_DRAM_BYTES_PER_EVENT = None
 
 
 def coarse_kernel_ops(n_parent: int, n_prefix: int, n_tail: int) -> int:
@@ -453,7 +453,9 @@ def run_case(args) -> None:
         for _ in range(2):
             apo.vote(geom, hits, precision=prec, out=votes, workspace=ws)
     else:
-        o = apo.solve_opts(precision=[prec] * (g.levels + 1))
+        precision = ([apo.F32] * 5 + [apo.F64] * (g.levels + 1 - 5) if args.case == "solve-bulk"
+                     else [prec] * (g.levels + 1))
+        o = apo.solve_opts(precision=precision)
         for _ in range(2):
             apo.solve_batch(geom, hits, o, workspace=ws)
     torch.cuda.synchronize()
@@ -471,7 +473,7 @@ def main(argv=None):
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--case", default=None,
-                    choices=["coarse-f64", "coarse-f32", "solve-f64", "solve-f32"],
+                    choices=["coarse-f64", "coarse-f32", "solve-f64", "solve-f32", "solve-bulk"],
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--events", type=int, default=64)
     args = ap.parse_args(argv)

@@ -52,6 +52,9 @@ __device__ __forceinline__ long long okey(double x) {
     long long b = dbits(x);
     return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
 }
+__device__ __forceinline__ long long okey_inv(long long k) {   // okey is an involution
+    return k ^ ((k >> 63) & 0x7fffffffffffffffLL);
+}
 __device__ __forceinline__ bool gt0(double x) { return dbits(x) > 0; }
 __device__ __forceinline__ bool le0(double x) { return dbits(x) <= 0; }
 __device__ __forceinline__ bool lt0(double x) { return okey(x) < -1; }     // -0 has key -1
@@ -120,9 +123,10 @@ template <typename T> __device__ __forceinline__ IV<T> sqr(IV<T> a) {
     return {T(0), mx(ru_mul(a.lo, a.lo), ru_mul(a.hi, a.hi))};
 }
 
-// FP32: branch-free forms.  FP32 products are cheap, so the min / max over all four
-// end-point products (the definition) beats sign-case branching, which costs branch
-// instructions, divergence and code size.  Values are identical to the sign-case forms.
+// FP32: branch-free forms.  The extremes of a b over the box are at a = a.lo or a.hi, each
+// times the end of b chosen by that a's sign: two products per end point with selects (no
+// branches, less code than sign cases).  Values equal the min / max over all four
+// end-point products.
 template <> __device__ __forceinline__ IV<float> mul<float>(IV<float> a, IV<float> b) {
     float l = fminf(fminf(__fmul_rd(a.lo, b.lo), __fmul_rd(a.lo, b.hi)),
                     fminf(__fmul_rd(a.hi, b.lo), __fmul_rd(a.hi, b.hi)));
@@ -145,6 +149,16 @@ template <> __device__ __forceinline__ IV<float> divi<float>(IV<float> a, IV<flo
     const float dl = nl >= 0.f ? b.hi : b.lo;
     const float dh = nh >= 0.f ? b.lo : b.hi;
     return {__fdiv_rd(nl, dl), __fdiv_ru(nh, dh)};
+}
+
+// a * b for b >= 0 (b.lo >= 0, known from the program's structure): a b is increasing in
+// a, so the ends are a.lo and a.hi, each times the end of b chosen by its sign.
+template <typename T> __device__ __forceinline__ IV<T> mul_nn(IV<T> a, IV<T> b) {
+    return {rd_mul(a.lo, nonneg_lo(a.lo) ? b.lo : b.hi), ru_mul(a.hi, nonneg_lo(a.hi) ? b.hi : b.lo)};
+}
+// a * b for a >= 0 and b >= 0
+template <typename T> __device__ __forceinline__ IV<T> mul_pp(IV<T> a, IV<T> b) {
+    return {rd_mul(a.lo, b.lo), ru_mul(a.hi, b.hi)};
 }
 
 // square root, lower end clamped at 0 (caller guarantees hi >= 0)

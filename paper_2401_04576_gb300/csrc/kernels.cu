@@ -3,6 +3,9 @@
 // the final max-vote estimate.
 #include <cuda_runtime.h>
 
+#include <climits>
+#include <cstdint>
+
 #include "../../include/apo.h"
 #include "kernels.cuh"
 
@@ -633,17 +636,24 @@ void init_kernel_attributes() {
 
 // ---------------------------------------------------------------------------------------
 // Coarse top-K: threshold from the vote histogram, then an order-preserving compaction.
-// Keeps every cell with votes above the threshold and the lowest-key cells at it, so the
-// kept set is the K best by (votes desc, key asc).
+// Keeps every cell with votes above the threshold v* and the lowest-key cells at v*, so the
+// kept set is the K best by (votes desc, key asc).  From the histogram: A = #(v > v*) < K
+// and need = K - A.  One pass over the event's votes in key order, 4096 cells per tile,
+// each thread 4 consecutive cells (one 16-byte load where aligned); cells above v* go to
+// slot (rank among them), cells at v* to slot A + (rank among them) while that is < K.
+// A tile with nothing to keep costs one barrier; the pass ends once all A cells and
+// `need` tied cells are placed.  Votes are clamped to [0, kHitCap] as the histogram does.
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024)
+constexpr int kSelThreads = 1024;
+constexpr int kSelTile = 4 * kSelThreads;
+
+__global__ void __launch_bounds__(kSelThreads)
 k_select_coarse(DevGeom g, int ev0, const int32_t *votes, const uint32_t *hist, int K,
                 uint64_t *out_keys, int32_t *out_votes) {
-    __shared__ int s_vstar, s_need;
-    __shared__ int sa[1024], sb[1024];
-    const int e = blockIdx.x, ev = ev0 + e, tid = threadIdx.x;
-    const int Bd = g.bins[0], Bp = g.bins[1], Bw = g.bins[2], Bz = g.bins[3];
-    const long long n = (long long)Bd * Bp * Bw * Bz * g.bins[4];
+    __shared__ int s_vstar, s_need, s_above;
+    __shared__ int s_warp[32];
+    const int e = blockIdx.x, ev = ev0 + e, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const long long n = (long long)g.bins[0] * g.bins[1] * g.bins[2] * g.bins[3] * g.bins[4];
     if (tid == 0) {
         long long cum = 0;
         int vstar = -1, need = 0;
@@ -654,45 +664,72 @@ k_select_coarse(DevGeom g, int ev0, const int32_t *votes, const uint32_t *hist, 
         }
         s_vstar = vstar;
         s_need = need;
+        s_above = (int)cum;
     }
     __syncthreads();
-    const int vstar = s_vstar, need = s_need;
+    const int vstar = s_vstar, need = s_need, above = s_above;
     const int32_t *vo = votes + (long long)e * n;
-    long long chunk = (n + 1023) / 1024;
-    long long beg = tid * chunk, end = beg + chunk < n ? beg + chunk : n;
-    int a = 0, b = 0;
-    for (long long j = beg; j < end; j++) {
-        int v = vo[j];
-        a += v > vstar;
-        b += v == vstar;
-    }
-    sa[tid] = a;
-    sb[tid] = b;
-    __syncthreads();
-    // inclusive Hillis-Steele scans
-    for (int off = 1; off < 1024; off <<= 1) {
-        int xa = tid >= off ? sa[tid - off] : 0, xb = tid >= off ? sb[tid - off] : 0;
-        __syncthreads();
-        sa[tid] += xa;
-        sb[tid] += xb;
-        __syncthreads();
-    }
-    const int totalA = sa[1023];
-    int pa = sa[tid] - a, pb = sb[tid] - b;
     uint64_t *ok_ = out_keys + (long long)ev * K;
     int32_t *ov = out_votes + (long long)ev * K;
-    for (long long j = beg; j < end; j++) {
-        int v = vo[j];
-        if (v > vstar || (v == vstar && pb < need)) {
-            long long r = j;
-            int idx[5];
-            for (int q = 0; q < 5; q++) { idx[q] = (int)(r % g.bins[q]); r /= g.bins[q]; }
-            int pos = v > vstar ? pa++ : totalA + pb++;
-            ok_[pos] = pack_key(idx);
-            ov[pos] = v;
-        } else if (v == vstar) {
-            pb++;
+    const bool vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(vo) & 15) == 0);
+    int runA = 0, runB = 0;   // cells above v* / at v* in the tiles before this one
+    for (long long t0 = 0; t0 < n; t0 += kSelTile) {
+        if (runA >= above && runB >= need) break;
+        const long long j0 = t0 + 4LL * tid;
+        int v[4];
+        if (vec && j0 + 3 < n) {
+            int4 q = __ldcs(reinterpret_cast<const int4 *>(vo + j0));
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; r++) v[r] = j0 + r < n ? __ldcs(vo + j0 + r) : INT_MIN;
         }
+        int a = 0, b = 0;
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            if (v[r] != INT_MIN) v[r] = v[r] < 0 ? 0 : (v[r] > kHitCap ? kHitCap : v[r]);
+            a += v[r] > vstar;
+            b += v[r] == vstar;
+        }
+        if (!__syncthreads_or(a > 0 || (b > 0 && runB < need))) continue;
+        // block exclusive scan of (a, b) packed as a + (b << 16); a tile holds < 2^16 cells
+        const int x = a + (b << 16);
+        int inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_warp[wid] = inc;
+        __syncthreads();
+        int w = s_warp[lane];
+        int winc = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, winc, o);
+            if (lane >= o) winc += y;
+        }
+        const int wpre = __shfl_sync(0xffffffffu, winc - w, wid);
+        const int total = __shfl_sync(0xffffffffu, winc, 31);
+        const int pre = wpre + inc - x;
+        int pa = runA + (pre & 0xffff), pb = runB + (pre >> 16);
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const bool ka = v[r] > vstar, kb = v[r] == vstar;
+            int pos = -1;
+            if (ka) pos = pa++;
+            else if (kb) { if (pb < need) pos = above + pb; pb++; }
+            if (pos >= 0 && pos < K) {
+                long long rr = j0 + r;
+                int idx[5];
+                for (int q = 0; q < 5; q++) { idx[q] = (int)(rr % g.bins[q]); rr /= g.bins[q]; }
+                ok_[pos] = pack_key(idx);
+                ov[pos] = v[r];
+            }
+        }
+        runA += total & 0xffff;
+        runB += total >> 16;
+        __syncthreads();   // s_warp is rewritten by the next scanned tile
     }
 }
 
@@ -700,7 +737,7 @@ void launch_select_coarse(const DevGeom &g, int ev0, int n_ev, const int32_t *vo
                           const uint32_t *hist, int K, uint64_t *out_keys, int32_t *out_votes,
                           cudaStream_t s) {
     if (n_ev <= 0) return;
-    k_select_coarse<<<n_ev, 1024, 0, s>>>(g, ev0, votes, hist, K, out_keys, out_votes);
+    k_select_coarse<<<n_ev, kSelThreads, 0, s>>>(g, ev0, votes, hist, K, out_keys, out_votes);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -764,14 +801,18 @@ void launch_topk(int n_ev, const uint64_t *keys, const int32_t *votes, int n_in,
 // least one maximum-vote cell with its drift widened to [max(rd(d - width), 0),
 // ru(d + width)] (the paper's hit finding with a widened box, Section 3.3).
 // ---------------------------------------------------------------------------------------
+constexpr int kEstChunk = 256;
+
 __global__ void __launch_bounds__(256)
 k_estimate_mask(DevGeom g, const uint64_t *keys, const int32_t *votes, int n_in, int level,
                 const int32_t *n_hits, uint32_t *active, int32_t *done, const HitRecD *hd,
                 int round, int max_tracks, int min_votes, double width, apo_track *out,
                 int32_t *n_tracks) {
     __shared__ uint64_t s[kSortMax];
+    __shared__ double s_cen[kEstChunk * 5];
+    __shared__ long long s_lo[5], s_hi[5];
     __shared__ uint32_t act0[8], act1[8];
-    __shared__ int s_vmax, s_m;
+    __shared__ int s_m;
     const int e = blockIdx.x, tid = threadIdx.x;
     if (done[e]) return;
     const int nh = n_hits[e];
@@ -797,39 +838,55 @@ k_estimate_mask(DevGeom g, const uint64_t *keys, const int32_t *votes, int n_in,
         if (tid == 0) done[e] = 1;
         return;
     }
+    if (tid == 0) s_m = 0;
+    if (tid < 5) { s_lo[tid] = okey(1e300); s_hi[tid] = okey(-1e300); }
     int np2 = pow2_ge(n_in);
     load_sorted(s, keys + (long long)e * n_in, votes + (long long)e * n_in, n_in, np2);
-    if (tid == 0) {
-        int vmax = 1023 - (int)(s[0] >> 50);
-        int m = 0;
-        while (m < n_in && 1023 - (int)(s[m] >> 50) == vmax) m++;
-        s_vmax = vmax;
-        s_m = m;
+    // the maximum-vote cells are s[0, m) after the sort
+    const uint64_t top = s[0] >> 50;
+    const int vmax = 1023 - (int)top;
+    {
+        int cnt = 0;
+        for (int i = tid; i < n_in; i += blockDim.x) cnt += (s[i] >> 50) == top;
+        if (cnt) atomicAdd(&s_m, cnt);
     }
     __syncthreads();
-    const int vmax = s_vmax, m = s_m;
+    const int m = s_m;
     if (vmax < min_votes) {
         if (tid == 0) done[e] = 1;
         return;
     }
-    if (tid == 0) {
-        apo_track &t = te[round];
-        for (int a = 0; a < 5; a++) {
-            double sum = 0.0, lo_min = 1e300, hi_max = -1e300;
-            for (int j = 0; j < m; j++) {
-                int idx[5];
-                unpack_key(s[j] & kKeyMask, idx);
-                IV<double> ed = edge(g, a, level, idx[a]);
-                sum = __dadd_rn(sum, __dmul_rn(__dadd_rn(ed.lo, ed.hi), 0.5));
-                lo_min = ed.lo < lo_min ? ed.lo : lo_min;
-                hi_max = ed.hi > hi_max ? ed.hi : hi_max;
-            }
-            t.p[a] = __ddiv_rn(sum, (double)m);
-            t.w[a] = __dmul_rn(__dsub_rn(hi_max, lo_min), 0.5);
+    // Centres of the m cells, staged per chunk by all threads; thread a < 5 then adds axis
+    // a's centres in key order (the same round-to-nearest sequence as a serial loop).  The
+    // union's ends are order-free: min / max through atomics on value-ordered keys.
+    double sum = 0.0;
+    for (int c0 = 0; c0 < m; c0 += kEstChunk) {
+        const int cn = m - c0 < kEstChunk ? m - c0 : kEstChunk;
+        for (int q = tid; q < cn * 5; q += blockDim.x) {
+            const int j = q / 5, a = q - 5 * j;
+            int idx[5];
+            unpack_key(s[c0 + j] & kKeyMask, idx);
+            IV<double> ed = edge(g, a, level, idx[a]);
+            s_cen[q] = __dmul_rn(__dadd_rn(ed.lo, ed.hi), 0.5);
+            atomicMin(&s_lo[a], okey(ed.lo));
+            atomicMax(&s_hi[a], okey(ed.hi));
         }
-        t.votes = vmax;
-        t.n_hits = nh;
-        n_tracks[e] = round + 1;
+        __syncthreads();
+        if (tid < 5)
+            for (int j = 0; j < cn; j++) sum = __dadd_rn(sum, s_cen[5 * j + tid]);
+        __syncthreads();
+    }
+    if (tid < 5) {
+        apo_track &t = te[round];
+        const double lo_min = __longlong_as_double(okey_inv(s_lo[tid]));
+        const double hi_max = __longlong_as_double(okey_inv(s_hi[tid]));
+        t.p[tid] = __ddiv_rn(sum, (double)m);
+        t.w[tid] = __dmul_rn(__dsub_rn(hi_max, lo_min), 0.5);
+        if (tid == 0) {
+            t.votes = vmax;
+            t.n_hits = nh;
+            n_tracks[e] = round + 1;
+        }
     }
     if (round + 1 >= max_tracks) {
         if (tid == 0) done[e] = 1;

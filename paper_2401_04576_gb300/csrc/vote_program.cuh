@@ -68,7 +68,7 @@ template <typename T> __device__ __forceinline__ IV<T> atan_iv(IV<T> x, const Se
     IV<T> y = sqr(x);
     IV<T> h = cst<T>(k, C_ATAN0 + 7);
 #pragma unroll
-    for (int j = 6; j >= 0; j--) h = sub(cst<T>(k, C_ATAN0 + j), mul(y, h));
+    for (int j = 6; j >= 0; j--) h = sub(cst<T>(k, C_ATAN0 + j), mul_nn(h, y));   // y >= 0
     IV<T> a = mul(x, h);
     T rem = ru_mul(ru_pow17(mag(x)), cst<T>(k, C_ATAN0 + 8).hi);
     a = add(a, pm(rem));
@@ -84,13 +84,18 @@ __device__ __forceinline__ void sincos_iv(IV<T> d, IV<T> &s, IV<T> &c, const Ser
     T m = mag(d);
     if (!le(m, T(1))) { s = {T(-1), T(1)}; c = {T(-1), T(1)}; return; }
     IV<T> y = sqr(d);
-    IV<T> S = sub(one, mul(y, cst<T>(k, C_SIN3)));
+    IV<T> S = sub(one, mul_pp(y, cst<T>(k, C_SIN3)));
     T m2 = ru_mul(m, m), m4 = ru_mul(m2, m2);
-    IV<T> sv = add(mul(d, S), pm(ru_mul(ru_mul(m4, m), cst<T>(k, C_SIN5).hi)));
+    IV<T> sv = add(mul_nn(d, S), pm(ru_mul(ru_mul(m4, m), cst<T>(k, C_SIN5).hi)));
     IV<T> cv = add(sub(one, half(y)), pm(ru_mul(m4, cst<T>(k, C_COS4).hi)));
     s = clamp1(sv);
     c = clamp1(cv);
 }
+
+// Products use mul_nn (second operand >= 0) or mul_pp (both >= 0) where the program's
+// structure guarantees the sign: rho > 0 after the mirror and its guard, 1/N > 0, squares,
+// the drift d, Q, R, tan^2(tau), 1 - cos(2 Phi^Ax), 1 - d^2/6 for |d| <= 1.  They return
+// the same end points as the general product.
 
 // Everything of the program that does not depend on tan(lambda).
 template <typename T> struct Pre {
@@ -113,12 +118,12 @@ __device__ __forceinline__ Pre<T> prefix(const Cell<T> &c, const Hit<T> &h, cons
     IV<T> wn = sub(mul(Yw, c.C0), mul(Xw, c.S0));
     IV<T> V = sub(wn, c.D);
     // xi = rho (x^Ax - x_c, y^Ax - y_c); |xi| = rho R_i^Ax
-    IV<T> Xt = mul(c.W, wt);
-    IV<T> Xn = sub(mul(c.W, V), one);
+    IV<T> Xt = mul_nn(wt, c.W);
+    IV<T> Xn = sub(mul_nn(V, c.W), one);
     p.N = sqrti(add(sqr(Xt), sqr(Xn)));
     if (le0(p.N.lo)) { p.guard = true; return p; }
     // rho ((R_i^Ax)^2 - R^2)
-    p.G0 = add(mul(c.W, sqr(wt)), mul(V, sub(Xn, one)));
+    p.G0 = add(mul_pp(c.W, sqr(wt)), mul(V, sub(Xn, one)));
     // turning angle psi = phi_i^Ax - phi0 from tan(psi/2) = Xt / (N - Xn)
     IV<T> den = sub(p.N, Xn);
     if (le0(den.lo)) { p.guard = true; return p; }
@@ -130,17 +135,17 @@ __device__ __forceinline__ Pre<T> prefix(const Cell<T> &c, const Hit<T> &h, cons
     p.rcA = sub(mul(Xt, E2), mul(Xn, E1));
     p.Ninv = recip(p.N);
     // sin / cos of Phi^Ax and of its double
-    p.sPA = clamp1(mul(p.rsA, p.Ninv));
-    p.cPA = clamp1(mul(p.rcA, p.Ninv));
+    p.sPA = clamp1(mul_nn(p.rsA, p.Ninv));
+    p.cPA = clamp1(mul_nn(p.rcA, p.Ninv));
     IV<T> cos2 = clamp1(sub(sqr(p.cPA), sqr(p.sPA)));
     p.sin2 = clamp1(scale2(mul(p.sPA, p.cPA)));
     // tan(lambda)-free factors of Eqs. (ApproxPhi_b,c) divided through by R
-    p.dW = mul(h.d, c.W);
+    p.dW = mul_pp(h.d, c.W);
     p.Nh = half(sqr(p.Ninv));
     p.psi_sPA = mul(p.psi, p.sPA);
-    p.dW_cPA = mul(p.dW, p.cPA);
-    p.inner_e = sub(add(mul(p.psi, sub(one, cos2)), mul(sqr(p.psi), p.sin2)),
-                    mul(mul(h.d, p.dW), p.sin2));
+    p.dW_cPA = mul_nn(p.cPA, p.dW);
+    p.inner_e = sub(add(mul_nn(p.psi, sub(one, cos2)), mul_nn(p.sin2, sqr(p.psi))),
+                    mul_nn(p.sin2, mul_pp(h.d, p.dW)));
     p.psi_cos2 = mul(p.psi, cos2);
     p.onepN = add(one, p.N);
     return p;
@@ -153,14 +158,15 @@ __device__ __forceinline__ bool tail(const Pre<T> &p, IV<T> L, const Hit<T> &h, 
                                      const SeriesConsts &k) {
     const IV<T> one{T(1), T(1)};
     IV<T> L2 = sqr(L);
-    IV<T> P1e = neg(mul(mul(L, p.psi_sPA), p.Ninv));
-    IV<T> P1o = neg(mul(mul(L, p.dW_cPA), p.Ninv));
-    IV<T> P2e = mul(mul(L2, p.inner_e), p.Nh);
-    IV<T> P2o = mul(mul(p.dW, add(scale2(mul(L2, p.psi_cos2)), mul(add(p.N, mul(L2, p.onepN)), p.sin2))),
-                    p.Nh);
+    IV<T> P1e = neg(mul_nn(mul(L, p.psi_sPA), p.Ninv));
+    IV<T> P1o = neg(mul_nn(mul(L, p.dW_cPA), p.Ninv));
+    IV<T> P2e = mul_nn(mul_nn(p.inner_e, L2), p.Nh);
+    IV<T> P2o = mul_nn(mul_nn(add(scale2(mul_nn(p.psi_cos2, L2)), mul_nn(p.sin2, add(p.N, mul_pp(L2, p.onepN)))),
+                              p.dW),
+                       p.Nh);
     // delta = Phi - Phi^Ax, parts even / odd in the drift sign
-    IV<T> de = add(mul(P1e, h.t), mul(P2e, h.t2));
-    IV<T> dod = add(mul(P1o, h.t), mul(P2o, h.t2));
+    IV<T> de = add(mul(P1e, h.t), mul_nn(P2e, h.t2));
+    IV<T> dod = add(mul(P1o, h.t), mul_nn(P2o, h.t2));
     IV<T> dP = add(de, dod);
     IV<T> dM = sub(de, dod);
     IV<T> sd, cd;
@@ -168,25 +174,25 @@ __device__ __forceinline__ bool tail(const Pre<T> &p, IV<T> L, const Hit<T> &h, 
     IV<T> sP = clamp1(add(mul(p.sPA, cd), mul(p.cPA, sd)));
     IV<T> cP = clamp1(sub(mul(p.cPA, cd), mul(p.sPA, sd)));
     // u_d^2 (Eq. normudi)
-    IV<T> u2 = add(add(add(one, mul(scale2(h.t), mul(L, sP))), mul(L2, h.t2)), mul(sqr(cP), h.t2));
+    IV<T> u2 = add(add(add(one, mul(scale2(h.t), mul(L, sP))), mul_pp(L2, h.t2)), mul_pp(sqr(cP), h.t2));
     if (le0(u2.lo)) return true;
-    IV<T> Q = mul(h.d, recip(sqrti(u2)));
-    IV<T> Qct = mul(Q, mul(cP, h.t));
-    IV<T> LQ = mul(L, Q);
+    IV<T> Q = mul_pp(h.d, recip(sqrti(u2)));
+    IV<T> Qct = mul_nn(mul(cP, h.t), Q);
+    IV<T> LQ = mul_nn(L, Q);
     IV<T> LQrsA = mul(LQ, p.rsA);
-    IV<T> a2 = mul(W, sqr(Q));
-    IV<T> a5 = mul(W, sqr(mul(LQ, h.t)));
+    IV<T> a2 = mul_pp(W, sqr(Q));
+    IV<T> a5 = mul_pp(W, sqr(mul(LQ, h.t)));
     IV<T> t2x = scale2(h.t);
     bool vote = false;
 #pragma unroll
     for (int sg = 0; sg < 2; sg++) {
         IV<T> dl = sg == 0 ? dP : dM;
-        IV<T> sp = mul(add(p.psi, dl), R);                                  // s_perp
+        IV<T> sp = mul_nn(add(p.psi, dl), R);                                  // s_perp
         IV<T> zS = sg == 0 ? sub(mul(L, sp), Qct) : add(mul(L, sp), Qct);   // z^St - z_ref
         IV<T> rct = sg == 0 ? sub(mul(zS, p.rcA), LQrsA) : add(mul(zS, p.rcA), LQrsA);
         IV<T> a1 = sg == 0 ? scale2(Q) : neg(scale2(Q));
         IV<T> a3 = mul(t2x, rct);
-        IV<T> a4 = mul(W, sqr(mul(zS, h.t)));
+        IV<T> a4 = mul_pp(W, sqr(mul(zS, h.t)));
         IV<T> Arad = sub(sub(sub(add(a1, a2), a3), a4), a5);
         IV<T> G = sub(p.G0, Arad);
         vote = vote || contains0(G);
