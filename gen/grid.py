@@ -15,8 +15,10 @@ The omega axis is split into two equal halves [-1, -0.15] and [0.15, 1] so that 
 straddles omega = 0.
 
 This module only defines the grid: the finest-level cell edges (rounded to nearest once
-here) and a table of outward-rounded enclosures of sin/cos over every phi0 cell of every
-level.  Both are inputs shared by every consumer; none of the voting arithmetic is here.
+here), a table of outward-rounded enclosures of sin/cos over every phi0 cell of every
+level, and a table of sin/cos at every phi0 cell's centre (lo + hi) / 2 (libm values, for
+the midpoint form of the vote).  All are inputs shared by every consumer; none of the
+voting arithmetic is here.
 """
 from __future__ import annotations
 
@@ -39,6 +41,7 @@ class Grid:
     sincos: np.ndarray      # float64[sum_L bins[1] << L, 4]: (sin_lo, sin_hi, cos_lo, cos_hi)
     sincos_offset: np.ndarray   # int64[levels + 1]: first row of level L in `sincos`
     ranges: tuple = ()
+    sincos_mid: np.ndarray = None   # float64[rows, 2]: (sin c, cos c), c = phi0 cell centre
 
     def n_fine(self, a: int) -> int:
         return int(self.bins[a]) << self.levels
@@ -118,7 +121,7 @@ def make_grid(bins, levels: int, topk: int,
     g = Grid(bins=bins, levels=levels, topk=topk, lo_edge=lo_e, hi_edge=hi_e,
              sincos=np.zeros((0, 4)), sincos_offset=np.zeros(levels + 1, np.int64),
              ranges=(d0, phi0, omega_abs, z0, tanl))
-    rows, offs, parent = [], [], None
+    rows, mids, offs, parent = [], [], [], None
     off = 0
     for L in range(levels + 1):
         n = int(bins[1]) << L
@@ -132,11 +135,14 @@ def make_grid(bins, levels: int, topk: int,
             c_hi = np.minimum(c_hi, p[:, 3])
         tab = np.stack([s_lo, s_hi, c_lo, c_hi], axis=1)
         rows.append(tab)
+        c = (a + b) * 0.5
+        mids.append(np.stack([np.sin(c), np.cos(c)], axis=1))
         offs.append(off)
         off += n
         parent = tab
     g.sincos = np.ascontiguousarray(np.concatenate(rows, axis=0))
     g.sincos_offset = np.asarray(offs, np.int64)
+    g.sincos_mid = np.ascontiguousarray(np.concatenate(mids, axis=0))
     return g
 
 

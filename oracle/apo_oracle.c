@@ -28,6 +28,7 @@
 #define SQRT sqrt
 #define NEXTUP(x) nextafter((x), INFINITY)
 #include "vote_program.inc"
+#include "midpoint.inc"
 #undef REAL
 #undef SFX
 #undef SQRT
@@ -59,6 +60,8 @@ typedef struct {
     const double *hi_edge[5];
     const double *sincos;         /* rows of (sin lo, sin hi, cos lo, cos hi) */
     const int64_t *sincos_offset; /* first row of level L */
+    const double *sincos_mid;     /* rows of (sin, cos) of each phi0 cell's centre, same
+                                     offsets; needed by the midpoint form only */
 } or_grid;
 
 /* One cell of `level` as 6 FP64 intervals: D, S0, C0, W, Z, L (lo, hi each). */
@@ -109,7 +112,7 @@ static int vote_pair(const double c[12], const double h[9], int prec, double *ou
 /* ------------------------------------------------------------------------------------ */
 /* Exported: one pair                                                                    */
 /* ------------------------------------------------------------------------------------ */
-int or_vote_pair(const double cell[12], const double hit[9], int prec, double out[5]) {
+int or_vote_pair(const double cell[12], const double hit[9], int prec, double out[9]) {
     int old = fegetround();
     fesetround(FE_DOWNWARD);
     int v = vote_pair(cell, hit, prec, out);
@@ -117,6 +120,15 @@ int or_vote_pair(const double cell[12], const double hit[9], int prec, double ou
     return v;
 }
 
+/* One pair in the midpoint form: scm = sin, cos of the phi0 centre; out[7] as in
+ * mid_vote_program. */
+int or_vote_pair_mid(const double cell[12], const double scm[2], const double hit[9], double out[7]) {
+    int old = fegetround();
+    fesetround(FE_DOWNWARD);
+    int v = mid_vote_program(cell, scm, hit, out);
+    fesetround(old);
+    return v;
+}
 
 /* ------------------------------------------------------------------------------------ */
 /* Cell keys                                                                             */
@@ -130,8 +142,16 @@ static uint64_t idx_to_key(const int32_t idx[5]) {
     return k;
 }
 
+/* sin, cos of the phi0 centre of cell idx at `level` */
+static void centre_sincos(const or_grid *g, int level, const int32_t idx[5], double scm[2]) {
+    const double *r = g->sincos_mid + 2 * (g->sincos_offset[level] + idx[1]);
+    scm[0] = r[0];
+    scm[1] = r[1];
+}
+
 /* votes of n cells of `level` (given by key) for one event's hits: Eq. (ApoVote) summed
- * over hits, one vote per (cell, hit) whichever drift sign passes (Section 3.1). */
+ * over hits, one vote per (cell, hit) whichever drift sign passes (Section 3.1).
+ * prec 0: FP64 intervals, 1: FP32 intervals, 3: the FP64 midpoint form. */
 void or_vote_cells(const or_grid *g, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
                    const double *drift, int32_t level, int32_t prec, const uint64_t *keys,
                    int64_t n, int32_t *votes) {
@@ -143,12 +163,14 @@ void or_vote_cells(const or_grid *g, const or_wires *w, int32_t n_hits, const in
         for (int64_t j = 0; j < n; j++) {
             int32_t idx[5];
             double c[12], h[9];
+            double scm[2] = {0, 0};
             key_to_idx(keys[j], idx);
             cell_intervals(g, level, idx, c);
+            if (prec == 3) centre_sincos(g, level, idx, scm);
             int32_t v = 0;
             for (int32_t i = 0; i < n_hits; i++) {
                 hit_constants(w, wire_id[i], drift[i], h);
-                v += vote_pair(c, h, prec, NULL);
+                v += prec == 3 ? mid_vote_program(c, scm, h, NULL) : vote_pair(c, h, prec, NULL);
             }
             votes[j] = v;
         }
@@ -242,7 +264,7 @@ static void estimate(const or_grid *g, int level, const uint64_t *keys, const in
 /* Whole coarse-to-fine search for one event (configuration of the grid: bins, levels,
  * top-K).  Level 0 is the full grid; at each level the K best cells survive and are
  * bisected along every axis; the last level's maximum-vote cells give the estimate.
- * prec[L] selects FP64 (0) or FP32 (1) intervals at level L.
+ * prec[L] selects FP64 (0) or FP32 (1) intervals or the FP64 midpoint form (3) at level L.
  * Trace outputs (may be NULL): frontier keys / votes kept after level L, K per level,
  * and the last level's votes (K * 32). */
 int or_solve_event(const or_grid *g, const or_wires *w, int32_t n_hits, const int32_t *wire_id,

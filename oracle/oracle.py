@@ -22,7 +22,8 @@ class OrWires(C.Structure):
 class OrGrid(C.Structure):
     _fields_ = [("bins", C.c_int32 * 5), ("levels", C.c_int32), ("topk", C.c_int32),
                 ("lo_edge", C.POINTER(C.c_double) * 5), ("hi_edge", C.POINTER(C.c_double) * 5),
-                ("sincos", C.POINTER(C.c_double)), ("sincos_offset", C.POINTER(C.c_int64))]
+                ("sincos", C.POINTER(C.c_double)), ("sincos_offset", C.POINTER(C.c_int64)),
+                ("sincos_mid", C.POINTER(C.c_double))]
 
 
 def lib():
@@ -33,6 +34,8 @@ def lib():
         dp, ip, up = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_uint64)
         L.or_vote_pair.argtypes = [dp, dp, C.c_int, dp]
         L.or_vote_pair.restype = C.c_int
+        L.or_vote_pair_mid.argtypes = [dp, dp, dp, dp]
+        L.or_vote_pair_mid.restype = C.c_int
         L.or_vote_cells.argtypes = [C.POINTER(OrGrid), C.POINTER(OrWires), C.c_int32, ip, dp,
                                     C.c_int32, C.c_int32, up, C.c_int64, ip]
         L.or_vote_cells.restype = None
@@ -86,6 +89,9 @@ class Tables:
         self._keep += [sc, so]
         g.sincos = _p(sc, C.c_double)
         g.sincos_offset = _p(so, C.c_int64)
+        sm = np.ascontiguousarray(grid.sincos_mid, np.float64)
+        self._keep.append(sm)
+        g.sincos_mid = _p(sm, C.c_double)
         self.cw, self.cg = w, g
 
 
@@ -99,11 +105,24 @@ def num_threads() -> int:
 
 def vote_pair(cell12, hit9, prec: int = 0):
     """Vote (0/1) of one (cell, hit) pair and the evaluated intervals
-    (G+ lo, G+ hi, G- lo, G- hi, guard flag)."""
+    (G+ lo, G+ hi, G- lo, G- hi, guard flag, delta+ lo, delta+ hi, delta- lo, delta- hi),
+    delta = Phi - Phi^Ax of each drift sign."""
     c = np.ascontiguousarray(cell12, np.float64)
     h = np.ascontiguousarray(hit9, np.float64)
-    out = np.zeros(5)
+    out = np.zeros(9)
     v = lib().or_vote_pair(_p(c, C.c_double), _p(h, C.c_double), int(prec), _p(out, C.c_double))
+    return int(v), out
+
+
+def vote_pair_mid(cell12, scm2, hit9):
+    """Midpoint-form vote (0/1) of one (cell, hit) pair and (G+ lo, G+ hi, G- lo, G- hi,
+    guard flags, d^Ax+, d^Ax-); scm2 = sin, cos of the phi0 centre."""
+    c = np.ascontiguousarray(cell12, np.float64)
+    m = np.ascontiguousarray(scm2, np.float64)
+    h = np.ascontiguousarray(hit9, np.float64)
+    out = np.zeros(7)
+    v = lib().or_vote_pair_mid(_p(c, C.c_double), _p(m, C.c_double), _p(h, C.c_double),
+                               _p(out, C.c_double))
     return int(v), out
 
 
@@ -142,6 +161,11 @@ def cell12(grid, level: int, idx5) -> np.ndarray:
     sc = grid.sincos[grid.sincos_offset[level] + idx5[1]]
     return np.array([lo[0], hi[0], sc[0], sc[1], sc[2], sc[3], lo[2], hi[2], lo[3], hi[3],
                      lo[4], hi[4]], np.float64)
+
+
+def scm2(grid, level: int, idx5) -> np.ndarray:
+    """sin, cos of the phi0 centre of a cell (from the grid's centre table)."""
+    return np.array(grid.sincos_mid[grid.sincos_offset[level] + idx5[1]], np.float64)
 
 
 def vote_cells(tab: Tables, wire_id, drift, level: int, keys, prec: int = 0) -> np.ndarray:

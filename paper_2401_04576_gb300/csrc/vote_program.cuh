@@ -139,13 +139,16 @@ __device__ __forceinline__ Pre<T> prefix(const Cell<T> &c, const Hit<T> &h, cons
     p.cPA = clamp1(mul_nn(p.rcA, p.Ninv));
     IV<T> cos2 = clamp1(sub(sqr(p.cPA), sqr(p.sPA)));
     p.sin2 = clamp1(scale2(mul(p.sPA, p.cPA)));
-    // tan(lambda)-free factors of Eqs. (ApproxPhi_b,c) divided through by R
+    // tan(lambda)-free factors of Eqs. (ApproxPhi_b,c), numerator and denominator divided
+    // by R^2: Phi1 = -lambda (psi sin Phi^Ax + (d rho) cos Phi^Ax) / N and
+    // Phi2 = [lambda^2 (psi (1 - cos 2Phi^Ax) + psi^2 sin 2Phi^Ax - (d rho)^2 sin 2Phi^Ax)
+    //         + (d rho) (2 lambda^2 psi cos 2Phi^Ax + (N + lambda^2 (1 + N)) sin 2Phi^Ax)] / (2 N^2)
     p.dW = mul_pp(h.d, c.W);
     p.Nh = half(sqr(p.Ninv));
     p.psi_sPA = mul(p.psi, p.sPA);
     p.dW_cPA = mul_nn(p.cPA, p.dW);
     p.inner_e = sub(add(mul_nn(p.psi, sub(one, cos2)), mul_nn(p.sin2, sqr(p.psi))),
-                    mul_nn(p.sin2, mul_pp(h.d, p.dW)));
+                    mul_nn(p.sin2, sqr(p.dW)));
     p.psi_cos2 = mul(p.psi, cos2);
     p.onepN = add(one, p.N);
     return p;

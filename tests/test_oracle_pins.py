@@ -180,6 +180,39 @@ def test_interval_encloses_point_model(wires, events):
     assert n > 400
 
 
+def test_phase_expansion_matches_paper_form(wires, events):
+    """On a voxel shrunk to a point, the interval program's phase corrections
+    delta+- = Phi - Phi^Ax (its rescaled form of Eqs. ApproxPhi_b,c) are thin and contain
+    Phi1 tan(tau) + Phi2 tan^2(tau) of the point model, which writes Eq. (ApproxPhi_c) as
+    printed, for each drift sign.  The G enclosure tests above cannot see an error in a
+    small term here: the vote program joins both signs' phases before sin/cos."""
+    rng = np.random.default_rng(15)
+    n = 0
+    for e in range(events.n_events):
+        p = np.array(events.tracks[e][0].params)
+        for h in events.hit_truth[e]:
+            pt = p + rng.normal(0, 1, 5) * np.array([1e-3, 3e-2, 1e-2, 1e-2, 3e-2])
+            s0, c0 = np.sin(pt[1]), np.cos(pt[1])
+            cell = np.array([pt[0], pt[0], s0, s0, c0, c0, pt[2], pt[2], pt[3], pt[3],
+                             pt[4], pt[4]])
+            _, out = O.vote_pair(cell, O.hit9(wires, h.wire, h.drift), 0)
+            if out[4]:
+                continue
+            wv = _wire5(wires, h.wire)
+            for sg in (0, 1):
+                d_st = (1 - 2 * sg) * h.drift * (1 if pt[2] > 0 else -1)
+                prm, wm, dm = (tuple(pt), wv, d_st) if pt[2] > 0 else pm.mirror(tuple(pt), wv, d_st)
+                a = pm.ax_quantities(prm, wm, prm[3])
+                Phi = pm.phi_approx(prm, wm, dm, prm[3])[0]
+                delta = Phi - a["PhiA"]
+                lo, hi = out[5 + 2 * sg], out[6 + 2 * sg]
+                tol = 1e-14 + 1e-12 * abs(delta)
+                assert lo - tol <= delta <= hi + tol, (e, h.wire, sg, lo, delta, hi)
+                assert hi - lo <= 1e-12 * (1 + abs(delta)), (lo, hi)
+                n += 1
+    assert n > 150
+
+
 def test_interval_encloses_point_model_wide_cells(wires, events):
     """Same enclosure on coarse-size cells (random points inside a level-2 cell)."""
     rng = np.random.default_rng(6)
