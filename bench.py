@@ -56,6 +56,18 @@ def coarse_kernel_ops(n_parent: int, n_prefix: int, n_tail: int) -> int:
     return n_parent * OPS_FULL + n_prefix * OPS_PREFIX + n_tail * OPS_TAIL
 
 
+def coarse_linear_index(g, params) -> int:
+    """Level-0 linear index (d0 fastest, tan(lambda) slowest) of the cell holding params."""
+    lin, mul = 0, 1
+    for a in range(5):
+        n = int(g.bins[a])
+        edges = g.lo_edge[a][::1 << g.levels]
+        i = int(np.clip(np.searchsorted(edges, params[a], side="right") - 1, 0, n - 1))
+        lin += i * mul
+        mul *= n
+    return lin
+
+
 def pairs_decided(n_hits: np.ndarray, n_coarse: int, levels: int, topk: int) -> float:
     """(cell, hit) pairs whose vote one step decides: all coarse cells and the topk * 32
     children of every bisection level, times the hits of each event."""
@@ -373,6 +385,50 @@ def run_apo(args) -> None:
                          "fp32_parent": p32, "fp32_prefix": q32, "fp32_tail": t32c,
                          "launches": n_launch}}
 
+    # midpoint form (Section 3.1: the quantities of d^Ax at the voxel centre): coarse launch
+    # time against the interval program's, solve throughput, and how its votes differ
+    midpoint = None
+    if not args.no_mid:
+        vmid = torch.empty_like(votes)
+        mms = []
+        for _ in range(max(2, args.steps)):
+            flush.fill_(1)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            apo.vote(geom, hits, precision=apo.F64_MID, out=vmid, workspace=ws, stream=stream)
+            s1.record(stream)
+            s1.synchronize()
+            mms.append(s0.elapsed_time(s1) / n_launch)
+        m_ms = statistics.mean(mms)
+        diff = vmid - votes
+        ncell = diff.numel()
+        truth_lin = np.array([coarse_linear_index(g, ev.tracks[e][0].params) for e in range(ev.n_events)])
+        rows = torch.arange(ev.n_events, device="cuda")
+        tl = torch.as_tensor(truth_lin, device="cuda")
+        t64 = votes[rows, tl].to(torch.int64)
+        tmid = vmid[rows, tl].to(torch.int64)
+        opts_mid = apo.solve_opts(precision=[apo.F64_MID] * (lv + 1))
+        msm = timed(opts_mid, max(2, args.steps), 1)
+        tm = reduce_max(sum(msm) / len(msm), world)
+        tracks_mid = apo.tracks_to_numpy(tracks, ev.n_events).copy()
+        dpm = np.abs(tracks_mid["p"][:, 0, :] - tracks64["p"][:, 0, :])
+        midpoint = {
+            "precision": "midpoint form at every level (FP64 point part, FP64 interval part)",
+            "coarse_launch_ms": m_ms, "coarse_launch_ms_fp64_intervals": k_ms,
+            "coarse_speedup_vs_fp64_intervals": k_ms / m_ms,
+            "ms_per_step": tm, "value": pairs * world / (tm * 1e-3), "unit": "evals/s",
+            "events_per_s": ev.n_events * world / (tm * 1e-3),
+            "coarse_cells_differing": (diff != 0).sum().item() / ncell,
+            "coarse_cells_more_votes": (diff > 0).sum().item() / ncell,
+            "coarse_cells_fewer_votes": (diff < 0).sum().item() / ncell,
+            "coarse_mean_abs_vote_difference": diff.abs().sum(dtype=torch.int64).item() / ncell,
+            "truth_cell_votes_lost_mean": float((t64 - tmid).clamp(min=0).float().mean().item()),
+            "truth_cell_events_losing_votes": float(((tmid < t64).float().mean()).item()),
+            "final_within_one_cell_of_fp64": float(np.mean(np.all(dpm <= fine_w[None, :] * (1 + 1e-9),
+                                                                  axis=1))),
+        }
+        del vmid, diff
+
     # end to end through the host-buffer entry point (pinned host inputs, tracks back)
     off_h = torch.from_numpy(np.ascontiguousarray(ev.offsets, np.int32)).pin_memory()
     wid_h = torch.from_numpy(np.ascontiguousarray(ev.wire_id, np.int32)).pin_memory()
@@ -417,7 +473,10 @@ def run_apo(args) -> None:
         "clocks": clocks,
         "roofline": roofline,
     }
+    if midpoint is not None:
+        line["midpoint"] = midpoint
     if not args.no_serve:
+        serve_sweep(geom, ev, [1000], 0.25)   # warm-up pass (first-use costs), discarded
         sweep = serve_sweep(geom, ev, [1000, 2000, 5000, 10000, 20000, 50000], args.serve_seconds)
         line["serving"] = {"workload": "Poisson arrivals of the batch's events into apo_serve "
                                        "(64-event slots, 4 slots), FP32 levels 0-4 / FP64 5-6",
@@ -471,6 +530,7 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-mid", action="store_true", help="skip the midpoint-form leg")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--case", default=None,
                     choices=["coarse-f64", "coarse-f32", "solve-f64", "solve-f32", "solve-bulk"],

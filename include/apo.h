@@ -46,8 +46,13 @@ typedef enum {
 /* interval precision of one level.  APO_F64: FP64 intervals.  APO_F32: FP32 intervals.
  * APO_F64_FILTERED: FP64 intervals evaluated only where the FP32 program votes first (FP32
  * intervals contain the FP64 ones, so the votes are exactly APO_F64's; it pays only where
- * most FP32 votes are "no"). */
-enum { APO_F64 = 0, APO_F32 = 1, APO_F64_FILTERED = 2 };
+ * most FP32 votes are "no").
+ * APO_F64_MID: the midpoint form of Section 3.1 (last paragraph): the quantities that build
+ * d^Ax (Eq. defdiAX_b) are evaluated at the voxel centre in round-to-nearest FP64, and only
+ * (x^Ax - x_c)^2 + (y^Ax - y_c)^2 - (R + d^Ax)^2 keeps the voxel's FP64 intervals.  Faster
+ * and not sound (a voxel holding the solution can lose a vote).  Needs the grid's
+ * sincos_mid table. */
+enum { APO_F64 = 0, APO_F32 = 1, APO_F64_FILTERED = 2, APO_F64_MID = 3 };
 
 #define APO_HIT_CAP 256      /* hits per event */
 #define APO_MAX_LEVELS 8     /* bisection levels after the coarse level */
@@ -69,7 +74,9 @@ typedef struct {
  * level-L cell idx spans [lo_edge[idx << (levels-L)], hi_edge[((idx+1) << (levels-L)) - 1]].
  * No omega cell may contain 0.  sincos: host array of rows (sin lo, sin hi, cos lo,
  * cos hi), outward enclosures of sin/cos over each phi0 cell, level by level (level L
- * starts at row sum_{l<L} bins[1] << l).  All copied.  Limits: bins[a] << levels <= 1024,
+ * starts at row sum_{l<L} bins[1] << l).  sincos_mid (may be NULL): rows (sin c, cos c) at
+ * each phi0 cell's centre c = (lo + hi) / 2, same row order; needed by APO_F64_MID only.
+ * All copied.  Limits: bins[a] << levels <= 1024,
  * bins[0] * bins[3] <= 256, bins[4] <= 32,
  * levels <= APO_MAX_LEVELS, 1 <= topk, topk * 32 <= 4096, topk <= number of level-0 cells. */
 typedef struct {
@@ -79,6 +86,7 @@ typedef struct {
     const double *lo_edge[5];
     const double *hi_edge[5];
     const double *sincos;
+    const double *sincos_mid;
 } apo_grid;
 
 /* A batch of events in CSR form; DEVICE arrays owned by the caller.  Event e owns hits

@@ -16,7 +16,8 @@ extern "C" {
 /* apo_vote on the full level-0 grid that also counts the work the coarse kernel does:
  * counts_out (device, 8 x uint64, zeroed by the call) receives FP64 parent-cell
  * evaluations, FP64 per-(cell, hit) prefix evaluations, FP64 tan(lambda) tail evaluations,
- * the number of coarse-kernel launches, then the same three FP32 counts. */
+ * the number of coarse-kernel launches, then the same three FP32 counts.  For APO_F64_MID
+ * slots 1 and 2 count the midpoint form's per-(cell, hit) prefixes and tan(lambda) tails. */
 int apo_diag_vote_coarse_counts(const apo_geometry *geom, const apo_hits *hits, int32_t precision,
                                 int32_t *votes_out, unsigned long long *counts_out,
                                 void *workspace, size_t workspace_bytes, void *stream);

@@ -14,7 +14,7 @@ import numpy as np
 from . import build as _build
 
 APO_OK, APO_EINVAL, APO_ENOMEM, APO_ECUDA, APO_ETIMEOUT, APO_EBUSY = 0, -1, -2, -3, -4, -5
-F64, F32, F64_FILTERED = 0, 1, 2
+F64, F32, F64_FILTERED, F64_MID = 0, 1, 2, 3
 HIT_CAP = 256
 MAX_LEVELS = 8
 MAX_TRACKS = 8
@@ -33,7 +33,8 @@ class ApoWires(C.Structure):
 
 class ApoGrid(C.Structure):
     _fields_ = [("bins", C.c_int32 * 5), ("levels", C.c_int32), ("topk", C.c_int32),
-                ("lo_edge", _dp * 5), ("hi_edge", _dp * 5), ("sincos", _dp)]
+                ("lo_edge", _dp * 5), ("hi_edge", _dp * 5), ("sincos", _dp),
+                ("sincos_mid", _dp)]
 
 
 class ApoHits(C.Structure):
@@ -162,6 +163,8 @@ class Geometry:
         g.levels = int(grid.levels)
         g.topk = int(grid.topk)
         g.sincos = dp(grid.sincos)
+        mid = getattr(grid, "sincos_mid", None)
+        g.sincos_mid = dp(mid) if mid is not None else None
         h = C.c_void_p()
         _check(lib().apo_geometry_create(C.byref(w), C.byref(g), C.byref(h)))
         self.handle = h

@@ -102,6 +102,15 @@ template <typename P> P *at(void *ws, size_t off) {
     return reinterpret_cast<P *>(static_cast<unsigned char *>(ws) + off);
 }
 
+// A level precision the geometry can evaluate.
+int check_precision(const apo_geometry *g, int p, const char *what) {
+    if (p != APO_F64 && p != APO_F32 && p != APO_F64_FILTERED && p != APO_F64_MID)
+        return fail(APO_EINVAL, "bad %s", what);
+    if (p == APO_F64_MID && !g->dg.sincos_mid)
+        return fail(APO_EINVAL, "APO_F64_MID needs the grid's sincos_mid table");
+    return APO_OK;
+}
+
 int check_geom(const apo_geometry *g) {
     if (!g) return fail(APO_EINVAL, "geometry is NULL");
     int dev = -1;
@@ -217,6 +226,7 @@ int apo_geometry_create(const apo_wires *w, const apo_grid *gr, apo_geometry **o
         rows += (long long)gr->bins[1] << L;
     }
     if (rc == APO_OK) rc = upload(gr->sincos, (size_t)rows * 4, &d.sincos);
+    if (rc == APO_OK && gr->sincos_mid) rc = upload(gr->sincos_mid, (size_t)rows * 2, &d.sincos_mid);
     if (rc == APO_OK) {
         SeriesConsts *dk = nullptr;
         cudaError_t e = cudaMalloc(&dk, sizeof(SeriesConsts));
@@ -264,8 +274,7 @@ int apo_vote(const apo_geometry *g, const apo_hits *hits, const uint64_t *cell_k
              void *ws, size_t ws_bytes, void *stream) {
     int rc;
     if ((rc = check_geom(g)) || (rc = check_hits(hits))) return rc;
-    if (precision != APO_F64 && precision != APO_F32 && precision != APO_F64_FILTERED)
-        return fail(APO_EINVAL, "bad precision");
+    if ((rc = check_precision(g, precision, "precision"))) return rc;
     if (level < 0 || level > g->dg.levels) return fail(APO_EINVAL, "level out of range");
     if (!votes_out) return fail(APO_EINVAL, "votes_out is NULL");
     if (!cell_keys && (level != 0 || n_cells_per_event != g->n_coarse))
@@ -361,8 +370,7 @@ int validate_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_
     const int lv = g->dg.levels;
     if (lv < 1) return fail(APO_EINVAL, "apo_solve_batch needs levels >= 1");
     for (int i = 0; i <= lv; i++)
-        if (o->precision[i] != APO_F64 && o->precision[i] != APO_F32 && o->precision[i] != APO_F64_FILTERED)
-            return fail(APO_EINVAL, "bad precision[%d]", i);
+        if ((rc = check_precision(g, o->precision[i], "precision[level]"))) return rc;
     if (o->max_tracks < 1 || o->max_tracks > APO_MAX_TRACKS)
         return fail(APO_EINVAL, "max_tracks must be in [1, %d]", APO_MAX_TRACKS);
     if (!(o->mask_sigma >= 0.0 && o->mask_sigma < 1.0)) return fail(APO_EINVAL, "mask_sigma out of range");
@@ -564,8 +572,7 @@ int apo_diag_vote_coarse_counts(const apo_geometry *g, const apo_hits *hits, int
     int rc;
     if ((rc = check_geom(g)) || (rc = check_hits(hits))) return rc;
     if (!votes_out || !counts) return fail(APO_EINVAL, "votes_out / counts_out is NULL");
-    if (precision != APO_F64 && precision != APO_F32 && precision != APO_F64_FILTERED)
-        return fail(APO_EINVAL, "bad precision");
+    if ((rc = check_precision(g, precision, "precision"))) return rc;
     Layout L;
     if ((rc = check_ws(g, hits->n_events, ws, ws_bytes, L))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

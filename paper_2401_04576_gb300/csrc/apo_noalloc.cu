@@ -77,10 +77,13 @@ extern "C" int apo_vote_coarse_noalloc(const apo_geometry *g, const apo_hits *hi
     }
     if (hits->n_events > 0 && (!hits->offsets || !hits->wire_id || !hits->drift))
         return err(APO_EINVAL, "hits arrays must be non-NULL");
-    if (precision != APO_F64 && precision != APO_F32 && precision != APO_F64_FILTERED)
+    if (precision != APO_F64 && precision != APO_F32 && precision != APO_F64_FILTERED &&
+        precision != APO_F64_MID)
         return err(APO_EINVAL, "bad precision");
     int gdev = -1;
     const DevGeom *dg = geometry_device_tables(g, &gdev);
+    if (precision == APO_F64_MID && !dg->sincos_mid)
+        return err(APO_EINVAL, "APO_F64_MID needs the grid's sincos_mid table");
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != gdev)
         return err(APO_EINVAL, "geometry is not on the current device");

@@ -374,6 +374,185 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Midpoint-form voting (APO_F64_MID, Section 3.1's variant with the quantities of d^Ax at
+// the voxel centre).  Coarse grid: the same block / thread layout as k_vote_coarse, the
+// tan(lambda)-free part shared by the tan(lambda) bins, bit-sliced counters; there is no
+// parent-cell test, because the midpoint form is not inclusion-isotonic (a parent's
+// centre says nothing about its children's centres).
+// ---------------------------------------------------------------------------------------
+struct MidSmem {
+    static constexpr size_t hits = 0;
+    static constexpr size_t hist = kHitCap * 80;
+    static constexpr size_t bar = hist + ((kHistBins * 4 + 15) & ~size_t(15));
+    static constexpr size_t Lc = bar + 16;
+    __host__ __device__ static size_t total(int Bl) { return Lc + 8 * Bl; }
+};
+
+__global__ void __launch_bounds__(256)
+k_vote_coarse_mid(DevGeom g, int ev0, const HitRecD *hd, const int32_t *n_hits,
+                  const uint32_t *active, int32_t *votes, uint32_t *hist, unsigned *status,
+                  unsigned long long *ctr) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int Bd = g.bins[0], Bp = g.bins[1], Bw = g.bins[2], Bz = g.bins[3], Bl = g.bins[4];
+    const int nthr = Bd * Bz;
+    const int e = blockIdx.y, ev = ev0 + e;
+    const int p = blockIdx.x % Bp, w = blockIdx.x / Bp;
+    const int tid = threadIdx.x;
+    unsigned char *hs = smem + MidSmem::hits;
+    uint32_t *hist_s = reinterpret_cast<uint32_t *>(smem + MidSmem::hist);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + MidSmem::bar);
+    double *Lc = reinterpret_cast<double *>(smem + MidSmem::Lc);
+
+    int nh = n_hits[ev];
+    if (nh < 0) nh = 0;
+    for (int i = tid; i < kHistBins; i += nthr) hist_s[i] = 0;
+    for (int l = tid; l < Bl; l += nthr) Lc[l] = pt::centre(edge(g, 4, 0, l));
+    bool ok = stage_to_smem(hs, hd + (long long)ev * kHitCap, (unsigned)nh * 80u, nullptr, nullptr, 0u,
+                            bar, status);
+    __syncthreads();
+    if (!ok) nh = 0;
+
+    const int d = tid % Bd, z = tid / Bd;
+    Cell<double> c{edge(g, 0, 0, d), sin_phi0(g, 0, p), cos_phi0(g, 0, p), edge(g, 2, 0, w),
+                   edge(g, 3, 0, z), {0.0, 0.0}};
+    MidCentre m;
+    sincos_phi0_centre(g, 0, p, m.S0, m.C0);
+    m.D = pt::centre(c.D);
+    m.W = pt::centre(c.W);
+    m.Z = pt::centre(c.Z);
+    const bool mir = mirror_cell(c);
+    if (mir) { m.D = -m.D; m.S0 = -m.S0; m.W = -m.W; }
+    const bool wguard = le0(c.W.lo);
+    const unsigned all = Bl >= 32 ? 0xffffffffu : ((1u << Bl) - 1u);
+    const uint32_t *act = active ? active + (long long)ev * 8 : nullptr;
+    uint32_t pl[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) pl[q] = 0u;
+    auto add_votes = [&](uint32_t mk) {
+#pragma unroll
+        for (int q = 0; q < 9; q++) {
+            const uint32_t cy = pl[q] & mk;
+            pl[q] ^= mk;
+            mk = cy;
+        }
+    };
+    unsigned n_pre = 0, n_tail = 0;
+    for (int h = 0; h < nh; h++) {
+        if (act && !((act[h >> 5] >> (h & 31)) & 1u)) continue;
+        if (wguard) { add_votes(all); continue; }
+        Hit<double> hh = load_hit<double>(hs + h * 80);
+        if (mir) mirror_hit(hh);
+        MidPre pre = mid_prefix(c, m, hh);
+        n_pre++;
+        if (pre.guard) { add_votes(all); continue; }
+        uint32_t v = 0;
+#pragma unroll 1
+        for (int l = 0; l < Bl; l++)
+            if (mid_tail(pre, Lc[l], hh, c.W)) v |= 1u << l;
+        n_tail += Bl;
+        add_votes(v);
+    }
+    const long long ncell = (long long)Bd * Bp * Bw * Bz * Bl;
+    int32_t *vo = votes + (long long)e * ncell;
+    for (int l = 0; l < Bl; l++) {
+        int v = 0;
+#pragma unroll
+        for (int q = 0; q < 9; q++) v |= (int)((pl[q] >> l) & 1u) << q;
+        long long lin = d + (long long)Bd * (p + (long long)Bp * (w + (long long)Bw * (z + (long long)Bz * l)));
+        vo[lin] = v;
+        atomicAdd(&hist_s[v], 1u);
+    }
+    __syncthreads();
+    for (int i = tid; i < kHistBins; i += nthr)
+        if (hist_s[i]) atomicAdd(&hist[(long long)e * kHistBins + i], hist_s[i]);
+    if (ctr) {   // work counters (diagnostics): midpoint prefixes / tails in the FP64 slots
+        unsigned long long v[2] = {n_pre, n_tail};
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            unsigned long long x = v[i];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if ((tid & 31) == 0 && x) atomicAdd(&ctr[1 + i], x);
+        }
+    }
+}
+
+// Midpoint form on explicit cells: given keys, or the 32 children of each parent key (in
+// the order of k_vote_cells).  One cell per thread, all hits of its event.
+__global__ void __launch_bounds__(256)
+k_vote_cells_mid(DevGeom g, const HitRecD *hd, const int32_t *n_hits, const uint32_t *active, int level,
+                 const uint64_t *keys, const uint64_t *parents, long long n_per_ev, uint64_t *out_keys,
+                 int32_t *out_votes, unsigned *status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char *hs = smem;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kHitCap * 80);
+    const int ev = blockIdx.y;
+    int nh = n_hits[ev];
+    if (nh < 0) nh = 0;
+    bool ok = stage_to_smem(hs, hd + (long long)ev * kHitCap, (unsigned)nh * 80u, nullptr, nullptr, 0u,
+                            bar, status);
+    __syncthreads();
+    if (!ok) nh = 0;
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_per_ev) return;
+    uint64_t key;
+    if (parents) {
+        uint64_t pk = parents[(long long)ev * (n_per_ev / 32) + j / 32];
+        int idx[5], b = (int)(j % 32);
+        unpack_key(pk, idx);
+#pragma unroll
+        for (int a = 0; a < 5; a++) idx[a] = 2 * idx[a] + ((b >> a) & 1);
+        key = pack_key(idx);
+    } else {
+        key = keys[(long long)ev * n_per_ev + j];
+    }
+    int idx[5];
+    unpack_key(key, idx);
+    const long long o = (long long)ev * n_per_ev + j;
+    bool valid = true;
+#pragma unroll
+    for (int a = 0; a < 5; a++) valid = valid && idx[a] < (g.bins[a] << level);
+    if (!valid) {   // a key outside the grid of this level: no lookup, vote count -1
+        out_votes[o] = -1;
+        if (out_keys) out_keys[o] = key;
+        return;
+    }
+    const IV<double> Le = edge(g, 4, level, idx[4]);
+    const Cell<double> c{edge(g, 0, level, idx[0]), sin_phi0(g, level, idx[1]), cos_phi0(g, level, idx[1]),
+                         edge(g, 2, level, idx[2]), edge(g, 3, level, idx[3]), Le};
+    MidCentre m;
+    sincos_phi0_centre(g, level, idx[1], m.S0, m.C0);
+    m.D = pt::centre(c.D);
+    m.W = pt::centre(c.W);
+    m.Z = pt::centre(c.Z);
+    const double Lm = pt::centre(Le);
+    const uint32_t *act = active ? active + (long long)ev * 8 : nullptr;
+    int v = 0;
+    for (int h = 0; h < nh; h++) {
+        if (act && !((act[h >> 5] >> (h & 31)) & 1u)) continue;
+        v += mid_vote_pair(c, m, Lm, load_hit<double>(hs + h * 80)) ? 1 : 0;
+    }
+    out_votes[o] = v;
+    if (out_keys) out_keys[o] = key;
+}
+
+static void launch_coarse_mid(const DevGeom &g, int ev0, int n_ev, const HitRecD *hd, const int32_t *n_hits,
+                              const uint32_t *active, int32_t *votes, uint32_t *hist, unsigned *status,
+                              cudaStream_t s, unsigned long long *ctr) {
+    dim3 grid(g.bins[1] * g.bins[2], n_ev);
+    k_vote_coarse_mid<<<grid, g.bins[0] * g.bins[3], MidSmem::total(g.bins[4]), s>>>(
+        g, ev0, hd, n_hits, active, votes, hist, status, ctr);
+}
+
+static void launch_cells_mid(const DevGeom &g, int n_ev, const HitRecD *hd, const int32_t *n_hits,
+                             const uint32_t *active, int level, const uint64_t *keys,
+                             const uint64_t *parents, long long n_per_ev, uint64_t *out_keys,
+                             int32_t *out_votes, unsigned *status, cudaStream_t s, int block) {
+    dim3 grid((unsigned)((n_per_ev + block - 1) / block), n_ev);
+    k_vote_cells_mid<<<grid, block, kHitCap * 80 + 16, s>>>(g, hd, n_hits, active, level, keys, parents,
+                                                            n_per_ev, out_keys, out_votes, status);
+}
+
 // Raises the dynamic shared-memory limit of a kernel once per process (the attribute is a
 // property of the function; setting it outside any stream capture keeps captures clean).
 static bool g_attr_coarse[3] = {false, false, false}, g_attr_cells[3] = {false, false, false},
@@ -403,7 +582,9 @@ void launch_vote_coarse(const DevGeom &g, int prec, int ev0, int n_ev, const Hit
                         unsigned *status, cudaStream_t s, unsigned long long *ctr,
                         const uint32_t *active) {
     if (n_ev <= 0) return;
-    if (prec == APO_F32)
+    if (prec == APO_F64_MID)
+        launch_coarse_mid(g, ev0, n_ev, hd, n_hits, active, votes, hist, status, s, ctr);
+    else if (prec == APO_F32)
         launch_coarse_mode<kModeF32>(g, ev0, n_ev, hd, hf, n_hits, active, votes, hist, status, s, ctr);
     else if (prec == APO_F64_FILTERED)
         launch_coarse_mode<kModeF64Filtered>(g, ev0, n_ev, hd, hf, n_hits, active, votes, hist, status, s, ctr);
@@ -571,7 +752,10 @@ static void launch_cells(const DevGeom &g, int prec, int n_ev, const HitRecD *hd
                          uint64_t *out_keys, int32_t *out_votes, unsigned *status, cudaStream_t s,
                          int block = 256) {
     if (block != 128) block = 256;
-    if (prec == APO_F32)
+    if (prec == APO_F64_MID)
+        launch_cells_mid(g, n_ev, hd, n_hits, active, level, keys, parents, n_per_ev, out_keys, out_votes,
+                         status, s, block);
+    else if (prec == APO_F32)
         launch_cells_mode<kModeF32>(g, n_ev, hd, hf, n_hits, active, level, keys, parents, n_per_ev,
                                     out_keys, out_votes, status, s, block);
     else if (prec == APO_F64_FILTERED)
@@ -608,6 +792,11 @@ void launch_vote_children(const DevGeom &g, int prec, int n_ev, const HitRecD *h
                           int32_t *child_votes, cudaStream_t s, const uint32_t *active, int block) {
     if (n_ev <= 0 || n_par <= 0) return;
     if (block != 128) block = 256;
+    if (prec == APO_F64_MID) {   // children in the order of k_vote_children: 32 per parent
+        launch_cells_mid(g, n_ev, hd, n_hits, active, child_level, nullptr, parents, (long long)n_par * 32,
+                         child_keys, child_votes, nullptr, s, block);
+        return;
+    }
     if (prec == APO_F32)
         launch_children_mode<kModeF32>(g, n_ev, hd, hf, n_hits, active, child_level, parents, n_par,
                                        child_keys, child_votes, s, block);

@@ -23,6 +23,7 @@ struct DevGeom {
     const double *hi_edge[5];
     const double *sincos;           // (sin lo, sin hi, cos lo, cos hi) per phi0 cell per level
     long long sincos_off[kMaxLevels + 1];
+    const double *sincos_mid;       // (sin, cos) at each phi0 cell's centre, same rows; may be null
     const double *wire[8];          // x0, y0, sin phis, cos phis, tan tau, sphi*t, cphi*t, t^2
     SeriesConsts k;
 };
@@ -45,6 +46,13 @@ __device__ __forceinline__ IV<double> sin_phi0(const DevGeom &g, int level, int 
 __device__ __forceinline__ IV<double> cos_phi0(const DevGeom &g, int level, int i) {
     const double *r = g.sincos + 4 * (g.sincos_off[level] + i);
     return {r[2], r[3]};
+}
+
+// sin / cos of the phi0 centre of cell i at `level` (midpoint form)
+__device__ __forceinline__ void sincos_phi0_centre(const DevGeom &g, int level, int i, double &s, double &c) {
+    const double *r = g.sincos_mid + 2 * (g.sincos_off[level] + i);
+    s = r[0];
+    c = r[1];
 }
 
 // Conversion of an FP64 interval to the working precision (outward for FP32).

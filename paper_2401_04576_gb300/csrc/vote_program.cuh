@@ -214,4 +214,186 @@ __device__ __forceinline__ bool vote_pair(Cell<T> c, Hit<T> h, const SeriesConst
     return tail(p, c.L, h, R, c.W, k);
 }
 
+// ---------------------------------------------------------------------------------------
+// Midpoint form, FP64 only: the faster, approximate variant of Section 3.1, where the
+// quantities that build d^Ax (Eq. defdiAX_b) are taken at the middle of the voxel.  The
+// point part runs the steps of the interval program on the voxel centre, per drift sign,
+// with plain round-to-nearest numbers, giving A = rho ((R + d^Ax)^2 - R^2) and
+// d^Ax = A / (sqrt(1 + rho A) + 1); the interval part tests 0 in
+// G = G0 - (2 d^Ax + rho d^Ax^2) with G0 = rho ((R^Ax)^2 - R^2) and rho over the voxel.
+// Not sound: a voxel holding the solution can lose the vote.  A point divisor or root
+// argument that is not positive makes the pair vote.  Every point step is an explicit
+// round-to-nearest intrinsic, never contracted into an FMA.
+// ---------------------------------------------------------------------------------------
+namespace pt {
+__device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ double clamp1(double x) { return x < -1.0 ? -1.0 : (x > 1.0 ? 1.0 : x); }
+__device__ __forceinline__ double centre(IV<double> a) { return mul(add(a.lo, a.hi), 0.5); }
+
+// atan with the steps of atan_iv and no remainder: two half-angle reductions, the
+// alternating series through x^15 in Horner form on x^2, times 4.
+__device__ __forceinline__ double atan(double x) {
+#pragma unroll
+    for (int i = 0; i < 2; i++) x = div(x, add(1.0, sqrt(add(1.0, mul(x, x)))));
+    const double y = mul(x, x);
+    double h = 1.0 / 15.0;
+    h = sub(1.0 / 13.0, mul(h, y));
+    h = sub(1.0 / 11.0, mul(h, y));
+    h = sub(1.0 / 9.0, mul(h, y));
+    h = sub(1.0 / 7.0, mul(h, y));
+    h = sub(1.0 / 5.0, mul(h, y));
+    h = sub(1.0 / 3.0, mul(h, y));
+    h = sub(1.0, mul(h, y));
+    return mul(mul(x, h), 4.0);
+}
+
+// sin / cos of the small phase correction: Taylor through d^9 / d^10 in nested Horner
+// form on y = d^2 with round-to-nearest 1/k constants.
+__device__ __forceinline__ void sincos(double d, double &s, double &c) {
+    const double y = mul(d, d);
+    double ps = sub(1.0, mul(y, 1.0 / 72.0));
+    ps = sub(1.0, mul(mul(y, 1.0 / 42.0), ps));
+    ps = sub(1.0, mul(mul(y, 1.0 / 20.0), ps));
+    ps = sub(1.0, mul(mul(y, 1.0 / 6.0), ps));
+    s = mul(d, ps);
+    double pc = sub(1.0, mul(y, 1.0 / 90.0));
+    pc = sub(1.0, mul(mul(y, 1.0 / 56.0), pc));
+    pc = sub(1.0, mul(mul(y, 1.0 / 30.0), pc));
+    pc = sub(1.0, mul(mul(y, 1.0 / 12.0), pc));
+    c = sub(1.0, mul(mul(y, 0.5), pc));
+}
+}  // namespace pt
+
+// Voxel centre (after the mirror): d0, sin / cos phi0, omega, z0 (tan(lambda) per tail).
+struct MidCentre { double D, S0, C0, W, Z; };
+
+// tan(lambda)-free part: point quantities at the centre and the interval G0 over the voxel.
+struct MidPre {
+    bool guard;   // a point divisor reached 0: both drift signs vote
+    IV<double> G0;
+    double R, W, psi, N, Ninv, sPA, cPA, rsA, rcA, sin2, Nh, dW, psi_sPA, dW_cPA, inner_e,
+        psi_cos2, onepN;
+};
+
+// c: the mirrored voxel (W > 0); m: its mirrored centre; h: the (mirrored) hit.
+__device__ __forceinline__ MidPre mid_prefix(const Cell<double> &c, const MidCentre &m,
+                                             const Hit<double> &h) {
+    using namespace pt;
+    const IV<double> one{1.0, 1.0};
+    MidPre p;
+    p.guard = false;
+    // interval part: G0 = rho ((R^Ax)^2 - R^2) over the voxel
+    {
+        IV<double> Xw = apo::add(h.x0, apo::mul(c.Z, h.spt));
+        IV<double> Yw = apo::sub(h.y0, apo::mul(c.Z, h.cpt));
+        IV<double> wt = apo::add(apo::mul(Xw, c.C0), apo::mul(Yw, c.S0));
+        IV<double> wn = apo::sub(apo::mul(Yw, c.C0), apo::mul(Xw, c.S0));
+        IV<double> V = apo::sub(wn, c.D);
+        IV<double> Xn = apo::sub(mul_nn(V, c.W), one);
+        p.G0 = apo::add(mul_pp(c.W, sqr(wt)), apo::mul(V, apo::sub(Xn, one)));
+    }
+    // point part at the centre
+    const double x0 = h.x0.lo, y0 = h.y0.lo, sph = h.sph.lo, cph = h.cph.lo, spt = h.spt.lo,
+                 cpt = h.cpt.lo, d = h.d.lo;
+    p.W = m.W;
+    p.R = div(1.0, m.W);
+    const double Xw = add(x0, mul(m.Z, spt));
+    const double Yw = sub(y0, mul(m.Z, cpt));
+    const double wt = add(mul(Xw, m.C0), mul(Yw, m.S0));
+    const double wn = sub(mul(Yw, m.C0), mul(Xw, m.S0));
+    const double V = sub(wn, m.D);
+    const double Xt = mul(wt, m.W);
+    const double Xn = sub(mul(V, m.W), 1.0);
+    p.N = sqrt(add(mul(Xt, Xt), mul(Xn, Xn)));
+    if (!(p.N > 0.0)) { p.guard = true; return p; }
+    const double den = sub(p.N, Xn);
+    if (!(den > 0.0)) { p.guard = true; return p; }
+    p.psi = mul(2.0, pt::atan(div(Xt, den)));
+    const double E1 = add(mul(m.C0, cph), mul(m.S0, sph));
+    const double E2 = sub(mul(m.C0, sph), mul(m.S0, cph));
+    p.rsA = add(mul(Xt, E1), mul(Xn, E2));
+    p.rcA = sub(mul(Xt, E2), mul(Xn, E1));
+    p.Ninv = div(1.0, p.N);
+    p.sPA = clamp1(mul(p.rsA, p.Ninv));
+    p.cPA = clamp1(mul(p.rcA, p.Ninv));
+    const double cos2 = clamp1(sub(mul(p.cPA, p.cPA), mul(p.sPA, p.sPA)));
+    p.sin2 = clamp1(mul(2.0, mul(p.sPA, p.cPA)));
+    p.dW = mul(d, m.W);
+    p.Nh = mul(0.5, mul(p.Ninv, p.Ninv));
+    p.psi_sPA = mul(p.psi, p.sPA);
+    p.dW_cPA = mul(p.cPA, p.dW);
+    p.inner_e = sub(add(mul(p.psi, sub(1.0, cos2)), mul(p.sin2, mul(p.psi, p.psi))),
+                    mul(p.sin2, mul(p.dW, p.dW)));
+    p.psi_cos2 = mul(p.psi, cos2);
+    p.onepN = add(1.0, p.N);
+    return p;
+}
+
+// The vote at the centre's tan(lambda) L (either drift sign), W the voxel's interval.
+__device__ __forceinline__ bool mid_tail(const MidPre &p, double L, const Hit<double> &h,
+                                         IV<double> W) {
+    using namespace pt;
+    const double t = h.t.lo, t2 = h.t2.lo, d = h.d.lo;
+    const double L2 = mul(L, L);
+    const double P1e = -mul(mul(L, p.psi_sPA), p.Ninv);
+    const double P1o = -mul(mul(L, p.dW_cPA), p.Ninv);
+    const double P2e = mul(mul(p.inner_e, L2), p.Nh);
+    const double P2o = mul(mul(add(mul(2.0, mul(p.psi_cos2, L2)), mul(p.sin2, add(p.N, mul(L2, p.onepN)))),
+                               p.dW),
+                           p.Nh);
+    const double de = add(mul(P1e, t), mul(P2e, t2));
+    const double dod = add(mul(P1o, t), mul(P2o, t2));
+    const double t2x = mul(2.0, t);
+    bool vote = false;
+#pragma unroll
+    for (int sg = 0; sg < 2; sg++) {
+        const double dl = sg == 0 ? add(de, dod) : sub(de, dod);
+        double sd, cd;
+        pt::sincos(dl, sd, cd);
+        const double sP = clamp1(add(mul(p.sPA, cd), mul(p.cPA, sd)));
+        const double cP = clamp1(sub(mul(p.cPA, cd), mul(p.sPA, sd)));
+        const double u2 = add(add(add(1.0, mul(t2x, mul(L, sP))), mul(L2, t2)), mul(mul(cP, cP), t2));
+        if (!(u2 > 0.0)) { vote = true; continue; }
+        const double Q = mul(d, div(1.0, sqrt(u2)));
+        const double Qct = mul(mul(cP, t), Q);
+        const double LQ = mul(L, Q);
+        const double LQrsA = mul(LQ, p.rsA);
+        const double a2 = mul(p.W, mul(Q, Q));
+        const double LQt = mul(LQ, t);
+        const double a5 = mul(p.W, mul(LQt, LQt));
+        const double sp = mul(add(p.psi, dl), p.R);
+        const double zS = sg == 0 ? sub(mul(L, sp), Qct) : add(mul(L, sp), Qct);
+        const double rct = sg == 0 ? sub(mul(zS, p.rcA), LQrsA) : add(mul(zS, p.rcA), LQrsA);
+        const double a1 = sg == 0 ? mul(2.0, Q) : -mul(2.0, Q);
+        const double a3 = mul(t2x, rct);
+        const double zSt = mul(zS, t);
+        const double a4 = mul(p.W, mul(zSt, zSt));
+        const double A = sub(sub(sub(add(a1, a2), a3), a4), a5);
+        const double r = add(1.0, mul(p.W, A));
+        if (!(r >= 0.0)) { vote = true; continue; }
+        const double dax = div(A, add(sqrt(r), 1.0));
+        const IV<double> x{dax, dax};
+        const IV<double> G = apo::sub(p.G0, apo::add(scale2(x), mul_pp(W, sqr(x))));
+        vote = vote || contains0(G);
+    }
+    return vote;
+}
+
+// Whole midpoint-form program for one (voxel, hit); voxel, centre and hit unmirrored.
+// m.L-less centre plus L = tan(lambda) centre.
+__device__ __forceinline__ bool mid_vote_pair(Cell<double> c, MidCentre m, double L, Hit<double> h) {
+    if (mirror_cell(c)) {
+        mirror_hit(h);
+        m.D = -m.D; m.S0 = -m.S0; m.W = -m.W;
+    }
+    if (le0(c.W.lo)) return true;
+    MidPre p = mid_prefix(c, m, h);
+    if (p.guard) return true;
+    return mid_tail(p, L, h, c.W);
+}
+
 }  // namespace apo
