@@ -137,12 +137,13 @@ class Hit:
 
 
 def simulate_track(tr: Track, w: Wires, rng: np.random.Generator | None,
-                   sigma: float = SIGMA_DRIFT) -> list[Hit]:
-    """All wires whose closest approach to the helix (over the outgoing arc, with the wire
-    point inside the chamber length) is under half a cell; drift = distance + N(0, sigma),
-    clipped at 0.  rng=None gives noiseless drifts."""
-    s_max = min(np.pi / abs(tr.omega), 1.5)
-    ns = 301
+                   sigma: float = SIGMA_DRIFT, s_max: float | None = None,
+                   max_drift: float | None = None, ns: int = 301) -> list[Hit]:
+    """All wires whose closest approach to the helix (over the arc 0 <= s < s_max, by
+    default the outgoing half turn, with the wire point inside the chamber length) is under
+    half a cell (and under max_drift when given); drift = distance + N(0, sigma), clipped
+    at 0.  rng=None gives noiseless drifts."""
+    s_max = min(np.pi / abs(tr.omega), 1.5) if s_max is None else s_max
     s_grid = np.linspace(0.0, s_max, ns)
     P, _, _ = _helix(tr, s_grid)
     # A wire can only be hit if its waist point lies within half a cell plus its largest
@@ -224,6 +225,8 @@ def simulate_track(tr: Track, w: Wires, rng: np.random.Generator | None,
         if not (0.0 < s[j] < s_max and lo[j] - step <= s[j] <= hi[j] + step):
             continue  # closest approach at the end of the arc: no perpendicular crossing
         if abs(zc[j]) > w.z_half_len or dist[j] >= w.half_cell[wid]:
+            continue
+        if max_drift is not None and dist[j] >= max_drift:
             continue
         drift = dist[j] if rng is None else max(dist[j] + rng.normal(0.0, sigma), 0.0)
         Phi = tr.omega * s[j] + tr.phi0 - w.phis[wid]

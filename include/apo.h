@@ -136,10 +136,15 @@ typedef struct {
     apo_tune tune;
     int32_t use_graph;       /* 1: record the whole search as a CUDA graph on the first call
                                 with these arguments, and replay it on later calls */
+    int32_t *hit_track;      /* device, may be NULL: for every hit of the batch (CSR order of
+                                apo_hits) the track whose final maximum-vote cells took it in
+                                the hit finding of Section 3.3 (0-based), or -1 if none did.
+                                apo_solve_batch_host and the server require NULL. */
 } apo_solve_opts;
 
 /* Fills *opts with: all levels FP64, one track, min_votes 0, mask_sigma 150e-6, no trace,
- * tune = {coarse_filter 0, cells_filter 1, cells_block 256, chunk 0}, no graph. */
+ * tune = {coarse_filter 0, cells_filter 1, cells_block 256, chunk 0}, no graph, no
+ * hit_track. */
 void apo_solve_opts_default(apo_solve_opts *opts);
 
 /* Text of the last error on this thread ("" if none). */

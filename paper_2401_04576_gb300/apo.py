@@ -54,7 +54,7 @@ class ApoSolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int32 * (MAX_LEVELS + 1)), ("max_tracks", C.c_int32),
                 ("min_votes", C.c_int32), ("mask_sigma", C.c_double),
                 ("trace_keys", C.c_void_p), ("trace_votes", C.c_void_p),
-                ("tune", ApoTune), ("use_graph", C.c_int32)]
+                ("tune", ApoTune), ("use_graph", C.c_int32), ("hit_track", C.c_void_p)]
 
 
 class ApoServeOpts(C.Structure):
@@ -217,7 +217,7 @@ class DeviceHits:
 
 def solve_opts(precision=None, levels: int = 0, max_tracks: int = 1, min_votes: int = 0,
                mask_sigma: float = 150e-6, trace_keys=None, trace_votes=None, tune=None,
-               use_graph: bool = False) -> ApoSolveOpts:
+               use_graph: bool = False, hit_track=None) -> ApoSolveOpts:
     o = ApoSolveOpts()
     lib().apo_solve_opts_default(C.byref(o))
     if tune is not None:
@@ -229,6 +229,7 @@ def solve_opts(precision=None, levels: int = 0, max_tracks: int = 1, min_votes: 
     o.max_tracks, o.min_votes, o.mask_sigma = int(max_tracks), int(min_votes), float(mask_sigma)
     o.trace_keys = _ptr(trace_keys).value
     o.trace_votes = _ptr(trace_votes).value
+    o.hit_track = _ptr(hit_track).value
     return o
 
 

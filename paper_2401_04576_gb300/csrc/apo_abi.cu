@@ -417,7 +417,8 @@ int enqueue_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_o
         return (p == APO_F64 && filt) ? (int)APO_F64_FILTERED : p;
     };
     CU(cudaMemsetAsync(status, 0, 256, s));
-    launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, active, done, status, s);
+    launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, active, done, status, s,
+                 o->hit_track);
     if ((rc = check_launch("stage"))) return rc;
     for (int e0 = 0; e0 < ne; e0 += chunk) {
         const int n = ne - e0 < chunk ? ne - e0 : chunk;
@@ -448,7 +449,8 @@ int enqueue_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_o
             }
             launch_estimate_mask(g->dg, n, cke, cve, K * 32, lv, nhe, acte, done + e0, hde, round,
                                  o->max_tracks, o->min_votes, width,
-                                 tracks_out + (size_t)e0 * o->max_tracks, ntr + e0, s);
+                                 tracks_out + (size_t)e0 * o->max_tracks, ntr + e0, s,
+                                 hits->offsets + e0, o->hit_track);
             if ((rc = check_launch("estimate_mask"))) return rc;
         }
     }
@@ -662,6 +664,7 @@ int apo_solve_batch_host(const apo_geometry *g, int32_t n_events, const int32_t 
     apo_solve_opts def;
     apo_solve_opts_default(&def);
     const apo_solve_opts *o = opts ? opts : &def;
+    if (o->hit_track) return fail(APO_EINVAL, "apo_solve_batch_host takes no hit_track (device output)");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     size_t off = L.end;
     int32_t *d_off = at<int32_t>(ws, off); off += align256(sizeof(int32_t) * (size_t)(n_events + 1));

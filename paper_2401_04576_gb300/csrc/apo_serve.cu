@@ -129,8 +129,6 @@ int launch_slot(apo_server *sv, Slot &s) {
     if (e != cudaSuccess) return fail_msg(APO_ECUDA, cudaGetErrorString(e));
     apo_hits h{n, s.d_off, s.d_wid, s.d_dr};
     apo_solve_opts so = sv->o.solve;
-    so.trace_keys = nullptr;
-    so.trace_votes = nullptr;
     so.use_graph = 0;
     int rc = apo_solve_batch(sv->g, &h, &so, s.d_tr, s.d_nt, s.dev, s.ws_bytes, s.stream);
     if (rc != APO_OK) return rc;
@@ -234,6 +232,8 @@ int apo_serve_create(const apo_geometry *g, const apo_serve_opts *opts, apo_serv
         return fail_msg(APO_EINVAL, "batch_events, max_slots and max_pending must be >= 1");
     if (o.solve.max_tracks < 1 || o.solve.max_tracks > APO_MAX_TRACKS)
         return fail_msg(APO_EINVAL, "solve.max_tracks out of range");
+    if (o.solve.hit_track || o.solve.trace_keys || o.solve.trace_votes)
+        return fail_msg(APO_EINVAL, "the server takes no per-batch device outputs (hit_track, trace)");
     int gdev = -1;
     geometry_device_tables(g, &gdev);
     if (cudaSetDevice(gdev) != cudaSuccess) return fail_msg(APO_ECUDA, "cannot select the geometry's device");

@@ -118,7 +118,7 @@ void launch_series_consts(SeriesConsts *dev_out, cudaStream_t s) {
 // ---------------------------------------------------------------------------------------
 __global__ void k_stage(DevGeom g, int n_events, const int32_t *offsets, const int32_t *wire_id,
                         const double *drift, HitRecD *hd, HitRecF *hf, int32_t *n_hits,
-                        uint32_t *active, int32_t *done, unsigned *status) {
+                        uint32_t *active, int32_t *done, unsigned *status, int32_t *hit_track) {
     int e = blockIdx.x;
     if (e >= n_events) return;
     __shared__ int bad;
@@ -135,6 +135,8 @@ __global__ void k_stage(DevGeom g, int n_events, const int32_t *offsets, const i
         }
         return;
     }
+    if (hit_track)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) hit_track[a + i] = -1;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         int w = wire_id[a + i];
         double d = drift[a + i];
@@ -168,10 +170,10 @@ __global__ void k_stage(DevGeom g, int n_events, const int32_t *offsets, const i
 
 void launch_stage(const DevGeom &g, int n_events, const int32_t *offsets, const int32_t *wire_id,
                   const double *drift, HitRecD *hd, HitRecF *hf, int32_t *n_hits, uint32_t *active,
-                  int32_t *done, unsigned *status, cudaStream_t s) {
+                  int32_t *done, unsigned *status, cudaStream_t s, int32_t *hit_track) {
     if (n_events <= 0) return;
     k_stage<<<n_events, 128, 0, s>>>(g, n_events, offsets, wire_id, drift, hd, hf, n_hits, active,
-                                      done, status);
+                                      done, status, hit_track);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -996,7 +998,7 @@ __global__ void __launch_bounds__(256)
 k_estimate_mask(DevGeom g, const uint64_t *keys, const int32_t *votes, int n_in, int level,
                 const int32_t *n_hits, uint32_t *active, int32_t *done, const HitRecD *hd,
                 int round, int max_tracks, int min_votes, double width, apo_track *out,
-                int32_t *n_tracks) {
+                int32_t *n_tracks, const int32_t *offsets, int32_t *hit_track) {
     __shared__ uint64_t s[kSortMax];
     __shared__ double s_cen[kEstChunk * 5];
     __shared__ long long s_lo[5], s_hi[5];
@@ -1077,7 +1079,8 @@ k_estimate_mask(DevGeom g, const uint64_t *keys, const int32_t *votes, int n_in,
             n_tracks[e] = round + 1;
         }
     }
-    if (round + 1 >= max_tracks) {
+    const bool last = round + 1 >= max_tracks;
+    if (last && !hit_track) {   // no later round needs the masks
         if (tid == 0) done[e] = 1;
         return;
     }
@@ -1099,20 +1102,27 @@ k_estimate_mask(DevGeom g, const uint64_t *keys, const int32_t *votes, int n_in,
     }
     __syncthreads();
     if (tid < 8) active[(long long)e * 8 + tid] = act1[tid];
+    if (hit_track) {   // the hits this track took: active before, masked now
+        const int a0 = offsets[e];
+        for (int i = tid; i < nh; i += blockDim.x)
+            if (((act0[i >> 5] & ~act1[i >> 5]) >> (i & 31)) & 1u) hit_track[a0 + i] = round;
+    }
     if (tid == 0) {
         int left = 0;
         for (int i = 0; i < 8; i++) left += __popc(act1[i]);
-        if (left == 0) done[e] = 1;
+        if (left == 0 || last) done[e] = 1;
     }
 }
 
 void launch_estimate_mask(const DevGeom &g, int n_ev, const uint64_t *keys, const int32_t *votes,
                           int n_in, int level, const int32_t *n_hits, uint32_t *active, int32_t *done,
                           const HitRecD *hd, int round, int max_tracks, int min_votes, double width,
-                          apo_track *out, int32_t *n_tracks, cudaStream_t s) {
+                          apo_track *out, int32_t *n_tracks, cudaStream_t s, const int32_t *offsets,
+                          int32_t *hit_track) {
     if (n_ev <= 0) return;
     k_estimate_mask<<<n_ev, 256, 0, s>>>(g, keys, votes, n_in, level, n_hits, active, done, hd, round,
-                                          max_tracks, min_votes, width, out, n_tracks);
+                                          max_tracks, min_votes, width, out, n_tracks, offsets,
+                                          hit_track);
 }
 
 }  // namespace apo

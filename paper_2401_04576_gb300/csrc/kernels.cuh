@@ -95,9 +95,11 @@ __device__ __forceinline__ void unpack_key(uint64_t k, int idx[5]) {
 enum : unsigned { ST_TIMEOUT = 1u, ST_BADHIT = 2u, ST_TOOMANY = 4u, ST_BADOFFS = 8u };
 
 // ---- launch wrappers (kernels.cu) ----
+// hit_track (may be null): set to -1 for every hit of the batch
 void launch_stage(const DevGeom &g, int n_events, const int32_t *offsets, const int32_t *wire_id,
                   const double *drift, HitRecD *hd, HitRecF *hf, int32_t *n_hits,
-                  uint32_t *active, int32_t *done, unsigned *status, cudaStream_t s);
+                  uint32_t *active, int32_t *done, unsigned *status, cudaStream_t s,
+                  int32_t *hit_track = nullptr);
 // active: per event 8 words of hit-activity bits (nullptr: every hit active)
 void launch_vote_coarse(const DevGeom &g, int prec, int ev0, int n_ev, const HitRecD *hd,
                         const HitRecF *hf, const int32_t *n_hits, int32_t *votes, uint32_t *hist,
@@ -118,10 +120,13 @@ void launch_select_coarse(const DevGeom &g, int ev0, int n_ev, const int32_t *vo
                           cudaStream_t s);
 void launch_topk(int n_ev, const uint64_t *keys, const int32_t *votes, int n_in, int K,
                  uint64_t *out_keys, int32_t *out_votes, cudaStream_t s);
+// offsets / hit_track (hit_track may be null): the batch's CSR offsets of these events and
+// the per-hit track index, written for the hits this round's track takes
 void launch_estimate_mask(const DevGeom &g, int n_ev, const uint64_t *keys, const int32_t *votes,
                           int n_in, int level, const int32_t *n_hits, uint32_t *active, int32_t *done,
                           const HitRecD *hd, int round, int max_tracks, int min_votes, double width,
-                          apo_track *out, int32_t *n_tracks, cudaStream_t s);
+                          apo_track *out, int32_t *n_tracks, cudaStream_t s,
+                          const int32_t *offsets = nullptr, int32_t *hit_track = nullptr);
 void launch_series_consts(SeriesConsts *dev_out, cudaStream_t s);
 double pipe_peak(int precision, int op);   // diag.cu: directed operations per second
 

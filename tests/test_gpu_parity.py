@@ -229,13 +229,15 @@ def test_refine_matches_oracle(wires, grid1, ev1):
 
 
 def _multi(geom, ev, grid, precision, max_tracks, min_votes):
-    o = apo.solve_opts(precision=precision, max_tracks=max_tracks, min_votes=min_votes)
+    ht = torch.full((int(ev.offsets[-1]),), 7, dtype=torch.int32, device="cuda")
+    o = apo.solve_opts(precision=precision, max_tracks=max_tracks, min_votes=min_votes,
+                       hit_track=ht)
     tracks, nt = apo.solve_batch(geom, _hits(ev), o)
     torch.cuda.synchronize()
-    return apo.tracks_to_numpy(tracks, ev.n_events, max_tracks), nt.cpu().numpy()
+    return apo.tracks_to_numpy(tracks, ev.n_events, max_tracks), nt.cpu().numpy(), ht.cpu().numpy()
 
 
-def _compare_multi(tab, ev, e, t, nt, precision, max_tracks, min_votes):
+def _compare_multi(tab, ev, e, t, nt, ht, precision, max_tracks, min_votes):
     a, b = ev.offsets[e], ev.offsets[e + 1]
     r = O.solve_event_multi(tab, ev.wire_id[a:b], ev.drift[a:b], max_tracks, min_votes,
                             prec_per_level=precision)
@@ -243,6 +245,8 @@ def _compare_multi(tab, ev, e, t, nt, precision, max_tracks, min_votes):
     for k in range(r["n_tracks"]):
         assert t[e, k]["votes"] == r["votes"][k], (e, k)
         assert np.array_equal(t[e, k]["p"], r["p"][k]) and np.array_equal(t[e, k]["w"], r["w"][k])
+    # which track took each hit (the hit finding of Section 3.3), -1 for none
+    np.testing.assert_array_equal(ht[a:b], r["hit_track"], err_msg=f"event {e}")
 
 
 @pytest.mark.parametrize("mixed", [False, True])
@@ -253,11 +257,12 @@ def test_multi_track_small_grid_bit_exact(wires, mixed):
     geom = apo.Geometry(g, wires)
     ev = chamber.multi_track_events(6, seed=41, w=wires)
     precision = ([apo.F32] * 2 + [apo.F64] * 2) if mixed else [apo.F64] * 4
-    t, nt = _multi(geom, ev, g, precision, 5, 6)
+    t, nt, ht = _multi(geom, ev, g, precision, 5, 6)
     tab = O.Tables(g, wires)
     for e in range(ev.n_events):
-        _compare_multi(tab, ev, e, t, nt, precision, 5, 6)
+        _compare_multi(tab, ev, e, t, nt, ht, precision, 5, 6)
     assert nt.sum() > ev.n_events
+    assert (ht >= 0).any() and (ht < 0).any()
 
 
 def test_multi_track_full_size_sampled(wires):
@@ -268,10 +273,10 @@ def test_multi_track_full_size_sampled(wires):
     geom = apo.Geometry(g, wires)
     ev = chamber.multi_track_events(4096, seed=4, w=wires)
     precision = [apo.F32] * 5 + [apo.F64] * 2
-    t, nt = _multi(geom, ev, g, precision, 5, 6)
+    t, nt, ht = _multi(geom, ev, g, precision, 5, 6)
     tab = O.Tables(g, wires)
     for e in (7, 3000):
-        _compare_multi(tab, ev, e, t, nt, precision, 5, 6)
+        _compare_multi(tab, ev, e, t, nt, ht, precision, 5, 6)
     assert np.all((nt >= 0) & (nt <= 5))
 
 
