@@ -29,6 +29,7 @@
 #define NEXTUP(x) nextafter((x), INFINITY)
 #include "vote_program.inc"
 #include "midpoint.inc"
+#include "fourd.inc"
 #undef REAL
 #undef SFX
 #undef SQRT
@@ -39,6 +40,7 @@
 #define SQRT sqrtf
 #define NEXTUP(x) nextafterf((x), INFINITY)
 #include "vote_program.inc"
+#include "fourd.inc"
 #undef REAL
 #undef SFX
 #undef SQRT
@@ -425,4 +427,361 @@ void or_sincos_iv(double lo, double hi, int prec, double out[4]) {
         out[0] = s.lo; out[1] = s.hi; out[2] = c.lo; out[3] = c.hi;
     }
     fesetround(old);
+}
+
+
+/* ==================================================================================== */
+/* The paper's own 4-D search (Sections 3.1-3.3, Table tabGridDef): voxels x_c x y_c x R  */
+/* x z0 with two tan(lambda)-sign accumulators, the disk pre-filter, the midpoint form,  */
+/* and three iterations with hit finding and a moving reference point.                  */
+/* ==================================================================================== */
+
+/* one iteration's grid for one event: axis a has n[a] voxels [lo + i w, lo + (i + 1) w] */
+typedef struct { double lo[4], w[4]; int32_t n[4]; } or4_grid;
+
+typedef struct {
+    double p_gev, b_tesla, disk_radius, hit_factor;
+    double glo[4];            /* lower corner of the global box of iterations 1 and 2 */
+    double w[3][4];           /* voxel size per iteration */
+    int32_t n[3][4];          /* voxels per axis per iteration */
+    int32_t precision;        /* 0: FP64, 1: FP32 */
+    int32_t n_iter;           /* 1 .. 3 */
+} or4_opts;
+
+typedef struct {
+    double value[4], err[4], ref[2];
+    int32_t sign, vmax, n_max, n_sel;
+} or4_iter;
+
+/* voxel edges (round to nearest; the caller holds FE_TONEAREST) */
+static void v4_edge(const or4_grid *g, int a, int i, double *lo, double *hi) {
+    *lo = g->lo[a] + (double)i * g->w[a];
+    *hi = g->lo[a] + (double)(i + 1) * g->w[a];
+}
+
+/* The vote of one hit for one voxel centre (m, z0c, sign) and the voxel's intervals. */
+static int v4_pair_d(const v4ctr_d *m, const v4pre_d *pre, double z0c, int sign, const double h[9],
+                     iv_d X, iv_d Y, iv_d Rv) {
+    double dax[2];
+    int g = v4_dax_d(pre, z0c, sign > 0 ? m->aL : -m->aL, h, dax);
+    fesetround(FE_DOWNWARD);
+    int v = 0;
+    for (int sg = 0; sg < 2 && !v; sg++)
+        v = (g >> sg & 1) ? 1 : v4_test_d(X, Y, Rv, mk_d(h[0], h[0]), mk_d(h[1], h[1]), dax[sg]);
+    fesetround(FE_TONEAREST);
+    return v;
+}
+static int v4_pair_f(const v4ctr_f *m, const v4pre_f *pre, float z0c, int sign, const float hf[9],
+                     const double h[9], iv_f X, iv_f Y, iv_f Rv) {
+    float dax[2];
+    int g = v4_dax_f(pre, z0c, sign > 0 ? m->aL : -m->aL, hf, dax);
+    fesetround(FE_DOWNWARD);
+    iv_f x0 = mk_f(rd32(h[0]), ru32(h[0])), y0 = mk_f(rd32(h[1]), ru32(h[1]));
+    int v = 0;
+    for (int sg = 0; sg < 2 && !v; sg++)
+        v = (g >> sg & 1) ? 1 : v4_test_f(X, Y, Rv, x0, y0, dax[sg]);
+    fesetround(FE_TONEAREST);
+    return v;
+}
+
+/* Votes of every voxel of grid g for one event, both signs: votes[s * nvox + lin] with
+ * lin = ix + nx (iy + ny (iR + nR iz)), s = 0 for tan(lambda) > 0.  active (may be NULL):
+ * 1 for the hits that vote.  Voxels outside the disk (Eq. ApoVoteDisk) or without a real
+ * tan(lambda) at their centre get 0. */
+void or4_vote_grid(const or4_opts *o, const or4_grid *g, const double ref[2], const or_wires *w,
+                   int32_t n_hits, const int32_t *wire_id, const double *drift,
+                   const uint8_t *active, int32_t *votes) {
+    const int nx = g->n[0], ny = g->n[1], nR = g->n[2], nz = g->n[3];
+    const int64_t nvox = (int64_t)nx * ny * nR * nz;
+    const int64_t ncol = (int64_t)nx * ny * nR;
+    #pragma omp parallel
+    {
+        int old = fegetround();
+        fesetround(FE_TONEAREST);
+        double *hc = (double *)malloc(sizeof(double) * 9 * (size_t)(n_hits > 0 ? n_hits : 1));
+        for (int32_t i = 0; i < n_hits; i++) hit_constants(w, wire_id[i], drift[i], hc + 9 * i);
+        #pragma omp for schedule(dynamic, 64)
+        for (int64_t col = 0; col < ncol; col++) {
+            const int ix = (int)(col % nx), iy = (int)((col / nx) % ny), iR = (int)(col / ((int64_t)nx * ny));
+            double xl, xh, yl, yh, rl, rh;
+            v4_edge(g, 0, ix, &xl, &xh);
+            v4_edge(g, 1, iy, &yl, &yh);
+            v4_edge(g, 2, iR, &rl, &rh);
+            const double xc = (xl + xh) * 0.5, yc = (yl + yh) * 0.5, Rc = (rl + rh) * 0.5;
+            int32_t cnt[2][64];
+            memset(cnt, 0, sizeof(cnt));
+            fesetround(FE_DOWNWARD);
+            int in_disk;
+            iv_d Xd = mk_d(xl, xh), Yd = mk_d(yl, yh), Rd = mk_d(rl, rh);
+            iv_f Xf = mk_f(rd32(xl), ru32(xh)), Yf = mk_f(rd32(yl), ru32(yh)), Rf = mk_f(rd32(rl), ru32(rh));
+            if (o->precision == 0) in_disk = v4_disk_d(Xd, Yd, Rd, o->disk_radius);
+            else in_disk = v4_disk_f(Xf, Yf, Rf, ru32(o->disk_radius));
+            fesetround(FE_TONEAREST);
+            if (in_disk) {
+                if (o->precision == 0) {
+                    v4ctr_d m = v4_centre_d(xc, yc, Rc, o->p_gev, o->b_tesla, ref[0], ref[1]);
+                    if (m.valid)
+                        for (int32_t i = 0; i < n_hits; i++) {
+                            if (active && !active[i]) continue;
+                            const double *h = hc + 9 * i;
+                            v4pre_d pre = v4_prefix_d(&m, h);
+                            for (int iz = 0; iz < nz; iz++) {
+                                double zl, zh;
+                                v4_edge(g, 3, iz, &zl, &zh);
+                                const double zc = (zl + zh) * 0.5;
+                                for (int s = 0; s < 2; s++)
+                                    cnt[s][iz] += pre.guard ? 1 : v4_pair_d(&m, &pre, zc, s == 0 ? 1 : -1, h, Xd, Yd, Rd);
+                            }
+                        }
+                } else {
+                    v4ctr_f m = v4_centre_f((float)xc, (float)yc, (float)Rc, (float)o->p_gev,
+                                            (float)o->b_tesla, (float)ref[0], (float)ref[1]);
+                    if (m.valid)
+                        for (int32_t i = 0; i < n_hits; i++) {
+                            if (active && !active[i]) continue;
+                            const double *h = hc + 9 * i;
+                            float hf[9];
+                            for (int k = 0; k < 9; k++) hf[k] = (float)h[k];
+                            v4pre_f pre = v4_prefix_f(&m, hf);
+                            for (int iz = 0; iz < nz; iz++) {
+                                double zl, zh;
+                                v4_edge(g, 3, iz, &zl, &zh);
+                                const float zc = (float)((zl + zh) * 0.5);
+                                for (int s = 0; s < 2; s++)
+                                    cnt[s][iz] += pre.guard ? 1 : v4_pair_f(&m, &pre, zc, s == 0 ? 1 : -1, hf, h, Xf, Yf, Rf);
+                            }
+                        }
+                }
+            }
+            for (int s = 0; s < 2; s++)
+                for (int iz = 0; iz < nz; iz++)
+                    votes[(int64_t)s * nvox + col + ncol * iz] = cnt[s][iz];
+        }
+        free(hc);
+        fesetround(old);
+    }
+}
+
+/* Values and errors of one iteration (Section 3.3: the centres and sizes of the maximum-
+ * vote voxels): the sign whose accumulator has the larger maximum (ties: tan(lambda) > 0);
+ * over its m maximum-vote voxels, value_a = lo_a + w_a (S_a / m + 1/2) with S_a the sum of
+ * their indices on axis a (exact integers), error_a = w_a (i_max - i_min + 1) / 2. */
+static void v4_estimate(const or4_grid *g, const int32_t *votes, or4_iter *it) {
+    const int64_t nvox = (int64_t)g->n[0] * g->n[1] * g->n[2] * g->n[3];
+    int32_t vm[2] = {0, 0};
+    for (int s = 0; s < 2; s++)
+        for (int64_t j = 0; j < nvox; j++)
+            if (votes[s * nvox + j] > vm[s]) vm[s] = votes[s * nvox + j];
+    const int s = vm[0] >= vm[1] ? 0 : 1;
+    it->sign = s == 0 ? 1 : -1;
+    it->vmax = vm[s];
+    int64_t m = 0, S[4] = {0, 0, 0, 0};
+    int32_t imin[4], imax[4];
+    for (int a = 0; a < 4; a++) { imin[a] = g->n[a]; imax[a] = -1; }
+    for (int64_t j = 0; j < nvox; j++) {
+        if (votes[s * nvox + j] != vm[s]) continue;
+        int32_t idx[4];
+        int64_t r = j;
+        for (int a = 0; a < 4; a++) { idx[a] = (int32_t)(r % g->n[a]); r /= g->n[a]; }
+        m++;
+        for (int a = 0; a < 4; a++) {
+            S[a] += idx[a];
+            if (idx[a] < imin[a]) imin[a] = idx[a];
+            if (idx[a] > imax[a]) imax[a] = idx[a];
+        }
+    }
+    it->n_max = (int32_t)m;
+    for (int a = 0; a < 4; a++) {
+        double mu = (double)S[a] / (double)m;
+        it->value[a] = g->lo[a] + g->w[a] * (mu + 0.5);
+        it->err[a] = (g->w[a] * (double)(imax[a] + 1 - imin[a])) * 0.5;
+    }
+}
+
+/* exported for the pins: the disk pre-filter of one voxel (x_c, y_c, R lo / hi) */
+int or4_disk(const double box[6], double radius, int32_t prec) {
+    int old = fegetround();
+    fesetround(FE_DOWNWARD);
+    int r = prec == 0 ? v4_disk_d(mk_d(box[0], box[1]), mk_d(box[2], box[3]), mk_d(box[4], box[5]), radius)
+                      : v4_disk_f(mk_f(rd32(box[0]), ru32(box[1])), mk_f(rd32(box[2]), ru32(box[3])),
+                                  mk_f(rd32(box[4]), ru32(box[5])), ru32(radius));
+    fesetround(old);
+    return r;
+}
+
+/* exported for the pins */
+void or4_estimate(const or4_grid *g, const int32_t *votes, or4_iter *it) {
+    int old = fegetround();
+    fesetround(FE_TONEAREST);
+    v4_estimate(g, votes, it);
+    fesetround(old);
+}
+
+/* Hit finding (Section 3.3): the box value +- factor * error, the chosen sign; a hit is
+ * taken when the vote holds on that box (same form as the voting). */
+static int v4_find_hits(const or4_opts *o, const or4_iter *it, const double ref[2], const or_wires *w,
+                        int32_t n_hits, const int32_t *wire_id, const double *drift, uint8_t *sel) {
+    double lo[4], hi[4], c[4];
+    for (int a = 0; a < 4; a++) {
+        double r = o->hit_factor * it->err[a];
+        lo[a] = it->value[a] - r;
+        hi[a] = it->value[a] + r;
+        c[a] = (lo[a] + hi[a]) * 0.5;
+    }
+    int n = 0;
+    for (int32_t i = 0; i < n_hits; i++) {
+        double h[9];
+        hit_constants(w, wire_id[i], drift[i], h);
+        int v = 0;
+        if (o->precision == 0) {
+            v4ctr_d m = v4_centre_d(c[0], c[1], c[2], o->p_gev, o->b_tesla, ref[0], ref[1]);
+            if (m.valid) {
+                v4pre_d pre = v4_prefix_d(&m, h);
+                v = pre.guard ? 1 : v4_pair_d(&m, &pre, c[3], it->sign, h, mk_d(lo[0], hi[0]),
+                                              mk_d(lo[1], hi[1]), mk_d(lo[2], hi[2]));
+            }
+        } else {
+            v4ctr_f m = v4_centre_f((float)c[0], (float)c[1], (float)c[2], (float)o->p_gev,
+                                    (float)o->b_tesla, (float)ref[0], (float)ref[1]);
+            if (m.valid) {
+                float hf[9];
+                for (int k = 0; k < 9; k++) hf[k] = (float)h[k];
+                v4pre_f pre = v4_prefix_f(&m, hf);
+                fesetround(FE_DOWNWARD);
+                iv_f X = mk_f(rd32(lo[0]), ru32(hi[0])), Y = mk_f(rd32(lo[1]), ru32(hi[1]));
+                iv_f Rv = mk_f(rd32(lo[2]), ru32(hi[2]));
+                fesetround(FE_TONEAREST);
+                v = pre.guard ? 1 : v4_pair_f(&m, &pre, (float)c[3], it->sign, hf, h, X, Y, Rv);
+            }
+        }
+        sel[i] = (uint8_t)v;
+        n += v;
+    }
+    return n;
+}
+
+/* New reference point: the waist point of the selected hit nearest to the found circle,
+ * | |(x0, y0) - (x_c, y_c)| - R | (first on ties); unchanged if no hit is selected. */
+static void v4_new_ref(const or4_iter *it, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
+                       const uint8_t *sel, double ref[2]) {
+    double best = INFINITY;
+    int bi = -1;
+    for (int32_t i = 0; i < n_hits; i++) {
+        if (!sel[i]) continue;
+        double dx = w->x0[wire_id[i]] - it->value[0], dy = w->y0[wire_id[i]] - it->value[1];
+        double dist = fabs(sqrt(dx * dx + dy * dy) - it->value[2]);
+        if (dist < best) { best = dist; bi = i; }
+    }
+    if (bi >= 0) { ref[0] = w->x0[wire_id[bi]]; ref[1] = w->y0[wire_id[bi]]; }
+}
+
+/* z0 of the found helix moved from reference point a to b: z0 + tan(lambda) R dpsi, dpsi
+ * the turn from a to b around the centre (half-angle form, in (-pi, pi)). */
+static double v4_move_z0(const or4_opts *o, const or4_iter *it, const double a[2], const double b[2]) {
+    double xc = it->value[0], yc = it->value[1], R = it->value[2];
+    double ax = a[0] - xc, ay = a[1] - yc, bx = b[0] - xc, by = b[1] - yc;
+    double sn = ax * by - ay * bx, cs = ax * bx + ay * by;
+    double den = sqrt(ax * ax + ay * ay) * sqrt(bx * bx + by * by) + cs;
+    double dpsi = den > 0 ? 2.0 * p_atan_d(sn / den) : 0.0;
+    double ratio = o->p_gev / ((0.3 * o->b_tesla) * R);
+    double aL = ratio > 1 ? sqrt(ratio * ratio - 1.0) : 0.0;
+    double L = it->sign > 0 ? aL : -aL;
+    return it->value[3] + L * (R * dpsi);
+}
+
+/* The three iterations for one event (Section 3.3): iteration 1 on the global grid with the
+ * reference point at the origin and every hit; iteration 2 on the global grid with finer
+ * voxels, the reference point moved to the selected hit nearest to the found circle and
+ * only the selected hits; iteration 3 on the box centred on iteration 2's values (z0 moved
+ * to the new reference point) with the finest voxels.  Hit finding after each iteration
+ * looks at every hit.  out: n_iter records; sel_out (may be NULL): the last selection. */
+int or4_solve_event(const or4_opts *o, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
+                    const double *drift, or4_iter *out, uint8_t *sel_out) {
+    int old = fegetround();
+    fesetround(FE_TONEAREST);
+    uint8_t *act = (uint8_t *)malloc((size_t)(n_hits > 0 ? n_hits : 1));
+    uint8_t *sel = (uint8_t *)malloc((size_t)(n_hits > 0 ? n_hits : 1));
+    for (int32_t i = 0; i < n_hits; i++) act[i] = 1;
+    double ref[2] = {0.0, 0.0};
+    or4_grid g;
+    for (int k = 0; k < o->n_iter && k < 3; k++) {
+        for (int a = 0; a < 4; a++) { g.w[a] = o->w[k][a]; g.n[a] = o->n[k][a]; }
+        if (k < 2) {
+            for (int a = 0; a < 4; a++) g.lo[a] = o->glo[a];
+        } else {
+            double ref_n[2] = {ref[0], ref[1]};
+            v4_new_ref(&out[k - 1], w, n_hits, wire_id, sel, ref_n);
+            double c[4] = {out[k - 1].value[0], out[k - 1].value[1], out[k - 1].value[2],
+                           v4_move_z0(o, &out[k - 1], ref, ref_n)};
+            ref[0] = ref_n[0]; ref[1] = ref_n[1];
+            for (int a = 0; a < 4; a++) g.lo[a] = c[a] - ((double)g.n[a] * g.w[a]) * 0.5;
+        }
+        if (k == 1) v4_new_ref(&out[0], w, n_hits, wire_id, sel, ref);
+        const int64_t nvox = (int64_t)g.n[0] * g.n[1] * g.n[2] * g.n[3];
+        int32_t *votes = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * nvox));
+        or4_vote_grid(o, &g, ref, w, n_hits, wire_id, drift, act, votes);
+        fesetround(FE_TONEAREST);
+        v4_estimate(&g, votes, &out[k]);
+        free(votes);
+        out[k].ref[0] = ref[0];
+        out[k].ref[1] = ref[1];
+        out[k].n_sel = v4_find_hits(o, &out[k], ref, w, n_hits, wire_id, drift, sel);
+        fesetround(FE_TONEAREST);
+        for (int32_t i = 0; i < n_hits; i++) act[i] = sel[i];
+    }
+    if (sel_out) memcpy(sel_out, sel, (size_t)n_hits);
+    free(act);
+    free(sel);
+    fesetround(old);
+    return 0;
+}
+
+/* One pair of the 4-D midpoint form (for the pins): box = (x_c, y_c, R, z0) lo/hi,
+ * sign of tan(lambda), reference point, hit; out (may be NULL): d^Ax+, d^Ax-, guard flags,
+ * |tan(lambda)| at the centre, psi. */
+int or4_vote_pair(const double box[8], int32_t sign, const double ref[2], const double hit[9],
+                  double p_gev, double b_tesla, int32_t prec, double out[5]) {
+    int old = fegetround();
+    fesetround(FE_TONEAREST);
+    double c[4];
+    for (int a = 0; a < 4; a++) c[a] = (box[2 * a] + box[2 * a + 1]) * 0.5;
+    int v = 0;
+    if (out) for (int i = 0; i < 5; i++) out[i] = 0;
+    if (prec == 0) {
+        v4ctr_d m = v4_centre_d(c[0], c[1], c[2], p_gev, b_tesla, ref[0], ref[1]);
+        if (m.valid) {
+            v4pre_d pre = v4_prefix_d(&m, hit);
+            if (out) { out[3] = m.aL; out[4] = pre.psi; }
+            if (pre.guard) { v = 1; if (out) out[2] = 3; }
+            else {
+                double dax[2];
+                int gflag = v4_dax_d(&pre, c[3], sign > 0 ? m.aL : -m.aL, hit, dax);
+                if (out) { out[0] = dax[0]; out[1] = dax[1]; out[2] = gflag; }
+                v = v4_pair_d(&m, &pre, c[3], sign, hit, mk_d(box[0], box[1]), mk_d(box[2], box[3]),
+                              mk_d(box[4], box[5]));
+            }
+        }
+    } else {
+        v4ctr_f m = v4_centre_f((float)c[0], (float)c[1], (float)c[2], (float)p_gev, (float)b_tesla,
+                                (float)ref[0], (float)ref[1]);
+        if (m.valid) {
+            float hf[9];
+            for (int k = 0; k < 9; k++) hf[k] = (float)hit[k];
+            v4pre_f pre = v4_prefix_f(&m, hf);
+            if (out) { out[3] = m.aL; out[4] = pre.psi; }
+            if (pre.guard) { v = 1; if (out) out[2] = 3; }
+            else {
+                float dax[2];
+                int gflag = v4_dax_f(&pre, (float)c[3], sign > 0 ? m.aL : -m.aL, hf, dax);
+                if (out) { out[0] = dax[0]; out[1] = dax[1]; out[2] = gflag; }
+                fesetround(FE_DOWNWARD);
+                iv_f X = mk_f(rd32(box[0]), ru32(box[1])), Y = mk_f(rd32(box[2]), ru32(box[3]));
+                iv_f Rv = mk_f(rd32(box[4]), ru32(box[5]));
+                fesetround(FE_TONEAREST);
+                v = v4_pair_f(&m, &pre, (float)c[3], sign, hf, hit, X, Y, Rv);
+            }
+        }
+    }
+    fesetround(old);
+    return v;
 }

@@ -26,6 +26,23 @@ class OrGrid(C.Structure):
                 ("sincos_mid", C.POINTER(C.c_double))]
 
 
+class Or4Grid(C.Structure):
+    _fields_ = [("lo", C.c_double * 4), ("w", C.c_double * 4), ("n", C.c_int32 * 4)]
+
+
+class Or4Opts(C.Structure):
+    _fields_ = [("p_gev", C.c_double), ("b_tesla", C.c_double), ("disk_radius", C.c_double),
+                ("hit_factor", C.c_double), ("glo", C.c_double * 4),
+                ("w", (C.c_double * 4) * 3), ("n", (C.c_int32 * 4) * 3),
+                ("precision", C.c_int32), ("n_iter", C.c_int32)]
+
+
+class Or4Iter(C.Structure):
+    _fields_ = [("value", C.c_double * 4), ("err", C.c_double * 4), ("ref", C.c_double * 2),
+                ("sign", C.c_int32), ("vmax", C.c_int32), ("n_max", C.c_int32),
+                ("n_sel", C.c_int32)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -53,6 +70,15 @@ def lib():
         L.or_sincos_iv.argtypes = [C.c_double, C.c_double, C.c_int, dp]
         L.or_op_counts.argtypes = [dp, dp, C.c_int, C.POINTER(C.c_ulonglong)]
         L.or_num_threads.restype = C.c_int
+        L.or4_vote_pair.argtypes = [dp, C.c_int32, dp, dp, C.c_double, C.c_double, C.c_int32, dp]
+        L.or4_vote_pair.restype = C.c_int
+        L.or4_vote_grid.argtypes = [C.POINTER(Or4Opts), C.POINTER(Or4Grid), dp, C.POINTER(OrWires),
+                                    C.c_int32, ip, dp, C.POINTER(C.c_uint8), ip]
+        L.or4_estimate.argtypes = [C.POINTER(Or4Grid), ip, C.POINTER(Or4Iter)]
+        L.or4_disk.argtypes = [dp, C.c_double, C.c_int32]
+        L.or4_disk.restype = C.c_int
+        L.or4_solve_event.argtypes = [C.POINTER(Or4Opts), C.POINTER(OrWires), C.c_int32, ip, dp,
+                                      C.POINTER(Or4Iter), C.POINTER(C.c_uint8)]
         L.or_set_num_threads.argtypes = [C.c_int]
         _lib = L
     return _lib
@@ -255,3 +281,92 @@ def solve_event_multi(tab: Tables, wire_id, drift, max_tracks: int, min_votes: i
     k = int(nf[0])
     return dict(n_tracks=k, p=p.reshape(max_tracks, 5)[:k], w=werr.reshape(max_tracks, 5)[:k],
                 votes=votes[:k], hit_track=ht[:n])
+
+
+# ---------------------------------------------------------------------------------------- #
+# The paper's own 4-D search (x_c, y_c, R, z0; Sections 3.1-3.3, Table tabGridDef)
+# ---------------------------------------------------------------------------------------- #
+def four_opts(p_gev=0.105, b_tesla=1.0, disk_radius=0.10, hit_factor=5.0, glo=None, w=None,
+              n=None, precision=0, n_iter=3) -> Or4Opts:
+    """Defaults: Table tabGridDef read in metres with z0 centred on the chamber middle:
+    iterations 1 and 2 on x_c, y_c in [-0.45, 0.45], R in [0.225, 0.375], z0 in [-0.75, 0.75]
+    with voxels 18 x 18 x 3.75 x 75 mm and 10 x 10 x 3.75 x 75 mm; iteration 3 on the
+    estimate +- (25, 25, 25, 400) mm with 1 x 1 x 1 x 40 mm voxels."""
+    o = Or4Opts()
+    o.p_gev, o.b_tesla, o.disk_radius, o.hit_factor = p_gev, b_tesla, disk_radius, hit_factor
+    glo = (-0.45, -0.45, 0.225, -0.75) if glo is None else glo
+    w = ((0.018, 0.018, 0.00375, 0.075), (0.010, 0.010, 0.00375, 0.075),
+         (0.001, 0.001, 0.001, 0.040)) if w is None else w
+    n = ((50, 50, 40, 20), (90, 90, 40, 20), (50, 50, 50, 20)) if n is None else n
+    for a in range(4):
+        o.glo[a] = glo[a]
+    for k in range(3):
+        for a in range(4):
+            o.w[k][a] = w[k][a]
+            o.n[k][a] = n[k][a]
+    o.precision, o.n_iter = precision, n_iter
+    return o
+
+
+def four_vote_pair(box8, sign, ref, hit9, p_gev=0.105, b_tesla=1.0, prec=0):
+    """4-D midpoint-form vote of one (voxel, hit) pair and (d^Ax+, d^Ax-, guard flags,
+    |tan(lambda)| at the centre, psi)."""
+    b = np.ascontiguousarray(box8, np.float64)
+    r = np.ascontiguousarray(ref, np.float64)
+    h = np.ascontiguousarray(hit9, np.float64)
+    out = np.zeros(5)
+    v = lib().or4_vote_pair(_p(b, C.c_double), int(sign), _p(r, C.c_double), _p(h, C.c_double),
+                            float(p_gev), float(b_tesla), int(prec), _p(out, C.c_double))
+    return int(v), out
+
+
+def four_grid(lo, w, n) -> Or4Grid:
+    g = Or4Grid()
+    for a in range(4):
+        g.lo[a], g.w[a], g.n[a] = lo[a], w[a], n[a]
+    return g
+
+
+def four_vote_grid(opts: Or4Opts, grid: Or4Grid, ref, tab: Tables, wire_id, drift, active=None):
+    """Votes (2, n_z0, n_R, n_y, n_x) of every voxel of one grid for one event; index 0 of
+    the first axis is tan(lambda) > 0."""
+    wid = np.ascontiguousarray(wire_id, np.int32)
+    dr = np.ascontiguousarray(drift, np.float64)
+    r = np.ascontiguousarray(ref, np.float64)
+    nvox = int(np.prod([grid.n[a] for a in range(4)]))
+    out = np.zeros(2 * nvox, np.int32)
+    act = None if active is None else np.ascontiguousarray(active, np.uint8)
+    lib().or4_vote_grid(C.byref(opts), C.byref(grid), _p(r, C.c_double), C.byref(tab.cw),
+                        int(wid.shape[0]), _p(wid, C.c_int32), _p(dr, C.c_double),
+                        None if act is None else _p(act, C.c_uint8), _p(out, C.c_int32))
+    return out.reshape(2, grid.n[3], grid.n[2], grid.n[1], grid.n[0])
+
+
+def four_disk(box6, radius=0.10, prec=0) -> bool:
+    """Disk pre-filter (Eq. ApoVoteDisk) of one voxel (x_c, y_c, R as lo, hi)."""
+    b = np.ascontiguousarray(box6, np.float64)
+    return bool(lib().or4_disk(_p(b, C.c_double), float(radius), int(prec)))
+
+
+def four_estimate(grid: Or4Grid, votes) -> dict:
+    v = np.ascontiguousarray(votes, np.int32).reshape(-1)
+    it = Or4Iter()
+    lib().or4_estimate(C.byref(grid), _p(v, C.c_int32), C.byref(it))
+    return _iter_dict(it)
+
+
+def _iter_dict(it) -> dict:
+    return dict(value=np.array(it.value[:]), err=np.array(it.err[:]), ref=np.array(it.ref[:]),
+                sign=int(it.sign), vmax=int(it.vmax), n_max=int(it.n_max), n_sel=int(it.n_sel))
+
+
+def four_solve_event(opts: Or4Opts, tab: Tables, wire_id, drift):
+    """The three iterations for one event: list of per-iteration dicts and the last hit
+    selection."""
+    wid = np.ascontiguousarray(wire_id, np.int32)
+    dr = np.ascontiguousarray(drift, np.float64)
+    its = (Or4Iter * 3)()
+    sel = np.zeros(max(wid.shape[0], 1), np.uint8)
+    lib().or4_solve_event(C.byref(opts), C.byref(tab.cw), int(wid.shape[0]), _p(wid, C.c_int32),
+                          _p(dr, C.c_double), its, _p(sel, C.c_uint8))
+    return [_iter_dict(its[k]) for k in range(opts.n_iter)], sel[:wid.shape[0]].astype(bool)

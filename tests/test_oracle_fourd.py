@@ -1,0 +1,184 @@
+"""Pins of the oracle's 4-D search (the paper's own workload, Sections 3.1-3.3), without a
+GPU.
+
+  * d^Ax of the midpoint form against the libm point model written in the paper's notation
+    (Eqs. ApproxPhi_a-d, normudi, EQSinter_c, defdiAX_b), with the reference point moved
+    off the origin, both drift signs and both signs of tan(lambda);
+  * a +-1 mm voxel around the true helix, with the reference point on the track so every
+    hit lies within half a turn of it, gets the vote of every noiseless hit in the true
+    tan(lambda) accumulator;
+  * the disk pre-filter (Eq. ApoVoteDisk) never drops a voxel holding a circle that passes
+    within the disk radius of the origin (dense sampling);
+  * the grid votes equal the pair-by-pair votes, voxels outside the disk get none;
+  * the estimate against brute force in numpy;
+  * the three iterations recover generated electrons.
+"""
+import numpy as np
+import pytest
+
+from gen import comet, grid as G
+from oracle import oracle as O, point_model as pm
+
+
+@pytest.fixture(scope="module")
+def wires():
+    return comet.make_wires()
+
+
+@pytest.fixture(scope="module")
+def events(wires):
+    return comet.events(8, seed=51, w=wires)
+
+
+@pytest.fixture(scope="module")
+def tab(wires):
+    return O.Tables(G.make_grid([4] * 5, 1, 4), wires)     # the wire table is what is used
+
+
+def _wire5(w, i):
+    return (w.x0[i], w.y0[i], w.sin_phis[i], w.cos_phis[i], w.tan_tau[i])
+
+
+def _model_dax(xc, yc, R, z0, tanl, ref, wire5, d_st):
+    """sqrt(A2 - F) - R from the point model, in the frame with the reference point at the
+    origin and z_ref = 0: d0 = |C - ref| - R, phi0 from C - ref (Eq. HelixEq_d)."""
+    cx, cy = xc - ref[0], yc - ref[1]
+    rc = np.hypot(cx, cy)
+    params = (rc - R, np.arctan2(-cx, cy), 1.0 / R, z0, tanl)
+    x0, y0, s, c, t = wire5
+    wire = (x0 - ref[0], y0 - ref[1], s, c, t)
+    a = pm.ax_quantities(params, wire, 0.0)
+    F = pm.F_approx(params, wire, d_st, z_ref=0.0)
+    return np.sqrt(a["RA"] ** 2 - F) - a["R"]
+
+
+def test_four_dax_matches_point_model(wires, events):
+    rng = np.random.default_rng(3)
+    n = 0
+    worst = 0.0
+    for e in range(events.n_events):
+        tr = events.tracks[e][0]
+        xc, yc, R = comet.helix_centre(tr)
+        hs = events.hit_truth[e]
+        for h in hs:
+            ref = np.array([wires.x0[hs[len(hs) // 2].wire], wires.y0[hs[len(hs) // 2].wire]])
+            c = np.array([xc, yc, R, 0.0]) + rng.normal(0, 1, 4) * np.array([2e-3, 2e-3, 2e-3, 0.05])
+            half = rng.uniform(1e-5, 5e-3, 4)
+            box = np.stack([c - half, c + half], axis=1).reshape(-1)
+            cen = (box[0::2] + box[1::2]) * 0.5
+            hv = O.hit9(wires, h.wire, h.drift)
+            for sign in (1, -1):
+                _, out = O.four_vote_pair(box, sign, ref, hv)
+                if out[2]:
+                    continue
+                tanl = sign * out[3]
+                for sg in (0, 1):
+                    d_st = h.drift if sg == 0 else -h.drift
+                    dm = _model_dax(cen[0], cen[1], cen[2], cen[3], tanl, ref, _wire5(wires, h.wire), d_st)
+                    err = abs(out[sg] - dm)
+                    worst = max(worst, err)
+                    assert err < 1e-9, (e, h.wire, sign, sg, out[sg], dm)
+                    n += 1
+    assert n > 400
+    assert worst < 1e-10
+
+
+def test_four_true_voxel_gets_every_noiseless_hit(wires, events):
+    """Reference point at the middle hit of the arc (every hit within half a turn of it),
+    voxel = truth +- 1 mm, z0 = the true z at the reference point: every hit votes in the
+    accumulator of the true sign of tan(lambda)."""
+    for e in range(events.n_events):
+        tr = events.tracks[e][0]
+        xc, yc, R = comet.helix_centre(tr)
+        hs = sorted(events.hit_truth[e], key=lambda h: h.s)
+        mid = hs[len(hs) // 2]
+        ref = np.array([wires.x0[mid.wire], wires.y0[mid.wire]])
+        # the wire's waist point is near, not on, the helix: take the true z of the helix
+        # at the phase of the reference point
+        z0 = comet.z_at_point(tr, ref[0], ref[1])
+        c = np.array([xc, yc, R, z0])
+        box = np.stack([c - 1e-3, c + 1e-3], axis=1).reshape(-1)
+        sign = 1 if tr.tanl > 0 else -1
+        votes = [O.four_vote_pair(box, sign, ref, O.hit9(wires, h.wire, h.drift))[0] for h in hs]
+        assert all(votes), (e, np.flatnonzero(np.array(votes) == 0))
+
+
+def test_four_disk_filter_keeps_every_circle_near_the_origin():
+    """Soundness of the disk test: a voxel holding a sampled (x_c, y_c, R) whose circle
+    passes within 0.1 m of the origin is kept, in FP64 and FP32; and voxels far from every
+    such circle are dropped (the test is not trivially true)."""
+    rng = np.random.default_rng(4)
+    kept_far = dropped = 0
+    for _ in range(4000):
+        ix, iy, iR = rng.integers(0, 50), rng.integers(0, 50), rng.integers(0, 40)
+        box = (-0.45 + ix * 0.018, -0.45 + (ix + 1) * 0.018, -0.45 + iy * 0.018,
+               -0.45 + (iy + 1) * 0.018, 0.225 + iR * 0.00375, 0.225 + (iR + 1) * 0.00375)
+        xs = box[0] + rng.uniform(0, 1, 256) * 0.018
+        ys = box[2] + rng.uniform(0, 1, 256) * 0.018
+        Rs = box[4] + rng.uniform(0, 1, 256) * 0.00375
+        gap = np.abs(np.hypot(xs, ys) - Rs)
+        for prec in (0, 1):
+            kept = O.four_disk(box, 0.10, prec)
+            if gap.min() <= 0.1:
+                assert kept, (box, prec)
+            elif gap.min() > 0.13:
+                kept_far += kept
+                dropped += not kept
+    assert dropped > 1000 and kept_far == 0
+
+
+def test_four_grid_votes_equal_pairs(wires, events, tab):
+    o = O.four_opts()
+    grid = O.four_grid((0.05, -0.25, 0.27, -0.3), (0.02, 0.02, 0.01, 0.1), (4, 5, 3, 6))
+    e = 0
+    a, b = events.offsets[e], events.offsets[e + 1]
+    wid, dr = events.wire_id[a:b], events.drift[a:b]
+    ref = (0.01, -0.02)
+    for prec in (0, 1):
+        o.precision = prec
+        votes = O.four_vote_grid(o, grid, ref, tab, wid, dr)
+        rng = np.random.default_rng(5)
+        for _ in range(25):
+            ix, iy, iR, iz = (int(rng.integers(0, grid.n[k])) for k in range(4))
+            box = []
+            for k, i in enumerate((ix, iy, iR, iz)):
+                box += [grid.lo[k] + i * grid.w[k], grid.lo[k] + (i + 1) * grid.w[k]]
+            in_disk = O.four_disk(box[:6], 0.10, prec)
+            for s, sign in ((0, 1), (1, -1)):
+                ref_v = sum(O.four_vote_pair(np.array(box), sign, ref, O.hit9(wires, int(wi), float(di)),
+                                             prec=prec)[0] for wi, di in zip(wid, dr)) if in_disk else 0
+                assert votes[s, iz, iR, iy, ix] == ref_v, (prec, s, ix, iy, iR, iz)
+
+
+def test_four_estimate_brute_force():
+    rng = np.random.default_rng(6)
+    grid = O.four_grid((-0.1, 0.2, 0.25, -0.5), (0.01, 0.02, 0.004, 0.05), (7, 6, 5, 4))
+    for trial in range(20):
+        votes = rng.integers(0, 6, size=(2, 4, 5, 6, 7)).astype(np.int32)
+        r = O.four_estimate(grid, votes)
+        vm = votes.reshape(2, -1).max(axis=1)
+        s = 0 if vm[0] >= vm[1] else 1
+        assert r["sign"] == (1 if s == 0 else -1) and r["vmax"] == vm[s]
+        iz, iR, iy, ix = np.nonzero(votes[s] == vm[s])
+        assert r["n_max"] == ix.size
+        for a, idx in enumerate((ix, iy, iR, iz)):
+            val = grid.lo[a] + grid.w[a] * (idx.sum() / idx.size + 0.5)
+            err = grid.w[a] * (idx.max() - idx.min() + 1) / 2
+            assert r["value"][a] == val and r["err"][a] == err, (trial, a)
+
+
+def test_four_three_iterations_recover_electrons(wires, events, tab):
+    """Two generated electrons: after the third iteration x_c, y_c, R within 2 mm, z0 at the
+    final reference point within 3 cm, and the sign of tan(lambda) right."""
+    o = O.four_opts()
+    for e in (1, 2):
+        a, b = events.offsets[e], events.offsets[e + 1]
+        its, sel = O.four_solve_event(o, tab, events.wire_id[a:b], events.drift[a:b])
+        tr = events.tracks[e][0]
+        xc, yc, R = comet.helix_centre(tr)
+        last = its[-1]
+        assert abs(last["value"][0] - xc) < 2e-3 and abs(last["value"][1] - yc) < 2e-3
+        assert abs(last["value"][2] - R) < 2e-3
+        assert abs(last["value"][3] - comet.z_at_point(tr, *last["ref"])) < 0.03
+        assert last["sign"] == (1 if tr.tanl > 0 else -1)
+        assert sel.sum() >= 0.8 * (b - a)
