@@ -285,6 +285,77 @@ def background_study(w, n_events: int = 1024, seed: int = 4) -> dict:
             "by_noise_fraction": rows}
 
 
+def paper_search_leg(n_events: int = 512, seed: int = 70, cpu_events: int = 1) -> dict:
+    """The paper's own search (Sections 3.1-3.3): COMET-like toy, 105 MeV/c electrons, 4-D
+    voxels x_c x y_c x R x z0 with two tan(lambda) accumulators, disk pre-filter, midpoint
+    form, the three iterations of Table tabGridDef with hit finding and the moving
+    reference point; time per track in FP64 and FP32 and the resolution per iteration
+    (Table HelixParametes' quantities).  cpu_events > 0 also times the oracle on that many
+    events (host cores)."""
+    import torch
+    from gen import comet
+    from paper_2401_04576_gb300 import apo
+    w = comet.make_wires()
+    ev = comet.events(n_events, seed=seed, w=w)
+    ch = apo.Chamber4(w)
+    hits = apo.DeviceHits.from_events(ev)
+    res = {"workload": f"{ev.n_events} electrons of 105 MeV/c from the origin in a 20-layer, "
+                       f"4,986-wire chamber (mean {ev.offsets[-1] / ev.n_events:.1f} hits, noiseless), "
+                       "3 iterations of Table tabGridDef (2M / 6.5M / 2.5M voxels x 2 signs before "
+                       "the disk filter), midpoint form",
+           "paper_context": {"s_per_track_4xK80": 1.2, "s_per_track_V100": 0.2,
+                             "rms_mm_iter3": {"x_c": 0.23, "y_c": 0.23, "R": 0.19, "z0": 2.68},
+                             "wrong_sign_fraction": [0.166, 0.047, 0.0],
+                             "within_1mm_10mm": 0.997}}
+    for prec, name in ((apo.F64, "fp64"), (apo.F32, "fp32")):
+        o = apo.four_opts(precision=prec)
+        ws = ch.workspace(ev.n_events, o)
+        out, sel = apo.solve4(ch, hits, o, workspace=ws)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(2):
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            apo.solve4(ch, hits, o, out=out, selected=sel, workspace=ws)
+            s1.record()
+            s1.synchronize()
+            ms.append(s0.elapsed_time(s1))
+        r = apo.iters4_to_numpy(out, ev.n_events, 3)
+        iters = []
+        for k in range(3):
+            d = []
+            for e in range(ev.n_events):
+                tr = ev.tracks[e][0]
+                xc, yc, R = comet.helix_centre(tr)
+                z0 = comet.z_at_point(tr, *r[e, k]["ref"])
+                v = r[e, k]["value"]
+                d.append([v[0] - xc, v[1] - yc, v[2] - R, v[3] - z0,
+                          float(r[e, k]["sign"] != (1 if tr.tanl > 0 else -1))])
+            d = np.array(d)
+            iters.append({"mean_mm": dict(zip(("x_c", "y_c", "R", "z0"), (d[:, :4].mean(0) * 1e3).round(3).tolist())),
+                          "rms_mm": dict(zip(("x_c", "y_c", "R", "z0"), (d[:, :4].std(0) * 1e3).round(3).tolist())),
+                          "wrong_sign_fraction": float(d[:, 4].mean()),
+                          "within_1mm_10mm": float(np.mean((np.abs(d[:, :3]) < 1e-3).all(1) &
+                                                           (np.abs(d[:, 3]) < 1e-2)))})
+        t = min(ms)
+        res[name] = {"ms_per_track": t / ev.n_events, "tracks_per_s": ev.n_events / (t * 1e-3),
+                     "batch_ms": t, "iterations": iters}
+    ch.close()
+    if cpu_events > 0:
+        from gen import grid as G
+        from oracle import oracle as O
+        tab = O.Tables(G.make_grid([4] * 5, 1, 4), w)
+        oo = O.four_opts()
+        t0 = time.perf_counter()
+        for e in range(cpu_events):
+            a, b = ev.offsets[e], ev.offsets[e + 1]
+            O.four_solve_event(oo, tab, ev.wire_id[a:b], ev.drift[a:b])
+        dt = time.perf_counter() - t0
+        res["cpu_oracle"] = {"s_per_track": dt / cpu_events, "cores": O.num_threads(),
+                             "kind": "oracle", "sample": f"{cpu_events} event(s), FP64, all 3 iterations"}
+    return res
+
+
 def cpu_baseline(w, g, ev, n_sample: int) -> dict:
     """The oracle as it stands, on the host cores, over the first n_sample events (full
     coarse-to-fine search each)."""
@@ -549,6 +620,8 @@ def run_apo(args) -> None:
             line["p50_p99_at_offered_per_s"] = below[-1]["offered_per_s"]
     if rank == 0 and not args.no_bg:
         line["background_rejection"] = background_study(w)
+    if rank == 0 and not args.no_paper4d:
+        line["paper_search_4d"] = paper_search_leg(cpu_events=0 if args.no_cpu_baseline else 1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, g, ev, args.cpu_sample)
     if rank == 0:
@@ -595,6 +668,7 @@ def main(argv=None):
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-mid", action="store_true", help="skip the midpoint-form leg")
     ap.add_argument("--no-bg", action="store_true", help="skip the background-rejection study")
+    ap.add_argument("--no-paper4d", action="store_true", help="skip the paper's own 4-D search")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--case", default=None,
                     choices=["coarse-f64", "coarse-f32", "solve-f64", "solve-f32", "solve-bulk"],

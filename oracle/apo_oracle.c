@@ -459,27 +459,30 @@ static void v4_edge(const or4_grid *g, int a, int i, double *lo, double *hi) {
     *hi = g->lo[a] + (double)(i + 1) * g->w[a];
 }
 
-/* The vote of one hit for one voxel centre (m, z0c, sign) and the voxel's intervals. */
-static int v4_pair_d(const v4ctr_d *m, const v4pre_d *pre, double z0c, int sign, const double h[9],
-                     iv_d X, iv_d Y, iv_d Rv) {
+/* The vote of one hit for one voxel centre (m, the prefix at its z0, sign) and the
+ * voxel's intervals X, Y, Rv, Z (either drift sign; a guard votes). */
+static int v4_pair_d(const v4ctr_d *m, const v4pre_d *pre, int sign, const double h[9], iv_d X, iv_d Y,
+                     iv_d Rv, iv_d Z) {
     double dax[2];
-    int g = v4_dax_d(pre, z0c, sign > 0 ? m->aL : -m->aL, h, dax);
+    int g = v4_dax_d(pre, sign > 0 ? m->aL : -m->aL, h, dax);
     fesetround(FE_DOWNWARD);
     int v = 0;
     for (int sg = 0; sg < 2 && !v; sg++)
-        v = (g >> sg & 1) ? 1 : v4_test_d(X, Y, Rv, mk_d(h[0], h[0]), mk_d(h[1], h[1]), dax[sg]);
+        v = (g >> sg & 1) ? 1 : v4_test_d(X, Y, Rv, Z, mk_d(h[0], h[0]), mk_d(h[1], h[1]),
+                                          mk_d(h[5], h[5]), mk_d(h[6], h[6]), dax[sg]);
     fesetround(FE_TONEAREST);
     return v;
 }
-static int v4_pair_f(const v4ctr_f *m, const v4pre_f *pre, float z0c, int sign, const float hf[9],
-                     const double h[9], iv_f X, iv_f Y, iv_f Rv) {
+static int v4_pair_f(const v4ctr_f *m, const v4pre_f *pre, int sign, const float hf[9], const double h[9],
+                     iv_f X, iv_f Y, iv_f Rv, iv_f Z) {
     float dax[2];
-    int g = v4_dax_f(pre, z0c, sign > 0 ? m->aL : -m->aL, hf, dax);
+    int g = v4_dax_f(pre, sign > 0 ? m->aL : -m->aL, hf, dax);
     fesetround(FE_DOWNWARD);
     iv_f x0 = mk_f(rd32(h[0]), ru32(h[0])), y0 = mk_f(rd32(h[1]), ru32(h[1]));
+    iv_f spt = mk_f(rd32(h[5]), ru32(h[5])), cpt = mk_f(rd32(h[6]), ru32(h[6]));
     int v = 0;
     for (int sg = 0; sg < 2 && !v; sg++)
-        v = (g >> sg & 1) ? 1 : v4_test_f(X, Y, Rv, x0, y0, dax[sg]);
+        v = (g >> sg & 1) ? 1 : v4_test_f(X, Y, Rv, Z, x0, y0, spt, cpt, dax[sg]);
     fesetround(FE_TONEAREST);
     return v;
 }
@@ -524,13 +527,14 @@ void or4_vote_grid(const or4_opts *o, const or4_grid *g, const double ref[2], co
                         for (int32_t i = 0; i < n_hits; i++) {
                             if (active && !active[i]) continue;
                             const double *h = hc + 9 * i;
-                            v4pre_d pre = v4_prefix_d(&m, h);
                             for (int iz = 0; iz < nz; iz++) {
                                 double zl, zh;
                                 v4_edge(g, 3, iz, &zl, &zh);
                                 const double zc = (zl + zh) * 0.5;
+                                v4pre_d pre = v4_prefix_d(&m, zc, h);
+                                iv_d Zd = mk_d(zl, zh);
                                 for (int s = 0; s < 2; s++)
-                                    cnt[s][iz] += pre.guard ? 1 : v4_pair_d(&m, &pre, zc, s == 0 ? 1 : -1, h, Xd, Yd, Rd);
+                                    cnt[s][iz] += pre.guard ? 1 : v4_pair_d(&m, &pre, s == 0 ? 1 : -1, h, Xd, Yd, Rd, Zd);
                             }
                         }
                 } else {
@@ -542,13 +546,16 @@ void or4_vote_grid(const or4_opts *o, const or4_grid *g, const double ref[2], co
                             const double *h = hc + 9 * i;
                             float hf[9];
                             for (int k = 0; k < 9; k++) hf[k] = (float)h[k];
-                            v4pre_f pre = v4_prefix_f(&m, hf);
                             for (int iz = 0; iz < nz; iz++) {
                                 double zl, zh;
                                 v4_edge(g, 3, iz, &zl, &zh);
                                 const float zc = (float)((zl + zh) * 0.5);
+                                v4pre_f pre = v4_prefix_f(&m, zc, hf);
+                                fesetround(FE_DOWNWARD);
+                                iv_f Zf = mk_f(rd32(zl), ru32(zh));
+                                fesetround(FE_TONEAREST);
                                 for (int s = 0; s < 2; s++)
-                                    cnt[s][iz] += pre.guard ? 1 : v4_pair_f(&m, &pre, zc, s == 0 ? 1 : -1, hf, h, Xf, Yf, Rf);
+                                    cnt[s][iz] += pre.guard ? 1 : v4_pair_f(&m, &pre, s == 0 ? 1 : -1, hf, h, Xf, Yf, Rf, Zf);
                             }
                         }
                 }
@@ -636,9 +643,9 @@ static int v4_find_hits(const or4_opts *o, const or4_iter *it, const double ref[
         if (o->precision == 0) {
             v4ctr_d m = v4_centre_d(c[0], c[1], c[2], o->p_gev, o->b_tesla, ref[0], ref[1]);
             if (m.valid) {
-                v4pre_d pre = v4_prefix_d(&m, h);
-                v = pre.guard ? 1 : v4_pair_d(&m, &pre, c[3], it->sign, h, mk_d(lo[0], hi[0]),
-                                              mk_d(lo[1], hi[1]), mk_d(lo[2], hi[2]));
+                v4pre_d pre = v4_prefix_d(&m, c[3], h);
+                v = pre.guard ? 1 : v4_pair_d(&m, &pre, it->sign, h, mk_d(lo[0], hi[0]),
+                                              mk_d(lo[1], hi[1]), mk_d(lo[2], hi[2]), mk_d(lo[3], hi[3]));
             }
         } else {
             v4ctr_f m = v4_centre_f((float)c[0], (float)c[1], (float)c[2], (float)o->p_gev,
@@ -646,12 +653,12 @@ static int v4_find_hits(const or4_opts *o, const or4_iter *it, const double ref[
             if (m.valid) {
                 float hf[9];
                 for (int k = 0; k < 9; k++) hf[k] = (float)h[k];
-                v4pre_f pre = v4_prefix_f(&m, hf);
+                v4pre_f pre = v4_prefix_f(&m, (float)c[3], hf);
                 fesetround(FE_DOWNWARD);
                 iv_f X = mk_f(rd32(lo[0]), ru32(hi[0])), Y = mk_f(rd32(lo[1]), ru32(hi[1]));
-                iv_f Rv = mk_f(rd32(lo[2]), ru32(hi[2]));
+                iv_f Rv = mk_f(rd32(lo[2]), ru32(hi[2])), Z = mk_f(rd32(lo[3]), ru32(hi[3]));
                 fesetround(FE_TONEAREST);
-                v = pre.guard ? 1 : v4_pair_f(&m, &pre, (float)c[3], it->sign, hf, h, X, Y, Rv);
+                v = pre.guard ? 1 : v4_pair_f(&m, &pre, it->sign, hf, h, X, Y, Rv, Z);
             }
         }
         sel[i] = (uint8_t)v;
@@ -676,13 +683,15 @@ static void v4_new_ref(const or4_iter *it, const or_wires *w, int32_t n_hits, co
 }
 
 /* z0 of the found helix moved from reference point a to b: z0 + tan(lambda) R dpsi, dpsi
- * the turn from a to b around the centre (half-angle form, in (-pi, pi)). */
+ * the phase of b minus that of a, both from the direction of the origin (as in the vote;
+ * 0 if either is undefined). */
 static double v4_move_z0(const or4_opts *o, const or4_iter *it, const double a[2], const double b[2]) {
     double xc = it->value[0], yc = it->value[1], R = it->value[2];
-    double ax = a[0] - xc, ay = a[1] - yc, bx = b[0] - xc, by = b[1] - yc;
-    double sn = ax * by - ay * bx, cs = ax * bx + ay * by;
-    double den = sqrt(ax * ax + ay * ay) * sqrt(bx * bx + by * by) + cs;
-    double dpsi = den > 0 ? 2.0 * p_atan_d(sn / den) : 0.0;
+    double ox = -xc, oy = -yc, on = sqrt(ox * ox + oy * oy);
+    int bad = !(on > 0);
+    double pa = bad ? 0.0 : v4_phase_d(ox, oy, on, a[0] - xc, a[1] - yc, &bad);
+    double pb = bad ? 0.0 : v4_phase_d(ox, oy, on, b[0] - xc, b[1] - yc, &bad);
+    double dpsi = bad ? 0.0 : pb - pa;
     double ratio = o->p_gev / ((0.3 * o->b_tesla) * R);
     double aL = ratio > 1 ? sqrt(ratio * ratio - 1.0) : 0.0;
     double L = it->sign > 0 ? aL : -aL;
@@ -750,15 +759,15 @@ int or4_vote_pair(const double box[8], int32_t sign, const double ref[2], const 
     if (prec == 0) {
         v4ctr_d m = v4_centre_d(c[0], c[1], c[2], p_gev, b_tesla, ref[0], ref[1]);
         if (m.valid) {
-            v4pre_d pre = v4_prefix_d(&m, hit);
+            v4pre_d pre = v4_prefix_d(&m, c[3], hit);
             if (out) { out[3] = m.aL; out[4] = pre.psi; }
             if (pre.guard) { v = 1; if (out) out[2] = 3; }
             else {
                 double dax[2];
-                int gflag = v4_dax_d(&pre, c[3], sign > 0 ? m.aL : -m.aL, hit, dax);
+                int gflag = v4_dax_d(&pre, sign > 0 ? m.aL : -m.aL, hit, dax);
                 if (out) { out[0] = dax[0]; out[1] = dax[1]; out[2] = gflag; }
-                v = v4_pair_d(&m, &pre, c[3], sign, hit, mk_d(box[0], box[1]), mk_d(box[2], box[3]),
-                              mk_d(box[4], box[5]));
+                v = v4_pair_d(&m, &pre, sign, hit, mk_d(box[0], box[1]), mk_d(box[2], box[3]),
+                              mk_d(box[4], box[5]), mk_d(box[6], box[7]));
             }
         }
     } else {
@@ -767,18 +776,18 @@ int or4_vote_pair(const double box[8], int32_t sign, const double ref[2], const 
         if (m.valid) {
             float hf[9];
             for (int k = 0; k < 9; k++) hf[k] = (float)hit[k];
-            v4pre_f pre = v4_prefix_f(&m, hf);
+            v4pre_f pre = v4_prefix_f(&m, (float)c[3], hf);
             if (out) { out[3] = m.aL; out[4] = pre.psi; }
             if (pre.guard) { v = 1; if (out) out[2] = 3; }
             else {
                 float dax[2];
-                int gflag = v4_dax_f(&pre, (float)c[3], sign > 0 ? m.aL : -m.aL, hf, dax);
+                int gflag = v4_dax_f(&pre, sign > 0 ? m.aL : -m.aL, hf, dax);
                 if (out) { out[0] = dax[0]; out[1] = dax[1]; out[2] = gflag; }
                 fesetround(FE_DOWNWARD);
                 iv_f X = mk_f(rd32(box[0]), ru32(box[1])), Y = mk_f(rd32(box[2]), ru32(box[3]));
-                iv_f Rv = mk_f(rd32(box[4]), ru32(box[5]));
+                iv_f Rv = mk_f(rd32(box[4]), ru32(box[5])), Z = mk_f(rd32(box[6]), ru32(box[7]));
                 fesetround(FE_TONEAREST);
-                v = v4_pair_f(&m, &pre, (float)c[3], sign, hf, hit, X, Y, Rv);
+                v = v4_pair_f(&m, &pre, sign, hf, hit, X, Y, Rv, Z);
             }
         }
     }

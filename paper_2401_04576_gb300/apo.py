@@ -57,6 +57,17 @@ class ApoSolveOpts(C.Structure):
                 ("tune", ApoTune), ("use_graph", C.c_int32), ("hit_track", C.c_void_p)]
 
 
+class Apo4Opts(C.Structure):
+    _fields_ = [("p_gev", C.c_double), ("b_tesla", C.c_double), ("disk_radius", C.c_double),
+                ("hit_factor", C.c_double), ("glo", C.c_double * 4),
+                ("w", (C.c_double * 4) * 3), ("n", (C.c_int32 * 4) * 3),
+                ("precision", C.c_int32), ("n_iter", C.c_int32)]
+
+
+APO4_ITER_DTYPE = np.dtype([("value", "<f8", (4,)), ("err", "<f8", (4,)), ("ref", "<f8", (2,)),
+                            ("sign", "<i4"), ("vmax", "<i4"), ("n_max", "<i4"), ("n_sel", "<i4")])
+
+
 class ApoServeOpts(C.Structure):
     _fields_ = [("solve", ApoSolveOpts), ("batch_events", C.c_int32), ("max_slots", C.c_int32),
                 ("device_bytes", C.c_size_t), ("max_pending", C.c_int32),
@@ -109,6 +120,13 @@ def lib():
         L.apo_diag_pipe_peak.argtypes = [i32, i32, C.POINTER(C.c_double)]
         L.apo_diag_wait_timeout.argtypes = [i32]
         L.apo_workspace_status.argtypes = [vp, i32, vp, vp]
+        L.apo4_opts_default.argtypes = [C.POINTER(Apo4Opts)]
+        L.apo4_chamber_create.argtypes = [C.POINTER(ApoWires), C.POINTER(vp)]
+        L.apo4_chamber_destroy.argtypes = [vp]
+        L.apo4_workspace_bytes.argtypes = [vp, i32, C.POINTER(Apo4Opts), C.POINTER(sz)]
+        L.apo4_solve_batch.argtypes = [vp, C.POINTER(ApoHits), C.POINTER(Apo4Opts), vp, vp, vp, sz, vp]
+        L.apo4_vote.argtypes = [vp, C.POINTER(ApoHits), C.POINTER(Apo4Opts), i32, vp, vp, vp, vp, vp,
+                                sz, vp]
         _lib = L
     return _lib
 
@@ -425,3 +443,99 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------------------- #
+# The paper's own 4-D search (include/apo4.h)
+# ---------------------------------------------------------------------------------------- #
+def four_opts(precision: int = F64, n_iter: int = 3, **kw) -> Apo4Opts:
+    """apo4_opts_default (Table tabGridDef in metres) with overrides: p_gev, b_tesla,
+    disk_radius, hit_factor, glo (4), w (3 x 4), n (3 x 4)."""
+    o = Apo4Opts()
+    lib().apo4_opts_default(C.byref(o))
+    o.precision, o.n_iter = int(precision), int(n_iter)
+    for k in ("p_gev", "b_tesla", "disk_radius", "hit_factor"):
+        if k in kw:
+            setattr(o, k, float(kw[k]))
+    if "glo" in kw:
+        for a in range(4):
+            o.glo[a] = kw["glo"][a]
+    for key in ("w", "n"):
+        if key in kw:
+            for i in range(3):
+                for a in range(4):
+                    getattr(o, key)[i][a] = kw[key][i][a]
+    return o
+
+
+class Chamber4:
+    """Device wire table for the 4-D search (apo4_chamber)."""
+
+    def __init__(self, wires):
+        keep = []
+
+        def dp(a):
+            a = np.ascontiguousarray(a, np.float64)
+            keep.append(a)
+            return a.ctypes.data_as(_dp)
+
+        w = ApoWires()
+        w.n_wires = int(wires.n)
+        for name in ("x0", "y0", "sin_phis", "cos_phis", "tan_tau", "sphi_t", "cphi_t", "t2"):
+            setattr(w, name, dp(getattr(wires, name)))
+        h = C.c_void_p()
+        _check(lib().apo4_chamber_create(C.byref(w), C.byref(h)))
+        self.handle = h
+
+    def workspace(self, n_events: int, opts: Apo4Opts):
+        n = C.c_size_t()
+        _check(lib().apo4_workspace_bytes(self.handle, int(n_events), C.byref(opts), C.byref(n)))
+        return _torch().empty(int(n.value), dtype=_torch().uint8, device="cuda")
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().apo4_chamber_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve4(ch: Chamber4, hits: DeviceHits, opts: Apo4Opts, out=None, selected=None,
+           workspace=None, stream=None):
+    """apo4_solve_batch: (uint8 tensor of apo4_iter records, n_events x n_iter; uint8
+    selection per hit)."""
+    torch = _torch()
+    ne = hits.n_events
+    if out is None:
+        out = torch.zeros(ne * opts.n_iter * APO4_ITER_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    if selected is None:
+        selected = torch.zeros(max(int(hits.wire_id.shape[0]), 1), dtype=torch.uint8, device="cuda")
+    ws = ch.workspace(ne, opts) if workspace is None else workspace
+    hc = hits.c()
+    _check(lib().apo4_solve_batch(ch.handle, C.byref(hc), C.byref(opts), _ptr(out), _ptr(selected),
+                                  _ptr(ws), ws.numel(), _stream_ptr(stream)))
+    return out, selected
+
+
+def iters4_to_numpy(out, n_events: int, n_iter: int) -> np.ndarray:
+    a = out.cpu().numpy() if hasattr(out, "cpu") else np.asarray(out)
+    return a.view(APO4_ITER_DTYPE).reshape(n_events, n_iter)
+
+
+def vote4(ch: Chamber4, hits: DeviceHits, opts: Apo4Opts, it: int, lo, ref, active=None,
+          out=None, workspace=None, stream=None):
+    """apo4_vote: int32 votes (n_events, 2, n_z0, n_R, n_y, n_x) of iteration it's grid."""
+    torch = _torch()
+    ne = hits.n_events
+    n = [opts.n[it][a] for a in range(4)]
+    if out is None:
+        out = torch.zeros((ne, 2, n[3], n[2], n[1], n[0]), dtype=torch.int32, device="cuda")
+    ws = ch.workspace(ne, opts) if workspace is None else workspace
+    hc = hits.c()
+    _check(lib().apo4_vote(ch.handle, C.byref(hc), C.byref(opts), int(it), _ptr(lo), _ptr(ref),
+                           _ptr(active), _ptr(out), _ptr(ws), ws.numel(), _stream_ptr(stream)))
+    return out

@@ -11,8 +11,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libapo.so")
-SOURCES = ["kernels.cu", "apo_abi.cu", "diag.cu", "apo_noalloc.cu", "apo_serve.cu"]
-HEADERS = ["interval.cuh", "vote_program.cuh", "kernels.cuh"]
+SOURCES = ["kernels.cu", "apo_abi.cu", "diag.cu", "apo_noalloc.cu", "apo_serve.cu", "apo4.cu"]
+HEADERS = ["interval.cuh", "vote_program.cuh", "kernels.cuh", "fourd.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          "--expt-relaxed-constexpr"]
@@ -27,7 +27,7 @@ def _nvcc() -> str:
 
 def _deps():
     return ([os.path.join(CSRC, s) for s in SOURCES + HEADERS] +
-            [os.path.join(ROOT, "include", "apo.h"), os.path.join(ROOT, "include", "apo_diag.h"),
+            [os.path.join(ROOT, "include", h) for h in ("apo.h", "apo_diag.h", "apo4.h")] + [
              os.path.abspath(__file__)])
 
 

@@ -2,8 +2,13 @@
 GPU.
 
   * d^Ax of the midpoint form against the libm point model written in the paper's notation
-    (Eqs. ApproxPhi_a-d, normudi, EQSinter_c, defdiAX_b), with the reference point moved
-    off the origin, both drift signs and both signs of tan(lambda);
+    (Eqs. ApproxPhi_a-d, normudi, EQSinter_c, defdiAX_b; z_ref = z0), with the reference
+    point moved off the origin (phases within half a turn of it, where the point model's
+    principal phase and the search's phase along the track agree), both drift signs and
+    both signs of tan(lambda);
+  * a +-1 mm voxel around the true helix gets the vote of every noiseless hit in the true
+    tan(lambda) accumulator, with the reference point at the origin (phases along the
+    track from the emission point, hits up to a full turn away);
   * a +-1 mm voxel around the true helix, with the reference point on the track so every
     hit lies within half a turn of it, gets the vote of every noiseless hit in the true
     tan(lambda) accumulator;
@@ -41,14 +46,14 @@ def _wire5(w, i):
 
 def _model_dax(xc, yc, R, z0, tanl, ref, wire5, d_st):
     """sqrt(A2 - F) - R from the point model, in the frame with the reference point at the
-    origin and z_ref = 0: d0 = |C - ref| - R, phi0 from C - ref (Eq. HelixEq_d)."""
+    origin and z_ref = z0: d0 = |C - ref| - R, phi0 from C - ref (Eq. HelixEq_d)."""
     cx, cy = xc - ref[0], yc - ref[1]
     rc = np.hypot(cx, cy)
     params = (rc - R, np.arctan2(-cx, cy), 1.0 / R, z0, tanl)
     x0, y0, s, c, t = wire5
     wire = (x0 - ref[0], y0 - ref[1], s, c, t)
-    a = pm.ax_quantities(params, wire, 0.0)
-    F = pm.F_approx(params, wire, d_st, z_ref=0.0)
+    a = pm.ax_quantities(params, wire, z0)
+    F = pm.F_approx(params, wire, d_st, z_ref=z0)
     return np.sqrt(a["RA"] ** 2 - F) - a["R"]
 
 
@@ -84,23 +89,24 @@ def test_four_dax_matches_point_model(wires, events):
 
 
 def test_four_true_voxel_gets_every_noiseless_hit(wires, events):
-    """Reference point at the middle hit of the arc (every hit within half a turn of it),
-    voxel = truth +- 1 mm, z0 = the true z at the reference point: every hit votes in the
-    accumulator of the true sign of tan(lambda)."""
+    """Voxel = truth +- 1 mm (z0 = the true z at the reference point), reference point at
+    the origin (the emission point; hits up to a full turn along the track) or at the
+    middle hit of the arc: every hit votes in the accumulator of the true sign of
+    tan(lambda)."""
     for e in range(events.n_events):
         tr = events.tracks[e][0]
         xc, yc, R = comet.helix_centre(tr)
         hs = sorted(events.hit_truth[e], key=lambda h: h.s)
         mid = hs[len(hs) // 2]
-        ref = np.array([wires.x0[mid.wire], wires.y0[mid.wire]])
-        # the wire's waist point is near, not on, the helix: take the true z of the helix
-        # at the phase of the reference point
-        z0 = comet.z_at_point(tr, ref[0], ref[1])
-        c = np.array([xc, yc, R, z0])
-        box = np.stack([c - 1e-3, c + 1e-3], axis=1).reshape(-1)
-        sign = 1 if tr.tanl > 0 else -1
-        votes = [O.four_vote_pair(box, sign, ref, O.hit9(wires, h.wire, h.drift))[0] for h in hs]
-        assert all(votes), (e, np.flatnonzero(np.array(votes) == 0))
+        for ref in (np.zeros(2), np.array([wires.x0[mid.wire], wires.y0[mid.wire]])):
+            # the wire's waist point is near, not on, the helix: take the true z of the
+            # helix at the phase of the reference point
+            z0 = comet.z_at_point(tr, ref[0], ref[1])
+            c = np.array([xc, yc, R, z0])
+            box = np.stack([c - 1e-3, c + 1e-3], axis=1).reshape(-1)
+            sign = 1 if tr.tanl > 0 else -1
+            votes = [O.four_vote_pair(box, sign, ref, O.hit9(wires, h.wire, h.drift))[0] for h in hs]
+            assert all(votes), (e, ref, np.flatnonzero(np.array(votes) == 0))
 
 
 def test_four_disk_filter_keeps_every_circle_near_the_origin():
