@@ -285,13 +285,14 @@ def background_study(w, n_events: int = 1024, seed: int = 4) -> dict:
             "by_noise_fraction": rows}
 
 
-def paper_search_leg(n_events: int = 512, seed: int = 70, cpu_events: int = 1) -> dict:
+def paper_search_leg(n_events: int = 512, seed: int = 70, cpu_events: int = 1, n_fp64: int = 64) -> dict:
     """The paper's own search (Sections 3.1-3.3): COMET-like toy, 105 MeV/c electrons, 4-D
     voxels x_c x y_c x R x z0 with two tan(lambda) accumulators, disk pre-filter, midpoint
     form, the three iterations of Table tabGridDef with hit finding and the moving
     reference point; time per track in FP64 and FP32 and the resolution per iteration
-    (Table HelixParametes' quantities).  cpu_events > 0 also times the oracle on that many
-    events (host cores)."""
+    (Table HelixParametes' quantities).  FP64 runs on the first n_fp64 events (its time
+    per track is the same on any batch of thousands of blocks), FP32 on all.  cpu_events
+    > 0 also times the oracle on that many events (host cores)."""
     import torch
     from gen import comet
     from paper_2401_04576_gb300 import apo
@@ -307,7 +308,10 @@ def paper_search_leg(n_events: int = 512, seed: int = 70, cpu_events: int = 1) -
                              "rms_mm_iter3": {"x_c": 0.23, "y_c": 0.23, "R": 0.19, "z0": 2.68},
                              "wrong_sign_fraction": [0.166, 0.047, 0.0],
                              "within_1mm_10mm": 0.997}}
+    ev_all, hits_all = ev, hits
     for prec, name in ((apo.F64, "fp64"), (apo.F32, "fp32")):
+        ev = ev_all.subset(range(min(n_fp64, ev_all.n_events))) if prec == apo.F64 else ev_all
+        hits = apo.DeviceHits.from_events(ev) if prec == apo.F64 else hits_all
         o = apo.four_opts(precision=prec)
         ws = ch.workspace(ev.n_events, o)
         out, sel = apo.solve4(ch, hits, o, workspace=ws)
@@ -339,8 +343,9 @@ def paper_search_leg(n_events: int = 512, seed: int = 70, cpu_events: int = 1) -
                                                            (np.abs(d[:, 3]) < 1e-2)))})
         t = min(ms)
         res[name] = {"ms_per_track": t / ev.n_events, "tracks_per_s": ev.n_events / (t * 1e-3),
-                     "batch_ms": t, "iterations": iters}
+                     "batch_ms": t, "tracks": ev.n_events, "iterations": iters}
     ch.close()
+    ev = ev_all
     if cpu_events > 0:
         from gen import grid as G
         from oracle import oracle as O
@@ -637,6 +642,19 @@ def run_case(args) -> None:
     the first --events events of the workload (for ncu captures of one launch)."""
     import torch
     from paper_2401_04576_gb300 import apo
+    if args.case.startswith("four"):
+        from gen import comet
+        w4 = comet.make_wires()
+        ev4 = comet.events(args.events, seed=70, w=w4)
+        ch = apo.Chamber4(w4)
+        h4 = apo.DeviceHits.from_events(ev4)
+        o4 = apo.four_opts(precision=apo.F32 if args.case == "four-f32" else apo.F64)
+        ws4 = ch.workspace(ev4.n_events, o4)
+        for _ in range(2):
+            apo.solve4(ch, h4, o4, workspace=ws4)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "events": ev4.n_events, "ok": True}))
+        return
     w, g, ev = make_inputs()
     ev = ev.subset(range(args.events))
     geom = apo.Geometry(g, w)
@@ -671,7 +689,8 @@ def main(argv=None):
     ap.add_argument("--no-paper4d", action="store_true", help="skip the paper's own 4-D search")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--case", default=None,
-                    choices=["coarse-f64", "coarse-f32", "solve-f64", "solve-f32", "solve-bulk"],
+                    choices=["coarse-f64", "coarse-f32", "solve-f64", "solve-f32", "solve-bulk",
+                             "four-f32", "four-f64"],
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--events", type=int, default=64)
     args = ap.parse_args(argv)

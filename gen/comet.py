@@ -19,6 +19,8 @@ Readings (the paper gives no more detail):
     half length, so the helix leaves |z| <= L/2 before completing a turn; "reaches the
     first three layers": 2 R exceeds the third layer's radius;
   * drift distances are the true distances (the paper adds no smearing);
+  * the paper's sample has 25-62 hits per track: tracks with fewer than 25 hits (the
+    steepest ones, which leave the chamber soonest) are redrawn;
   * the simulated arc is one full turn; a wire gets one hit, at its global closest
     approach, when that distance is under 8 mm and under half a cell.
 """
@@ -88,9 +90,9 @@ def draw_electron(rng: np.random.Generator) -> chamber.Track:
 
 
 def events(n_events: int, seed: int, w: chamber.Wires | None = None,
-           min_hits: int = 10) -> chamber.Events:
+           min_hits: int = 25) -> chamber.Events:
     """n_events single-electron events (noiseless drifts); tracks with fewer than
-    min_hits hits are redrawn."""
+    min_hits hits are redrawn (25: the lower end of the paper's 25-62)."""
     w = make_wires() if w is None else w
     rng = np.random.default_rng(seed)
     per, tracks, truths = [], [], []

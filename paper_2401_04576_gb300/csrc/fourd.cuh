@@ -26,12 +26,12 @@ __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b);
 __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
 
-// atan: three half-angle reductions (|x| below tan(pi/16) for any argument; the phases
-// reach 2 pi), the alternating series through x^15 (Horner on x^2), times 8; no remainder
-// term.  1/(2k+1) are round-to-nearest constants of T.
+// atan for |x| <= 1 (phase4 only asks for half angles up to pi/4): two half-angle
+// reductions (|x| below tan(pi/16)), the alternating series through x^15 (Horner on x^2),
+// times 4; no remainder term.  1/(2k+1) are round-to-nearest constants of T.
 template <typename T> __device__ __forceinline__ T atan(T x) {
 #pragma unroll
-    for (int i = 0; i < 3; i++) x = div(x, add(T(1), sqrt(add(T(1), mul(x, x)))));
+    for (int i = 0; i < 2; i++) x = div(x, add(T(1), sqrt(add(T(1), mul(x, x)))));
     const T y = mul(x, x);
     T h = T(1) / T(15);
     h = sub(T(1) / T(13), mul(h, y));
@@ -41,7 +41,7 @@ template <typename T> __device__ __forceinline__ T atan(T x) {
     h = sub(T(1) / T(5), mul(h, y));
     h = sub(T(1) / T(3), mul(h, y));
     h = sub(T(1), mul(h, y));
-    return mul(mul(x, h), T(8));
+    return mul(mul(x, h), T(4));
 }
 
 // sin / cos of the small phase correction: Taylor through d^9 / d^10, nested Horner on d^2.
