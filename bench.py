@@ -179,6 +179,7 @@ def serve_sweep(geom, ev, rates, seconds: float, batch_events: int = 64, max_slo
            for e in range(ev.n_events)]
     out = []
     rng = np.random.default_rng(5)
+    import torch
     for rate in rates:
         srv = apo.Server(geom, solve, batch_events=batch_events, max_slots=max_slots,
                          max_pending=max_pending)
@@ -199,6 +200,8 @@ def serve_sweep(geom, ev, rates, seconds: float, batch_events: int = 64, max_slo
         th = threading.Thread(target=poller)
         th.start()
         rejected = 0
+        clk = ClockSampler(torch.cuda.current_device())
+        clk.__enter__()
         t0 = time.perf_counter()
         for i in range(n):
             due = t0 + arrivals[i]
@@ -210,6 +213,7 @@ def serve_sweep(geom, ev, rates, seconds: float, batch_events: int = 64, max_slo
             else:
                 rejected += 1
         srv.drain(120000)
+        clk.__exit__(None, None, None)
         stop.set()
         th.join(timeout=120)
         lat = np.array([1e3 * (t_done[i] - t_arr[i]) for i in t_arr if i in t_done])
@@ -220,7 +224,8 @@ def serve_sweep(geom, ev, rates, seconds: float, batch_events: int = 64, max_slo
                     "sustained_per_s": lat.size / max(t_end - t0, 1e-9),
                     "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
                     "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
-                    "batches": batches, "max_slots_in_flight": max_busy})
+                    "batches": batches, "max_slots_in_flight": max_busy,
+                    "sm_mhz": clk.summary().get("sm_mhz")})
     return out
 
 
@@ -566,6 +571,50 @@ def run_apo(args) -> None:
         }
         del vmid, diff
 
+    # exact phase (Eq. CSAXtoPHI_a enclosed instead of expanded) on the first 256 events:
+    # coarse launch time against the expansion's, vote differences, whole-search time
+    exact = None
+    if not args.no_exact:
+        sub = ev.subset(range(min(256, ev.n_events)))
+        hs = apo.DeviceHits.from_events(sub)
+        v64 = apo.vote(geom, hs, precision=apo.F64, workspace=ws, stream=stream)
+        vex = torch.empty_like(v64)
+        ems, fms = [], []
+        for _ in range(2):
+            for prec_, acc, out_ in ((apo.F64_EXACT, ems, vex), (apo.F64, fms, v64)):
+                flush.fill_(1)
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                apo.vote(geom, hs, precision=prec_, out=out_, workspace=ws, stream=stream)
+                s1.record(stream)
+                s1.synchronize()
+                acc.append(s0.elapsed_time(s1))
+        dv = vex - v64
+        nc = dv.numel()
+        tr_sub = torch.zeros(sub.n_events * apo.TRACK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        nt_sub = torch.zeros(sub.n_events, dtype=torch.int32, device="cuda")
+        oex = apo.solve_opts(precision=[apo.F64_EXACT] * (lv + 1))
+        apo.solve_batch(geom, hs, oex, tracks=tr_sub, n_tracks=nt_sub, workspace=ws, stream=stream)
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        apo.solve_batch(geom, hs, oex, tracks=tr_sub, n_tracks=nt_sub, workspace=ws, stream=stream)
+        s1.record(stream)
+        s1.synchronize()
+        t_ex = s0.elapsed_time(s1)
+        tex = apo.tracks_to_numpy(tr_sub, sub.n_events)
+        dpx = np.abs(tex["p"][:, 0, :] - tracks64["p"][:sub.n_events, 0, :])
+        exact = {"precision": "FP64 intervals, exact phase at every level",
+                 "events": sub.n_events,
+                 "coarse_ms": min(ems), "coarse_ms_expansion": min(fms),
+                 "coarse_cost_vs_expansion": min(ems) / min(fms),
+                 "coarse_cells_differing": (dv != 0).sum().item() / nc,
+                 "coarse_cells_more_votes": (dv > 0).sum().item() / nc,
+                 "coarse_cells_fewer_votes": (dv < 0).sum().item() / nc,
+                 "search_events_per_s": sub.n_events / (t_ex * 1e-3),
+                 "final_within_one_cell_of_expansion": float(np.mean(np.all(dpx <= fine_w[None, :] * (1 + 1e-9), axis=1)))}
+        del v64, vex, dv
+
     # end to end through the host-buffer entry point (pinned host inputs, tracks back)
     off_h = torch.from_numpy(np.ascontiguousarray(ev.offsets, np.int32)).pin_memory()
     wid_h = torch.from_numpy(np.ascontiguousarray(ev.wire_id, np.int32)).pin_memory()
@@ -612,6 +661,8 @@ def run_apo(args) -> None:
     }
     if midpoint is not None:
         line["midpoint"] = midpoint
+    if exact is not None:
+        line["exact_phase"] = exact
     if not args.no_serve:
         serve_sweep(geom, ev, [1000], 0.25)   # warm-up pass (first-use costs), discarded
         sweep = serve_sweep(geom, ev, [1000, 2000, 5000, 10000, 20000, 50000], args.serve_seconds)
@@ -687,6 +738,7 @@ def main(argv=None):
     ap.add_argument("--no-mid", action="store_true", help="skip the midpoint-form leg")
     ap.add_argument("--no-bg", action="store_true", help="skip the background-rejection study")
     ap.add_argument("--no-paper4d", action="store_true", help="skip the paper's own 4-D search")
+    ap.add_argument("--no-exact", action="store_true", help="skip the exact-phase leg")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--case", default=None,
                     choices=["coarse-f64", "coarse-f32", "solve-f64", "solve-f32", "solve-bulk",

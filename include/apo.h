@@ -51,8 +51,11 @@ typedef enum {
  * d^Ax (Eq. defdiAX_b) are evaluated at the voxel centre in round-to-nearest FP64, and only
  * (x^Ax - x_c)^2 + (y^Ax - y_c)^2 - (R + d^Ax)^2 keeps the voxel's FP64 intervals.  Faster
  * and not sound (a voxel holding the solution can lose a vote).  Needs the grid's
- * sincos_mid table. */
-enum { APO_F64 = 0, APO_F32 = 1, APO_F64_FILTERED = 2, APO_F64_MID = 3 };
+ * sincos_mid table.
+ * APO_F64_EXACT: FP64 intervals with the exact phase of Eq. CSAXtoPHI_a (an interval
+ * fixed-point enclosure per drift sign, started from the expansion of Eqs. ApproxPhi_a-d)
+ * instead of the expansion; sound for the unexpanded equations, several times costlier. */
+enum { APO_F64 = 0, APO_F32 = 1, APO_F64_FILTERED = 2, APO_F64_MID = 3, APO_F64_EXACT = 4 };
 
 #define APO_HIT_CAP 256      /* hits per event */
 #define APO_MAX_LEVELS 8     /* bisection levels after the coarse level */

@@ -29,6 +29,7 @@
 #define NEXTUP(x) nextafter((x), INFINITY)
 #include "vote_program.inc"
 #include "midpoint.inc"
+#include "exactphi.inc"
 #include "fourd.inc"
 #undef REAL
 #undef SFX
@@ -94,8 +95,16 @@ static void hit_constants(const or_wires *w, int32_t wid, double drift, double h
 static float rd32(double x) { volatile float r = (float)x; return r; }   /* FE_DOWNWARD */
 static float ru32(double x) { volatile float r = (float)(-x); return -r; }
 
-/* The vote of one (cell, hit) pair.  prec 0: FP64 intervals, 1: FP32 intervals. */
+/* The vote of one (cell, hit) pair.  prec 0: FP64 intervals, 1: FP32 intervals, 4: FP64
+ * intervals with the exact phase (exactphi.inc). */
 static int vote_pair(const double c[12], const double h[9], int prec, double *out) {
+    if (prec == 4) {
+        iv_d C[6], H[9];
+        for (int i = 0; i < 6; i++) C[i] = mk_d(c[2 * i], c[2 * i + 1]);
+        for (int i = 0; i < 9; i++) H[i] = mk_d(h[i], h[i]);
+        return exact_vote_program_d(C[0], C[1], C[2], C[3], C[4], C[5], H[0], H[1], H[2], H[3],
+                                    H[4], H[5], H[6], H[7], H[8], out);
+    }
     if (prec == 0) {
         iv_d C[6], H[9];
         for (int i = 0; i < 6; i++) C[i] = mk_d(c[2 * i], c[2 * i + 1]);
@@ -153,7 +162,8 @@ static void centre_sincos(const or_grid *g, int level, const int32_t idx[5], dou
 
 /* votes of n cells of `level` (given by key) for one event's hits: Eq. (ApoVote) summed
  * over hits, one vote per (cell, hit) whichever drift sign passes (Section 3.1).
- * prec 0: FP64 intervals, 1: FP32 intervals, 3: the FP64 midpoint form. */
+ * prec 0: FP64 intervals, 1: FP32 intervals, 3: the FP64 midpoint form, 4: FP64 intervals
+ * with the exact phase. */
 void or_vote_cells(const or_grid *g, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
                    const double *drift, int32_t level, int32_t prec, const uint64_t *keys,
                    int64_t n, int32_t *votes) {

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 SRC = [os.path.join(HERE, "apo_oracle.c")]
-DEPS = SRC + [os.path.join(HERE, f) for f in ("vote_program.inc", "midpoint.inc", "fourd.inc")]
+DEPS = SRC + [os.path.join(HERE, f) for f in ("vote_program.inc", "midpoint.inc", "exactphi.inc", "fourd.inc")]
 # No FMA contraction, no fast-math, rounding-mode-aware code generation.
 CFLAGS = ["-O1", "-std=c11", "-frounding-math", "-ffp-contract=off", "-fno-fast-math",
           "-fno-builtin", "-fopenmp", "-shared", "-fPIC", "-Wall", "-Wno-unknown-pragmas"]

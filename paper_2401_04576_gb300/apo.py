@@ -14,7 +14,7 @@ import numpy as np
 from . import build as _build
 
 APO_OK, APO_EINVAL, APO_ENOMEM, APO_ECUDA, APO_ETIMEOUT, APO_EBUSY = 0, -1, -2, -3, -4, -5
-F64, F32, F64_FILTERED, F64_MID = 0, 1, 2, 3
+F64, F32, F64_FILTERED, F64_MID, F64_EXACT = 0, 1, 2, 3, 4
 HIT_CAP = 256
 MAX_LEVELS = 8
 MAX_TRACKS = 8

@@ -104,7 +104,7 @@ template <typename P> P *at(void *ws, size_t off) {
 
 // A level precision the geometry can evaluate.
 int check_precision(const apo_geometry *g, int p, const char *what) {
-    if (p != APO_F64 && p != APO_F32 && p != APO_F64_FILTERED && p != APO_F64_MID)
+    if (p != APO_F64 && p != APO_F32 && p != APO_F64_FILTERED && p != APO_F64_MID && p != APO_F64_EXACT)
         return fail(APO_EINVAL, "bad %s", what);
     if (p == APO_F64_MID && !g->dg.sincos_mid)
         return fail(APO_EINVAL, "APO_F64_MID needs the grid's sincos_mid table");

@@ -78,7 +78,7 @@ extern "C" int apo_vote_coarse_noalloc(const apo_geometry *g, const apo_hits *hi
     if (hits->n_events > 0 && (!hits->offsets || !hits->wire_id || !hits->drift))
         return err(APO_EINVAL, "hits arrays must be non-NULL");
     if (precision != APO_F64 && precision != APO_F32 && precision != APO_F64_FILTERED &&
-        precision != APO_F64_MID)
+        precision != APO_F64_MID && precision != APO_F64_EXACT)
         return err(APO_EINVAL, "bad precision");
     int gdev = -1;
     const DevGeom *dg = geometry_device_tables(g, &gdev);

@@ -189,10 +189,17 @@ void launch_stage(const DevGeom &g, int n_events, const int32_t *offsets, const 
 // Writes votes[e][lin], lin = d + Bd (p + Bp (w + Bw (z + Bz l))), and the per-event
 // histogram of vote counts.
 // ---------------------------------------------------------------------------------------
-enum : int { kModeF32 = 0, kModeF64 = 1, kModeF64Filtered = 2 };
+enum : int { kModeF32 = 0, kModeF64 = 1, kModeF64Filtered = 2, kModeF64Exact = 3 };
+// precisions a mode evaluates: FP64 intervals (all but FP32), FP32 intervals (FP32 and the
+// FP32-first filter); kModeF64Exact uses the exact-phase program for its FP64 steps
+template <int MODE> struct ModeOf {
+    static constexpr bool k64 = MODE != kModeF32;
+    static constexpr bool k32 = MODE == kModeF32 || MODE == kModeF64Filtered;
+    static constexpr bool exact = MODE == kModeF64Exact;
+};
 
 template <int MODE> struct CoarseSmem {
-    static constexpr bool k64 = MODE != kModeF32, k32 = MODE != kModeF64;
+    static constexpr bool k64 = ModeOf<MODE>::k64, k32 = ModeOf<MODE>::k32;
     static constexpr size_t hits64 = 0;
     static constexpr size_t hits32 = k64 ? kHitCap * 80 : 0;
     static constexpr size_t hist = hits32 + (k32 ? kHitCap * 80 : 0);
@@ -264,7 +271,11 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
             if (h >= nh || (act && !((act[h >> 5] >> (h & 31)) & 1u))) return false;
             bool v = true;
             if (k32) { v = vote_pair<float>(par32, load_hit<float>(h32s + h * 80), k); n_par32++; }
-            if (k64 && v) { v = vote_pair<double>(par, load_hit<double>(h64s + h * 80), k); n_par64++; }
+            if (k64 && v) {
+                v = ModeOf<MODE>::exact ? vote_pair_exact(par, load_hit<double>(h64s + h * 80), k)
+                                        : vote_pair<double>(par, load_hit<double>(h64s + h * 80), k);
+                n_par64++;
+            }
             return v;
         };
         const int lane = tid & 31, warp = tid >> 5, nfull = nthr >> 5;
@@ -346,7 +357,9 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
                 int l = __ffs(lm) - 1;
                 lm &= lm - 1;
                 n_tail64++;
-                if (tail<double>(p64, L64[l], h64, R, c.W, k)) v64 |= 1u << l;
+                const bool tv = ModeOf<MODE>::exact ? tail_exact(p64, L64[l], h64, R, c.W, k)
+                                                    : tail<double>(p64, L64[l], h64, R, c.W, k);
+                if (tv) v64 |= 1u << l;
             }
             add_votes(v64);
         }
@@ -557,8 +570,8 @@ static void launch_cells_mid(const DevGeom &g, int n_ev, const HitRecD *hd, cons
 
 // Raises the dynamic shared-memory limit of a kernel once per process (the attribute is a
 // property of the function; setting it outside any stream capture keeps captures clean).
-static bool g_attr_coarse[3] = {false, false, false}, g_attr_cells[3] = {false, false, false},
-            g_attr_children[3] = {false, false, false};
+static bool g_attr_coarse[4] = {false, false, false, false}, g_attr_cells[4] = {false, false, false, false},
+            g_attr_children[4] = {false, false, false, false};
 
 template <typename K> static void smem_limit_once(K kernel, bool &flag) {
     if (!flag) {
@@ -586,6 +599,8 @@ void launch_vote_coarse(const DevGeom &g, int prec, int ev0, int n_ev, const Hit
     if (n_ev <= 0) return;
     if (prec == APO_F64_MID)
         launch_coarse_mid(g, ev0, n_ev, hd, n_hits, active, votes, hist, status, s, ctr);
+    else if (prec == APO_F64_EXACT)
+        launch_coarse_mode<kModeF64Exact>(g, ev0, n_ev, hd, hf, n_hits, active, votes, hist, status, s, ctr);
     else if (prec == APO_F32)
         launch_coarse_mode<kModeF32>(g, ev0, n_ev, hd, hf, n_hits, active, votes, hist, status, s, ctr);
     else if (prec == APO_F64_FILTERED)
@@ -604,7 +619,7 @@ __global__ void __launch_bounds__(256)
 k_vote_cells(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
              const uint32_t *active, int level, const uint64_t *keys, const uint64_t *parents,
              long long n_per_ev, uint64_t *out_keys, int32_t *out_votes, unsigned *status) {
-    constexpr bool k64 = MODE != kModeF32, k32 = MODE != kModeF64;
+    constexpr bool k64 = ModeOf<MODE>::k64, k32 = ModeOf<MODE>::k32;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *h64s = smem;
     unsigned char *h32s = smem + (k64 ? kHitCap * 80 : 0);
@@ -652,7 +667,9 @@ k_vote_cells(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_h
         if (act && !((act[h >> 5] >> (h & 31)) & 1u)) continue;
         bool vt = true;
         if (k32) vt = vote_pair<float>(c32, load_hit<float>(h32s + h * 80), k);
-        if (k64 && vt) vt = vote_pair<double>(c, load_hit<double>(h64s + h * 80), k);
+        if (k64 && vt)
+            vt = ModeOf<MODE>::exact ? vote_pair_exact(c, load_hit<double>(h64s + h * 80), k)
+                                     : vote_pair<double>(c, load_hit<double>(h64s + h * 80), k);
         v += vt ? 1 : 0;
     }
     out_votes[o] = v;
@@ -667,7 +684,7 @@ __global__ void __launch_bounds__(256)
 k_vote_children(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
                 const uint32_t *active, int level, const uint64_t *parents, int n_par,
                 uint64_t *out_keys, int32_t *out_votes, unsigned *status) {
-    constexpr bool k64 = MODE != kModeF32, k32 = MODE != kModeF64;
+    constexpr bool k64 = ModeOf<MODE>::k64, k32 = ModeOf<MODE>::k32;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *h64s = smem;
     unsigned char *h32s = smem + (k64 ? kHitCap * 80 : 0);
@@ -724,8 +741,13 @@ k_vote_children(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *
         if (mir) mirror_hit(h64);
         Pre<double> p64 = prefix<double>(c, h64, k);
         if (p64.guard) { v0++; v1++; continue; }
-        if ((lm & 1u) && tail<double>(p64, c.L, h64, R, c.W, k)) v0++;
-        if ((lm & 2u) && tail<double>(p64, L1, h64, R, c.W, k)) v1++;
+        if (ModeOf<MODE>::exact) {
+            if ((lm & 1u) && tail_exact(p64, c.L, h64, R, c.W, k)) v0++;
+            if ((lm & 2u) && tail_exact(p64, L1, h64, R, c.W, k)) v1++;
+        } else {
+            if ((lm & 1u) && tail<double>(p64, c.L, h64, R, c.W, k)) v0++;
+            if ((lm & 2u) && tail<double>(p64, L1, h64, R, c.W, k)) v1++;
+        }
     }
     // output order: child b at 32 j' + b, child b + 16 at 32 j' + b + 16 (j' = parent)
     const long long o = (long long)ev * n_par * 32 + (j / 16) * 32 + b;
@@ -742,7 +764,7 @@ static void launch_cells_mode(const DevGeom &g, int n_ev, const HitRecD *hd, con
                               uint64_t *out_keys, int32_t *out_votes, unsigned *status, cudaStream_t s,
                               int block) {
     smem_limit_once(k_vote_cells<MODE>, g_attr_cells[MODE]);
-    size_t sm = (MODE != kModeF32 ? kHitCap * 80 : 0) + (MODE != kModeF64 ? kHitCap * 80 : 0) + 16;
+    size_t sm = (ModeOf<MODE>::k64 ? kHitCap * 80 : 0) + (ModeOf<MODE>::k32 ? kHitCap * 80 : 0) + 16;
     dim3 grid((unsigned)((n_per_ev + block - 1) / block), n_ev);
     k_vote_cells<MODE><<<grid, block, sm, s>>>(g, hd, hf, n_hits, active, level, keys, parents, n_per_ev,
                                                 out_keys, out_votes, status);
@@ -757,6 +779,9 @@ static void launch_cells(const DevGeom &g, int prec, int n_ev, const HitRecD *hd
     if (prec == APO_F64_MID)
         launch_cells_mid(g, n_ev, hd, n_hits, active, level, keys, parents, n_per_ev, out_keys, out_votes,
                          status, s, block);
+    else if (prec == APO_F64_EXACT)
+        launch_cells_mode<kModeF64Exact>(g, n_ev, hd, hf, n_hits, active, level, keys, parents, n_per_ev,
+                                         out_keys, out_votes, status, s, block);
     else if (prec == APO_F32)
         launch_cells_mode<kModeF32>(g, n_ev, hd, hf, n_hits, active, level, keys, parents, n_per_ev,
                                     out_keys, out_votes, status, s, block);
@@ -781,7 +806,7 @@ static void launch_children_mode(const DevGeom &g, int n_ev, const HitRecD *hd, 
                                  const int32_t *n_hits, const uint32_t *active, int level,
                                  const uint64_t *parents, int n_par, uint64_t *out_keys,
                                  int32_t *out_votes, cudaStream_t s, int block) {
-    size_t sm = (MODE != kModeF32 ? kHitCap * 80 : 0) + (MODE != kModeF64 ? kHitCap * 80 : 0) + 16;
+    size_t sm = (ModeOf<MODE>::k64 ? kHitCap * 80 : 0) + (ModeOf<MODE>::k32 ? kHitCap * 80 : 0) + 16;
     smem_limit_once(k_vote_children<MODE>, g_attr_children[MODE]);
     dim3 grid((unsigned)(((long long)n_par * 16 + block - 1) / block), n_ev);
     k_vote_children<MODE><<<grid, block, sm, s>>>(g, hd, hf, n_hits, active, level, parents, n_par,
@@ -799,7 +824,10 @@ void launch_vote_children(const DevGeom &g, int prec, int n_ev, const HitRecD *h
                          child_keys, child_votes, nullptr, s, block);
         return;
     }
-    if (prec == APO_F32)
+    if (prec == APO_F64_EXACT)
+        launch_children_mode<kModeF64Exact>(g, n_ev, hd, hf, n_hits, active, child_level, parents, n_par,
+                                            child_keys, child_votes, s, block);
+    else if (prec == APO_F32)
         launch_children_mode<kModeF32>(g, n_ev, hd, hf, n_hits, active, child_level, parents, n_par,
                                        child_keys, child_votes, s, block);
     else if (prec == APO_F64_FILTERED)
@@ -822,7 +850,10 @@ void init_kernel_attributes() {
     cudaFuncSetAttribute(k_vote_children<kModeF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_vote_children<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_vote_children<kModeF64Filtered>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    for (int i = 0; i < 3; i++) g_attr_coarse[i] = g_attr_cells[i] = g_attr_children[i] = true;
+    cudaFuncSetAttribute(k_vote_coarse<kModeF64Exact>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_cells<kModeF64Exact>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_children<kModeF64Exact>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    for (int i = 0; i < 4; i++) g_attr_coarse[i] = g_attr_cells[i] = g_attr_children[i] = true;
 }
 
 // ---------------------------------------------------------------------------------------

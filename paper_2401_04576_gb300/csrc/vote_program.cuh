@@ -215,6 +215,104 @@ __device__ __forceinline__ bool vote_pair(Cell<T> c, Hit<T> h, const SeriesConst
 }
 
 // ---------------------------------------------------------------------------------------
+// Exact phase, FP64 only: Eq. CSAXtoPHI_a solved for delta = Phi - Phi^Ax instead of its
+// expansion.  In the frame of the program (times rho, N = rho R^Ax) delta solves
+//   delta = g(delta) = atan( rho (rho s^tau) t / (N^2 + rho (rho c^tau) t) ),
+//   rho c^tau = -lambda q rho s^Ax + z^St rho c^Ax,  rho s^tau = -lambda q rho c^Ax - z^St rho s^Ax,
+// with q, u_d, z^St and s_perp = R (psi + delta) at that delta.  Per drift sign: X0 = the
+// expansion's delta + [-2^-8, 2^-8]; if g(X0) lies in X0 every point of the cell has a
+// solution in X0, and X <- g(X) meet X twice more keeps every solution; otherwise (or a
+// zero divisor) the pair votes.  The rest of the program then uses delta = X per sign.
+// ---------------------------------------------------------------------------------------
+constexpr double kExactEps = 0.00390625;
+
+__device__ __forceinline__ IV<double> exact_g(IV<double> dl, int sg, const Pre<double> &p, IV<double> R,
+                                              IV<double> W, IV<double> N2, IV<double> L, IV<double> L2,
+                                              const Hit<double> &h, const SeriesConsts &k, bool &ok) {
+    const IV<double> one{1.0, 1.0};
+    IV<double> sd, cd;
+    sincos_iv(dl, sd, cd, k);
+    const IV<double> sP = clamp1(add(mul(p.sPA, cd), mul(p.cPA, sd)));
+    const IV<double> cP = clamp1(sub(mul(p.cPA, cd), mul(p.sPA, sd)));
+    const IV<double> u2 = add(add(add(one, mul(scale2(h.t), mul(L, sP))), mul(L2, h.t2)), mul(sqr(cP), h.t2));
+    if (le0(u2.lo)) { ok = false; return {-1.0, 1.0}; }
+    const IV<double> Q = mul(h.d, recip(sqrti(u2)));
+    const IV<double> Qct = mul(Q, mul(cP, h.t));
+    const IV<double> LQ = mul(L, Q);
+    const IV<double> sp = mul(add(p.psi, dl), R);
+    const IV<double> zS = sg == 0 ? sub(mul(L, sp), Qct) : add(mul(L, sp), Qct);
+    const IV<double> rct = sg == 0 ? sub(mul(zS, p.rcA), mul(LQ, p.rsA)) : add(mul(zS, p.rcA), mul(LQ, p.rsA));
+    const IV<double> rst = sg == 0 ? sub(neg(mul(LQ, p.rcA)), mul(zS, p.rsA)) : sub(mul(LQ, p.rcA), mul(zS, p.rsA));
+    const IV<double> den = add(N2, mul(mul(W, rct), h.t));
+    if (le0(den.lo)) { ok = false; return {-1.0, 1.0}; }
+    return atan_iv(divi(mul(mul(W, rst), h.t), den), k);
+}
+
+// The tan(lambda)-dependent rest with the exact phase; returns the vote.
+__device__ __forceinline__ bool tail_exact(const Pre<double> &p, IV<double> L, const Hit<double> &h,
+                                           IV<double> R, IV<double> W, const SeriesConsts &k) {
+    const IV<double> one{1.0, 1.0};
+    const IV<double> L2 = sqr(L);
+    const IV<double> N2 = sqr(p.N);
+    // the expansion's delta per sign (as in tail), the starting point
+    const IV<double> P1e = neg(mul(mul(L, p.psi_sPA), p.Ninv));
+    const IV<double> P1o = neg(mul(mul(L, p.dW_cPA), p.Ninv));
+    const IV<double> P2e = mul(mul(L2, p.inner_e), p.Nh);
+    const IV<double> P2o = mul(mul(p.dW, add(scale2(mul(L2, p.psi_cos2)), mul(add(p.N, mul(L2, p.onepN)), p.sin2))),
+                               p.Nh);
+    const IV<double> de = add(mul(P1e, h.t), mul(P2e, h.t2));
+    const IV<double> dod = add(mul(P1o, h.t), mul(P2o, h.t2));
+    bool vote = false;
+#pragma unroll 1
+    for (int sg = 0; sg < 2; sg++) {
+        const IV<double> dl = sg == 0 ? add(de, dod) : sub(de, dod);
+        IV<double> X = add(dl, IV<double>{-kExactEps, kExactEps});
+        bool ok = true;
+        const IV<double> Y = exact_g(X, sg, p, R, W, N2, L, L2, h, k, ok);
+        if (!ok || !(Y.lo >= X.lo && Y.hi <= X.hi)) { vote = true; continue; }
+        X = Y;
+#pragma unroll 1
+        for (int it = 0; it < 2 && ok; it++) {
+            const IV<double> Z = exact_g(X, sg, p, R, W, N2, L, L2, h, k, ok);
+            X = {X.lo > Z.lo ? X.lo : Z.lo, X.hi < Z.hi ? X.hi : Z.hi};
+        }
+        if (!ok || X.lo > X.hi) { vote = true; continue; }
+        IV<double> sd, cd;
+        sincos_iv(X, sd, cd, k);
+        const IV<double> sP = clamp1(add(mul(p.sPA, cd), mul(p.cPA, sd)));
+        const IV<double> cP = clamp1(sub(mul(p.cPA, cd), mul(p.sPA, sd)));
+        const IV<double> u2 = add(add(add(one, mul(scale2(h.t), mul(L, sP))), mul(L2, h.t2)), mul(sqr(cP), h.t2));
+        if (le0(u2.lo)) { vote = true; continue; }
+        const IV<double> Q = mul(h.d, recip(sqrti(u2)));
+        const IV<double> Qct = mul(Q, mul(cP, h.t));
+        const IV<double> LQ = mul(L, Q);
+        const IV<double> LQrsA = mul(LQ, p.rsA);
+        const IV<double> a2 = mul(W, sqr(Q));
+        const IV<double> a5 = mul(W, sqr(mul(LQ, h.t)));
+        const IV<double> sp = mul(add(p.psi, X), R);
+        const IV<double> zS = sg == 0 ? sub(mul(L, sp), Qct) : add(mul(L, sp), Qct);
+        const IV<double> rct = sg == 0 ? sub(mul(zS, p.rcA), LQrsA) : add(mul(zS, p.rcA), LQrsA);
+        const IV<double> a1 = sg == 0 ? scale2(Q) : neg(scale2(Q));
+        const IV<double> a3 = mul(scale2(h.t), rct);
+        const IV<double> a4 = mul(W, sqr(mul(zS, h.t)));
+        const IV<double> Arad = sub(sub(sub(add(a1, a2), a3), a4), a5);
+        const IV<double> G = sub(p.G0, Arad);
+        vote = vote || contains0(G);
+    }
+    return vote;
+}
+
+// Whole exact-phase program for one (cell, hit); the cell is given unmirrored.
+__device__ __forceinline__ bool vote_pair_exact(Cell<double> c, Hit<double> h, const SeriesConsts &k) {
+    if (mirror_cell(c)) mirror_hit(h);
+    if (le0(c.W.lo)) return true;
+    const IV<double> R = recip(c.W);
+    const Pre<double> p = prefix(c, h, k);
+    if (p.guard) return true;
+    return tail_exact(p, c.L, h, R, c.W, k);
+}
+
+// ---------------------------------------------------------------------------------------
 // Midpoint form, FP64 only: the faster, approximate variant of Section 3.1, where the
 // quantities that build d^Ax (Eq. defdiAX_b) are taken at the middle of the voxel.  The
 // point part runs the steps of the interval program on the voxel centre, per drift sign,
