@@ -593,7 +593,9 @@ def run_apo(args) -> None:
         nc = dv.numel()
         tr_sub = torch.zeros(sub.n_events * apo.TRACK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
         nt_sub = torch.zeros(sub.n_events, dtype=torch.int32, device="cuda")
-        oex = apo.solve_opts(precision=[apo.F64_EXACT] * (lv + 1))
+        # the expansion on the two coarsest levels (their wide cells defeat the inclusion
+        # proof, and a failed proof votes), the exact phase on levels 2 .. lv
+        oex = apo.solve_opts(precision=[apo.F64] * 2 + [apo.F64_EXACT] * (lv - 1))
         apo.solve_batch(geom, hs, oex, tracks=tr_sub, n_tracks=nt_sub, workspace=ws, stream=stream)
         torch.cuda.synchronize()
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -604,7 +606,8 @@ def run_apo(args) -> None:
         t_ex = s0.elapsed_time(s1)
         tex = apo.tracks_to_numpy(tr_sub, sub.n_events)
         dpx = np.abs(tex["p"][:, 0, :] - tracks64["p"][:sub.n_events, 0, :])
-        exact = {"precision": "FP64 intervals, exact phase at every level",
+        exact = {"precision": "FP64 intervals; coarse figures: exact phase on the level-0 grid; "
+                              "search: expansion on levels 0-1, exact phase on levels 2-6",
                  "events": sub.n_events,
                  "coarse_ms": min(ems), "coarse_ms_expansion": min(fms),
                  "coarse_cost_vs_expansion": min(ems) / min(fms),
