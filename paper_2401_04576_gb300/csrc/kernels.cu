@@ -215,23 +215,40 @@ template <int MODE> struct CoarseSmem {
 #ifndef APO_F32_COARSE_MIN_BLOCKS
 #define APO_F32_COARSE_MIN_BLOCKS 3
 #endif
-#ifndef APO_F64_COARSE_MIN_BLOCKS
-#define APO_F64_COARSE_MIN_BLOCKS 1
+// The FP64 modes split each (phi0, omega) tile's (d0, z0) cells over APO_F64_COARSE_SPLIT
+// blocks (consecutive ranges of the d0-fastest index): smaller blocks with the same register
+// budget let more warps share an SM, which hides more FP64 latency.
+#ifndef APO_F64_COARSE_SPLIT
+#define APO_F64_COARSE_SPLIT 2
 #endif
+#ifndef APO_F64_COARSE_MIN_BLOCKS
+#define APO_F64_COARSE_MIN_BLOCKS (APO_F64_COARSE_SPLIT == 1 ? 1 : 3)
+#endif
+template <int MODE> struct CoarseShape {
+    static constexpr int split = MODE == kModeF32 ? 1 : APO_F64_COARSE_SPLIT;
+    static constexpr int threads = 256 / split;
+    static constexpr int min_blocks = MODE == kModeF32 ? APO_F32_COARSE_MIN_BLOCKS : APO_F64_COARSE_MIN_BLOCKS;
+};
 
 template <int MODE>
-__global__ void __launch_bounds__(256, MODE == kModeF32 ? APO_F32_COARSE_MIN_BLOCKS : APO_F64_COARSE_MIN_BLOCKS)
+__global__ void __launch_bounds__(CoarseShape<MODE>::threads, CoarseShape<MODE>::min_blocks)
 k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
               const uint32_t *active, int32_t *votes, uint32_t *hist, unsigned *status,
               unsigned long long *ctr) {
     using S = CoarseSmem<MODE>;
     constexpr bool k64 = S::k64, k32 = S::k32;
+    constexpr int split = CoarseShape<MODE>::split;
     extern __shared__ __align__(16) unsigned char smem[];
     const int Bd = g.bins[0], Bp = g.bins[1], Bw = g.bins[2], Bz = g.bins[3], Bl = g.bins[4];
-    const int nthr = Bd * Bz;
+    const int ntile = Bd * Bz;                    // (d0, z0) cells of one (phi0, omega) tile
+    const int per = (ntile + split - 1) / split;  // of them in this block
+    const int nthr = blockDim.x;
     const int e = blockIdx.y, ev = ev0 + e;
-    const int p = blockIdx.x % Bp, w = blockIdx.x / Bp;
+    const int part = blockIdx.x % split, pw = blockIdx.x / split;
+    const int p = pw % Bp, w = pw / Bp;
     const int tid = threadIdx.x;
+    const int c0 = part * per, c1 = c0 + per < ntile ? c0 + per : ntile;   // this block's cells
+    const bool has_cell = c0 + tid < c1;
     unsigned char *h64s = smem + S::hits64;
     unsigned char *h32s = smem + S::hits32;
     uint32_t *hist_s = reinterpret_cast<uint32_t *>(smem + S::hist);
@@ -260,8 +277,10 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
     unsigned n_par32 = 0, n_pre32 = 0, n_tail32 = 0, n_par64 = 0, n_pre64 = 0, n_tail64 = 0;
     // parent cell test, one hit per thread
     {
-        IV<double> D0 = edge(g, 0, 0, 0), D1 = edge(g, 0, 0, Bd - 1);
-        IV<double> Z0 = edge(g, 3, 0, 0), Z1 = edge(g, 3, 0, Bz - 1);
+        IV<double> D0 = edge(g, 0, 0, c1 - c0 >= Bd ? 0 : c0 % Bd);
+        IV<double> D1 = edge(g, 0, 0, c1 - c0 >= Bd ? Bd - 1 : (c1 - 1) % Bd);
+        if (c0 / Bd != (c1 - 1) / Bd) { D0 = edge(g, 0, 0, 0); D1 = edge(g, 0, 0, Bd - 1); }
+        IV<double> Z0 = edge(g, 3, 0, c0 / Bd), Z1 = edge(g, 3, 0, (c1 - 1) / Bd);
         IV<double> L0 = edge(g, 4, 0, 0), L1 = edge(g, 4, 0, Bl - 1);
         Cell<double> par{{D0.lo, D1.hi}, S0, C0, W, {Z0.lo, Z1.hi}, {L0.lo, L1.hi}};
         Cell<float> par32{to_prec<float>(par.D), to_prec<float>(S0), to_prec<float>(C0),
@@ -292,7 +311,8 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
     }
     __syncthreads();
 
-    const int d = tid % Bd, z = tid / Bd;
+    const int cell = has_cell ? c0 + tid : c0;   // threads past the block's cells idle
+    const int d = cell % Bd, z = cell / Bd;
     Cell<double> c{edge(g, 0, 0, d), S0, C0, W, edge(g, 3, 0, z), L64[0]};
     Cell<float> c32{to_prec<float>(c.D), to_prec<float>(S0), to_prec<float>(C0), to_prec<float>(W),
                     to_prec<float>(c.Z), L32[0]};
@@ -315,7 +335,7 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
             m = c;
         }
     };
-    for (int wd = 0; wd < 8; wd++) {
+    for (int wd = 0; wd < 8 && has_cell; wd++) {
         uint32_t m = mask_s[wd];
         while (m) {
             int h = wd * 32 + __ffs(m) - 1;
@@ -366,7 +386,7 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
     }
     const long long ncell = (long long)Bd * Bp * Bw * Bz * Bl;
     int32_t *vo = votes + (long long)e * ncell;
-    for (int l = 0; l < Bl; l++) {
+    for (int l = 0; l < Bl && has_cell; l++) {
         int v = 0;
 #pragma unroll
         for (int q = 0; q < 9; q++) v |= (int)((pl[q] >> l) & 1u) << q;
@@ -586,8 +606,9 @@ template <int MODE> static void launch_coarse_mode(const DevGeom &g, int ev0, in
                                                   uint32_t *hist, unsigned *status, cudaStream_t s,
                                                   unsigned long long *ctr) {
     smem_limit_once(k_vote_coarse<MODE>, g_attr_coarse[MODE]);
-    dim3 grid(g.bins[1] * g.bins[2], n_ev);
-    int nthr = g.bins[0] * g.bins[3];
+    constexpr int split = CoarseShape<MODE>::split;
+    dim3 grid(g.bins[1] * g.bins[2] * split, n_ev);
+    const int nthr = (g.bins[0] * g.bins[3] + split - 1) / split;
     size_t sm = CoarseSmem<MODE>::total(g.bins[4], nthr);
     k_vote_coarse<MODE><<<grid, nthr, sm, s>>>(g, ev0, hd, hf, n_hits, active, votes, hist, status, ctr);
 }

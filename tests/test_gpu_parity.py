@@ -59,6 +59,21 @@ def test_coarse_votes_bit_exact(wires, grid1, ev1, prec):
         np.testing.assert_array_equal(got[e], ref)
 
 
+@pytest.mark.parametrize("prec", [apo.F64, apo.F32, apo.F64_FILTERED, apo.F64_EXACT])
+def test_coarse_votes_ragged_grid(wires, prec):
+    """Uneven bins (7 x 6 x 8 x 5 x 9): an odd number of (d0, z0) cells per tile, so the
+    FP64 kernels' split of a tile over two blocks leaves one thread without a cell."""
+    grid = G.make_grid([7, 6, 8, 5, 9], 3, 16)
+    ev = chamber.single_track_events(3, seed=44, w=wires)
+    geom = apo.Geometry(grid, wires)
+    got = apo.vote(geom, _hits(ev), precision=prec).cpu().numpy()
+    tab = O.Tables(grid, wires)
+    oprec = {apo.F64: 0, apo.F64_FILTERED: 0, apo.F32: 1, apo.F64_EXACT: 4}[prec]
+    for e in range(ev.n_events):
+        a, b = ev.offsets[e], ev.offsets[e + 1]
+        np.testing.assert_array_equal(got[e], O.vote_coarse(tab, ev.wire_id[a:b], ev.drift[a:b], oprec))
+
+
 @pytest.mark.parametrize("prec", [apo.F64, apo.F32, apo.F64_FILTERED])
 def test_cell_votes_every_level_bit_exact(wires, grid2, ev2, prec):
     """Random cells and cells around the true helix at every level 0..6."""
