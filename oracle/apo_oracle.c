@@ -699,8 +699,9 @@ static double v4_move_z0(const or4_opts *o, const or4_iter *it, const double a[2
     double xc = it->value[0], yc = it->value[1], R = it->value[2];
     double ox = -xc, oy = -yc, on = sqrt(ox * ox + oy * oy);
     int bad = !(on > 0);
-    double pa = bad ? 0.0 : v4_phase_d(ox, oy, on, a[0] - xc, a[1] - yc, &bad);
-    double pb = bad ? 0.0 : v4_phase_d(ox, oy, on, b[0] - xc, b[1] - yc, &bad);
+    double ax = a[0] - xc, ay = a[1] - yc, bx = b[0] - xc, by = b[1] - yc;
+    double pa = bad ? 0.0 : v4_phase_d(ox, oy, on, ax, ay, sqrt(ax * ax + ay * ay), &bad);
+    double pb = bad ? 0.0 : v4_phase_d(ox, oy, on, bx, by, sqrt(bx * bx + by * by), &bad);
     double dpsi = bad ? 0.0 : pb - pa;
     double ratio = o->p_gev / ((0.3 * o->b_tesla) * R);
     double aL = ratio > 1 ? sqrt(ratio * ratio - 1.0) : 0.0;

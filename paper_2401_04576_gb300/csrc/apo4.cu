@@ -222,9 +222,9 @@ k4_vote(Iter4 it, int ev0, const int32_t *n_hits, const HitRecD *hd, const uint3
                 for (int iz = 0; iz < nz; iz++) {
                     const Pre4<T> pre = prefix4<T>(m, s_zc[iz], h);
                     if (pre.guard) { b0 |= 1u << iz; b1 |= 1u << iz; continue; }
-                    const IV<T> Z = s_z[iz];
-                    if (pair4<T>(m, pre, 1, h, X, Y, Rv, Z, wi)) b0 |= 1u << iz;
-                    if (pair4<T>(m, pre, -1, h, X, Y, Rv, Z, wi)) b1 |= 1u << iz;
+                    const IV<T> A2 = a2_4<T>(X, Y, s_z[iz], wi);
+                    if (pair4<T>(m, pre, 1, h, A2, Rv)) b0 |= 1u << iz;
+                    if (pair4<T>(m, pre, -1, h, A2, Rv)) b1 |= 1u << iz;
                 }
                 add_votes(0, b0);
                 add_votes(1, b1);
@@ -392,7 +392,7 @@ k4_finish(Iter4 it, int k, int n_iter, bool has_next, Iter4 nxt, double g0, doub
         if (m.valid) {
             const HitP<T> h = hit_point<T>(r);
             const Pre4<T> pre = prefix4<T>(m, rn<T>(c[3]), h);
-            v = pre.guard || pair4<T>(m, pre, s_sign, h, X, Y, Rv, Z, hit_iv<T>(r));
+            v = pre.guard || pair4<T>(m, pre, s_sign, h, a2_4<T>(X, Y, Z, hit_iv<T>(r)), Rv);
         }
         if (v) {
             atomicOr(&s_act[i >> 5], 1u << (i & 31));
@@ -425,8 +425,12 @@ k4_finish(Iter4 it, int k, int n_iter, bool has_next, Iter4 nxt, double g0, doub
         const double ox = -xc, oy = -yc;
         const double on = __dsqrt_rn(__dadd_rn(__dmul_rn(ox, ox), __dmul_rn(oy, oy)));
         bool bad = !(on > 0.0);
-        const double pa = bad ? 0.0 : phase4<double>(ox, oy, on, __dsub_rn(rf[0], xc), __dsub_rn(rf[1], yc), bad);
-        const double pb = bad ? 0.0 : phase4<double>(ox, oy, on, __dsub_rn(r0, xc), __dsub_rn(r1, yc), bad);
+        const double ax = __dsub_rn(rf[0], xc), ay = __dsub_rn(rf[1], yc);
+        const double bx = __dsub_rn(r0, xc), by = __dsub_rn(r1, yc);
+        const double pa = bad ? 0.0 : phase4<double>(ox, oy, on, ax, ay,
+                                                     __dsqrt_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay))), bad);
+        const double pb = bad ? 0.0 : phase4<double>(ox, oy, on, bx, by,
+                                                     __dsqrt_rn(__dadd_rn(__dmul_rn(bx, bx), __dmul_rn(by, by))), bad);
         const double dpsi = bad ? 0.0 : __dsub_rn(pb, pa);
         const double ratio = __ddiv_rn(it.p_gev, __dmul_rn(__dmul_rn(0.3, it.b_tesla), R));
         const double aL = ratio > 1.0 ? __dsqrt_rn(__dsub_rn(__dmul_rn(ratio, ratio), 1.0)) : 0.0;

@@ -65,16 +65,17 @@ template <typename T> __device__ __forceinline__ void sincos(T d, T &s, T &c) {
 // it and the reference point's phase.
 template <typename T> struct Ctr4 { T xc, yc, R, aL, ox, oy, on, psi_ref; bool valid, guard; };
 
-// Phase of the point (dx, dy) from the centre, counter-clockwise from the direction
-// (ox, oy) of norm on, in [0, 2 pi).  With r = on |d|, r sin = o x d, r cos = o . d: for
-// cos >= 0 the angle is 2 atan(sin / (1 + cos)), otherwise +-pi - 2 atan(sin / (1 - cos))
-// (the complementary half angle), so neither denominator cancels; bad when r = 0.
+// Phase of the point (dx, dy) = |d| (cos, sin) from the centre, counter-clockwise from
+// the direction (ox, oy) of norm on, in [0, 2 pi).  With r = on |d|, r sin = o x d, r cos =
+// o . d: for cos >= 0 the angle is 2 atan(sin / (1 + cos)), otherwise +-pi - 2 atan(sin /
+// (1 - cos)) (the complementary half angle), so neither denominator cancels.  dn = |d|,
+// from the caller; bad when r = 0.
 template <typename T>
-__device__ __forceinline__ T phase4(T ox, T oy, T on, T dx, T dy, bool &bad) {
+__device__ __forceinline__ T phase4(T ox, T oy, T on, T dx, T dy, T dn, bool &bad) {
     using namespace p4;
     const T sn = sub(mul(ox, dy), mul(oy, dx));
     const T cs = add(mul(ox, dx), mul(oy, dy));
-    const T r = mul(on, sqrt(add(mul(dx, dx), mul(dy, dy))));
+    const T r = mul(on, dn);
     if (!(r > T(0))) { bad = true; return T(0); }
     T ph;
     if (cs >= T(0)) ph = mul(T(2), p4::atan(div(sn, add(r, cs))));
@@ -99,12 +100,15 @@ __device__ __forceinline__ Ctr4<T> centre4(T xc, T yc, T R, T p_gev, T b_t, T xr
     m.guard = false;
     m.psi_ref = T(0);
     if (!(m.on > T(0))) m.guard = true;
-    else m.psi_ref = phase4<T>(m.ox, m.oy, m.on, sub(xr, xc), sub(yr, yc), m.guard);
+    else {
+        const T ex = sub(xr, xc), ey = sub(yr, yc);
+        m.psi_ref = phase4<T>(m.ox, m.oy, m.on, ex, ey, sqrt(add(mul(ex, ex), mul(ey, ey))), m.guard);
+    }
     return m;
 }
 
 // z0- and sign-free point quantities of one (voxel centre, hit).
-template <typename T> struct Pre4 { bool guard; T R, RA, A2, sA, cA, sPA, cPA, cos2, sin2, psi, Rpsi; };
+template <typename T> struct Pre4 { bool guard; T R, RA, iRA, hiA2, sA, cA, sPA, cPA, cos2, sin2, psi, Rpsi; };
 
 // Hit constants as point values of T: x0, y0, sin phi_s, cos phi_s, tan tau,
 // sin phi_s tan tau, cos phi_s tan tau, tan^2 tau, d.
@@ -119,19 +123,22 @@ __device__ __forceinline__ Pre4<T> prefix4(const Ctr4<T> &m, T z0, const HitP<T>
     p.R = m.R;
     const T xw = add(h.x0, mul(z0, h.spt)), yw = sub(h.y0, mul(z0, h.cpt));   // EQSinter_d,e
     const T dx = sub(xw, m.xc), dy = sub(yw, m.yc);
-    p.A2 = add(mul(dx, dx), mul(dy, dy));
-    p.RA = sqrt(p.A2);
+    p.RA = sqrt(add(mul(dx, dx), mul(dy, dy)));
     if (!(p.RA > T(0)) || m.guard) { p.guard = true; return p; }
+    // 1 / R^Ax and 1 / (2 (R^Ax)^2): the divisions by R^Ax are products with these
+    p.iRA = div(T(1), p.RA);
+    const T iA2 = mul(p.iRA, p.iRA);
+    p.hiA2 = mul(T(0.5), iA2);
     // c^Ax, s^Ax of Eq. defEQApo1
     p.cA = sub(mul(dx, h.sph), mul(dy, h.cph));
     p.sA = add(mul(dx, h.cph), mul(dy, h.sph));
-    p.sPA = div(p.sA, p.RA);
-    p.cPA = div(p.cA, p.RA);
-    p.cos2 = div(sub(mul(p.cA, p.cA), mul(p.sA, p.sA)), p.A2);
-    p.sin2 = div(mul(mul(T(2), p.sA), p.cA), p.A2);
+    p.sPA = mul(p.sA, p.iRA);
+    p.cPA = mul(p.cA, p.iRA);
+    p.cos2 = mul(sub(mul(p.cA, p.cA), mul(p.sA, p.sA)), iA2);
+    p.sin2 = mul(mul(mul(T(2), p.sA), p.cA), iA2);
     // psi: the wire point's phase minus the reference point's
     bool bad = false;
-    const T ph = phase4<T>(m.ox, m.oy, m.on, dx, dy, bad);
+    const T ph = phase4<T>(m.ox, m.oy, m.on, dx, dy, p.RA, bad);
     if (bad) { p.guard = true; return p; }
     p.psi = sub(ph, m.psi_ref);
     p.Rpsi = mul(p.R, p.psi);
@@ -148,11 +155,11 @@ __device__ __forceinline__ int dax4(const Pre4<T> &p, T L, const HitP<T> &h, T d
 #pragma unroll
     for (int sg = 0; sg < 2; sg++) {
         const T ds = sg == 0 ? h.d : -h.d;
-        const T Phi1 = div(-add(mul(zA, p.sPA), mul(mul(L, ds), p.cPA)), RA);      // ApproxPhi_b
-        const T Phi2 = div(add(sub(mul(mul(L, R), zA), mul(mul(mul(L, zA), sub(R, mul(T(2), ds))), p.cos2)),
+        const T Phi1 = -mul(add(mul(zA, p.sPA), mul(mul(L, ds), p.cPA)), p.iRA);   // ApproxPhi_b
+        const T Phi2 = mul(add(sub(mul(mul(L, R), zA), mul(mul(mul(L, zA), sub(R, mul(T(2), ds))), p.cos2)),
                                mul(add(mul(zA, zA), mul(ds, add(RA, mul(mul(L, L), sub(add(R, RA), ds))))),
                                    p.sin2)),
-                           mul(T(2), p.A2));                                        // ApproxPhi_c
+                           p.hiA2);                                                 // ApproxPhi_c
         const T dl = add(mul(Phi1, t), mul(Phi2, t2));                             // ApproxPhi_a
         T sd, cd;
         p4::sincos(dl, sd, cd);
@@ -174,16 +181,20 @@ __device__ __forceinline__ int dax4(const Pre4<T> &p, T L, const HitP<T> &h, T d
     return guard;
 }
 
-// 0 in (x^Ax - X)^2 + (y^Ax - Y)^2 - (Rv + dax)^2, directed, with the wire point
-// x^Ax = x0 + Z spt, y^Ax = y0 - Z cpt over the voxel's z0 interval Z.
+// (x^Ax - X)^2 + (y^Ax - Y)^2, directed, with the wire point x^Ax = x0 + Z spt,
+// y^Ax = y0 - Z cpt over the voxel's z0 interval Z (shared by both signs of tan(lambda)
+// and both drift signs).
 template <typename T> struct HitI { IV<T> x0, y0, spt, cpt; };
 
 template <typename T>
-__device__ __forceinline__ bool test4(IV<T> X, IV<T> Y, IV<T> Rv, IV<T> Z, const HitI<T> &w, T dax) {
+__device__ __forceinline__ IV<T> a2_4(IV<T> X, IV<T> Y, IV<T> Z, const HitI<T> &w) {
     const IV<T> xw = add(w.x0, mul(Z, w.spt)), yw = sub(w.y0, mul(Z, w.cpt));
-    const IV<T> A2 = add(sqr(sub(xw, X)), sqr(sub(yw, Y)));
-    const IV<T> G = sub(A2, sqr(add(Rv, IV<T>{dax, dax})));
-    return contains0(G);
+    return add(sqr(sub(xw, X)), sqr(sub(yw, Y)));
+}
+
+// 0 in A2 - (Rv + dax)^2
+template <typename T> __device__ __forceinline__ bool test4(IV<T> A2, IV<T> Rv, T dax) {
+    return contains0(sub(A2, sqr(add(Rv, IV<T>{dax, dax}))));
 }
 
 // Disk pre-filter, Eq. ApoVoteDisk: 0 in X^2 + Y^2 - (Rv + [-rd, rd])^2.
@@ -193,17 +204,17 @@ __device__ __forceinline__ bool disk4(IV<T> X, IV<T> Y, IV<T> Rv, T rd) {
     return contains0(G);
 }
 
-// The vote of one hit at one centre (prefix at its z0) and sign over the voxel
-// (X, Y, Rv, Z): either drift sign (a guard votes).
+// The vote of one hit at one centre (prefix at its z0) and sign over the voxel (A2 of its
+// x_c, y_c, z0 and the wire; Rv): either drift sign (a guard votes).
 template <typename T>
 __device__ __forceinline__ bool pair4(const Ctr4<T> &m, const Pre4<T> &pre, int sign, const HitP<T> &h,
-                                      IV<T> X, IV<T> Y, IV<T> Rv, IV<T> Z, const HitI<T> &w) {
+                                      IV<T> A2, IV<T> Rv) {
     T dax[2];
     const int g = dax4(pre, sign > 0 ? m.aL : -m.aL, h, dax);
     if (g & 1) return true;
-    if (test4(X, Y, Rv, Z, w, dax[0])) return true;
+    if (test4(A2, Rv, dax[0])) return true;
     if (g & 2) return true;
-    return test4(X, Y, Rv, Z, w, dax[1]);
+    return test4(A2, Rv, dax[1]);
 }
 
 }  // namespace apo
