@@ -92,3 +92,30 @@ def test_key_round_trip_and_order():
     keys = G.cell_key(idx)
     np.testing.assert_array_equal(G.key_indices(keys), idx)
     assert np.all(np.diff(keys.astype(np.float64)) > 0)   # linear order == key order
+
+
+def test_comet_toy_matches_the_paper_description():
+    """The 20-layer toy (4,986 wires, 496-837 mm, +-0.1 rad stereo) and its electrons: from
+    the origin, p = 105 MeV/c, less than one turn inside the chamber, reaching the third
+    layer, 25 or more hits, drifts under 8 mm and equal to the true distance."""
+    import numpy as np
+    from gen import comet
+    w = comet.make_wires()
+    assert w.n == 4986 and len(set(w.layer.tolist())) == 20
+    r = np.hypot(w.x0, w.y0)
+    assert abs(r.min() - 0.496) < 1e-12 and abs(r.max() - 0.837) < 1e-12
+    assert np.allclose(np.abs(np.arctan(w.tan_tau)), 0.1)
+    ev = comet.events(40, seed=9, w=w)
+    nh = np.diff(ev.offsets)
+    assert nh.min() >= 25 and nh.max() <= 62
+    lo, hi = comet.pt_range()
+    for e in range(ev.n_events):
+        tr = ev.tracks[e][0]
+        pt = 0.3 * comet.B_TESLA / tr.omega
+        assert lo - 1e-12 <= pt <= hi + 1e-12
+        assert abs(np.hypot(pt, pt * tr.tanl) - comet.P_GEV) < 1e-12
+        xc, yc, R = comet.helix_centre(tr)
+        assert abs(np.hypot(xc, yc) - R) < 1e-12                  # the circle passes the origin
+        assert 2 * np.pi * R * abs(tr.tanl) > comet.Z_HALF_LEN    # leaves within a turn
+        for h in ev.hit_truth[e]:
+            assert h.drift == h.dist < comet.MAX_DRIFT
