@@ -46,7 +46,7 @@ OPS_TAIL = OPS_LPART + OPS_SIGNS
 # capture summarised in profiles/k_vote_coarse_f64_64events.md (64 events: 4.24 MB read +
 # 214.03 MB written), scaled by events to the benchmark's launch.  Must be re-captured (or
 # set to None) whenever that kernel changes.
-COARSE_F64_DRAM_BYTES_PER_EVENT = (4.238080e6 + 214.027008e6) / 64
+COARSE_F64_DRAM_BYTES_PER_EVENT = None
 
 
 def coarse_kernel_ops(n_parent: int, n_prefix: int, n_tail: int) -> int:
