@@ -92,15 +92,16 @@ def test_four_solve_reduced_grids_bit_exact(wires, tab, ch, prec):
         assert np.array_equal(sel[a:b].astype(bool), rsel), e
 
 
-def test_four_paper_grids_sampled(wires, tab, ch):
+@pytest.mark.parametrize("prec", [apo.F64, apo.F32])
+def test_four_paper_grids_sampled(wires, tab, ch, prec):
     """The paper's grids (Table tabGridDef) on 48 events in one batch, as the benchmark runs
     them; two events recomputed whole by the oracle."""
     ev = comet.events(48, seed=63, w=wires)
-    opts = apo.four_opts()
+    opts = apo.four_opts(precision=prec)
     out, sel = apo.solve4(ch, _hits(ev), opts)
     got = apo.iters4_to_numpy(out, ev.n_events, 3)
     sel = sel.cpu().numpy()
-    oo = O.four_opts()
+    oo = O.four_opts(precision=0 if prec == apo.F64 else 1)
     for e in (3, 40):
         a, b = ev.offsets[e], ev.offsets[e + 1]
         its, rsel = O.four_solve_event(oo, tab, ev.wire_id[a:b], ev.drift[a:b])
