@@ -27,10 +27,18 @@ int32_t apo_diag_coarse_launches(const apo_geometry *geom, int32_t n_events);
 
 /* Throughput microbenchmark of one directed-rounding operation on the current device:
  * precision APO_F64 / APO_F32, op 0 = add (__dadd_rd), 1 = mul (__dmul_rd), 2 = an
- * alternating add/mul chain.  Many independent chains per thread, every SM busy.
- * *ops_per_s = operations per second.  Synchronous, about 0.1 s. */
+ * alternating add/mul chain; FP64 only: 3 = alternating rd square root (the library's own
+ * integer-pipe form) and mul by 3, 4 = the same with the CUDA library's __dsqrt_rd.  Many
+ * independent chains per thread, every SM busy.  *ops_per_s = operations per second.
+ * Synchronous, about 0.1 s. */
 int apo_diag_pipe_peak(int32_t precision, int32_t op, double *ops_per_s);
 
+/* Elementwise correctly rounded FP64 operations on device arrays x -> out (n elements, on
+ * `stream`), for testing the library's integer-pipe square root and reciprocal against
+ * the CUDA library: op 0-2 = reciprocal rounded down / up / to nearest (integer pipe),
+ * 3-5 = square root rd / ru / rn (integer pipe), 6-11 = the same six with the CUDA
+ * library's __drcp_* / __dsqrt_*.  Every op accepts any double. */
+int apo_diag_dops(int32_t op, const double *x, double *out, int64_t n, void *stream);
 /* Exercises the device-side wait limit: one kernel waits on a barrier that nothing
  * completes, for at most `limit_polls` polls, then records a timeout in a status word and
  * ends normally.  Returns APO_ETIMEOUT when the status word shows it (the expected

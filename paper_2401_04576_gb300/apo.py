@@ -119,6 +119,7 @@ def lib():
         L.apo_diag_coarse_launches.restype = i32
         L.apo_diag_pipe_peak.argtypes = [i32, i32, C.POINTER(C.c_double)]
         L.apo_diag_wait_timeout.argtypes = [i32]
+        L.apo_diag_dops.argtypes = [i32, vp, vp, C.c_int64, vp]
         L.apo_workspace_status.argtypes = [vp, i32, vp, vp]
         L.apo4_opts_default.argtypes = [C.POINTER(Apo4Opts)]
         L.apo4_chamber_create.argtypes = [C.POINTER(ApoWires), C.POINTER(vp)]
@@ -370,6 +371,22 @@ def pipe_peak(precision: int = F64) -> float:
         _check(lib().apo_diag_pipe_peak(int(precision), op, C.byref(r)))
         best = max(best, r.value)
     return best
+
+
+def pipe_rate(precision: int, op: int) -> float:
+    """One op of the directed-rounding pipe microbenchmark (apo_diag_pipe_peak)."""
+    r = C.c_double()
+    _check(lib().apo_diag_pipe_peak(int(precision), int(op), C.byref(r)))
+    return r.value
+
+
+def dops(op: int, x, stream=None):
+    """apo_diag_dops: elementwise FP64 reciprocal / square root (op 0-5 the library's
+    integer-pipe forms rd / ru / rn, 6-11 the CUDA library's) of a float64 CUDA tensor."""
+    assert x.dtype == _torch().float64 and x.is_cuda and x.is_contiguous()
+    out = _torch().empty_like(x)
+    _check(lib().apo_diag_dops(int(op), _ptr(x), _ptr(out), x.numel(), _stream_ptr(stream)))
+    return out
 
 
 def coarse_launches(geom: Geometry, n_events: int) -> int:

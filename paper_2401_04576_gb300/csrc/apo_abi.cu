@@ -648,6 +648,14 @@ int apo_diag_pipe_peak(int32_t precision, int32_t op, double *ops_per_s) {
     return APO_OK;
 }
 
+int apo_diag_dops(int32_t op, const double *x, double *out, int64_t n, void *stream) {
+    if (op < 0 || op > 11) return fail(APO_EINVAL, "bad op");
+    if (n < 0 || (n > 0 && (!x || !out))) return fail(APO_EINVAL, "bad arguments");
+    if (launch_dops(op, x, out, n, static_cast<cudaStream_t>(stream)))
+        return fail(APO_ECUDA, "dops launch failed");
+    return APO_OK;
+}
+
 int apo_solve_batch_host(const apo_geometry *g, int32_t n_events, const int32_t *offsets,
                          const int32_t *wire_id, const double *drift, const apo_solve_opts *opts,
                          apo_track *tracks_out, int32_t *n_tracks_out, void *ws, size_t ws_bytes,

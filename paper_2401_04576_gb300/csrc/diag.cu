@@ -9,6 +9,9 @@ namespace apo {
 constexpr int kChains = 8;
 constexpr int kIters = 2048;
 
+__device__ __forceinline__ double dsqrt_lib(double x) { return __dsqrt_rd(x); }
+__device__ __forceinline__ float dsqrt_lib(float x) { return __fsqrt_rd(x); }
+
 template <typename T, int OP>
 __global__ void __launch_bounds__(256) k_pipe(T seed, T *sink) {
     T x[kChains];
@@ -21,7 +24,9 @@ __global__ void __launch_bounds__(256) k_pipe(T seed, T *sink) {
         for (int c = 0; c < kChains; c++) {
             if (OP == 0) x[c] = rd_add(x[c], a);
             else if (OP == 1) x[c] = rd_mul(x[c], m);
-            else x[c] = (i & 1) ? rd_mul(x[c], m) : ru_add(x[c], a);
+            else if (OP == 2) x[c] = (i & 1) ? rd_mul(x[c], m) : ru_add(x[c], a);
+            else if (OP == 3) x[c] = (i & 1) ? rd_mul(x[c], T(3)) : rd_sqrt(x[c]);
+            else x[c] = (i & 1) ? rd_mul(x[c], T(3)) : dsqrt_lib(x[c]);
         }
     }
     T s = T(0);
@@ -60,11 +65,48 @@ double pipe_peak(int precision, int op) {
     if (precision == 0) {
         if (op == 0) return run_pipe<double, 0>();
         if (op == 1) return run_pipe<double, 1>();
+        if (op == 3) return run_pipe<double, 3>();
+        if (op == 4) return run_pipe<double, 4>();
         return run_pipe<double, 2>();
     }
     if (op == 0) return run_pipe<float, 0>();
     if (op == 1) return run_pipe<float, 1>();
     return run_pipe<float, 2>();
+}
+
+// Elementwise scalar operations for the tests of ipipe.cuh.
+__global__ void k_dops(int op, const double *__restrict__ x, double *__restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        double r;
+        switch (op) {
+            case 0: r = ipipe::rcp_rd(v); break;
+            case 1: r = ipipe::rcp_ru(v); break;
+            case 2: r = ipipe::rcp_rn(v); break;
+            case 3: r = ipipe::sqrt_rd(v); break;
+            case 4: r = ipipe::sqrt_ru(v); break;
+            case 5: r = ipipe::sqrt_rn(v); break;
+            case 6: r = __drcp_rd(v); break;
+            case 7: r = __drcp_ru(v); break;
+            case 8: r = __drcp_rn(v); break;
+            case 9: r = __dsqrt_rd(v); break;
+            case 10: r = __dsqrt_ru(v); break;
+            default: r = __dsqrt_rn(v); break;
+        }
+        out[i] = r;
+    }
+}
+
+int launch_dops(int op, const double *x, double *out, long long n, cudaStream_t s) {
+    if (n <= 0) return 0;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (n + 255) / 256;
+    const int blocks = (int)(want < (long long)sms * 8 ? want : (long long)sms * 8);
+    k_dops<<<blocks, 256, 0, s>>>(op, x, out, n);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace apo

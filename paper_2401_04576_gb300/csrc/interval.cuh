@@ -8,6 +8,8 @@
 #pragma once
 #include <cstdint>
 
+#include "ipipe.cuh"
+
 namespace apo {
 
 template <typename T> struct IV { T lo, hi; };
@@ -21,10 +23,11 @@ __device__ __forceinline__ double rd_mul(double a, double b) { return __dmul_rd(
 __device__ __forceinline__ double ru_mul(double a, double b) { return __dmul_ru(a, b); }
 __device__ __forceinline__ double rd_div(double a, double b) { return __ddiv_rd(a, b); }
 __device__ __forceinline__ double ru_div(double a, double b) { return __ddiv_ru(a, b); }
-__device__ __forceinline__ double rd_rcp(double a) { return __drcp_rd(a); }
-__device__ __forceinline__ double ru_rcp(double a) { return __drcp_ru(a); }
-__device__ __forceinline__ double rd_sqrt(double a) { return __dsqrt_rd(a); }
-__device__ __forceinline__ double ru_sqrt(double a) { return __dsqrt_ru(a); }
+// square root and reciprocal: correctly rounded on the integer pipe (ipipe.cuh)
+__device__ __forceinline__ double rd_rcp(double a) { return ipipe::rcp_rd(a); }
+__device__ __forceinline__ double ru_rcp(double a) { return ipipe::rcp_ru(a); }
+__device__ __forceinline__ double rd_sqrt(double a) { return ipipe::sqrt_rd(a); }
+__device__ __forceinline__ double ru_sqrt(double a) { return ipipe::sqrt_ru(a); }
 
 __device__ __forceinline__ float rd_add(float a, float b) { return __fadd_rd(a, b); }
 __device__ __forceinline__ float ru_add(float a, float b) { return __fadd_ru(a, b); }

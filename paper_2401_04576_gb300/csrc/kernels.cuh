@@ -129,6 +129,7 @@ void launch_estimate_mask(const DevGeom &g, int n_ev, const uint64_t *keys, cons
                           const int32_t *offsets = nullptr, int32_t *hit_track = nullptr);
 void launch_series_consts(SeriesConsts *dev_out, cudaStream_t s);
 double pipe_peak(int precision, int op);   // diag.cu: directed operations per second
+int launch_dops(int op, const double *x, double *out, long long n, cudaStream_t s);   // diag.cu
 
 // apo_abi.cu: the device tables and device ordinal of a geometry handle, and the message
 // returned by apo_last_error() on this thread.
