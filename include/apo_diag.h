@@ -33,11 +33,12 @@ int32_t apo_diag_coarse_launches(const apo_geometry *geom, int32_t n_events);
  * Synchronous, about 0.1 s. */
 int apo_diag_pipe_peak(int32_t precision, int32_t op, double *ops_per_s);
 
-/* Elementwise correctly rounded FP64 operations on device arrays x -> out (n elements, on
- * `stream`), for testing the library's integer-pipe square root and reciprocal against
- * the CUDA library: op 0-2 = reciprocal rounded down / up / to nearest (integer pipe),
- * 3-5 = square root rd / ru / rn (integer pipe), 6-11 = the same six with the CUDA
- * library's __drcp_* / __dsqrt_*.  Every op accepts any double. */
+/* Elementwise FP64 operations on device arrays x -> out (n elements, on `stream`), for
+ * testing the library's integer-pipe operations against the CUDA library: op 0-2 =
+ * reciprocal rounded down / up / to nearest (integer pipe), 3-5 = square root rd / ru /
+ * rn (integer pipe), 6-11 = the same six with the CUDA library's __drcp_* / __dsqrt_*;
+ * 12-14 = quotient x[i] / x[i ^ 1] rd / ru / rn (integer pipe; n must be even), 15-17 =
+ * the same with __ddiv_*.  Every op accepts any double. */
 int apo_diag_dops(int32_t op, const double *x, double *out, int64_t n, void *stream);
 /* Exercises the device-side wait limit: one kernel waits on a barrier that nothing
  * completes, for at most `limit_polls` polls, then records a timeout in a status word and

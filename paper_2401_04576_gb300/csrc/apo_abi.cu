@@ -649,8 +649,9 @@ int apo_diag_pipe_peak(int32_t precision, int32_t op, double *ops_per_s) {
 }
 
 int apo_diag_dops(int32_t op, const double *x, double *out, int64_t n, void *stream) {
-    if (op < 0 || op > 11) return fail(APO_EINVAL, "bad op");
+    if (op < 0 || op > 17) return fail(APO_EINVAL, "bad op");
     if (n < 0 || (n > 0 && (!x || !out))) return fail(APO_EINVAL, "bad arguments");
+    if (op >= 12 && op <= 17 && (n & 1)) return fail(APO_EINVAL, "quotients need an even n");
     if (launch_dops(op, x, out, n, static_cast<cudaStream_t>(stream)))
         return fail(APO_ECUDA, "dops launch failed");
     return APO_OK;

@@ -75,6 +75,7 @@ double pipe_peak(int precision, int op) {
 }
 
 // Elementwise scalar operations for the tests of ipipe.cuh.
+// x has an even number of elements when op is a quotient (12-17).
 __global__ void k_dops(int op, const double *__restrict__ x, double *__restrict__ out, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -92,7 +93,14 @@ __global__ void k_dops(int op, const double *__restrict__ x, double *__restrict_
             case 8: r = __drcp_rn(v); break;
             case 9: r = __dsqrt_rd(v); break;
             case 10: r = __dsqrt_ru(v); break;
-            default: r = __dsqrt_rn(v); break;
+            case 11: r = __dsqrt_rn(v); break;
+            // quotients x[i] / x[i ^ 1]
+            case 12: r = ipipe::div_rd(v, x[i ^ 1]); break;
+            case 13: r = ipipe::div_ru(v, x[i ^ 1]); break;
+            case 14: r = ipipe::div_rn(v, x[i ^ 1]); break;
+            case 15: r = __ddiv_rd(v, x[i ^ 1]); break;
+            case 16: r = __ddiv_ru(v, x[i ^ 1]); break;
+            default: r = __ddiv_rn(v, x[i ^ 1]); break;
         }
         out[i] = r;
     }

@@ -18,8 +18,8 @@ namespace p4 {
 __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
-__device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ double div(double a, double b) { return ipipe::div_rn(a, b); }
+__device__ __forceinline__ double sqrt(double a) { return ipipe::sqrt_rn(a); }
 __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }

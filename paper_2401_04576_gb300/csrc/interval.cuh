@@ -21,9 +21,10 @@ __device__ __forceinline__ double rd_sub(double a, double b) { return __dsub_rd(
 __device__ __forceinline__ double ru_sub(double a, double b) { return __dsub_ru(a, b); }
 __device__ __forceinline__ double rd_mul(double a, double b) { return __dmul_rd(a, b); }
 __device__ __forceinline__ double ru_mul(double a, double b) { return __dmul_ru(a, b); }
-__device__ __forceinline__ double rd_div(double a, double b) { return __ddiv_rd(a, b); }
-__device__ __forceinline__ double ru_div(double a, double b) { return __ddiv_ru(a, b); }
-// square root and reciprocal: correctly rounded on the integer pipe (ipipe.cuh)
+__device__ __forceinline__ double rd_div(double a, double b) { return ipipe::div_rd(a, b); }
+__device__ __forceinline__ double ru_div(double a, double b) { return ipipe::div_ru(a, b); }
+// quotient (above), square root and reciprocal: correctly rounded on the integer pipe
+// (ipipe.cuh)
 __device__ __forceinline__ double rd_rcp(double a) { return ipipe::rcp_rd(a); }
 __device__ __forceinline__ double ru_rcp(double a) { return ipipe::rcp_ru(a); }
 __device__ __forceinline__ double rd_sqrt(double a) { return ipipe::sqrt_rd(a); }
@@ -169,7 +170,9 @@ template <typename T> __device__ __forceinline__ IV<T> sqrti(IV<T> a) {
     return {gt0(a.lo) ? rd_sqrt(a.lo) : T(0), ru_sqrt(a.hi)};
 }
 
+// exact scalings by powers of two
 template <typename T> __device__ __forceinline__ IV<T> scale2(IV<T> a) { return {a.lo * T(2), a.hi * T(2)}; }
+template <typename T> __device__ __forceinline__ IV<T> scale4(IV<T> a) { return {a.lo * T(4), a.hi * T(4)}; }
 template <typename T> __device__ __forceinline__ IV<T> half(IV<T> a) { return {a.lo * T(0.5), a.hi * T(0.5)}; }
 template <typename T> __device__ __forceinline__ IV<T> clamp1(IV<T> a) {
     return {mx(a.lo, T(-1)), mn(a.hi, T(1))};

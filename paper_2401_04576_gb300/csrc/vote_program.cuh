@@ -72,7 +72,7 @@ template <typename T> __device__ __forceinline__ IV<T> atan_iv(IV<T> x, const Se
     IV<T> a = mul(x, h);
     T rem = ru_mul(ru_pow17(mag(x)), cst<T>(k, C_ATAN0 + 8).hi);
     a = add(a, pm(rem));
-    return {a.lo * T(4), a.hi * T(4)};
+    return scale4(a);
 }
 
 // sin and cos over an interval d with |d| <= 1 (d is the small stereo correction of the
@@ -327,8 +327,8 @@ namespace pt {
 __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
-__device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ double div(double a, double b) { return ipipe::div_rn(a, b); }
+__device__ __forceinline__ double sqrt(double a) { return ipipe::sqrt_rn(a); }
 __device__ __forceinline__ double clamp1(double x) { return x < -1.0 ? -1.0 : (x > 1.0 ? 1.0 : x); }
 __device__ __forceinline__ double centre(IV<double> a) { return mul(add(a.lo, a.hi), 0.5); }
 

@@ -1,9 +1,9 @@
-"""The library's integer-pipe FP64 square root and reciprocal (rounded down, up and to
-nearest) against the CUDA library's __dsqrt_* / __drcp_* bit for bit, on random bit
-patterns over the whole normal range, on the edge significands (1, 1 + 2^-52, 2 - 2^-52),
-perfect squares and their neighbours, the ends of the exponent range, and the arguments
-outside the fast path (zero, subnormals, infinities, NaN, negatives); and a sample against
-exact rational rounding computed here."""
+"""The library's integer-pipe FP64 square root, reciprocal and quotient (rounded down, up
+and to nearest) against the CUDA library's __dsqrt_* / __drcp_* / __ddiv_* bit for bit,
+on random bit patterns over the whole normal range, on the edge significands (1, 1 + 2^-52, 2 - 2^-52), perfect squares
+and their neighbours, the ends of the exponent range, and the arguments outside the fast
+path (zero, subnormals, infinities, NaN, negatives); and a sample against exact rational
+rounding computed here."""
 import math
 from fractions import Fraction
 
@@ -52,9 +52,48 @@ def test_ipipe_matches_cuda_library():
     for k, name in enumerate(OPS):
         got = apo.dops(k, xt).cpu().numpy()
         ref = apo.dops(k + 6, xt).cpu().numpy()
-        same = (got.view(np.uint64) == ref.view(np.uint64)) | (np.isnan(got) & np.isnan(ref))
-        bad = np.flatnonzero(~same)
+        bad = np.flatnonzero(~_same(got, ref))
         assert bad.size == 0, (name, bad.size, [(x[i], got[i], ref[i]) for i in bad[:5]])
+
+
+def _same(got, ref):
+    return (got.view(np.uint64) == ref.view(np.uint64)) | (np.isnan(got) & np.isnan(ref))
+
+
+def _pairs():
+    """(a, b) interleaved: random signs and significands, exponent differences over the
+    whole range (quotients that overflow, underflow or go subnormal included), equal
+    significands, zero numerators, and special divisors."""
+    rng = np.random.default_rng(13)
+    n = 1 << 20
+    ea = rng.integers(1, 2047, n, dtype=np.uint64)
+    eb = np.clip(ea.astype(np.int64) + rng.integers(-1100, 1100, n), 1, 2046).astype(np.uint64)
+    fa = rng.integers(0, 1 << 52, n, dtype=np.uint64)
+    fb = np.where(rng.random(n) < 0.05, fa, rng.integers(0, 1 << 52, n, dtype=np.uint64))
+    sa = rng.integers(0, 2, n, dtype=np.uint64) << np.uint64(63)
+    sb = rng.integers(0, 2, n, dtype=np.uint64) << np.uint64(63)
+    a = _bits_to_f64(sa | (ea << np.uint64(52)) | fa)
+    b = _bits_to_f64(sb | (eb << np.uint64(52)) | fb)
+    a[::97] = 0.0
+    a[1::97] = -0.0
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1e-310, -1e-310,
+                        np.finfo(np.float64).max, np.finfo(np.float64).tiny, 1.0, -3.0])
+    a2 = np.repeat(special, special.size)
+    b2 = np.tile(special, special.size)
+    a, b = np.concatenate([a, a2]), np.concatenate([b, b2])
+    out = np.empty(2 * a.size)
+    out[0::2], out[1::2] = a, b
+    return out
+
+
+def test_ipipe_quotients():
+    x = _pairs()
+    xt = torch.as_tensor(x, device="cuda")
+    for k, name in enumerate(("div_rd", "div_ru", "div_rn")):
+        got = apo.dops(12 + k, xt).cpu().numpy()[0::2]
+        ref = apo.dops(15 + k, xt).cpu().numpy()[0::2]
+        bad = np.flatnonzero(~_same(got, ref))
+        assert bad.size == 0, (name, bad.size, [(x[2 * i], x[2 * i + 1], got[i], ref[i]) for i in bad[:5]])
 
 
 def _exact(name, v):
@@ -94,3 +133,18 @@ def test_ipipe_exact_rounding_sample():
         got = apo.dops(k, xt).cpu().numpy()
         for i in range(0, x.size, 7):
             assert got[i] == _exact(name, float(x[i])), (name, x[i], got[i])
+    # quotients within 2^+-41 of 1 (normal), negative divisors
+    x = x[(exp > 100) & (exp < 1900)]
+    b = -(x * rng.uniform(0.5, 2.0, x.size)) * np.ldexp(1.0, rng.integers(-40, 40, x.size))
+    pairs = np.empty(2 * x.size)
+    pairs[0::2], pairs[1::2] = x, b
+    pt = torch.as_tensor(pairs, device="cuda")
+    for k, mode in enumerate(("rd", "ru", "rn")):
+        got = apo.dops(12 + k, pt).cpu().numpy()[0::2]
+        for i in range(0, x.size, 7):
+            t = Fraction(float(x[i])) / Fraction(float(b[i]))
+            q = float(x[i]) / float(b[i])
+            cands = (q, math.nextafter(q, -math.inf), math.nextafter(q, math.inf))
+            want = {"rd": max(c for c in cands if Fraction(c) <= t),
+                    "ru": min(c for c in cands if Fraction(c) >= t), "rn": q}[mode]
+            assert got[i] == want, (mode, x[i], b[i], got[i], want)
