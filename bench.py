@@ -724,7 +724,8 @@ def run_case(args) -> None:
     geom = apo.Geometry(g, w)
     hits = apo.DeviceHits.from_events(ev)
     ws = geom.workspace(ev.n_events)
-    prec = apo.F64 if args.case.endswith("f64") else apo.F32
+    prec = (apo.F64_MID if args.case == "coarse-mid" else
+            apo.F64 if args.case.endswith("f64") else apo.F32)
     if args.case.startswith("coarse"):
         votes = torch.empty((ev.n_events, geom.n_coarse), dtype=torch.int32, device="cuda")
         for _ in range(2):
@@ -754,7 +755,7 @@ def main(argv=None):
     ap.add_argument("--no-exact", action="store_true", help="skip the exact-phase leg")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--case", default=None,
-                    choices=["coarse-f64", "coarse-f32", "solve-f64", "solve-f32", "solve-bulk",
+                    choices=["coarse-f64", "coarse-f32", "coarse-mid", "solve-f64", "solve-f32", "solve-bulk",
                              "four-f32", "four-f64"],
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--events", type=int, default=64)

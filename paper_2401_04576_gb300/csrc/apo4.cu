@@ -154,23 +154,54 @@ __device__ __forceinline__ double edge4(double lo, int i, double w) { return __d
 __device__ __forceinline__ double mid4(double a, double b) { return __dmul_rn(__dadd_rn(a, b), 0.5); }
 
 // ---------------------------------------------------------------------------------------
-// Voting.  Block: 128 voxel columns (x_c, y_c, R) of one event; each thread runs every
+// Voting.  Block: a tile of kTile4 voxel columns (x_c, y_c, R) of one event.  First the
+// block tests every column of its tile against the disk pre-filter (Eq. ApoVoteDisk) and
+// the centre's validity, writes zero votes for the columns that fail, and lists the rest
+// in shared memory.  Then its 128 threads share out the listed columns: each runs every
 // active hit over its column's z0 voxels and both signs of tan(lambda), sharing the z0-
-// and sign-free part per hit; vote counters bit-sliced over the z0 voxels.
+// and sign-free part per hit, with vote counters bit-sliced over the z0 voxels.  Listing
+// first keeps the lanes of a warp on columns that all do the work; on the first
+// iteration's wide grid most warps would otherwise mix passing and failing columns.
 // ---------------------------------------------------------------------------------------
+constexpr int kTile4 = 512;
+
+template <typename T> struct Col4 {
+    IV<T> X, Y, Rv;
+    Ctr4<T> m;
+};
+
 template <typename T>
-__global__ void __launch_bounds__(128)
+__device__ __forceinline__ Col4<T> column4(const Iter4 &it, const double *le, const double *rf,
+                                           long long col) {
+    const int ix = (int)(col % it.n[0]);
+    const int iy = (int)((col / it.n[0]) % it.n[1]);
+    const int iR = (int)(col / ((long long)it.n[0] * it.n[1]));
+    const double xl = edge4(le[0], ix, it.w[0]), xh = edge4(le[0], ix + 1, it.w[0]);
+    const double yl = edge4(le[1], iy, it.w[1]), yh = edge4(le[1], iy + 1, it.w[1]);
+    const double rl = edge4(le[2], iR, it.w[2]), rh = edge4(le[2], iR + 1, it.w[2]);
+    Col4<T> c;
+    c.X = box_iv<T>(xl, xh);
+    c.Y = box_iv<T>(yl, yh);
+    c.Rv = box_iv<T>(rl, rh);
+    c.m = centre4<T>(rn<T>(mid4(xl, xh)), rn<T>(mid4(yl, yh)), rn<T>(mid4(rl, rh)),
+                     rn<T>(it.p_gev), rn<T>(it.b_tesla), rn<T>(rf[0]), rn<T>(rf[1]));
+    return c;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 3 : 5)
 k4_vote(Iter4 it, int ev0, const int32_t *n_hits, const HitRecD *hd, const uint32_t *active,
         const double *lo, const double *ref, int32_t *votes, int32_t *vmax) {
     __shared__ HitP<T> s_h[kHitCap];
     __shared__ HitI<T> s_w[kHitCap];
     __shared__ T s_zc[32];
     __shared__ IV<T> s_z[32];
-    __shared__ int s_n, s_vmax[2];
+    __shared__ short s_col[kTile4];
+    __shared__ int s_n, s_np, s_vmax[2];
     const int el = blockIdx.y, e = ev0 + el, tid = threadIdx.x;
     int nh = n_hits[e];
     if (nh < 0) nh = 0;
-    if (tid == 0) { s_n = 0; s_vmax[0] = s_vmax[1] = 0; }
+    if (tid == 0) { s_n = 0; s_np = 0; s_vmax[0] = s_vmax[1] = 0; }
     __syncthreads();
     const uint32_t *act = active + (long long)e * 8;
     for (int i = tid; i < nh; i += blockDim.x) {
@@ -186,17 +217,28 @@ k4_vote(Iter4 it, int ev0, const int32_t *n_hits, const HitRecD *hd, const uint3
         s_zc[iz] = rn<T>(mid4(zl, zh));
         s_z[iz] = box_iv<T>(zl, zh);
     }
+    const double *rf = ref + (long long)e * 2;
+    const int nz = it.n[3];
+    int32_t *vo = votes + (long long)el * 2 * it.nvox;
+    const long long col0 = (long long)blockIdx.x * kTile4;
+    // disk pre-filter of the tile; failing columns get zero votes
+    for (int k = tid; k < kTile4; k += blockDim.x) {
+        const long long col = col0 + k;
+        if (col >= it.ncol) break;
+        const Col4<T> c = column4<T>(it, le, rf, col);
+        if (disk4<T>(c.X, c.Y, c.Rv, up<T>(it.disk_radius)) && c.m.valid) {
+            s_col[atomicAdd(&s_np, 1)] = (short)k;
+        } else {
+            for (int s = 0; s < 2; s++)
+                for (int iz = 0; iz < nz; iz++) vo[(long long)s * it.nvox + col + it.ncol * iz] = 0;
+        }
+    }
     __syncthreads();
-    const int na = s_n, nz = it.n[3];
-    const long long col = (long long)blockIdx.x * blockDim.x + tid;
-    if (col < it.ncol) {
-        const int ix = (int)(col % it.n[0]);
-        const int iy = (int)((col / it.n[0]) % it.n[1]);
-        const int iR = (int)(col / ((long long)it.n[0] * it.n[1]));
-        const double xl = edge4(le[0], ix, it.w[0]), xh = edge4(le[0], ix + 1, it.w[0]);
-        const double yl = edge4(le[1], iy, it.w[1]), yh = edge4(le[1], iy + 1, it.w[1]);
-        const double rl = edge4(le[2], iR, it.w[2]), rh = edge4(le[2], iR + 1, it.w[2]);
-        const IV<T> X = box_iv<T>(xl, xh), Y = box_iv<T>(yl, yh), Rv = box_iv<T>(rl, rh);
+    const int na = s_n, np = s_np;
+    int mx[2] = {0, 0};
+    for (int i = tid; i < np; i += blockDim.x) {
+        const long long col = col0 + s_col[i];
+        const Col4<T> c = column4<T>(it, le, rf, col);
         uint32_t pl[2][9];
 #pragma unroll
         for (int s = 0; s < 2; s++)
@@ -205,33 +247,25 @@ k4_vote(Iter4 it, int ev0, const int32_t *n_hits, const HitRecD *hd, const uint3
         auto add_votes = [&](int s, uint32_t m) {
 #pragma unroll
             for (int q = 0; q < 9; q++) {
-                const uint32_t c = pl[s][q] & m;
+                const uint32_t cy = pl[s][q] & m;
                 pl[s][q] ^= m;
-                m = c;
+                m = cy;
             }
         };
-        const double* rf = ref + (long long)e * 2;
-        const Ctr4<T> m = centre4<T>(rn<T>(mid4(xl, xh)), rn<T>(mid4(yl, yh)), rn<T>(mid4(rl, rh)),
-                                     rn<T>(it.p_gev), rn<T>(it.b_tesla), rn<T>(rf[0]), rn<T>(rf[1]));
-        const uint32_t all = nz >= 32 ? 0xffffffffu : ((1u << nz) - 1u);
-        if (disk4<T>(X, Y, Rv, up<T>(it.disk_radius)) && m.valid) {
-            for (int j = 0; j < na; j++) {
-                const HitP<T> h = s_h[j];
-                const HitI<T> wi = s_w[j];
-                uint32_t b0 = 0, b1 = 0;
-                for (int iz = 0; iz < nz; iz++) {
-                    const Pre4<T> pre = prefix4<T>(m, s_zc[iz], h);
-                    if (pre.guard) { b0 |= 1u << iz; b1 |= 1u << iz; continue; }
-                    const IV<T> A2 = a2_4<T>(X, Y, s_z[iz], wi);
-                    if (pair4<T>(m, pre, 1, h, A2, Rv)) b0 |= 1u << iz;
-                    if (pair4<T>(m, pre, -1, h, A2, Rv)) b1 |= 1u << iz;
-                }
-                add_votes(0, b0);
-                add_votes(1, b1);
+        for (int j = 0; j < na; j++) {
+            const HitP<T> h = s_h[j];
+            const HitI<T> wi = s_w[j];
+            uint32_t b0 = 0, b1 = 0;
+            for (int iz = 0; iz < nz; iz++) {
+                const Pre4<T> pre = prefix4<T>(c.m, s_zc[iz], h);
+                if (pre.guard) { b0 |= 1u << iz; b1 |= 1u << iz; continue; }
+                const IV<T> A2 = a2_4<T>(c.X, c.Y, s_z[iz], wi);
+                if (pair4<T>(c.m, pre, 1, h, A2, c.Rv)) b0 |= 1u << iz;
+                if (pair4<T>(c.m, pre, -1, h, A2, c.Rv)) b1 |= 1u << iz;
             }
+            add_votes(0, b0);
+            add_votes(1, b1);
         }
-        int mx[2] = {0, 0};
-        int32_t *vo = votes + (long long)el * 2 * it.nvox;
         for (int s = 0; s < 2; s++)
             for (int iz = 0; iz < nz; iz++) {
                 int v = 0;
@@ -240,9 +274,9 @@ k4_vote(Iter4 it, int ev0, const int32_t *n_hits, const HitRecD *hd, const uint3
                 vo[(long long)s * it.nvox + col + it.ncol * iz] = v;
                 mx[s] = v > mx[s] ? v : mx[s];
             }
-        atomicMax(&s_vmax[0], mx[0]);
-        atomicMax(&s_vmax[1], mx[1]);
     }
+    if (mx[0] > 0) atomicMax(&s_vmax[0], mx[0]);
+    if (mx[1] > 0) atomicMax(&s_vmax[1], mx[1]);
     __syncthreads();
     if (tid < 2 && s_vmax[tid] > 0) atomicMax(&vmax[(long long)e * 2 + tid], s_vmax[tid]);
 }
@@ -452,7 +486,7 @@ template <typename T>
 void launch_vote4(const Iter4 &it, int ev0, int n, const int32_t *nh, const HitRecD *hd,
                   const uint32_t *active, const double *lo, const double *ref, int32_t *votes,
                   int32_t *vmax, cudaStream_t s) {
-    dim3 grid((unsigned)((it.ncol + 127) / 128), n);
+    dim3 grid((unsigned)((it.ncol + kTile4 - 1) / kTile4), n);
     k4_vote<T><<<grid, 128, 0, s>>>(it, ev0, nh, hd, active, lo, ref, votes, vmax);
 }
 
