@@ -502,9 +502,37 @@ def run_apo(args) -> None:
                                        apo._stream_ptr(stream))
     apo._check(rc)
     n_par, n_pre, n_tail, n_launch, p32, q32, t32c, _ = (int(x) for x in counts.cpu().tolist())
-    votes32 = apo.vote(geom, hits, precision=apo.F32, workspace=ws, stream=stream)
+    votes32 = torch.empty_like(votes)
+    counts32 = torch.zeros(8, dtype=torch.int64, device="cuda")
+    rc = L.apo_diag_vote_coarse_counts(geom.handle, C.byref(hc), apo.F32, apo._ptr(votes32),
+                                       apo._ptr(counts32), apo._ptr(ws), ws.numel(),
+                                       apo._stream_ptr(stream))
+    apo._check(rc)
     superset_violations = int((votes32 < votes).sum().item())
     n_cells_cmp = int(votes.numel())
+    c32 = [int(x) for x in counts32.cpu().tolist()]
+    # the FP32 coarse kernel (dominant in the FP32-bulk solve): counted FP32 directed
+    # operations / live launch time, against the measured FP32 directed add/mul rate
+    ops32_coarse = coarse_kernel_ops(c32[4], c32[5], c32[6]) / max(c32[3], 1)
+    kms32 = []
+    for _ in range(max(3, args.steps)):
+        flush.fill_(1)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        apo.vote(geom, hits, precision=apo.F32, out=votes32, workspace=ws, stream=stream)
+        s1.record(stream)
+        s1.synchronize()
+        kms32.append(s0.elapsed_time(s1) / max(c32[3], 1))
+    k32_ms = statistics.mean(kms32)
+    peak32 = apo.pipe_peak(apo.F32)
+    roofline32 = {"bound": "issue", "kernel": "k_vote_coarse<float>",
+                  "achieved": ops32_coarse / (k32_ms * 1e-3) / 1e12, "peak": peak32 / 1e12,
+                  "unit": "TFLOP/s", "frac": ops32_coarse / (k32_ms * 1e-3) / peak32,
+                  "launch_ms": k32_ms, "ops_per_launch": ops32_coarse,
+                  "peak_source": "measured: libapo directed-rounding FP32 add/mul microbenchmark "
+                                 "(apo_diag_pipe_peak) on this GPU, this run",
+                  "work": {"fp32_parent": c32[4], "fp32_prefix": c32[5], "fp32_tail": c32[6],
+                           "launches": c32[3]}}
     del votes32
     ops_launch = coarse_kernel_ops(n_par, n_pre, n_tail) / max(n_launch, 1)
     ops32_launch = coarse_kernel_ops(p32, q32, t32c) / max(n_launch, 1)
@@ -664,7 +692,8 @@ def run_apo(args) -> None:
                       "precision": "FP32 levels 0-4, FP64 levels 5-6",
                       "final_within_one_cell_of_fp64": agree,
                       "coarse_superset_violations": superset_violations,
-                      "coarse_cells_compared": n_cells_cmp},
+                      "coarse_cells_compared": n_cells_cmp,
+                      "coarse_roofline": roofline32},
         "step_ms_p50": float(np.percentile(ms64, 50)), "step_ms_p99": float(np.percentile(ms64, 99)),
         "e2e": {"value": pairs * world / (t_e2e * 1e-3), "unit": "evals/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e},

@@ -21,8 +21,9 @@ def test_op_constants_match_oracle_counter():
         cell = O.cell12(g, L, idx)
         for i in range(ev.n_hits(0)):
             wid = ev.wire_id[ev.offsets[0] + i]
-            c = O.op_counts(cell, O.hit9(w, wid, ev.drift[ev.offsets[0] + i]), 0)
-            assert c.tolist() == [bench.OPS_CELL, bench.OPS_PREFIX, bench.OPS_LPART, bench.OPS_SIGNS]
+            for prec in (0, 1):   # FP64 and FP32 run the same sequence of operations
+                c = O.op_counts(cell, O.hit9(w, wid, ev.drift[ev.offsets[0] + i]), prec)
+                assert c.tolist() == [bench.OPS_CELL, bench.OPS_PREFIX, bench.OPS_LPART, bench.OPS_SIGNS]
     assert bench.OPS_FULL == sum([bench.OPS_CELL, bench.OPS_PREFIX, bench.OPS_LPART, bench.OPS_SIGNS])
 
 
