@@ -77,6 +77,30 @@ def test_four_vote_grid_bit_exact(wires, tab, ch, prec):
 
 
 @pytest.mark.parametrize("prec", [apo.F64, apo.F32])
+def test_four_vote_tiles_without_disk_columns(wires, tab, ch, prec):
+    """Event 0's grid lies far from the origin, so no column of any tile passes the disk
+    pre-filter (every vote 0); event 1's 1,152 columns fill two tiles of 512 and a
+    ragged third, mixing passing and failing columns."""
+    ev = comet.events(2, seed=65, w=wires)
+    n = (12, 12, 8, 6)
+    w = (0.075, 0.075, 0.01875, 0.25)
+    opts = apo.four_opts(precision=prec, n=(n, n, n), w=(w, w, w))
+    lo = np.array([[2.0, 2.0, 0.225, -0.75], [-0.45, -0.45, 0.225, -0.75]])
+    refs = np.zeros((2, 2))
+    act = np.ones(int(ev.offsets[-1]), np.uint8)
+    got = apo.vote4(ch, _hits(ev), opts, 0, torch.as_tensor(lo, device="cuda"),
+                    torch.as_tensor(refs, device="cuda"),
+                    active=torch.as_tensor(act, device="cuda")).cpu().numpy()
+    oo = O.four_opts(precision=0 if prec == apo.F64 else 1)
+    for e in range(2):
+        a, b = ev.offsets[e], ev.offsets[e + 1]
+        ref = O.four_vote_grid(oo, O.four_grid(lo[e], w, n), refs[e], tab, ev.wire_id[a:b],
+                               ev.drift[a:b], act[a:b])
+        np.testing.assert_array_equal(got[e], ref, err_msg=f"event {e}")
+    assert got[0].max() == 0 and got[1].max() > 0
+
+
+@pytest.mark.parametrize("prec", [apo.F64, apo.F32])
 def test_four_solve_reduced_grids_bit_exact(wires, tab, ch, prec):
     ev = comet.events(5, seed=62, w=wires)
     opts = apo.four_opts(precision=prec, w=RW, n=RN)
