@@ -160,6 +160,11 @@ template <> __device__ __forceinline__ IV<float> divi<float>(IV<float> a, IV<flo
 template <typename T> __device__ __forceinline__ IV<T> mul_nn(IV<T> a, IV<T> b) {
     return {rd_mul(a.lo, nonneg_lo(a.lo) ? b.lo : b.hi), ru_mul(a.hi, nonneg_lo(a.hi) ? b.hi : b.lo)};
 }
+// a * b for b <= 0 (b.hi <= 0): a b is decreasing in a, so the ends are a.hi and a.lo, each
+// times the end of b chosen by its sign.
+template <typename T> __device__ __forceinline__ IV<T> mul_np(IV<T> a, IV<T> b) {
+    return {rd_mul(a.hi, nonneg_lo(a.hi) ? b.lo : b.hi), ru_mul(a.lo, nonneg_lo(a.lo) ? b.hi : b.lo)};
+}
 // a * b for a >= 0 and b >= 0
 template <typename T> __device__ __forceinline__ IV<T> mul_pp(IV<T> a, IV<T> b) {
     return {rd_mul(a.lo, b.lo), ru_mul(a.hi, b.hi)};

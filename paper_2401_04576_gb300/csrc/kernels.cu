@@ -355,8 +355,21 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
                     lm = 0;
                     n_tail32 += Bl;
 #pragma unroll 1
-                    for (int l = 0; l < Bl; l++)
-                        if (tail<float>(p32, L32[l], h32, R32, c32.W, k)) lm |= 1u << l;
+                    for (int l = 0; l < Bl; l++) {
+                        const IV<float> Ll = L32[l];
+                        bool tv;
+                        if (MODE == kModeF32) {
+                            // the block's threads share the bin: a uniform branch on L's sign
+                            // (in the filtered FP64 mode the three FP32 tails cost more code
+                            // than they save)
+                            tv = Ll.lo >= 0.f ? tail<float, 1>(p32, Ll, h32, R32, c32.W, k)
+                               : Ll.hi <= 0.f ? tail<float, -1>(p32, Ll, h32, R32, c32.W, k)
+                                              : tail<float, 0>(p32, Ll, h32, R32, c32.W, k);
+                        } else {
+                            tv = tail<float>(p32, Ll, h32, R32, c32.W, k);
+                        }
+                        if (tv) lm |= 1u << l;
+                    }
                 }
                 if (!k64) {
                     add_votes(lm);

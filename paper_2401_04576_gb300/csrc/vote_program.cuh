@@ -154,15 +154,29 @@ __device__ __forceinline__ Pre<T> prefix(const Cell<T> &c, const Hit<T> &h, cons
     return p;
 }
 
+// Products and square of tan(lambda) L when the caller knows its sign: LS = 1 for L >= 0,
+// -1 for L <= 0, 0 when unknown.  Each returns the same end points as the general form.
+template <int LS, typename T> __device__ __forceinline__ IV<T> lmul(IV<T> a, IV<T> L) {
+    if (LS > 0) return mul_nn(a, L);
+    if (LS < 0) return mul_np(a, L);
+    return mul(L, a);
+}
+template <int LS, typename T> __device__ __forceinline__ IV<T> lsqr(IV<T> L) {
+    if (LS > 0) return mul_pp(L, L);
+    if (LS < 0) return {rd_mul(L.hi, L.hi), ru_mul(L.lo, L.lo)};
+    return sqr(L);
+}
+
 // The tan(lambda)-dependent rest: Phi (ApproxPhi_a), u_d (normudi), z^St (EQSinter_c),
-// c^tau and the radicand of Eq. (defdiAX_b); returns the vote (either drift sign).
-template <typename T>
+// c^tau and the radicand of Eq. (defdiAX_b); returns the vote (either drift sign).  LS: the
+// sign of L when the caller knows it (see lmul).
+template <typename T, int LS = 0>
 __device__ __forceinline__ bool tail(const Pre<T> &p, IV<T> L, const Hit<T> &h, IV<T> R, IV<T> W,
                                      const SeriesConsts &k) {
     const IV<T> one{T(1), T(1)};
-    IV<T> L2 = sqr(L);
-    IV<T> P1e = neg(mul_nn(mul(L, p.psi_sPA), p.Ninv));
-    IV<T> P1o = neg(mul_nn(mul(L, p.dW_cPA), p.Ninv));
+    IV<T> L2 = lsqr<LS>(L);
+    IV<T> P1e = neg(mul_nn(lmul<LS>(p.psi_sPA, L), p.Ninv));
+    IV<T> P1o = neg(mul_nn(lmul<LS>(p.dW_cPA, L), p.Ninv));
     IV<T> P2e = mul_nn(mul_nn(p.inner_e, L2), p.Nh);
     IV<T> P2o = mul_nn(mul_nn(add(scale2(mul_nn(p.psi_cos2, L2)), mul_nn(p.sin2, add(p.N, mul_pp(L2, p.onepN)))),
                               p.dW),
@@ -177,7 +191,7 @@ __device__ __forceinline__ bool tail(const Pre<T> &p, IV<T> L, const Hit<T> &h, 
     IV<T> sP = clamp1(add(mul(p.sPA, cd), mul(p.cPA, sd)));
     IV<T> cP = clamp1(sub(mul(p.cPA, cd), mul(p.sPA, sd)));
     // u_d^2 (Eq. normudi)
-    IV<T> u2 = add(add(add(one, mul(scale2(h.t), mul(L, sP))), mul_pp(L2, h.t2)), mul_pp(sqr(cP), h.t2));
+    IV<T> u2 = add(add(add(one, mul(scale2(h.t), lmul<LS>(sP, L))), mul_pp(L2, h.t2)), mul_pp(sqr(cP), h.t2));
     if (le0(u2.lo)) return true;
     IV<T> Q = mul_pp(h.d, recip(sqrti(u2)));
     IV<T> Qct = mul_nn(mul(cP, h.t), Q);
@@ -191,7 +205,7 @@ __device__ __forceinline__ bool tail(const Pre<T> &p, IV<T> L, const Hit<T> &h, 
     for (int sg = 0; sg < 2; sg++) {
         IV<T> dl = sg == 0 ? dP : dM;
         IV<T> sp = mul_nn(add(p.psi, dl), R);                                  // s_perp
-        IV<T> zS = sg == 0 ? sub(mul(L, sp), Qct) : add(mul(L, sp), Qct);   // z^St - z_ref
+        IV<T> zS = sg == 0 ? sub(lmul<LS>(sp, L), Qct) : add(lmul<LS>(sp, L), Qct);   // z^St - z_ref
         IV<T> rct = sg == 0 ? sub(mul(zS, p.rcA), LQrsA) : add(mul(zS, p.rcA), LQrsA);
         IV<T> a1 = sg == 0 ? scale2(Q) : neg(scale2(Q));
         IV<T> a3 = mul(t2x, rct);
