@@ -30,8 +30,13 @@ __device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
 // reductions (|x| below tan(pi/16)), the alternating series through x^15 (Horner on x^2),
 // times 4; no remainder term.  1/(2k+1) are round-to-nearest constants of T.
 template <typename T> __device__ __forceinline__ T atan(T x) {
+    if (sizeof(T) == 8) {   // FP64: one copy of the reduction (see atan_iv)
+#pragma unroll 1
+        for (int i = 0; i < 2; i++) x = div(x, add(T(1), sqrt(add(T(1), mul(x, x)))));
+    } else {
 #pragma unroll
-    for (int i = 0; i < 2; i++) x = div(x, add(T(1), sqrt(add(T(1), mul(x, x)))));
+        for (int i = 0; i < 2; i++) x = div(x, add(T(1), sqrt(add(T(1), mul(x, x)))));
+    }
     const T y = mul(x, x);
     T h = T(1) / T(15);
     h = sub(T(1) / T(13), mul(h, y));

@@ -63,8 +63,14 @@ template <typename T> __device__ __forceinline__ T ru_pow17(T m) {
 // the alternating series through x^15 in Horner form on x^2, remainder |x|^17/17, times 4.
 template <typename T> __device__ __forceinline__ IV<T> atan_iv(IV<T> x, const SeriesConsts &k) {
     const IV<T> one{T(1), T(1)};
+    if (sizeof(T) == 8) {   // FP64: one copy of the reduction (its root and quotient are
+                            // long integer-pipe sequences), less instruction fetch
+#pragma unroll 1
+        for (int i = 0; i < 2; i++) x = divi(x, add(one, sqrti(add(one, sqr(x)))));
+    } else {
 #pragma unroll
-    for (int i = 0; i < 2; i++) x = divi(x, add(one, sqrti(add(one, sqr(x)))));
+        for (int i = 0; i < 2; i++) x = divi(x, add(one, sqrti(add(one, sqr(x)))));
+    }
     IV<T> y = sqr(x);
     IV<T> h = cst<T>(k, C_ATAN0 + 7);
 #pragma unroll
