@@ -43,10 +43,10 @@ OPS_TAIL = OPS_LPART + OPS_SIGNS
 
 
 # DRAM bytes (read + write) of one k_vote_coarse<FP64> launch per event, from the ncu
-# capture summarised in profiles/k_vote_coarse_f64_64events.md (64 events: 3.78 MB read +
-# 213.91 MB written), scaled by events to the benchmark's launch.  Must be re-captured (or
+# capture summarised in profiles/k_vote_coarse_f64_64events.md (64 events: 3.93 MB read +
+# 214.01 MB written), scaled by events to the benchmark's launch.  Must be re-captured (or
 # set to None) whenever that kernel changes.
-COARSE_F64_DRAM_BYTES_PER_EVENT = (3.775488e6 + 213.909760e6) / 64
+COARSE_F64_DRAM_BYTES_PER_EVENT = (3.930624e6 + 214.013440e6) / 64
 
 
 def coarse_kernel_ops(n_parent: int, n_prefix: int, n_tail: int) -> int:
