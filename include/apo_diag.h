@@ -40,6 +40,16 @@ int apo_diag_pipe_peak(int32_t precision, int32_t op, double *ops_per_s);
  * 12-14 = quotient x[i] / x[i ^ 1] rd / ru / rn (integer pipe; n must be even), 15-17 =
  * the same with __ddiv_*.  Every op accepts any double. */
 int apo_diag_dops(int32_t op, const double *x, double *out, int64_t n, void *stream);
+/* The vote program's evaluated intervals for n explicit (cell, hit) pairs, on `stream`,
+ * for comparing end points with the oracle (Eq. ApoVote; G = rho F per drift sign).
+ * Device arrays: cells[12 n] = (d0, sin phi0, cos phi0, omega, z0, tan(lambda)) as lo, hi
+ * pairs; hits[9 n] = (x0, y0, sin phi_s, cos phi_s, tan tau, sin phi_s tan tau,
+ * cos phi_s tan tau, tan^2 tau, drift); out[10 n] = the vote (0 / 1), G+ lo, G+ hi, G- lo,
+ * G- hi, a guard flag (1 when a divisor reached 0 and the pair votes unevaluated), and the
+ * phase corrections delta+ lo, hi, delta- lo, hi; zeros past a guard.  precision APO_F64
+ * or APO_F32 (cells and hits rounded outward to FP32 first; results widened to double). */
+int apo_diag_vote_pair_ends(const apo_geometry *geom, int32_t precision, const double *cells,
+                            const double *hits, double *out, int64_t n, void *stream);
 /* Exercises the device-side wait limit: one kernel waits on a barrier that nothing
  * completes, for at most `limit_polls` polls, then records a timeout in a status word and
  * ends normally.  Returns APO_ETIMEOUT when the status word shows it (the expected

@@ -120,6 +120,7 @@ def lib():
         L.apo_diag_pipe_peak.argtypes = [i32, i32, C.POINTER(C.c_double)]
         L.apo_diag_wait_timeout.argtypes = [i32]
         L.apo_diag_dops.argtypes = [i32, vp, vp, C.c_int64, vp]
+        L.apo_diag_vote_pair_ends.argtypes = [vp, i32, vp, vp, vp, C.c_int64, vp]
         L.apo_workspace_status.argtypes = [vp, i32, vp, vp]
         L.apo4_opts_default.argtypes = [C.POINTER(Apo4Opts)]
         L.apo4_chamber_create.argtypes = [C.POINTER(ApoWires), C.POINTER(vp)]
@@ -386,6 +387,20 @@ def dops(op: int, x, stream=None):
     assert x.dtype == _torch().float64 and x.is_cuda and x.is_contiguous()
     out = _torch().empty_like(x)
     _check(lib().apo_diag_dops(int(op), _ptr(x), _ptr(out), x.numel(), _stream_ptr(stream)))
+    return out
+
+
+def vote_pair_ends(geom: Geometry, cells, hits, precision: int = F64, stream=None):
+    """apo_diag_vote_pair_ends: (n, 10) float64 CUDA tensor (vote, G+ lo/hi, G- lo/hi,
+    guard, delta+ lo/hi, delta- lo/hi) for float64 CUDA tensors cells (n, 12), hits (n, 9)."""
+    torch = _torch()
+    assert cells.dtype == torch.float64 and hits.dtype == torch.float64
+    cells, hits = cells.contiguous(), hits.contiguous()
+    n = cells.shape[0]
+    assert hits.shape[0] == n
+    out = torch.empty((n, 10), dtype=torch.float64, device=cells.device)
+    _check(lib().apo_diag_vote_pair_ends(geom.handle, int(precision), _ptr(cells), _ptr(hits),
+                                         _ptr(out), n, _stream_ptr(stream)))
     return out
 
 

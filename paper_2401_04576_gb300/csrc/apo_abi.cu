@@ -657,6 +657,18 @@ int apo_diag_dops(int32_t op, const double *x, double *out, int64_t n, void *str
     return APO_OK;
 }
 
+int apo_diag_vote_pair_ends(const apo_geometry *g, int32_t precision, const double *cells,
+                            const double *hits, double *out, int64_t n, void *stream) {
+    int rc;
+    if ((rc = check_geom(g))) return rc;
+    if (precision != APO_F64 && precision != APO_F32) return fail(APO_EINVAL, "bad precision");
+    if (n < 0 || (n > 0 && (!cells || !hits || !out))) return fail(APO_EINVAL, "bad arguments");
+    if (launch_pair_ends(g->dg.k, precision == APO_F64 ? 0 : 1, cells, hits, out, n,
+                         static_cast<cudaStream_t>(stream)))
+        return fail(APO_ECUDA, "pair-ends launch failed");
+    return APO_OK;
+}
+
 int apo_solve_batch_host(const apo_geometry *g, int32_t n_events, const int32_t *offsets,
                          const int32_t *wire_id, const double *drift, const apo_solve_opts *opts,
                          apo_track *tracks_out, int32_t *n_tracks_out, void *ws, size_t ws_bytes,

@@ -106,6 +106,46 @@ __global__ void k_dops(int op, const double *__restrict__ x, double *__restrict_
     }
 }
 
+// The vote program's end points for explicit (cell, hit) pairs: cells as 12 doubles (D, sin
+// phi0, cos phi0, omega, z0, tan(lambda), lo / hi each), hits as 9 doubles (x0, y0, sin
+// phi_s, cos phi_s, tan tau, sin phi_s tan tau, cos phi_s tan tau, tan^2 tau, drift).  FP32
+// rounds both outward, as the staging and the cell lookup do.  out: 10 doubles per pair,
+// the vote then the 9 of vote_pair_ends.
+__global__ void k_pair_ends(SeriesConsts k, int precision, const double *__restrict__ cells,
+                            const double *__restrict__ hits, double *__restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double *c = cells + 12 * i, *h = hits + 9 * i;
+        double *o = out + 10 * i;
+        bool v;
+        if (precision == 0) {
+            Cell<double> cd{{c[0], c[1]}, {c[2], c[3]}, {c[4], c[5]}, {c[6], c[7]}, {c[8], c[9]}, {c[10], c[11]}};
+            Hit<double> hd;
+            IV<double> *f = &hd.x0;
+            for (int j = 0; j < 9; j++) f[j] = {h[j], h[j]};
+            v = vote_pair_ends<double>(cd, hd, k, o + 1);
+        } else {
+            Cell<float> cf;
+            IV<float> *cc = &cf.D;
+            for (int j = 0; j < 6; j++) cc[j] = {__double2float_rd(c[2 * j]), __double2float_ru(c[2 * j + 1])};
+            Hit<float> hf;
+            IV<float> *f = &hf.x0;
+            for (int j = 0; j < 9; j++) f[j] = {__double2float_rd(h[j]), __double2float_ru(h[j])};
+            v = vote_pair_ends<float>(cf, hf, k, o + 1);
+        }
+        o[0] = v ? 1.0 : 0.0;
+    }
+}
+
+int launch_pair_ends(const SeriesConsts &k, int precision, const double *cells, const double *hits,
+                     double *out, long long n, cudaStream_t s) {
+    if (n <= 0) return 0;
+    const long long want = (n + 127) / 128;
+    const int blocks = (int)(want < 4096 ? want : 4096);
+    k_pair_ends<<<blocks, 128, 0, s>>>(k, precision, cells, hits, out, n);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int launch_dops(int op, const double *x, double *out, long long n, cudaStream_t s) {
     if (n <= 0) return 0;
     int dev = 0, sms = 0;

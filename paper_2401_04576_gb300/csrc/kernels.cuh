@@ -130,6 +130,8 @@ void launch_estimate_mask(const DevGeom &g, int n_ev, const uint64_t *keys, cons
 void launch_series_consts(SeriesConsts *dev_out, cudaStream_t s);
 double pipe_peak(int precision, int op);   // diag.cu: directed operations per second
 int launch_dops(int op, const double *x, double *out, long long n, cudaStream_t s);   // diag.cu
+int launch_pair_ends(const SeriesConsts &k, int precision, const double *cells, const double *hits,
+                     double *out, long long n, cudaStream_t s);                        // diag.cu
 
 // apo_abi.cu: the device tables and device ordinal of a geometry handle, and the message
 // returned by apo_last_error() on this thread.

@@ -175,10 +175,11 @@ template <int LS, typename T> __device__ __forceinline__ IV<T> lsqr(IV<T> L) {
 
 // The tan(lambda)-dependent rest: Phi (ApproxPhi_a), u_d (normudi), z^St (EQSinter_c),
 // c^tau and the radicand of Eq. (defdiAX_b); returns the vote (either drift sign).  LS: the
-// sign of L when the caller knows it (see lmul).
-template <typename T, int LS = 0>
+// sign of L when the caller knows it (see lmul).  OUT: also store the evaluated intervals
+// in ends (see vote_pair_ends); the voting kernels use OUT = false.
+template <typename T, int LS = 0, bool OUT = false>
 __device__ __forceinline__ bool tail(const Pre<T> &p, IV<T> L, const Hit<T> &h, IV<T> R, IV<T> W,
-                                     const SeriesConsts &k) {
+                                     const SeriesConsts &k, double *ends = nullptr) {
     const IV<T> one{T(1), T(1)};
     IV<T> L2 = lsqr<LS>(L);
     IV<T> P1e = neg(mul_nn(lmul<LS>(p.psi_sPA, L), p.Ninv));
@@ -192,13 +193,17 @@ __device__ __forceinline__ bool tail(const Pre<T> &p, IV<T> L, const Hit<T> &h, 
     IV<T> dod = add(mul(P1o, h.t), mul_nn(P2o, h.t2));
     IV<T> dP = add(de, dod);
     IV<T> dM = sub(de, dod);
+    if (OUT) { ends[5] = dP.lo; ends[6] = dP.hi; ends[7] = dM.lo; ends[8] = dM.hi; }
     IV<T> sd, cd;
     sincos_iv(hull(dP, dM), sd, cd, k);
     IV<T> sP = clamp1(add(mul(p.sPA, cd), mul(p.cPA, sd)));
     IV<T> cP = clamp1(sub(mul(p.cPA, cd), mul(p.sPA, sd)));
     // u_d^2 (Eq. normudi)
     IV<T> u2 = add(add(add(one, mul(scale2(h.t), lmul<LS>(sP, L))), mul_pp(L2, h.t2)), mul_pp(sqr(cP), h.t2));
-    if (le0(u2.lo)) return true;
+    if (le0(u2.lo)) {
+        if (OUT) ends[4] = 1;
+        return true;
+    }
     IV<T> Q = mul_pp(h.d, recip(sqrti(u2)));
     IV<T> Qct = mul_nn(mul(cP, h.t), Q);
     IV<T> LQ = mul_nn(L, Q);
@@ -218,9 +223,26 @@ __device__ __forceinline__ bool tail(const Pre<T> &p, IV<T> L, const Hit<T> &h, 
         IV<T> a4 = mul_pp(W, sqr(mul(zS, h.t)));
         IV<T> Arad = sub(sub(sub(add(a1, a2), a3), a4), a5);
         IV<T> G = sub(p.G0, Arad);
+        if (OUT) { ends[2 * sg] = G.lo; ends[2 * sg + 1] = G.hi; }
         vote = vote || contains0(G);
     }
     return vote;
+}
+
+// Whole program for one (cell, hit), cell unmirrored, with the evaluated intervals in
+// ends[9]: G+ lo / hi, G- lo / hi, a guard flag (1 when a divisor reached 0 and the pair
+// votes unevaluated), then delta = Phi - Phi^Ax of the drift signs + and - (lo / hi each);
+// zeros where the program stopped before computing them.  Used to compare end points
+// with the oracle.
+template <typename T>
+__device__ __forceinline__ bool vote_pair_ends(Cell<T> c, Hit<T> h, const SeriesConsts &k, double *ends) {
+    for (int i = 0; i < 9; i++) ends[i] = 0.0;
+    if (mirror_cell(c)) mirror_hit(h);
+    if (le0(c.W.lo)) { ends[4] = 1; return true; }
+    IV<T> R = recip(c.W);
+    Pre<T> p = prefix(c, h, k);
+    if (p.guard) { ends[4] = 1; return true; }
+    return tail<T, 0, true>(p, c.L, h, R, c.W, k, ends);
 }
 
 // Whole program for one (cell, hit); the cell is given unmirrored.
