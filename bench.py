@@ -42,10 +42,11 @@ OPS_FULL = OPS_CELL + OPS_PREFIX + OPS_LPART + OPS_SIGNS
 OPS_TAIL = OPS_LPART + OPS_SIGNS
 
 
-# DRAM bytes (read + write) of one k_vote_coarse<FP64> launch per event, from the ncu
-# capture summarised in profiles/k_vote_coarse_f64_64events.md (64 events: 3.93 MB read +
-# 214.01 MB written), scaled by events to the benchmark's launch.  Must be re-captured (or
-# set to None) whenever that kernel changes.
+# DRAM bytes (read + write) of one k_vote_coarse<FP64> launch per event: an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, --clock-control none) of one 64-event
+# launch of that kernel on the 16^5 grid read 3.93 MB and wrote 214.01 MB (the vote
+# array); scaled by events to the benchmark's launch.  Must be re-captured (or set to None)
+# whenever that kernel changes.
 COARSE_F64_DRAM_BYTES_PER_EVENT = (3.930624e6 + 214.013440e6) / 64
 
 

@@ -291,6 +291,21 @@ void apo_serve_destroy(apo_server *srv);
 int apo_vote_coarse_noalloc(const apo_geometry *geom, const apo_hits *hits, int32_t precision,
                             int32_t *votes_out, void *stream);
 
+/* Status of the last apo_vote_coarse_noalloc call on the current device (its status word
+ * lives in the same fixed array, so apo_workspace_status cannot see it).  Synchronises
+ * `stream` (the stream of that call), then writes the raw status bits to *flags_out (host,
+ * may be NULL): APO_STATUS_TIMEOUT (a device wait ran out of its poll limit; the votes are
+ * untrusted), APO_STATUS_BADHIT (a wire id out of range or a negative / non-finite drift),
+ * APO_STATUS_TOOMANY (an event above APO_HIT_CAP hits), APO_STATUS_BADOFFS (decreasing
+ * offsets).  A malformed event gets zero votes and does not stop the batch.  Returns
+ * APO_ETIMEOUT if the timeout bit is set, else APO_EINVAL if any malformed-event bit is set,
+ * else APO_OK.  Each apo_vote_coarse_noalloc call clears the word first. */
+#define APO_STATUS_TIMEOUT 1u
+#define APO_STATUS_BADHIT 2u
+#define APO_STATUS_TOOMANY 4u
+#define APO_STATUS_BADOFFS 8u
+int apo_vote_coarse_noalloc_status(uint32_t *flags_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

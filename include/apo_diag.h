@@ -57,6 +57,11 @@ int apo_diag_vote_pair_ends(const apo_geometry *geom, int32_t precision, const d
  * stays usable afterwards. */
 int apo_diag_wait_timeout(int32_t limit_polls);
 
+/* The same wait on the status word of apo_vote_coarse_noalloc's fixed array (queued on
+ * `stream`): afterwards apo_vote_coarse_noalloc_status reports APO_ETIMEOUT, until the next
+ * apo_vote_coarse_noalloc call clears the word. */
+int apo_diag_noalloc_wait_timeout(int32_t limit_polls, void *stream);
+
 /* Reads the status word of a workspace after the work queued on it (synchronises
  * `stream`): APO_ETIMEOUT if a device wait ran out, APO_OK otherwise. */
 int apo_workspace_status(const apo_geometry *geom, int32_t n_events, const void *workspace,

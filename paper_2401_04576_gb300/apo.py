@@ -16,6 +16,7 @@ from . import build as _build
 APO_OK, APO_EINVAL, APO_ENOMEM, APO_ECUDA, APO_ETIMEOUT, APO_EBUSY = 0, -1, -2, -3, -4, -5
 F64, F32, F64_FILTERED, F64_MID, F64_EXACT = 0, 1, 2, 3, 4
 HIT_CAP = 256
+STATUS_TIMEOUT, STATUS_BADHIT, STATUS_TOOMANY, STATUS_BADOFFS = 1, 2, 4, 8
 MAX_LEVELS = 8
 MAX_TRACKS = 8
 
@@ -122,6 +123,9 @@ def lib():
         L.apo_diag_dops.argtypes = [i32, vp, vp, C.c_int64, vp]
         L.apo_diag_vote_pair_ends.argtypes = [vp, i32, vp, vp, vp, C.c_int64, vp]
         L.apo_workspace_status.argtypes = [vp, i32, vp, vp]
+        L.apo_vote_coarse_noalloc.argtypes = [vp, C.POINTER(ApoHits), i32, vp, vp]
+        L.apo_vote_coarse_noalloc_status.argtypes = [C.POINTER(C.c_uint32), vp]
+        L.apo_diag_noalloc_wait_timeout.argtypes = [i32, vp]
         L.apo4_opts_default.argtypes = [C.POINTER(Apo4Opts)]
         L.apo4_chamber_create.argtypes = [C.POINTER(ApoWires), C.POINTER(vp)]
         L.apo4_chamber_destroy.argtypes = [vp]
@@ -356,6 +360,26 @@ def wait_timeout_test(limit_polls: int = 1000) -> int:
     """apo_diag_wait_timeout: status of a device wait on a barrier nothing completes
     (APO_ETIMEOUT expected)."""
     return int(lib().apo_diag_wait_timeout(int(limit_polls)))
+
+
+def vote_coarse_noalloc(geom: Geometry, hits: DeviceHits, out, precision: int = F64,
+                        stream=None) -> int:
+    """apo_vote_coarse_noalloc into `out` (device int32, n_events x n_coarse); returns the
+    status code."""
+    hc = hits.c()
+    return int(lib().apo_vote_coarse_noalloc(geom.handle, C.byref(hc), int(precision), _ptr(out),
+                                             _stream_ptr(stream)))
+
+
+def noalloc_status(stream=None):
+    """(status code, raw status bits) of the last apo_vote_coarse_noalloc call."""
+    f = C.c_uint32(0)
+    rc = lib().apo_vote_coarse_noalloc_status(C.byref(f), _stream_ptr(stream))
+    return int(rc), int(f.value)
+
+
+def noalloc_wait_timeout_test(limit_polls: int = 1000, stream=None) -> int:
+    return int(lib().apo_diag_noalloc_wait_timeout(int(limit_polls), _stream_ptr(stream)))
 
 
 def workspace_status(geom: Geometry, n_events: int, workspace, stream=None) -> int:

@@ -12,6 +12,7 @@
 #include <mutex>
 
 #include "../../include/apo.h"
+#include "../../include/apo_diag.h"
 #include "kernels.cuh"
 
 using namespace apo;
@@ -107,6 +108,43 @@ extern "C" int apo_vote_coarse_noalloc(const apo_geometry *g, const apo_hits *hi
     if (e != cudaSuccess) return err(APO_ECUDA, cudaGetErrorString(e));
     launch_stage(*dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, active, done, status, s);
     launch_vote_coarse(*dg, precision, 0, ne, hd, hf, nh, votes_out, hist, status, s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return err(APO_ECUDA, cudaGetErrorString(e));
+    return APO_OK;
+}
+
+// The status bits published in apo.h are the kernels' own status bits.
+static_assert(APO_STATUS_TIMEOUT == ST_TIMEOUT && APO_STATUS_BADHIT == ST_BADHIT &&
+                  APO_STATUS_TOOMANY == ST_TOOMANY && APO_STATUS_BADOFFS == ST_BADOFFS,
+              "status bits");
+
+extern "C" int apo_vote_coarse_noalloc_status(uint32_t *flags_out, void *stream) {
+    void *base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc != APO_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, static_cast<unsigned char *>(base) + kOffStatus, sizeof(unsigned),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return err(APO_ECUDA, cudaGetErrorString(e));
+    if (flags_out) *flags_out = h;
+    if (h & ST_TIMEOUT) return err(APO_ETIMEOUT, "a device wait ran out of its poll limit");
+    if (h & (ST_BADHIT | ST_TOOMANY | ST_BADOFFS))
+        return err(APO_EINVAL, "malformed event(s) in the last apo_vote_coarse_noalloc call (zero votes)");
+    return APO_OK;
+}
+
+extern "C" int apo_diag_noalloc_wait_timeout(int32_t limit_polls, void *stream) {
+    if (limit_polls < 1) return err(APO_EINVAL, "limit_polls < 1");
+    void *base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc != APO_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned *status = reinterpret_cast<unsigned *>(static_cast<unsigned char *>(base) + kOffStatus);
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return err(APO_ECUDA, cudaGetErrorString(e));
+    launch_wait_never(limit_polls, status, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return err(APO_ECUDA, cudaGetErrorString(e));
     return APO_OK;
