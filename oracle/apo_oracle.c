@@ -326,6 +326,39 @@ static int vote_pair_drift_iv(const double c[12], const double h[9], double d_lo
                           H[5], H[6], H[7], H[8], NULL);
 }
 
+/* Hit finding of Section 3.3 on a set of cells (the final maximum-vote cells of a found
+ * track): hit i (with active[i] set, or every hit if active is NULL) is taken when it votes
+ * (FP64) for at least one of the n cells (keys at `level`) with its drift widened to
+ * [max(d - width, 0), d + width]; the widened end points are rounded outward.  taken[i] = 1
+ * for taken hits, otherwise left unchanged.  Must run under FE_DOWNWARD. */
+static void mask_hits(const or_grid *g, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
+                      const double *drift, const uint8_t *active, int32_t level,
+                      const uint64_t *keys, int64_t n, double width, uint8_t *taken) {
+    for (int64_t j = 0; j < n; j++) {
+        int32_t idx[5];
+        double c[12], h[9];
+        key_to_idx(keys[j], idx);
+        cell_intervals(g, level, idx, c);
+        for (int32_t i = 0; i < n_hits; i++) {
+            if ((active && !active[i]) || taken[i]) continue;
+            hit_constants(w, wire_id[i], drift[i], h);
+            volatile double lo = drift[i] - width;              /* rounded down */
+            volatile double hi = -((-drift[i]) - width);        /* rounded up */
+            double dlo = lo > 0 ? lo : 0.0;
+            if (vote_pair_drift_iv(c, h, dlo, hi)) taken[i] = 1;
+        }
+    }
+}
+
+void or_mask_hits(const or_grid *g, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
+                  const double *drift, const uint8_t *active, int32_t level, const uint64_t *keys,
+                  int64_t n, double width, uint8_t *taken) {
+    int old = fegetround();
+    fesetround(FE_DOWNWARD);
+    mask_hits(g, w, n_hits, wire_id, drift, active, level, keys, n, width, taken);
+    fesetround(old);
+}
+
 /* Multi-track extraction (the paper's hit finding of Section 3.3, applied to several
  * tracks): search the event's active hits; if the best final vote count is below
  * min_votes or no hit is active, stop; otherwise record the track and deactivate every
@@ -345,6 +378,9 @@ int or_solve_event_multi(const or_grid *g, const or_wires *w, int32_t n_hits, co
     int32_t *ia = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_hits > 0 ? n_hits : 1));
     uint64_t *lk = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)K * 32);
     int32_t *lv = (int32_t *)malloc(sizeof(int32_t) * (size_t)K * 32);
+    uint64_t *mk = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)K * 32);
+    uint8_t *act = (uint8_t *)malloc((size_t)(n_hits > 0 ? n_hits : 1));
+    uint8_t *tk = (uint8_t *)malloc((size_t)(n_hits > 0 ? n_hits : 1));
     for (int32_t i = 0; i < n_hits; i++) hit_track[i] = -1;
     *n_found = 0;
     for (int32_t t = 0; t < max_tracks; t++) {
@@ -357,27 +393,18 @@ int or_solve_event_multi(const or_grid *g, const or_wires *w, int32_t n_hits, co
         if (best < min_votes) break;
         votes[t] = best;
         *n_found = t + 1;
+        /* the final maximum-vote cells, in the order of the last level's cells */
+        int64_t nmax = 0;
+        for (int64_t j = 0; j < (int64_t)K * 32; j++)
+            if (lv[j] == best) mk[nmax++] = lk[j];
+        for (int32_t i = 0; i < n_hits; i++) { act[i] = hit_track[i] < 0; tk[i] = 0; }
         int old = fegetround();
         fesetround(FE_DOWNWARD);
-        for (int64_t j = 0; j < (int64_t)K * 32; j++) {
-            if (lv[j] != best) continue;
-            int32_t idx[5];
-            double c[12], h[9];
-            key_to_idx(lk[j], idx);
-            cell_intervals(g, g->levels, idx, c);
-            for (int32_t q = 0; q < na; q++) {
-                int32_t i = ia[q];
-                if (hit_track[i] >= 0) continue;
-                hit_constants(w, wire_id[i], drift[i], h);
-                volatile double lo = drift[i] - width;              /* rounded down */
-                volatile double hi = -((-drift[i]) - width);        /* rounded up */
-                double dlo = lo > 0 ? lo : 0.0;
-                if (vote_pair_drift_iv(c, h, dlo, hi)) hit_track[i] = t;
-            }
-        }
+        mask_hits(g, w, n_hits, wire_id, drift, act, g->levels, mk, nmax, width, tk);
         fesetround(old);
+        for (int32_t i = 0; i < n_hits; i++) if (tk[i]) hit_track[i] = t;
     }
-    free(wa); free(da); free(ia); free(lk); free(lv);
+    free(wa); free(da); free(ia); free(lk); free(lv); free(mk); free(act); free(tk);
     return 0;
 }
 

@@ -15,18 +15,22 @@ CFLAGS = ["-O1", "-std=c11", "-frounding-math", "-ffp-contract=off", "-fno-fast-
           "-fno-builtin", "-fopenmp", "-shared", "-fPIC", "-Wall", "-Wno-unknown-pragmas"]
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, variant: str = "", defines=()) -> str:
+    """Builds liboracle.so, or liboracle_<variant>.so compiled with extra -D defines (the
+    tests' reference variants)."""
     os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB):
-        t_lib = os.path.getmtime(LIB)
+    lib = LIB if not variant else os.path.join(OUT_DIR, "liboracle_%s.so" % variant)
+    if not force and os.path.exists(lib):
+        t_lib = os.path.getmtime(lib)
         if all(os.path.getmtime(p) <= t_lib for p in DEPS):
-            return LIB
+            return lib
     cc = os.environ.get("CC", "gcc")
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [cc, *CFLAGS, *SRC, "-o", tmp, "-lm"]
+    tmp = lib + ".tmp%d" % os.getpid()
+    extra = ["-D" + d for d in defines] + (["-Wno-unused-function"] if defines else [])
+    cmd = [cc, *CFLAGS, *extra, *SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

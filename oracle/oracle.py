@@ -46,42 +46,50 @@ class Or4Iter(C.Structure):
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
-        dp, ip, up = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_uint64)
-        L.or_vote_pair.argtypes = [dp, dp, C.c_int, dp]
-        L.or_vote_pair.restype = C.c_int
-        L.or_vote_pair_mid.argtypes = [dp, dp, dp, dp]
-        L.or_vote_pair_mid.restype = C.c_int
-        L.or_vote_cells.argtypes = [C.POINTER(OrGrid), C.POINTER(OrWires), C.c_int32, ip, dp,
-                                    C.c_int32, C.c_int32, up, C.c_int64, ip]
-        L.or_vote_cells.restype = None
-        L.or_coarse_keys.argtypes = [C.POINTER(OrGrid), up]
-        L.or_topk.argtypes = [up, ip, C.c_int64, C.c_int32, up, ip]
-        L.or_topk.restype = C.c_int64
-        L.or_children.argtypes = [up, C.c_int64, up]
-        L.or_solve_event.argtypes = [C.POINTER(OrGrid), C.POINTER(OrWires), C.c_int32, ip, dp,
-                                     ip, dp, dp, ip, up, ip, up, ip]
-        L.or_solve_event.restype = C.c_int
-        L.or_solve_event_multi.argtypes = [C.POINTER(OrGrid), C.POINTER(OrWires), C.c_int32, ip, dp,
-                                           ip, C.c_int32, C.c_int32, C.c_double, dp, dp, ip, ip, ip]
-        L.or_solve_event_multi.restype = C.c_int
-        L.or_atan_iv.argtypes = [C.c_double, C.c_double, C.c_int, dp]
-        L.or_sincos_iv.argtypes = [C.c_double, C.c_double, C.c_int, dp]
-        L.or_op_counts.argtypes = [dp, dp, C.c_int, C.POINTER(C.c_ulonglong)]
-        L.or_num_threads.restype = C.c_int
-        L.or4_vote_pair.argtypes = [dp, C.c_int32, dp, dp, C.c_double, C.c_double, C.c_int32, dp]
-        L.or4_vote_pair.restype = C.c_int
-        L.or4_vote_grid.argtypes = [C.POINTER(Or4Opts), C.POINTER(Or4Grid), dp, C.POINTER(OrWires),
-                                    C.c_int32, ip, dp, C.POINTER(C.c_uint8), ip]
-        L.or4_estimate.argtypes = [C.POINTER(Or4Grid), ip, C.POINTER(Or4Iter)]
-        L.or4_disk.argtypes = [dp, C.c_double, C.c_int32]
-        L.or4_disk.restype = C.c_int
-        L.or4_solve_event.argtypes = [C.POINTER(Or4Opts), C.POINTER(OrWires), C.c_int32, ip, dp,
-                                      C.POINTER(Or4Iter), C.POINTER(C.c_uint8)]
-        L.or_set_num_threads.argtypes = [C.c_int]
-        _lib = L
+        _lib = load(_build.build())
     return _lib
+
+
+def load(path):
+    """Loads a build of the oracle (liboracle.so or a reference variant) with its
+    signatures."""
+    L = C.CDLL(path)
+    dp, ip, up = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_uint64)
+    L.or_vote_pair.argtypes = [dp, dp, C.c_int, dp]
+    L.or_vote_pair.restype = C.c_int
+    L.or_vote_pair_mid.argtypes = [dp, dp, dp, dp]
+    L.or_vote_pair_mid.restype = C.c_int
+    L.or_vote_cells.argtypes = [C.POINTER(OrGrid), C.POINTER(OrWires), C.c_int32, ip, dp,
+                                C.c_int32, C.c_int32, up, C.c_int64, ip]
+    L.or_vote_cells.restype = None
+    L.or_coarse_keys.argtypes = [C.POINTER(OrGrid), up]
+    L.or_topk.argtypes = [up, ip, C.c_int64, C.c_int32, up, ip]
+    L.or_topk.restype = C.c_int64
+    L.or_children.argtypes = [up, C.c_int64, up]
+    L.or_solve_event.argtypes = [C.POINTER(OrGrid), C.POINTER(OrWires), C.c_int32, ip, dp,
+                                 ip, dp, dp, ip, up, ip, up, ip]
+    L.or_solve_event.restype = C.c_int
+    L.or_solve_event_multi.argtypes = [C.POINTER(OrGrid), C.POINTER(OrWires), C.c_int32, ip, dp,
+                                       ip, C.c_int32, C.c_int32, C.c_double, dp, dp, ip, ip, ip]
+    L.or_solve_event_multi.restype = C.c_int
+    L.or_mask_hits.argtypes = [C.POINTER(OrGrid), C.POINTER(OrWires), C.c_int32, ip, dp,
+                               C.POINTER(C.c_uint8), C.c_int32, up, C.c_int64, C.c_double,
+                               C.POINTER(C.c_uint8)]
+    L.or_atan_iv.argtypes = [C.c_double, C.c_double, C.c_int, dp]
+    L.or_sincos_iv.argtypes = [C.c_double, C.c_double, C.c_int, dp]
+    L.or_op_counts.argtypes = [dp, dp, C.c_int, C.POINTER(C.c_ulonglong)]
+    L.or_num_threads.restype = C.c_int
+    L.or4_vote_pair.argtypes = [dp, C.c_int32, dp, dp, C.c_double, C.c_double, C.c_int32, dp]
+    L.or4_vote_pair.restype = C.c_int
+    L.or4_vote_grid.argtypes = [C.POINTER(Or4Opts), C.POINTER(Or4Grid), dp, C.POINTER(OrWires),
+                                C.c_int32, ip, dp, C.POINTER(C.c_uint8), ip]
+    L.or4_estimate.argtypes = [C.POINTER(Or4Grid), ip, C.POINTER(Or4Iter)]
+    L.or4_disk.argtypes = [dp, C.c_double, C.c_int32]
+    L.or4_disk.restype = C.c_int
+    L.or4_solve_event.argtypes = [C.POINTER(Or4Opts), C.POINTER(OrWires), C.c_int32, ip, dp,
+                                  C.POINTER(Or4Iter), C.POINTER(C.c_uint8)]
+    L.or_set_num_threads.argtypes = [C.c_int]
+    return L
 
 
 def _p(a, ct):
@@ -194,12 +202,15 @@ def scm2(grid, level: int, idx5) -> np.ndarray:
     return np.array(grid.sincos_mid[grid.sincos_offset[level] + idx5[1]], np.float64)
 
 
-def vote_cells(tab: Tables, wire_id, drift, level: int, keys, prec: int = 0) -> np.ndarray:
+def vote_cells(tab: Tables, wire_id, drift, level: int, keys, prec: int = 0,
+               L=None) -> np.ndarray:
+    """Votes of cells (keys at `level`) for one event's hits; L: another build of the
+    oracle (default: liboracle.so)."""
     wid = np.ascontiguousarray(wire_id, np.int32)
     dr = np.ascontiguousarray(drift, np.float64)
     k = np.ascontiguousarray(keys, np.uint64)
     out = np.zeros(k.shape[0], np.int32)
-    lib().or_vote_cells(C.byref(tab.cg), C.byref(tab.cw), int(wid.shape[0]), _p(wid, C.c_int32),
+    (L or lib()).or_vote_cells(C.byref(tab.cg), C.byref(tab.cw), int(wid.shape[0]), _p(wid, C.c_int32),
                         _p(dr, C.c_double), int(level), int(prec), _p(k, C.c_uint64),
                         int(k.shape[0]), _p(out, C.c_int32))
     return out
@@ -281,6 +292,20 @@ def solve_event_multi(tab: Tables, wire_id, drift, max_tracks: int, min_votes: i
     k = int(nf[0])
     return dict(n_tracks=k, p=p.reshape(max_tracks, 5)[:k], w=werr.reshape(max_tracks, 5)[:k],
                 votes=votes[:k], hit_track=ht[:n])
+
+
+def mask_hits(tab: Tables, wire_id, drift, level: int, keys, width: float, active=None) -> np.ndarray:
+    """Hit finding on a set of cells (see or_mask_hits): bool per hit, taken by a cell."""
+    wid = np.ascontiguousarray(wire_id, np.int32)
+    dr = np.ascontiguousarray(drift, np.float64)
+    k = np.ascontiguousarray(keys, np.uint64)
+    n = wid.shape[0]
+    act = None if active is None else np.ascontiguousarray(active, np.uint8)
+    out = np.zeros(max(n, 1), np.uint8)
+    lib().or_mask_hits(C.byref(tab.cg), C.byref(tab.cw), int(n), _p(wid, C.c_int32),
+                       _p(dr, C.c_double), None if act is None else _p(act, C.c_uint8), int(level),
+                       _p(k, C.c_uint64), int(k.shape[0]), float(width), _p(out, C.c_uint8))
+    return out[:n].astype(bool)
 
 
 # ---------------------------------------------------------------------------------------- #

@@ -113,7 +113,7 @@ __device__ __forceinline__ Ctr4<T> centre4(T xc, T yc, T R, T p_gev, T b_t, T xr
 }
 
 // z0- and sign-free point quantities of one (voxel centre, hit).
-template <typename T> struct Pre4 { bool guard; T R, RA, iRA, hiA2, sA, cA, sPA, cPA, cos2, sin2, psi, Rpsi; };
+template <typename T> struct Pre4 { bool guard; T R, RA, A2, sA, cA, sPA, cPA, cos2, sin2, psi, Rpsi; };
 
 // Hit constants as point values of T: x0, y0, sin phi_s, cos phi_s, tan tau,
 // sin phi_s tan tau, cos phi_s tan tau, tan^2 tau, d.
@@ -128,19 +128,16 @@ __device__ __forceinline__ Pre4<T> prefix4(const Ctr4<T> &m, T z0, const HitP<T>
     p.R = m.R;
     const T xw = add(h.x0, mul(z0, h.spt)), yw = sub(h.y0, mul(z0, h.cpt));   // EQSinter_d,e
     const T dx = sub(xw, m.xc), dy = sub(yw, m.yc);
-    p.RA = sqrt(add(mul(dx, dx), mul(dy, dy)));
+    p.A2 = add(mul(dx, dx), mul(dy, dy));
+    p.RA = sqrt(p.A2);
     if (!(p.RA > T(0)) || m.guard) { p.guard = true; return p; }
-    // 1 / R^Ax and 1 / (2 (R^Ax)^2): the divisions by R^Ax are products with these
-    p.iRA = div(T(1), p.RA);
-    const T iA2 = mul(p.iRA, p.iRA);
-    p.hiA2 = mul(T(0.5), iA2);
     // c^Ax, s^Ax of Eq. defEQApo1
     p.cA = sub(mul(dx, h.sph), mul(dy, h.cph));
     p.sA = add(mul(dx, h.cph), mul(dy, h.sph));
-    p.sPA = mul(p.sA, p.iRA);
-    p.cPA = mul(p.cA, p.iRA);
-    p.cos2 = mul(sub(mul(p.cA, p.cA), mul(p.sA, p.sA)), iA2);
-    p.sin2 = mul(mul(mul(T(2), p.sA), p.cA), iA2);
+    p.sPA = div(p.sA, p.RA);
+    p.cPA = div(p.cA, p.RA);
+    p.cos2 = div(sub(mul(p.cA, p.cA), mul(p.sA, p.sA)), p.A2);
+    p.sin2 = div(mul(mul(T(2), p.sA), p.cA), p.A2);
     // psi: the wire point's phase minus the reference point's
     bool bad = false;
     const T ph = phase4<T>(m.ox, m.oy, m.on, dx, dy, p.RA, bad);
@@ -160,11 +157,11 @@ __device__ __forceinline__ int dax4(const Pre4<T> &p, T L, const HitP<T> &h, T d
 #pragma unroll
     for (int sg = 0; sg < 2; sg++) {
         const T ds = sg == 0 ? h.d : -h.d;
-        const T Phi1 = -mul(add(mul(zA, p.sPA), mul(mul(L, ds), p.cPA)), p.iRA);   // ApproxPhi_b
-        const T Phi2 = mul(add(sub(mul(mul(L, R), zA), mul(mul(mul(L, zA), sub(R, mul(T(2), ds))), p.cos2)),
+        const T Phi1 = div(-add(mul(zA, p.sPA), mul(mul(L, ds), p.cPA)), RA);      // ApproxPhi_b
+        const T Phi2 = div(add(sub(mul(mul(L, R), zA), mul(mul(mul(L, zA), sub(R, mul(T(2), ds))), p.cos2)),
                                mul(add(mul(zA, zA), mul(ds, add(RA, mul(mul(L, L), sub(add(R, RA), ds))))),
                                    p.sin2)),
-                           p.hiA2);                                                 // ApproxPhi_c
+                           mul(T(2), p.A2));                                        // ApproxPhi_c
         const T dl = add(mul(Phi1, t), mul(Phi2, t2));                             // ApproxPhi_a
         T sd, cd;
         p4::sincos(dl, sd, cd);
