@@ -28,7 +28,20 @@ import numpy as np
 
 AXES = ("d0", "phi0", "omega", "z0", "tanl")
 N_AXES = 5
-KEY_BITS = 10            # bits per axis in a cell key (idx < 1024)
+KEY_BITS = 10            # minimum bits per axis in a cell key
+
+
+def key_bits_for(bins, levels: int) -> list:
+    """Bits of each axis in a cell key: max(10, ceil(log2(bins[a] << levels))); axis a
+    starts at bit sum(bits[:a]), d0 lowest (so a grid whose finest level has at most 1024
+    cells per axis uses 10 bits per axis)."""
+    out = []
+    for b in bins:
+        n, bits = int(b) << int(levels), KEY_BITS
+        while (1 << bits) < n:
+            bits += 1
+        out.append(bits)
+    return out
 
 
 @dataclass
@@ -54,6 +67,9 @@ class Grid:
 
     def n_coarse(self) -> int:
         return int(np.prod(self.bins.astype(np.int64)))
+
+    def key_bits(self) -> list:
+        return key_bits_for(self.bins, self.levels)
 
 
 def _uniform_edges(lo: float, hi: float, n: int):
@@ -104,7 +120,7 @@ def make_grid(bins, levels: int, topk: int,
               z0=(-0.10, 0.10), tanl=(-0.8, 0.8)) -> Grid:
     bins = np.asarray(bins, np.int32)
     assert bins.shape == (5,) and bins[2] % 2 == 0, "omega bins are split evenly per sign"
-    assert all(int(b) << levels <= (1 << KEY_BITS) for b in bins)
+    assert sum(key_bits_for(bins, levels)) <= 64 and all(int(b) << levels <= 1 << 16 for b in bins)
     lo_e, hi_e = [], []
     for a, rng in enumerate((d0, phi0, None, z0, tanl)):
         n = int(bins[a]) << levels
@@ -146,20 +162,27 @@ def make_grid(bins, levels: int, topk: int,
     return g
 
 
-def cell_key(idx5) -> np.ndarray:
-    """Packed uint64 key sum_a idx_a << (10 a); idx5 has shape (..., 5)."""
+def _layout(grid):
+    bits = [KEY_BITS] * N_AXES if grid is None else grid.key_bits()
+    return bits, [int(sum(bits[:a])) for a in range(N_AXES)]
+
+
+def cell_key(idx5, grid: Grid | None = None) -> np.ndarray:
+    """Packed uint64 key sum_a idx_a << s_a (s_a from key_bits_for; 10 a without a grid);
+    idx5 has shape (..., 5)."""
+    bits, sh = _layout(grid)
     idx5 = np.asarray(idx5, np.uint64)
     k = np.zeros(idx5.shape[:-1], np.uint64)
     for a in range(N_AXES):
-        k |= idx5[..., a] << np.uint64(KEY_BITS * a)
+        k |= idx5[..., a] << np.uint64(sh[a])
     return k
 
 
-def key_indices(keys) -> np.ndarray:
+def key_indices(keys, grid: Grid | None = None) -> np.ndarray:
+    bits, sh = _layout(grid)
     keys = np.asarray(keys, np.uint64)
-    m = np.uint64((1 << KEY_BITS) - 1)
-    return np.stack([(keys >> np.uint64(KEY_BITS * a)) & m for a in range(N_AXES)],
-                    axis=-1).astype(np.int64)
+    return np.stack([(keys >> np.uint64(sh[a])) & np.uint64((1 << bits[a]) - 1)
+                     for a in range(N_AXES)], axis=-1).astype(np.int64)
 
 
 def coarse_index_to_idx5(lin, bins) -> np.ndarray:

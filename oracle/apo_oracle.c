@@ -95,28 +95,35 @@ static void hit_constants(const or_wires *w, int32_t wid, double drift, double h
 static float rd32(double x) { volatile float r = (float)x; return r; }   /* FE_DOWNWARD */
 static float ru32(double x) { volatile float r = (float)(-x); return -r; }
 
+/* Flag bit of a precision code: apply the direction condition of the vote program (the
+ * hit lies on the outgoing arc, downstream of the POCA). */
+#define OR_OUTGOING 16
+/* vote-count bins of the max-set schedule's histogram (counts are at most the hit cap) */
+#define APO_OR_HIST 257
+
 /* The vote of one (cell, hit) pair.  prec 0: FP64 intervals, 1: FP32 intervals, 4: FP64
- * intervals with the exact phase (exactphi.inc). */
-static int vote_pair(const double c[12], const double h[9], int prec, double *out) {
+ * intervals with the exact phase (exactphi.inc); optionally | OR_OUTGOING. */
+static int vote_pair(const double c[12], const double h[9], int prec_code, double *out) {
+    const int og = (prec_code & OR_OUTGOING) != 0, prec = prec_code & ~OR_OUTGOING;
     if (prec == 4) {
         iv_d C[6], H[9];
         for (int i = 0; i < 6; i++) C[i] = mk_d(c[2 * i], c[2 * i + 1]);
         for (int i = 0; i < 9; i++) H[i] = mk_d(h[i], h[i]);
         return exact_vote_program_d(C[0], C[1], C[2], C[3], C[4], C[5], H[0], H[1], H[2], H[3],
-                                    H[4], H[5], H[6], H[7], H[8], out);
+                                    H[4], H[5], H[6], H[7], H[8], og, out);
     }
     if (prec == 0) {
         iv_d C[6], H[9];
         for (int i = 0; i < 6; i++) C[i] = mk_d(c[2 * i], c[2 * i + 1]);
         for (int i = 0; i < 9; i++) H[i] = mk_d(h[i], h[i]);
         return vote_program_d(C[0], C[1], C[2], C[3], C[4], C[5], H[0], H[1], H[2], H[3],
-                              H[4], H[5], H[6], H[7], H[8], out);
+                              H[4], H[5], H[6], H[7], H[8], og, out);
     } else {
         iv_f C[6], H[9];
         for (int i = 0; i < 6; i++) C[i] = mk_f(rd32(c[2 * i]), ru32(c[2 * i + 1]));
         for (int i = 0; i < 9; i++) H[i] = mk_f(rd32(h[i]), ru32(h[i]));
         return vote_program_f(C[0], C[1], C[2], C[3], C[4], C[5], H[0], H[1], H[2], H[3],
-                              H[4], H[5], H[6], H[7], H[8], out);
+                              H[4], H[5], H[6], H[7], H[8], og, out);
     }
 }
 
@@ -144,12 +151,33 @@ int or_vote_pair_mid(const double cell[12], const double scm[2], const double hi
 /* ------------------------------------------------------------------------------------ */
 /* Cell keys                                                                             */
 /* ------------------------------------------------------------------------------------ */
-static void key_to_idx(uint64_t key, int32_t idx[5]) {
-    for (int a = 0; a < 5; a++) idx[a] = (int32_t)((key >> (10 * a)) & 1023u);
+/* Key layout: idx_a occupies bits_a = max(10, ceil(log2(bins_a << levels))) bits starting
+ * at s_a = bits_0 + ... + bits_(a-1), d0 lowest; g = NULL means 10 bits per axis. */
+static void key_layout(const or_grid *g, int sh[5], uint64_t mk[5]) {
+    int s = 0;
+    for (int a = 0; a < 5; a++) {
+        int bits = 10;
+        if (g) {
+            int64_t n = (int64_t)g->bins[a] << g->levels;
+            while (((int64_t)1 << bits) < n) bits++;
+        }
+        sh[a] = s;
+        mk[a] = ((uint64_t)1 << bits) - 1;
+        s += bits;
+    }
 }
-static uint64_t idx_to_key(const int32_t idx[5]) {
+static void key_to_idx(const or_grid *g, uint64_t key, int32_t idx[5]) {
+    int sh[5];
+    uint64_t mk[5];
+    key_layout(g, sh, mk);
+    for (int a = 0; a < 5; a++) idx[a] = (int32_t)((key >> sh[a]) & mk[a]);
+}
+static uint64_t idx_to_key(const or_grid *g, const int32_t idx[5]) {
+    int sh[5];
+    uint64_t mk[5];
+    key_layout(g, sh, mk);
     uint64_t k = 0;
-    for (int a = 0; a < 5; a++) k |= (uint64_t)idx[a] << (10 * a);
+    for (int a = 0; a < 5; a++) k |= (uint64_t)idx[a] << sh[a];
     return k;
 }
 
@@ -163,7 +191,7 @@ static void centre_sincos(const or_grid *g, int level, const int32_t idx[5], dou
 /* votes of n cells of `level` (given by key) for one event's hits: Eq. (ApoVote) summed
  * over hits, one vote per (cell, hit) whichever drift sign passes (Section 3.1).
  * prec 0: FP64 intervals, 1: FP32 intervals, 3: the FP64 midpoint form, 4: FP64 intervals
- * with the exact phase. */
+ * with the exact phase; | OR_OUTGOING (not with 3) adds the direction condition. */
 void or_vote_cells(const or_grid *g, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
                    const double *drift, int32_t level, int32_t prec, const uint64_t *keys,
                    int64_t n, int32_t *votes) {
@@ -171,18 +199,19 @@ void or_vote_cells(const or_grid *g, const or_wires *w, int32_t n_hits, const in
     {
         int old = fegetround();
         fesetround(FE_DOWNWARD);
+        const int base = prec & ~OR_OUTGOING;   /* the midpoint form takes no direction flag */
         #pragma omp for schedule(dynamic, 256)
         for (int64_t j = 0; j < n; j++) {
             int32_t idx[5];
             double c[12], h[9];
             double scm[2] = {0, 0};
-            key_to_idx(keys[j], idx);
+            key_to_idx(g, keys[j], idx);
             cell_intervals(g, level, idx, c);
-            if (prec == 3) centre_sincos(g, level, idx, scm);
+            if (base == 3) centre_sincos(g, level, idx, scm);
             int32_t v = 0;
             for (int32_t i = 0; i < n_hits; i++) {
                 hit_constants(w, wire_id[i], drift[i], h);
-                v += prec == 3 ? mid_vote_program(c, scm, h, NULL) : vote_pair(c, h, prec, NULL);
+                v += base == 3 ? mid_vote_program(c, scm, h, NULL) : vote_pair(c, h, prec, NULL);
             }
             votes[j] = v;
         }
@@ -198,7 +227,7 @@ static void coarse_keys(const or_grid *g, uint64_t *keys) {
         int64_t r = j;
         int32_t idx[5];
         for (int a = 0; a < 5; a++) { idx[a] = (int32_t)(r % g->bins[a]); r /= g->bins[a]; }
-        keys[j] = idx_to_key(idx);
+        keys[j] = idx_to_key(g, idx);
     }
 }
 
@@ -230,13 +259,13 @@ int64_t or_topk(const uint64_t *keys, const int32_t *votes, int64_t n, int32_t K
 }
 
 /* each cell -> its 32 children (index 2 idx_a + bit_a, bit_a = bit a of the child number) */
-void or_children(const uint64_t *keys, int64_t n, uint64_t *children) {
+void or_children(const or_grid *g, const uint64_t *keys, int64_t n, uint64_t *children) {
     for (int64_t j = 0; j < n; j++) {
         int32_t idx[5], c[5];
-        key_to_idx(keys[j], idx);
+        key_to_idx(g, keys[j], idx);
         for (int b = 0; b < 32; b++) {
             for (int a = 0; a < 5; a++) c[a] = 2 * idx[a] + ((b >> a) & 1);
-            children[32 * j + b] = idx_to_key(c);
+            children[32 * j + b] = idx_to_key(g, c);
         }
     }
 }
@@ -259,7 +288,7 @@ static void estimate(const or_grid *g, int level, const uint64_t *keys, const in
         double sum = 0, lo_min = INFINITY, hi_max = -INFINITY;
         for (int64_t j = 0; j < m; j++) {
             int32_t idx[5];
-            key_to_idx(a[j].key, idx);
+            key_to_idx(g, a[j].key, idx);
             double lo = g->lo_edge[ax][(int64_t)idx[ax] << sh];
             double hi = g->hi_edge[ax][(((int64_t)idx[ax] + 1) << sh) - 1];
             sum += (lo + hi) / 2;
@@ -297,7 +326,7 @@ int or_solve_event(const or_grid *g, const or_wires *w, int32_t n_hits, const in
     int64_t m = or_topk(keys, votes, n0, K, fk, fv);
     if (trace_keys) { memcpy(trace_keys, fk, sizeof(uint64_t) * (size_t)m); memcpy(trace_votes, fv, sizeof(int32_t) * (size_t)m); }
     for (int L = 1; L <= g->levels; L++) {
-        or_children(fk, m, ck);
+        or_children(g, fk, m, ck);
         or_vote_cells(g, w, n_hits, wire_id, drift, L, prec[L], ck, m * 32, cv);
         if (L == g->levels) {
             estimate(g, L, ck, cv, m * 32, p, werr, best_votes);
@@ -315,15 +344,131 @@ int or_solve_event(const or_grid *g, const or_wires *w, int32_t n_hits, const in
     return 0;
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Max-set schedule                                                                       */
+/* ------------------------------------------------------------------------------------ */
+static int kv_key_cmp(const void *pa, const void *pb) {
+    uint64_t a = ((const kv *)pa)->key, b = ((const kv *)pb)->key;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+/* Estimate of Section 3.3 over the cells of `level` whose votes equal vmax (m of them):
+ * per axis, with n_i of them at index i and centre c_i = (lo_i + hi_i) / 2, the value is
+ * (sum over i ascending of n_i c_i) / m and the error (max hi - min lo) / 2, all in
+ * round-to-nearest.  (The mean of the cells' centres, summed by index, so the result does
+ * not depend on the order the cells come in.) */
+static void estimate_groups(const or_grid *g, int level, const uint64_t *keys, const int32_t *votes,
+                            int64_t n, int32_t vmax, double p[5], double werr[5], int64_t *m_out) {
+    int sh = g->levels - level;
+    int64_t m = 0;
+    for (int64_t j = 0; j < n; j++) m += votes[j] == vmax;
+    for (int ax = 0; ax < 5; ax++) {
+        int64_t nb = (int64_t)g->bins[ax] << level;
+        int64_t *cnt = (int64_t *)calloc((size_t)nb, sizeof(int64_t));
+        for (int64_t j = 0; j < n; j++) {
+            if (votes[j] != vmax) continue;
+            int32_t idx[5];
+            key_to_idx(g, keys[j], idx);
+            cnt[idx[ax]]++;
+        }
+        double sum = 0, lo_min = INFINITY, hi_max = -INFINITY;
+        for (int64_t i = 0; i < nb; i++) {
+            if (!cnt[i]) continue;
+            double lo = g->lo_edge[ax][i << sh];
+            double hi = g->hi_edge[ax][((i + 1) << sh) - 1];
+            sum += (double)cnt[i] * ((lo + hi) / 2);
+            if (lo < lo_min) lo_min = lo;
+            if (hi > hi_max) hi_max = hi;
+        }
+        p[ax] = m ? sum / (double)m : 0.0;
+        werr[ax] = m ? (hi_max - lo_min) / 2 : 0.0;
+        free(cnt);
+    }
+    *m_out = m;
+}
+
+/* Coarse-to-fine search that keeps whole vote groups (Section 3.3: the result is the set
+ * of maximum-vote voxels).  At each level every cell is voted; with vmax the best count,
+ * the kept set is {votes >= T} for the smallest T >= max(vmax - slack, min(vmax, 1)) with
+ * at most max_keep cells.  If even the vmax group exceeds max_keep, or at the last level,
+ * the search ends there and the estimate is taken over that level's vmax group.  Kept cells
+ * are bisected along every axis.  prec[L]: as or_vote_cells (with or without
+ * OR_OUTGOING).  Outputs: p, werr, *best_votes = vmax, *final_level, *n_final = the size of
+ * the final vmax group; trace (may be NULL): per level L <= final level, trace_count[L]
+ * cells kept (0 at the final level) and their keys / votes in ascending key order at
+ * trace_keys / trace_votes + L * max_keep. */
+int or_solve_event_maxset(const or_grid *g, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
+                          const double *drift, const int32_t *prec, int32_t max_keep, int32_t slack,
+                          double p[5], double werr[5], int32_t *best_votes, int32_t *final_level,
+                          int64_t *n_final, int32_t *trace_count, uint64_t *trace_keys,
+                          int32_t *trace_votes) {
+    int64_t n = 1;
+    for (int a = 0; a < 5; a++) n *= g->bins[a];
+    uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    int32_t *votes = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    coarse_keys(g, keys);
+    or_vote_cells(g, w, n_hits, wire_id, drift, 0, prec[0], keys, n, votes);
+    if (trace_count) for (int L = 0; L <= g->levels; L++) trace_count[L] = 0;
+    for (int L = 0;; L++) {
+        int32_t vmax = 0;
+        for (int64_t j = 0; j < n; j++) if (votes[j] > vmax) vmax = votes[j];
+        int64_t cnt[APO_OR_HIST];
+        memset(cnt, 0, sizeof(cnt));
+        for (int64_t j = 0; j < n; j++) {
+            int32_t v = votes[j] < 0 ? 0 : (votes[j] >= APO_OR_HIST ? APO_OR_HIST - 1 : votes[j]);
+            cnt[v]++;
+        }
+        if (L == g->levels || cnt[vmax] > max_keep) {
+            estimate_groups(g, L, keys, votes, n, vmax, p, werr, n_final);
+            *best_votes = vmax;
+            *final_level = L;
+            break;
+        }
+        int32_t lb = vmax - slack;
+        int32_t floor1 = vmax < 1 ? vmax : 1;
+        if (lb < floor1) lb = floor1;
+        int32_t T = vmax;
+        int64_t kept = cnt[vmax];
+        while (T - 1 >= lb && kept + cnt[T - 1] <= max_keep) { T--; kept += cnt[T]; }
+        kv *kk = (kv *)malloc(sizeof(kv) * (size_t)(kept > 0 ? kept : 1));
+        int64_t m = 0;
+        for (int64_t j = 0; j < n; j++)
+            if (votes[j] >= T) { kk[m].key = keys[j]; kk[m].votes = votes[j]; m++; }
+        qsort(kk, (size_t)m, sizeof(kv), kv_key_cmp);
+        uint64_t *fk = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(m > 0 ? m : 1));
+        for (int64_t q = 0; q < m; q++) fk[q] = kk[q].key;
+        if (trace_count) {
+            trace_count[L] = (int32_t)m;
+            for (int64_t q = 0; q < m; q++) {
+                trace_keys[(size_t)L * max_keep + q] = kk[q].key;
+                trace_votes[(size_t)L * max_keep + q] = kk[q].votes;
+            }
+        }
+        free(kk);
+        free(keys);
+        free(votes);
+        n = m * 32;
+        keys = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+        votes = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+        or_children(g, fk, m, keys);
+        free(fk);
+        or_vote_cells(g, w, n_hits, wire_id, drift, L + 1, prec[L + 1], keys, n, votes);
+    }
+    free(keys);
+    free(votes);
+    return 0;
+}
+
 /* The vote of one (cell, hit) pair with the drift widened to the interval [d_lo, d_hi]
  * (FP64): used to find the hits of a found track. */
-static int vote_pair_drift_iv(const double c[12], const double h[9], double d_lo, double d_hi) {
+static int vote_pair_drift_iv(const double c[12], const double h[9], double d_lo, double d_hi,
+                              int outgoing) {
     iv_d C[6], H[9];
     for (int i = 0; i < 6; i++) C[i] = mk_d(c[2 * i], c[2 * i + 1]);
     for (int i = 0; i < 8; i++) H[i] = mk_d(h[i], h[i]);
     H[8] = mk_d(d_lo, d_hi);
     return vote_program_d(C[0], C[1], C[2], C[3], C[4], C[5], H[0], H[1], H[2], H[3], H[4],
-                          H[5], H[6], H[7], H[8], NULL);
+                          H[5], H[6], H[7], H[8], outgoing, NULL);
 }
 
 /* Hit finding of Section 3.3 on a set of cells (the final maximum-vote cells of a found
@@ -333,11 +478,11 @@ static int vote_pair_drift_iv(const double c[12], const double h[9], double d_lo
  * for taken hits, otherwise left unchanged.  Must run under FE_DOWNWARD. */
 static void mask_hits(const or_grid *g, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
                       const double *drift, const uint8_t *active, int32_t level,
-                      const uint64_t *keys, int64_t n, double width, uint8_t *taken) {
+                      const uint64_t *keys, int64_t n, double width, int outgoing, uint8_t *taken) {
     for (int64_t j = 0; j < n; j++) {
         int32_t idx[5];
         double c[12], h[9];
-        key_to_idx(keys[j], idx);
+        key_to_idx(g, keys[j], idx);
         cell_intervals(g, level, idx, c);
         for (int32_t i = 0; i < n_hits; i++) {
             if ((active && !active[i]) || taken[i]) continue;
@@ -345,17 +490,17 @@ static void mask_hits(const or_grid *g, const or_wires *w, int32_t n_hits, const
             volatile double lo = drift[i] - width;              /* rounded down */
             volatile double hi = -((-drift[i]) - width);        /* rounded up */
             double dlo = lo > 0 ? lo : 0.0;
-            if (vote_pair_drift_iv(c, h, dlo, hi)) taken[i] = 1;
+            if (vote_pair_drift_iv(c, h, dlo, hi, outgoing)) taken[i] = 1;
         }
     }
 }
 
 void or_mask_hits(const or_grid *g, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
                   const double *drift, const uint8_t *active, int32_t level, const uint64_t *keys,
-                  int64_t n, double width, uint8_t *taken) {
+                  int64_t n, double width, int outgoing, uint8_t *taken) {
     int old = fegetround();
     fesetround(FE_DOWNWARD);
-    mask_hits(g, w, n_hits, wire_id, drift, active, level, keys, n, width, taken);
+    mask_hits(g, w, n_hits, wire_id, drift, active, level, keys, n, width, outgoing, taken);
     fesetround(old);
 }
 
@@ -400,7 +545,8 @@ int or_solve_event_multi(const or_grid *g, const or_wires *w, int32_t n_hits, co
         for (int32_t i = 0; i < n_hits; i++) { act[i] = hit_track[i] < 0; tk[i] = 0; }
         int old = fegetround();
         fesetround(FE_DOWNWARD);
-        mask_hits(g, w, n_hits, wire_id, drift, act, g->levels, mk, nmax, width, tk);
+        mask_hits(g, w, n_hits, wire_id, drift, act, g->levels, mk, nmax, width,
+                  (prec[g->levels] & OR_OUTGOING) != 0, tk);
         fesetround(old);
         for (int32_t i = 0; i < n_hits; i++) if (tk[i]) hit_track[i] = t;
     }

@@ -12,6 +12,7 @@ import numpy as np
 from . import build as _build
 
 _lib = None
+OUTGOING = 16   # precision flag bit: the direction condition of the vote program
 
 
 class OrWires(C.Structure):
@@ -65,7 +66,11 @@ def load(path):
     L.or_coarse_keys.argtypes = [C.POINTER(OrGrid), up]
     L.or_topk.argtypes = [up, ip, C.c_int64, C.c_int32, up, ip]
     L.or_topk.restype = C.c_int64
-    L.or_children.argtypes = [up, C.c_int64, up]
+    L.or_children.argtypes = [C.c_void_p, up, C.c_int64, up]
+    L.or_solve_event_maxset.argtypes = [C.POINTER(OrGrid), C.POINTER(OrWires), C.c_int32, ip, dp,
+                                        ip, C.c_int32, C.c_int32, dp, dp, ip, ip,
+                                        C.POINTER(C.c_int64), ip, up, ip]
+    L.or_solve_event_maxset.restype = C.c_int
     L.or_solve_event.argtypes = [C.POINTER(OrGrid), C.POINTER(OrWires), C.c_int32, ip, dp,
                                  ip, dp, dp, ip, up, ip, up, ip]
     L.or_solve_event.restype = C.c_int
@@ -74,7 +79,7 @@ def load(path):
     L.or_solve_event_multi.restype = C.c_int
     L.or_mask_hits.argtypes = [C.POINTER(OrGrid), C.POINTER(OrWires), C.c_int32, ip, dp,
                                C.POINTER(C.c_uint8), C.c_int32, up, C.c_int64, C.c_double,
-                               C.POINTER(C.c_uint8)]
+                               C.c_int, C.POINTER(C.c_uint8)]
     L.or_atan_iv.argtypes = [C.c_double, C.c_double, C.c_int, dp]
     L.or_sincos_iv.argtypes = [C.c_double, C.c_double, C.c_int, dp]
     L.or_op_counts.argtypes = [dp, dp, C.c_int, C.POINTER(C.c_ulonglong)]
@@ -236,10 +241,12 @@ def topk(keys, votes, K: int):
     return ok[:m], ov[:m]
 
 
-def children(keys) -> np.ndarray:
+def children(keys, tab: Tables | None = None) -> np.ndarray:
+    """The 32 children of each key (key layout of tab's grid; 10 bits per axis without)."""
     k = np.ascontiguousarray(keys, np.uint64)
     out = np.zeros(k.shape[0] * 32, np.uint64)
-    lib().or_children(_p(k, C.c_uint64), int(k.shape[0]), _p(out, C.c_uint64))
+    lib().or_children(None if tab is None else C.byref(tab.cg), _p(k, C.c_uint64),
+                      int(k.shape[0]), _p(out, C.c_uint64))
     return out
 
 
@@ -268,6 +275,37 @@ def solve_event(tab: Tables, wire_id, drift, prec_per_level=None):
                 trace_votes=tv.reshape(lv + 1, K), last_keys=lk, last_votes=lvv)
 
 
+def solve_event_maxset(tab: Tables, wire_id, drift, max_keep: int, slack: int = 0,
+                       prec_per_level=None, trace: bool = False):
+    """Max-set search of one event (see or_solve_event_maxset).  prec_per_level: codes as
+    vote_cells (e.g. F32 | OUTGOING).  Returns dict p, w, votes, final_level, n_final and,
+    with trace, per level the kept (keys, votes) in key order."""
+    g = tab.grid
+    lv = g.levels
+    prec = np.zeros(lv + 1, np.int32) if prec_per_level is None else \
+        np.ascontiguousarray(prec_per_level, np.int32)
+    wid = np.ascontiguousarray(wire_id, np.int32)
+    dr = np.ascontiguousarray(drift, np.float64)
+    p, werr = np.zeros(5), np.zeros(5)
+    best, fl = np.zeros(1, np.int32), np.zeros(1, np.int32)
+    nf = np.zeros(1, np.int64)
+    tc = np.zeros(lv + 1, np.int32)
+    tk = np.zeros((lv + 1) * max_keep if trace else 1, np.uint64)
+    tv = np.zeros((lv + 1) * max_keep if trace else 1, np.int32)
+    lib().or_solve_event_maxset(C.byref(tab.cg), C.byref(tab.cw), int(wid.shape[0]),
+                                _p(wid, C.c_int32), _p(dr, C.c_double), _p(prec, C.c_int32),
+                                int(max_keep), int(slack), _p(p, C.c_double),
+                                _p(werr, C.c_double), _p(best, C.c_int32), _p(fl, C.c_int32),
+                                _p(nf, C.c_int64), _p(tc, C.c_int32) if trace else None,
+                                _p(tk, C.c_uint64) if trace else None,
+                                _p(tv, C.c_int32) if trace else None)
+    r = dict(p=p, w=werr, votes=int(best[0]), final_level=int(fl[0]), n_final=int(nf[0]))
+    if trace:
+        tk, tv = tk.reshape(lv + 1, max_keep), tv.reshape(lv + 1, max_keep)
+        r["trace"] = [(tk[L, :tc[L]].copy(), tv[L, :tc[L]].copy()) for L in range(lv + 1)]
+    return r
+
+
 def solve_event_multi(tab: Tables, wire_id, drift, max_tracks: int, min_votes: int,
                       mask_sigma: float = 150e-6, prec_per_level=None):
     """Multi-track extraction of one event (see or_solve_event_multi).  Returns dict with
@@ -294,7 +332,8 @@ def solve_event_multi(tab: Tables, wire_id, drift, max_tracks: int, min_votes: i
                 votes=votes[:k], hit_track=ht[:n])
 
 
-def mask_hits(tab: Tables, wire_id, drift, level: int, keys, width: float, active=None) -> np.ndarray:
+def mask_hits(tab: Tables, wire_id, drift, level: int, keys, width: float, active=None,
+              outgoing: bool = False) -> np.ndarray:
     """Hit finding on a set of cells (see or_mask_hits): bool per hit, taken by a cell."""
     wid = np.ascontiguousarray(wire_id, np.int32)
     dr = np.ascontiguousarray(drift, np.float64)
@@ -304,7 +343,8 @@ def mask_hits(tab: Tables, wire_id, drift, level: int, keys, width: float, activ
     out = np.zeros(max(n, 1), np.uint8)
     lib().or_mask_hits(C.byref(tab.cg), C.byref(tab.cw), int(n), _p(wid, C.c_int32),
                        _p(dr, C.c_double), None if act is None else _p(act, C.c_uint8), int(level),
-                       _p(k, C.c_uint64), int(k.shape[0]), float(width), _p(out, C.c_uint8))
+                       _p(k, C.c_uint64), int(k.shape[0]), float(width), int(bool(outgoing)),
+                       _p(out, C.c_uint8))
     return out[:n].astype(bool)
 
 
