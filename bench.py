@@ -229,15 +229,143 @@ def serve_sweep(geom, ev, rates, seconds: float, batch_events: int = 64, max_slo
         lat = np.array([1e3 * (t_done[i] - t_arr[i]) for i in t_arr if i in t_done])
         t_end = max(t_done.values()) if t_done else t0
         batches, max_busy = srv.stats()
+        c50, c99, cn = srv.latency()
         srv.close()
         out.append({"offered_per_s": rate, "completed": int(lat.size), "rejected": rejected,
                     "sustained_per_s": lat.size / max(t_end - t0, 1e-9),
-                    "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
-                    "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+                    "p50_ms": c50 if cn else None, "p99_ms": c99 if cn else None,
+                    "latency_clock": "library: submit accepted -> batch seen complete",
+                    "python_p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+                    "python_p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
                     "batches": batches, "max_slots_in_flight": max_busy,
                     "sm_mhz": clk.summary().get("sm_mhz")})
     sys.setswitchinterval(switch)
     return out
+
+
+MAXSET = dict(name="1024 single-track events, 2 x 256 x 16 x 2 x 8 coarse cells (d0, phi0, "
+                   "omega, z0, tanl), max-set schedule (whole maximum-vote groups, up to "
+                   "32768 cells per level), 5 bisection levels, direction condition",
+              bins=[2, 256, 16, 2, 8], levels=5, max_keep=32768)
+
+
+def truth_recovery(g, level_of, tracks_p, tracks_w, truth) -> dict:
+    """How the final estimates relate to the generated helices: the fraction of events
+    whose estimate box (value +- error, per axis) holds the generated helix, the fraction
+    within 1 and within 3 final cells of it on every axis, and the median distance in final
+    cells per axis (d0, phi0, omega, z0, tanl).  level_of: the level whose cells are the
+    "final cells" of each event."""
+    cw = np.stack([[g.hi_edge[a][0] - g.lo_edge[a][0] for a in range(5)]])   # finest cell
+    cw = cw * (2.0 ** (g.levels - np.asarray(level_of, np.float64)))[:, None]
+    dist = np.abs(tracks_p - truth) / cw
+    inside = np.all(np.abs(tracks_p - truth) <= tracks_w * (1 + 1e-12), axis=1)
+    return {"in_estimate_box": float(inside.mean()),
+            "within_1_final_cell": float(np.mean(np.all(dist <= 1.0, axis=1))),
+            "within_3_final_cells": float(np.mean(np.all(dist <= 3.0, axis=1))),
+            "median_final_cells": [float(x) for x in np.median(dist, axis=0)],
+            "events": int(len(inside))}
+
+
+def maxset_leg(w, ev, steps: int, flush, world: int = 1, per_event: int = 32) -> dict:
+    """The max-set schedule on the anisotropic grid: events/s of the FP32-bulk form (FP32
+    levels 0-3, FP64 levels 4-5) and of the plain FP64 form (every level FP64), both with
+    the direction condition; (cell, hit) pairs evaluated per second; the truth recovery of
+    each; and the plain FP64 form one event per call (the per-event path: latency and
+    events/s)."""
+    import torch
+    from gen import grid as G
+    from paper_2401_04576_gb300 import apo
+    g = G.make_grid(MAXSET["bins"], MAXSET["levels"], 64)
+    geom = apo.Geometry(g, w)
+    hits = apo.DeviceHits.from_events(ev)
+    lv, K, ne = g.levels, MAXSET["max_keep"], ev.n_events
+    nh = np.diff(ev.offsets).astype(np.float64)
+    truth = np.array([t[0].params for t in ev.tracks])
+    stream = torch.cuda.current_stream()
+    out = {"workload": MAXSET["name"], "n_events": ne, "coarse_cells": geom.n_coarse,
+           "levels": lv, "max_keep": K}
+    forms = {"fp32_bulk": [apo.F32 | apo.OUTGOING] * 4 + [apo.F64 | apo.OUTGOING] * 2,
+             "fp64": [apo.F64 | apo.OUTGOING] * (lv + 1)}
+    for name, prec in forms.items():
+        fl = torch.zeros(ne, dtype=torch.int32, device="cuda")
+        tc = torch.zeros(ne * (lv + 1), dtype=torch.int32, device="cuda")
+        o = apo.solve_opts(precision=prec, schedule=apo.SCHED_MAXSET, max_keep=K,
+                           final_level=fl, trace_count=tc)
+        ws = geom.workspace(ne, opts=o)
+        tracks = torch.zeros(ne * apo.TRACK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        ntr = torch.zeros(ne, dtype=torch.int32, device="cuda")
+        apo.solve_batch(geom, hits, o, tracks=tracks, n_tracks=ntr, workspace=ws, stream=stream)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            apo.solve_batch(geom, hits, o, tracks=tracks, n_tracks=ntr, workspace=ws, stream=stream)
+            s1.record(stream)
+            s1.synchronize()
+            ms.append(s0.elapsed_time(s1))
+        t = reduce_max(statistics.mean(ms), world)
+        tr = apo.tracks_to_numpy(tracks, ne)[:, 0]
+        flv = fl.cpu().numpy()
+        kept = tc.cpu().numpy().reshape(ne, lv + 1).astype(np.float64)
+        # cells voted per event: the level-0 grid, then 32 children of every kept cell
+        cells = geom.n_coarse + 32.0 * kept.sum(axis=1)
+        pairs = float(np.sum(cells * nh))
+        out[name] = {"precision": ("FP32 levels 0-3, FP64 levels 4-5" if name == "fp32_bulk"
+                                   else "FP64 at every level") + ", direction condition",
+                     "ms_per_step": t, "events_per_s": ne * world / (t * 1e-3),
+                     "pairs_evaluated_per_s": pairs * world / (t * 1e-3),
+                     "cells_per_event_mean": float(cells.mean()),
+                     "kept_cells_per_level_max": [int(x) for x in kept.max(axis=0)],
+                     "events_ending_early": int(np.sum(flv < lv)),
+                     "truth_recovery": truth_recovery(g, flv, tr["p"], tr["w"], truth)}
+        del ws
+    # the plain FP64 form one event per call, synchronised after each (per-event path)
+    o1 = apo.solve_opts(precision=forms["fp64"], schedule=apo.SCHED_MAXSET, max_keep=K)
+    ws1 = geom.workspace(1, opts=o1)
+    lat = []
+    for e in range(min(per_event, ne) + 1):
+        sub = apo.DeviceHits.from_events(ev.subset([e]))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        apo.solve_batch(geom, sub, o1, workspace=ws1, stream=stream)
+        torch.cuda.synchronize()
+        if e > 0:
+            lat.append(1e3 * (time.perf_counter() - t0))
+    out["fp64_per_event"] = {"events": len(lat), "p50_ms": float(np.percentile(lat, 50)),
+                             "p99_ms": float(np.percentile(lat, 99)),
+                             "events_per_s": len(lat) / (sum(lat) * 1e-3)}
+    out["fp32_bulk_vs_fp64_per_event"] = (out["fp32_bulk"]["events_per_s"] /
+                                          out["fp64_per_event"]["events_per_s"])
+    geom.close()
+    return out
+
+
+def config1_latency(w, n: int = 50) -> dict:
+    """The plain method on one event at a time (10^5 coarse cells, top-16, 4 levels, FP64):
+    latency of apo_solve_batch_host (host arrays in, track out) per event, p50 / p99."""
+    from gen import chamber, grid as G
+    from paper_2401_04576_gb300 import apo
+    g = G.make_grid([10] * 5, 4, 16)
+    geom = apo.Geometry(g, w)
+    ev = chamber.single_track_events(n + 1, seed=1, w=w)
+    o = apo.solve_opts(precision=[apo.F64] * 5)
+    import torch
+    ws = torch.empty(apo.host_workspace_bytes(geom, 1, apo.HIT_CAP, o), dtype=torch.uint8,
+                     device="cuda")
+    lat = []
+    for e in range(n + 1):
+        sub = ev.subset([e])
+        t0 = time.perf_counter()
+        apo.solve_batch_host(geom, sub.offsets, sub.wire_id, sub.drift, o, workspace=ws)
+        if e > 0:
+            lat.append(1e3 * (time.perf_counter() - t0))
+    geom.close()
+    return {"workload": "one single-track event per call (seed 1), 10^5 coarse cells, top-16, "
+                        "4 levels, FP64, through apo_solve_batch_host",
+            "events": n, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99))}
 
 
 def background_study(w, n_events: int = 1024, seed: int = 4) -> dict:
@@ -491,6 +619,11 @@ def run_apo(args) -> None:
     fine_w = np.array([g.hi_edge[a][0] - g.lo_edge[a][0] for a in range(5)])
     dp = np.abs(tracks32["p"][:, 0, :] - tracks64["p"][:, 0, :])
     agree = float(np.mean(np.all(dp <= fine_w[None, :] * (1 + 1e-9), axis=1)))
+    truth = np.array([t[0].params for t in ev.tracks])
+    rec64 = truth_recovery(g, np.full(ev.n_events, lv), tracks64["p"][:, 0, :],
+                           tracks64["w"][:, 0, :], truth)
+    rec32 = truth_recovery(g, np.full(ev.n_events, lv), tracks32["p"][:, 0, :],
+                           tracks32["w"][:, 0, :], truth)
 
     # roofline of the dominant kernel (coarse vote): counted work / live launch time
     votes = torch.empty((ev.n_events, geom.n_coarse), dtype=torch.int32, device="cuda")
@@ -688,10 +821,21 @@ def run_apo(args) -> None:
                    "hits_per_event_mean": float(nh.mean()),
                    "l2": "flushed between timed steps (256 MiB write)"},
         "events_per_s": ev.n_events * world / (t_step * 1e-3),
+        "pairs": {"decided_per_step": pairs,
+                  "note": "value counts every (cell, hit) pair whose vote a step decides: "
+                          "coarse cells x hits + bisected cells x hits.  The coarse kernel "
+                          "decides most of them without evaluating the pair: the exact "
+                          "parent-cell test and the shared tan(lambda)-free prefix",
+                  "coarse_decided_per_step": float(np.sum(nh)) * geom.n_coarse,
+                  "coarse_tails_evaluated_per_step": float(n_tail),
+                  "coarse_prefixes_evaluated_per_step": float(n_pre),
+                  "refine_evaluated_per_step": float(np.sum(nh)) * lv * g.topk * 32},
+        "truth_recovery": rec64,
         "fp32_bulk": {"ms_per_step": t32, "value": pairs * world / (t32 * 1e-3),
                       "unit": "evals/s", "events_per_s": ev.n_events * world / (t32 * 1e-3),
                       "precision": "FP32 levels 0-4, FP64 levels 5-6",
                       "final_within_one_cell_of_fp64": agree,
+                      "truth_recovery": rec32,
                       "coarse_superset_violations": superset_violations,
                       "coarse_cells_compared": n_cells_cmp,
                       "coarse_roofline": roofline32},
@@ -717,8 +861,12 @@ def run_apo(args) -> None:
             line["p50_ms"] = below[-1]["p50_ms"]
             line["p99_ms"] = below[-1]["p99_ms"]
             line["p50_p99_at_offered_per_s"] = below[-1]["offered_per_s"]
+    if not args.no_maxset:
+        line["recovery_maxset"] = maxset_leg(w, ev, max(2, args.steps), flush, world)
     if rank == 0 and not args.no_bg:
-        line["background_rejection"] = background_study(w)
+        line["background_rejection"] = background_study(w, n_events=args.bg_events)
+    if rank == 0 and not args.no_config1:
+        line["config1_latency"] = config1_latency(w)
     if rank == 0 and not args.no_paper4d:
         line["paper_search_4d"] = paper_search_leg(cpu_events=0 if args.no_cpu_baseline else 1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -783,6 +931,10 @@ def main(argv=None):
     ap.add_argument("--no-bg", action="store_true", help="skip the background-rejection study")
     ap.add_argument("--no-paper4d", action="store_true", help="skip the paper's own 4-D search")
     ap.add_argument("--no-exact", action="store_true", help="skip the exact-phase leg")
+    ap.add_argument("--no-maxset", action="store_true", help="skip the max-set (recovery) leg")
+    ap.add_argument("--no-config1", action="store_true", help="skip the one-event latency leg")
+    ap.add_argument("--bg-events", type=int, default=4096,
+                    help="events of the multi-track background study")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--case", default=None,
                     choices=["coarse-f64", "coarse-f32", "coarse-mid", "solve-f64", "solve-f32", "solve-bulk",

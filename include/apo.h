@@ -21,7 +21,9 @@
  * (-sin phi0, cos phi0)), 1 phi0 [rad] (tangent azimuth at the POCA), 2 omega [1/m]
  * (signed curvature; helix centre (-(R+d0) sin phi0, (R+d0) cos phi0), R = 1/omega),
  * 3 z0 [m] (z at the POCA), 4 tanl = tan(dip angle).  A level-L cell index idx_a is in
- * [0, bins[a] << L); its key is sum_a idx_a << (10 a); its 32 children are 2 idx_a + bit_a.
+ * [0, bins[a] << L); its key is sum_a idx_a << s_a, where axis a is b_a = max(10,
+ * ceil(log2(bins[a] << levels))) bits wide and s_a = b_0 + ... + b_(a-1) (so 10 a when every
+ * axis has at most 1024 finest cells); its 32 children are 2 idx_a + bit_a.
  */
 #ifndef APO_H
 #define APO_H
@@ -57,6 +59,27 @@ typedef enum {
  * instead of the expansion; sound for the unexpanded equations, several times costlier. */
 enum { APO_F64 = 0, APO_F32 = 1, APO_F64_FILTERED = 2, APO_F64_MID = 3, APO_F64_EXACT = 4 };
 
+/* Flag OR-ed into any precision above except APO_F64_MID: the direction condition.  The
+ * track is taken to leave its point of closest approach (POCA) to the origin and each hit
+ * to lie on that outgoing arc, at a turning angle psi >= 0 from the POCA along the helix
+ * (the paper's toy tracks start at the target, Section 3.2).  A hit then votes for a cell
+ * only where psi can be >= 0; sin psi has the sign of the wire point's coordinate along the
+ * helix tangent at the POCA, and a cell where that coordinate is negative throughout gets
+ * no vote from the hit.  Without the flag, a helix and the same helix run backwards,
+ * (-d0, phi0 + pi, -omega, z0, -tanl), get identical votes. */
+#define APO_OUTGOING 16
+
+/* Coarse-to-fine schedules of apo_solve_batch.  APO_SCHED_TOPK: at each level the grid's
+ * topk cells by (votes desc, key asc) survive.  APO_SCHED_MAXSET: whole vote groups
+ * survive (Section 3.3 takes the result from the set of maximum-vote voxels): with vmax the
+ * level's best count, the kept cells are {votes >= T} for the smallest T >= max(vmax -
+ * slack, min(vmax, 1)) with at most max_keep of them; if the vmax group alone exceeds
+ * max_keep, the event's search ends at that level.  The estimate is over the last level's
+ * vmax group: per axis the mean of the cells' centres, summed by cell index in ascending
+ * order (n_i centre_i for the n_i cells at index i, round-to-nearest), and the half-extent
+ * of their union. */
+enum { APO_SCHED_TOPK = 0, APO_SCHED_MAXSET = 1 };
+
 #define APO_HIT_CAP 256      /* hits per event */
 #define APO_MAX_LEVELS 8     /* bisection levels after the coarse level */
 #define APO_MAX_TRACKS 8     /* tracks per event in multi-track extraction */
@@ -79,9 +102,10 @@ typedef struct {
  * cos hi), outward enclosures of sin/cos over each phi0 cell, level by level (level L
  * starts at row sum_{l<L} bins[1] << l).  sincos_mid (may be NULL): rows (sin c, cos c) at
  * each phi0 cell's centre c = (lo + hi) / 2, same row order; needed by APO_F64_MID only.
- * All copied.  Limits: bins[a] << levels <= 1024,
- * bins[0] * bins[3] <= 256, bins[4] <= 32,
- * levels <= APO_MAX_LEVELS, 1 <= topk, topk * 32 <= 4096, topk <= number of level-0 cells. */
+ * All copied.  Limits: bins[a] << levels <= 65536 with the key widths above summing to at
+ * most 64 bits, bins[0] * bins[3] <= 256, bins[4] <= 32, levels <= APO_MAX_LEVELS,
+ * 1 <= topk, topk * 32 <= 4096, topk <= number of level-0 cells.  APO_SCHED_TOPK needs the
+ * key widths to sum to at most 50 bits. */
 typedef struct {
     int32_t bins[5];
     int32_t levels;
@@ -143,11 +167,22 @@ typedef struct {
                                 apo_hits) the track whose final maximum-vote cells took it in
                                 the hit finding of Section 3.3 (0-based), or -1 if none did.
                                 apo_solve_batch_host and the server require NULL. */
+    int32_t schedule;        /* APO_SCHED_TOPK (default) or APO_SCHED_MAXSET */
+    int32_t max_keep;        /* APO_SCHED_MAXSET: cells kept per event and level, >= 1 */
+    int32_t slack;           /* APO_SCHED_MAXSET: vote groups down to vmax - slack are kept */
+    int32_t *final_level;    /* device, may be NULL (APO_SCHED_MAXSET): per event, the level
+                                whose vmax group gave the estimate */
+    int32_t *n_final;        /* device, may be NULL (APO_SCHED_MAXSET): per event, the size of
+                                that group */
+    int32_t *trace_count;    /* device, may be NULL (APO_SCHED_MAXSET): n_events x (levels + 1)
+                                kept counts; trace_keys / trace_votes are then n_events x
+                                (levels + 1) x max_keep, the kept cells of each level before
+                                the final one (in the order of the level's cells) */
 } apo_solve_opts;
 
 /* Fills *opts with: all levels FP64, one track, min_votes 0, mask_sigma 150e-6, no trace,
  * tune = {coarse_filter 0, cells_filter 1, cells_block 256, chunk 0}, no graph, no
- * hit_track. */
+ * hit_track, schedule APO_SCHED_TOPK, max_keep 32768, slack 0. */
 void apo_solve_opts_default(apo_solve_opts *opts);
 
 /* Text of the last error on this thread ("" if none). */
@@ -269,6 +304,12 @@ int apo_serve_drain(apo_server *srv, int32_t timeout_ms);
 
 /* Batches launched so far and the largest number of slots that were in flight at once. */
 int apo_serve_stats(const apo_server *srv, int32_t *batches, int32_t *max_busy_slots);
+
+/* Latency measured inside the library for every event finished so far: from
+ * apo_serve_submit accepting the event to the scheduling thread seeing its batch complete
+ * (steady clock; the thread polls every 50 us).  Writes the median and the 99th percentile
+ * in ms (nearest rank: the ceil(p n)-th smallest of n) and n; zeros before any event. */
+int apo_serve_latency(const apo_server *srv, double *p50_ms, double *p99_ms, int64_t *n_events);
 
 /* Stops the scheduling thread after the batches in flight and frees the slots. */
 void apo_serve_destroy(apo_server *srv);

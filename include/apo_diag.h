@@ -46,8 +46,9 @@ int apo_diag_dops(int32_t op, const double *x, double *out, int64_t n, void *str
  * pairs; hits[9 n] = (x0, y0, sin phi_s, cos phi_s, tan tau, sin phi_s tan tau,
  * cos phi_s tan tau, tan^2 tau, drift); out[10 n] = the vote (0 / 1), G+ lo, G+ hi, G- lo,
  * G- hi, a guard flag (1 when a divisor reached 0 and the pair votes unevaluated), and the
- * phase corrections delta+ lo, hi, delta- lo, hi; zeros past a guard.  precision APO_F64
- * or APO_F32 (cells and hits rounded outward to FP32 first; results widened to double). */
+ * phase corrections delta+ lo, hi, delta- lo, hi; zeros past a guard; the flag is 2 when
+ * the direction condition refused the vote.  precision APO_F64 or APO_F32 (cells and hits
+ * rounded outward to FP32 first; results widened to double), optionally | APO_OUTGOING. */
 int apo_diag_vote_pair_ends(const apo_geometry *geom, int32_t precision, const double *cells,
                             const double *hits, double *out, int64_t n, void *stream);
 /* Exercises the device-side wait limit: one kernel waits on a barrier that nothing

@@ -15,6 +15,8 @@ from . import build as _build
 
 APO_OK, APO_EINVAL, APO_ENOMEM, APO_ECUDA, APO_ETIMEOUT, APO_EBUSY = 0, -1, -2, -3, -4, -5
 F64, F32, F64_FILTERED, F64_MID, F64_EXACT = 0, 1, 2, 3, 4
+OUTGOING = 16                      # precision flag: the direction condition
+SCHED_TOPK, SCHED_MAXSET = 0, 1
 HIT_CAP = 256
 STATUS_TIMEOUT, STATUS_BADHIT, STATUS_TOOMANY, STATUS_BADOFFS = 1, 2, 4, 8
 MAX_LEVELS = 8
@@ -55,7 +57,10 @@ class ApoSolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int32 * (MAX_LEVELS + 1)), ("max_tracks", C.c_int32),
                 ("min_votes", C.c_int32), ("mask_sigma", C.c_double),
                 ("trace_keys", C.c_void_p), ("trace_votes", C.c_void_p),
-                ("tune", ApoTune), ("use_graph", C.c_int32), ("hit_track", C.c_void_p)]
+                ("tune", ApoTune), ("use_graph", C.c_int32), ("hit_track", C.c_void_p),
+                ("schedule", C.c_int32), ("max_keep", C.c_int32), ("slack", C.c_int32),
+                ("final_level", C.c_void_p), ("n_final", C.c_void_p),
+                ("trace_count", C.c_void_p)]
 
 
 class Apo4Opts(C.Structure):
@@ -113,6 +118,8 @@ def lib():
         L.apo_serve_drain.argtypes = [vp, i32]
         L.apo_serve_stats.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         L.apo_serve_destroy.argtypes = [vp]
+        L.apo_serve_latency.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                        C.POINTER(C.c_int64)]
         L.apo_autotune.argtypes = [vp, C.POINTER(ApoHits), C.POINTER(ApoSolveOpts), vp, sz, vp,
                                    C.POINTER(ApoTune), C.POINTER(C.c_float)]
         L.apo_diag_vote_coarse_counts.argtypes = [vp, C.POINTER(ApoHits), i32, vp, vp, vp, sz, vp]
@@ -212,9 +219,9 @@ class Geometry:
                                          None if opts is None else C.byref(opts), C.byref(n)))
         return int(n.value)
 
-    def workspace(self, n_events: int, extra: int = 0):
+    def workspace(self, n_events: int, extra: int = 0, opts: ApoSolveOpts | None = None):
         torch = _torch()
-        return torch.empty(self.workspace_bytes(n_events) + extra, dtype=torch.uint8,
+        return torch.empty(self.workspace_bytes(n_events, opts) + extra, dtype=torch.uint8,
                            device="cuda")
 
 
@@ -241,7 +248,9 @@ class DeviceHits:
 
 def solve_opts(precision=None, levels: int = 0, max_tracks: int = 1, min_votes: int = 0,
                mask_sigma: float = 150e-6, trace_keys=None, trace_votes=None, tune=None,
-               use_graph: bool = False, hit_track=None) -> ApoSolveOpts:
+               use_graph: bool = False, hit_track=None, schedule: int = SCHED_TOPK,
+               max_keep: int | None = None, slack: int = 0, final_level=None, n_final=None,
+               trace_count=None) -> ApoSolveOpts:
     o = ApoSolveOpts()
     lib().apo_solve_opts_default(C.byref(o))
     if tune is not None:
@@ -254,6 +263,12 @@ def solve_opts(precision=None, levels: int = 0, max_tracks: int = 1, min_votes: 
     o.trace_keys = _ptr(trace_keys).value
     o.trace_votes = _ptr(trace_votes).value
     o.hit_track = _ptr(hit_track).value
+    o.schedule, o.slack = int(schedule), int(slack)
+    if max_keep is not None:
+        o.max_keep = int(max_keep)
+    o.final_level = _ptr(final_level).value
+    o.n_final = _ptr(n_final).value
+    o.trace_count = _ptr(trace_count).value
     return o
 
 
@@ -301,7 +316,7 @@ def solve_batch(geom: Geometry, hits: DeviceHits, opts: ApoSolveOpts | None = No
                              device="cuda")
     if n_tracks is None:
         n_tracks = torch.zeros(hits.n_events, dtype=torch.int32, device="cuda")
-    ws = geom.workspace(hits.n_events) if workspace is None else workspace
+    ws = geom.workspace(hits.n_events, opts=o) if workspace is None else workspace
     hc = hits.c()
     _check(lib().apo_solve_batch(geom.handle, C.byref(hc), C.byref(o), _ptr(tracks),
                                  _ptr(n_tracks), _ptr(ws), ws.numel(), _stream_ptr(stream)))
@@ -312,7 +327,7 @@ def autotune(geom: Geometry, hits: DeviceHits, opts: ApoSolveOpts | None = None,
              stream=None):
     """apo_autotune: the fastest execution knobs for this batch (results never change)."""
     o = opts if opts is not None else solve_opts()
-    ws = geom.workspace(hits.n_events) if workspace is None else workspace
+    ws = geom.workspace(hits.n_events, opts=o) if workspace is None else workspace
     best = ApoTune()
     ms = C.c_float()
     hc = hits.c()
@@ -326,8 +341,10 @@ def tracks_to_numpy(tracks, n_events: int, max_tracks: int = 1) -> np.ndarray:
     return a.view(TRACK_DTYPE).reshape(n_events, max_tracks)
 
 
-def host_workspace_bytes(geom: Geometry, n_events: int, n_hits: int) -> int:
-    return geom.workspace_bytes(n_events) + int(lib().apo_host_extra_bytes(int(n_events), int(n_hits)))
+def host_workspace_bytes(geom: Geometry, n_events: int, n_hits: int,
+                         opts: ApoSolveOpts | None = None) -> int:
+    return geom.workspace_bytes(n_events, opts) + int(lib().apo_host_extra_bytes(int(n_events),
+                                                                                 int(n_hits)))
 
 
 def solve_batch_host(geom: Geometry, offsets: np.ndarray, wire_id: np.ndarray, drift: np.ndarray,
@@ -341,7 +358,7 @@ def solve_batch_host(geom: Geometry, offsets: np.ndarray, wire_id: np.ndarray, d
     ws = workspace
     if ws is None:
         torch = _torch()
-        ws = torch.empty(host_workspace_bytes(geom, n_ev, int(offsets[-1])), dtype=torch.uint8,
+        ws = torch.empty(host_workspace_bytes(geom, n_ev, int(offsets[-1]), o), dtype=torch.uint8,
                          device="cuda")
     if out is None:
         out = np.zeros((n_ev, int(o.max_tracks)), TRACK_DTYPE)
@@ -488,6 +505,12 @@ class Server:
         b, m = C.c_int32(), C.c_int32()
         _check(lib().apo_serve_stats(self.handle, C.byref(b), C.byref(m)))
         return int(b.value), int(m.value)
+
+    def latency(self):
+        """(p50 ms, p99 ms, events) measured inside the library (accepted -> batch done)."""
+        p50, p99, n = C.c_double(), C.c_double(), C.c_int64()
+        _check(lib().apo_serve_latency(self.handle, C.byref(p50), C.byref(p99), C.byref(n)))
+        return float(p50.value), float(p99.value), int(n.value)
 
     def close(self):
         if getattr(self, "handle", None) and self.handle.value:

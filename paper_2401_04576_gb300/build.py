@@ -11,7 +11,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libapo.so")
-SOURCES = ["kernels.cu", "apo_abi.cu", "diag.cu", "apo_noalloc.cu", "apo_serve.cu", "apo4.cu"]
+SOURCES = ["kernels.cu", "apo_abi.cu", "diag.cu", "apo_noalloc.cu", "apo_serve.cu", "apo4.cu",
+           "maxset.cu"]
 HEADERS = ["interval.cuh", "vote_program.cuh", "kernels.cuh", "fourd.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",

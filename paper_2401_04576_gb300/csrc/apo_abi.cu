@@ -68,11 +68,22 @@ namespace {
 
 // Workspace regions for a batch of n_events.
 struct Layout {
-    size_t status, n_hits, hd, hf, votes, hist, fk, fv, ck, cv, mask, done, ntr, tune_tracks, end;
-    int chunk;
+    size_t status, n_hits, hd, hf, votes, hist, fk, fv, ck, cv, mask, done, ntr, tune_tracks;
+    size_t ms_front, ms_count, ms_stop, ms_ck, ms_cv, end;
+    int chunk, ms_chunk;
 };
 
-Layout layout(const apo_geometry *g, int n_events) {
+// Events per chunk of the max-set schedule: its children arrays hold max_keep x 32 cells per
+// event; a chunk keeps them within 2 GiB (and within the level-0 chunk).
+int maxset_chunk(const Layout &L, int max_keep) {
+    long long per = (long long)max_keep * 32 * (sizeof(uint64_t) + sizeof(int32_t));
+    long long c = (2LL << 30) / (per > 0 ? per : 1);
+    if (c < 1) c = 1;
+    if (c > L.chunk) c = L.chunk;
+    return (int)c;
+}
+
+Layout layout(const apo_geometry *g, int n_events, const apo_solve_opts *opts = nullptr) {
     Layout L;
     const int K = g->dg.topk;
     long long chunk = (1LL << 28) / (g->n_coarse > 0 ? g->n_coarse : 1);
@@ -94,6 +105,18 @@ Layout layout(const apo_geometry *g, int n_events) {
     L.done = o; o = align256(o + sizeof(int32_t) * (size_t)n_events);
     L.ntr = o; o = align256(o + sizeof(int32_t) * (size_t)n_events);
     L.tune_tracks = o; o = align256(o + sizeof(apo_track) * (size_t)n_events * APO_MAX_TRACKS);
+    L.ms_chunk = 0;
+    L.ms_front = L.ms_count = L.ms_stop = L.ms_ck = L.ms_cv = o;
+    if (opts && opts->schedule == APO_SCHED_MAXSET && opts->max_keep > 0) {
+        const size_t K = (size_t)opts->max_keep;
+        const int c = maxset_chunk(L, opts->max_keep);
+        L.ms_chunk = c;
+        L.ms_front = o; o = align256(o + sizeof(uint64_t) * (size_t)c * K);
+        L.ms_count = o; o = align256(o + sizeof(int32_t) * (size_t)c);
+        L.ms_stop = o; o = align256(o + sizeof(int32_t) * (size_t)c);
+        L.ms_ck = o; o = align256(o + sizeof(uint64_t) * (size_t)c * K * 32);
+        L.ms_cv = o; o = align256(o + sizeof(int32_t) * (size_t)c * K * 32);
+    }
     L.end = o;
     return L;
 }
@@ -103,12 +126,29 @@ template <typename P> P *at(void *ws, size_t off) {
 }
 
 // A level precision the geometry can evaluate.
-int check_precision(const apo_geometry *g, int p, const char *what) {
-    if (p != APO_F64 && p != APO_F32 && p != APO_F64_FILTERED && p != APO_F64_MID && p != APO_F64_EXACT)
+int check_precision(const apo_geometry *g, int p_code, const char *what) {
+    const int p = p_code & ~APO_OUTGOING;
+    if ((p_code & ~(APO_OUTGOING | 7)) != 0 ||
+        (p != APO_F64 && p != APO_F32 && p != APO_F64_FILTERED && p != APO_F64_MID && p != APO_F64_EXACT))
         return fail(APO_EINVAL, "bad %s", what);
+    if (p == APO_F64_MID && (p_code & APO_OUTGOING))
+        return fail(APO_EINVAL, "APO_OUTGOING does not apply to APO_F64_MID");
     if (p == APO_F64_MID && !g->dg.sincos_mid)
         return fail(APO_EINVAL, "APO_F64_MID needs the grid's sincos_mid table");
     return APO_OK;
+}
+
+// The device tables for one precision code: the geometry's, with the direction flag set.
+DevGeom geom_for(const apo_geometry *g, int p_code) {
+    DevGeom d = g->dg;
+    d.k.outgoing = (p_code & APO_OUTGOING) ? 1 : 0;
+    return d;
+}
+
+int key_bits_total(const DevGeom &d) {
+    int t = 0;
+    for (int a = 0; a < 5; a++) t += d.key_bits[a];
+    return t;
 }
 
 int check_geom(const apo_geometry *g) {
@@ -128,8 +168,9 @@ int check_hits(const apo_hits *h) {
     return APO_OK;
 }
 
-int check_ws(const apo_geometry *g, int n_events, void *ws, size_t bytes, Layout &L) {
-    L = layout(g, n_events);
+int check_ws(const apo_geometry *g, int n_events, void *ws, size_t bytes, Layout &L,
+             const apo_solve_opts *opts = nullptr) {
+    L = layout(g, n_events, opts);
     if (!ws) return fail(APO_EINVAL, "workspace is NULL");
     if (reinterpret_cast<uintptr_t>(ws) % 256)
         return fail(APO_EINVAL, "workspace must be 256-byte aligned");
@@ -160,6 +201,9 @@ void apo_solve_opts_default(apo_solve_opts *o) {
     o->min_votes = 0;
     o->mask_sigma = 150e-6;
     o->tune.cells_filter = 1;   // measured faster on bisected cells, identical votes
+    o->schedule = APO_SCHED_TOPK;
+    o->max_keep = 32768;
+    o->slack = 0;
 }
 
 int apo_geometry_create(const apo_wires *w, const apo_grid *gr, apo_geometry **out) {
@@ -173,12 +217,19 @@ int apo_geometry_create(const apo_wires *w, const apo_grid *gr, apo_geometry **o
     if (gr->levels < 0 || gr->levels > APO_MAX_LEVELS) return fail(APO_EINVAL, "levels out of range");
     if (gr->topk < 1 || gr->topk * 32 > 4096) return fail(APO_EINVAL, "topk must be in [1, 128]");
     long long n0 = 1;
+    int kbits[5], kshift[5], ktot = 0;
     for (int a = 0; a < 5; a++) {
-        if (gr->bins[a] < 1 || ((long long)gr->bins[a] << gr->levels) > 1024)
-            return fail(APO_EINVAL, "bins[%d] << levels must be in [1, 1024]", a);
+        if (gr->bins[a] < 1 || ((long long)gr->bins[a] << gr->levels) > 65536)
+            return fail(APO_EINVAL, "bins[%d] << levels must be in [1, 65536]", a);
         if (!gr->lo_edge[a] || !gr->hi_edge[a]) return fail(APO_EINVAL, "edge table %d is NULL", a);
         n0 *= gr->bins[a];
+        int b = 10;
+        while ((1LL << b) < ((long long)gr->bins[a] << gr->levels)) b++;
+        kbits[a] = b;
+        kshift[a] = ktot;
+        ktot += b;
     }
+    if (ktot > 64) return fail(APO_EINVAL, "cell keys need %d > 64 bits", ktot);
     if (!gr->sincos) return fail(APO_EINVAL, "sincos table is NULL");
     if (gr->bins[0] * gr->bins[3] > 256)
         return fail(APO_EINVAL, "bins[0] * bins[3] must be <= 256 (one thread each in a block)");
@@ -194,6 +245,7 @@ int apo_geometry_create(const apo_wires *w, const apo_grid *gr, apo_geometry **o
     int dev = 0;
     CU(cudaGetDevice(&dev));
     init_kernel_attributes();
+    init_maxset_attributes();
     apo_geometry *g = new apo_geometry();
     g->device = dev;
     g->n_coarse = n0;
@@ -203,6 +255,7 @@ int apo_geometry_create(const apo_wires *w, const apo_grid *gr, apo_geometry **o
     d.levels = gr->levels;
     d.topk = gr->topk;
     d.n_wires = w->n_wires;
+    for (int a = 0; a < 5; a++) { d.key_bits[a] = kbits[a]; d.key_shift[a] = kshift[a]; }
     auto upload = [&](const double *src, size_t n, const double **dst) -> int {
         void *p = nullptr;
         cudaError_t e = cudaMalloc(&p, n * sizeof(double));
@@ -234,6 +287,7 @@ int apo_geometry_create(const apo_wires *w, const apo_grid *gr, apo_geometry **o
             launch_series_consts(dk, 0);
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaMemcpy(&d.k, dk, sizeof(SeriesConsts), cudaMemcpyDeviceToHost);
+            d.k.outgoing = 0;
             cudaFree(dk);
         }
         if (e != cudaSuccess) rc = fail(APO_ECUDA, "series constants: %s", cudaGetErrorString(e));
@@ -256,10 +310,10 @@ void apo_geometry_destroy(apo_geometry *g) {
 
 int64_t apo_coarse_cells(const apo_geometry *g) { return g ? g->n_coarse : 0; }
 
-int apo_workspace_bytes(const apo_geometry *g, int32_t n_events, const apo_solve_opts *, size_t *bytes) {
+int apo_workspace_bytes(const apo_geometry *g, int32_t n_events, const apo_solve_opts *opts, size_t *bytes) {
     if (!g || !bytes) return fail(APO_EINVAL, "NULL argument");
     if (n_events < 0) return fail(APO_EINVAL, "n_events < 0");
-    *bytes = layout(g, n_events).end;
+    *bytes = layout(g, n_events, opts).end;
     return APO_OK;
 }
 
@@ -293,17 +347,19 @@ int apo_vote(const apo_geometry *g, const apo_hits *hits, const uint64_t *cell_k
     launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh,
                  at<uint32_t>(ws, L.mask), at<int32_t>(ws, L.done), status, s);
     if ((rc = check_launch("stage"))) return rc;
+    const DevGeom dg = geom_for(g, precision);
+    const int prec = precision & ~APO_OUTGOING;
     if (!cell_keys) {
         uint32_t *hist = at<uint32_t>(ws, L.hist);
         for (int e0 = 0; e0 < ne; e0 += L.chunk) {
             int n = ne - e0 < L.chunk ? ne - e0 : L.chunk;
             CU(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)n * kHistBins, s));
-            launch_vote_coarse(g->dg, precision, e0, n, hd, hf, nh, votes_out + (size_t)e0 * g->n_coarse,
+            launch_vote_coarse(dg, prec, e0, n, hd, hf, nh, votes_out + (size_t)e0 * g->n_coarse,
                                hist, status, s);
             if ((rc = check_launch("vote_coarse"))) return rc;
         }
     } else {
-        launch_vote_keys(g->dg, precision, ne, hd, hf, nh, level, cell_keys, n_cells_per_event,
+        launch_vote_keys(dg, prec, ne, hd, hf, nh, level, cell_keys, n_cells_per_event,
                          votes_out, s);
         if ((rc = check_launch("vote_keys"))) return rc;
     }
@@ -320,6 +376,7 @@ int apo_refine(const apo_geometry *g, const apo_hits *hits, const uint64_t *keys
     if (!keys_in && (level != 0 || n_in != g->n_coarse))
         return fail(APO_EINVAL, "implicit keys need level 0 and n_in = apo_coarse_cells");
     if (keys_in && (n_in < 1 || n_in > 4096)) return fail(APO_EINVAL, "n_in must be in [1, 4096]");
+    if (key_bits_total(g->dg) > 50) return fail(APO_EINVAL, "top-K selection needs keys of at most 50 bits");
     Layout L;
     if ((rc = check_ws(g, hits->n_events, ws, ws_bytes, L))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -342,7 +399,7 @@ int apo_refine(const apo_geometry *g, const apo_hits *hits, const uint64_t *keys
     }
     if (kept_keys) CU(cudaMemcpyAsync(kept_keys, fk, sizeof(uint64_t) * (size_t)ne * K, cudaMemcpyDeviceToDevice, s));
     if (kept_votes) CU(cudaMemcpyAsync(kept_votes, fv, sizeof(int32_t) * (size_t)ne * K, cudaMemcpyDeviceToDevice, s));
-    launch_children(fk, (long long)ne * K, children_out, s);
+    launch_children(g->dg, fk, (long long)ne * K, children_out, s);
     return check_launch("children");
 }
 
@@ -378,7 +435,21 @@ int validate_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_
         return fail(APO_EINVAL, "tune.cells_block must be 0, 128 or 256");
     if (o->tune.chunk_events < 0) return fail(APO_EINVAL, "tune.chunk_events < 0");
     if (!tracks_out && hits->n_events > 0) return fail(APO_EINVAL, "tracks_out is NULL");
-    return check_ws(g, hits->n_events, ws, ws_bytes, L);
+    if (o->schedule == APO_SCHED_MAXSET) {
+        if (o->max_tracks != 1) return fail(APO_EINVAL, "APO_SCHED_MAXSET searches one track per event");
+        if (o->hit_track) return fail(APO_EINVAL, "APO_SCHED_MAXSET takes no hit_track");
+        if (o->max_keep < 1 || o->max_keep > (1 << 20)) return fail(APO_EINVAL, "max_keep must be in [1, 2^20]");
+        if (o->slack < 0) return fail(APO_EINVAL, "slack < 0");
+        if (maxset_smem_bytes(g->dg) > 64 * 1024)
+            return fail(APO_EINVAL, "APO_SCHED_MAXSET needs sum_a bins[a] << levels <= 16384");
+    } else if (o->schedule == APO_SCHED_TOPK) {
+        if (key_bits_total(g->dg) > 50) return fail(APO_EINVAL, "APO_SCHED_TOPK needs keys of at most 50 bits");
+        if (o->trace_count || o->final_level || o->n_final)
+            return fail(APO_EINVAL, "trace_count / final_level / n_final belong to APO_SCHED_MAXSET");
+    } else {
+        return fail(APO_EINVAL, "bad schedule");
+    }
+    return check_ws(g, hits->n_events, ws, ws_bytes, L, o);
 }
 
 // NVTX range for the host-side queueing of one phase (visible in Nsight timelines).
@@ -386,6 +457,84 @@ struct NvtxRange {
     explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
     ~NvtxRange() { nvtxRangePop(); }
 };
+
+// The max-set schedule (APO_SCHED_MAXSET) for every chunk of events: level-0 voting of the
+// whole grid (one thread per cell), then per level the selection of whole vote groups and
+// the voting of the kept cells' children, until each event's search has ended.
+template <typename PrecAt>
+int enqueue_maxset(const apo_geometry *g, const apo_hits *hits, const apo_solve_opts *o, const DevGeom *gl,
+                   PrecAt prec_at, apo_track *tracks_out, int32_t *n_tracks_out, void *ws, const Layout &L,
+                   cudaStream_t s) {
+    int rc;
+    const int lv = g->dg.levels, K = o->max_keep, ne = hits->n_events;
+    unsigned *status = at<unsigned>(ws, L.status);
+    int32_t *nh = at<int32_t>(ws, L.n_hits);
+    HitRecD *hd = at<HitRecD>(ws, L.hd);
+    HitRecF *hf = at<HitRecF>(ws, L.hf);
+    int32_t *votes = at<int32_t>(ws, L.votes);
+    uint64_t *front = at<uint64_t>(ws, L.ms_front);
+    int32_t *count = at<int32_t>(ws, L.ms_count);
+    int32_t *stop = at<int32_t>(ws, L.ms_stop);
+    uint64_t *ck = at<uint64_t>(ws, L.ms_ck);
+    int32_t *cv = at<int32_t>(ws, L.ms_cv);
+    int32_t *ntr = n_tracks_out ? n_tracks_out : at<int32_t>(ws, L.ntr);
+    const int block = o->tune.cells_block ? o->tune.cells_block : 256;
+    const int chunk = (o->tune.chunk_events > 0 && o->tune.chunk_events < L.ms_chunk) ? o->tune.chunk_events
+                                                                                      : L.ms_chunk;
+    CU(cudaMemsetAsync(status, 0, 256, s));
+    launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, at<uint32_t>(ws, L.mask),
+                 at<int32_t>(ws, L.done), status, s);
+    if ((rc = check_launch("stage"))) return rc;
+    for (int e0 = 0; e0 < ne; e0 += chunk) {
+        NvtxRange range_chunk("apo max-set chunk");
+        const int n = ne - e0 < chunk ? ne - e0 : chunk;
+        const HitRecD *hde = hd + (size_t)e0 * kHitCap;
+        const HitRecF *hfe = hf + (size_t)e0 * kHitCap;
+        const int32_t *nhe = nh + e0;
+        CU(cudaMemsetAsync(stop, 0, sizeof(int32_t) * (size_t)n, s));
+        MaxsetArgs A{};
+        A.levels = lv;
+        A.max_keep = K;
+        A.slack = o->slack;
+        A.min_votes = o->min_votes;
+        A.n_coarse = g->n_coarse;
+        A.front = front;
+        A.count_out = count;
+        A.stop = stop;
+        A.n_hits = nhe;
+        A.tracks = tracks_out + e0;
+        A.n_tracks = ntr + e0;
+        A.final_level = o->final_level ? o->final_level + e0 : nullptr;
+        A.n_final = o->n_final ? o->n_final + e0 : nullptr;
+        A.trace_keys = o->trace_count && o->trace_keys ? o->trace_keys + (size_t)e0 * (lv + 1) * K : nullptr;
+        A.trace_votes = o->trace_count && o->trace_votes ? o->trace_votes + (size_t)e0 * (lv + 1) * K : nullptr;
+        A.trace_count = o->trace_count ? o->trace_count + (size_t)e0 * (lv + 1) : nullptr;
+        if (A.trace_count) CU(cudaMemsetAsync(A.trace_count, 0, sizeof(int32_t) * (size_t)n * (lv + 1), s));
+        // level 0: every cell of the grid, one thread each, in linear (= key) order
+        launch_vote_keys(gl[0], prec_at(0), n, hde, hfe, nhe, 0, nullptr, g->n_coarse, votes, s);
+        if ((rc = check_launch("vote_coarse_cells"))) return rc;
+        A.level = 0;
+        A.votes = votes;
+        A.keys = nullptr;
+        A.count_in = nullptr;
+        A.stride = g->n_coarse;
+        launch_maxset_select(gl[0], n, A, s);
+        if ((rc = check_launch("maxset_select"))) return rc;
+        for (int lev = 1; lev <= lv; lev++) {
+            launch_vote_children(gl[lev], prec_at(lev), n, hde, hfe, nhe, lev, front, K, ck, cv, s, nullptr,
+                                 block, count);
+            if ((rc = check_launch("vote_children"))) return rc;
+            A.level = lev;
+            A.votes = cv;
+            A.keys = ck;
+            A.count_in = count;
+            A.stride = (long long)K * 32;
+            launch_maxset_select(gl[lev], n, A, s);
+            if ((rc = check_launch("maxset_select"))) return rc;
+        }
+    }
+    return APO_OK;
+}
 
 // Queues the whole search on stream s (no host synchronisation, capturable).
 int enqueue_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_opts *o,
@@ -412,10 +561,14 @@ int enqueue_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_o
     const int chunk = (o->tune.chunk_events > 0 && o->tune.chunk_events < L.chunk) ? o->tune.chunk_events : L.chunk;
     const int block = o->tune.cells_block ? o->tune.cells_block : 256;
     auto prec_at = [&](int lev) {
-        int p = o->precision[lev];
+        int p = o->precision[lev] & ~APO_OUTGOING;
         bool filt = lev == 0 ? o->tune.coarse_filter != 0 : o->tune.cells_filter != 0;
         return (p == APO_F64 && filt) ? (int)APO_F64_FILTERED : p;
     };
+    DevGeom gl[APO_MAX_LEVELS + 1];   // per level: the geometry with that level's direction flag
+    for (int lev = 0; lev <= lv; lev++) gl[lev] = geom_for(g, o->precision[lev]);
+    if (o->schedule == APO_SCHED_MAXSET)
+        return enqueue_maxset(g, hits, o, gl, prec_at, tracks_out, n_tracks_out, ws, L, s);
     CU(cudaMemsetAsync(status, 0, 256, s));
     launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, active, done, status, s,
                  o->hit_track);
@@ -434,20 +587,20 @@ int enqueue_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_o
         for (int round = 0; round < o->max_tracks; round++) {
             NvtxRange range_round("apo search round");
             CU(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)n * kHistBins, s));
-            launch_vote_coarse(g->dg, prec_at(0), e0, n, hd, hf, nh, votes, hist, status, s, nullptr, active);
+            launch_vote_coarse(gl[0], prec_at(0), e0, n, hd, hf, nh, votes, hist, status, s, nullptr, active);
             if ((rc = check_launch("vote_coarse"))) return rc;
             launch_select_coarse(g->dg, e0, n, votes, hist, K, fk, fv, s);
             if ((rc = check_launch("select_coarse"))) return rc;
             if (round == 0 && (rc = trace_copy(o, g, e0, n, 0, fke, fve, s))) return rc;
             for (int lev = 1; lev <= lv; lev++) {
-                launch_vote_children(g->dg, prec_at(lev), n, hde, hfe, nhe, lev, fke, K, cke, cve, s, acte,
+                launch_vote_children(gl[lev], prec_at(lev), n, hde, hfe, nhe, lev, fke, K, cke, cve, s, acte,
                                      block);
                 if ((rc = check_launch("vote_children"))) return rc;
                 launch_topk(n, cke, cve, K * 32, K, fke, fve, s);
                 if ((rc = check_launch("topk"))) return rc;
                 if (round == 0 && (rc = trace_copy(o, g, e0, n, lev, fke, fve, s))) return rc;
             }
-            launch_estimate_mask(g->dg, n, cke, cve, K * 32, lv, nhe, acte, done + e0, hde, round,
+            launch_estimate_mask(gl[lv], n, cke, cve, K * 32, lv, nhe, acte, done + e0, hde, round,
                                  o->max_tracks, o->min_votes, width,
                                  tracks_out + (size_t)e0 * o->max_tracks, ntr + e0, s,
                                  hits->offsets + e0, o->hit_track);
@@ -527,10 +680,13 @@ int apo_autotune(const apo_geometry *g, const apo_hits *hits, const apo_solve_op
     o.use_graph = 0;
     o.trace_keys = nullptr;
     o.trace_votes = nullptr;
+    o.trace_count = nullptr;
+    o.final_level = nullptr;
+    o.n_final = nullptr;
     std::memset(&o.tune, 0, sizeof(o.tune));
     Layout L;
     apo_track *tt = nullptr;
-    int rc = check_ws(g, hits ? hits->n_events : 0, ws, ws_bytes, L);
+    int rc = check_ws(g, hits ? hits->n_events : 0, ws, ws_bytes, L, &o);
     if (rc) return rc;
     tt = at<apo_track>(ws, L.tune_tracks);
     if ((rc = validate_solve(g, hits, &o, tt, ws, ws_bytes, L))) return rc;
@@ -661,9 +817,11 @@ int apo_diag_vote_pair_ends(const apo_geometry *g, int32_t precision, const doub
                             const double *hits, double *out, int64_t n, void *stream) {
     int rc;
     if ((rc = check_geom(g))) return rc;
-    if (precision != APO_F64 && precision != APO_F32) return fail(APO_EINVAL, "bad precision");
+    const int base = precision & ~APO_OUTGOING;
+    if ((base != APO_F64 && base != APO_F32) || (precision & ~(APO_OUTGOING | 7)))
+        return fail(APO_EINVAL, "bad precision");
     if (n < 0 || (n > 0 && (!cells || !hits || !out))) return fail(APO_EINVAL, "bad arguments");
-    if (launch_pair_ends(g->dg.k, precision == APO_F64 ? 0 : 1, cells, hits, out, n,
+    if (launch_pair_ends(geom_for(g, precision).k, base == APO_F64 ? 0 : 1, cells, hits, out, n,
                          static_cast<cudaStream_t>(stream)))
         return fail(APO_ECUDA, "pair-ends launch failed");
     return APO_OK;
@@ -679,13 +837,15 @@ int apo_solve_batch_host(const apo_geometry *g, int32_t n_events, const int32_t 
     const int64_t n_hits = n_events > 0 ? offsets[n_events] : 0;
     if (n_hits < 0) return fail(APO_EINVAL, "offsets[n_events] < 0");
     if (n_hits > 0 && (!wire_id || !drift)) return fail(APO_EINVAL, "hit arrays are NULL");
-    Layout L = layout(g, n_events);
-    const size_t need = L.end + apo_host_extra_bytes(n_events, n_hits);
-    if (!ws || ws_bytes < need) return fail(APO_ENOMEM, "workspace too small: %zu < %zu", ws_bytes, need);
     apo_solve_opts def;
     apo_solve_opts_default(&def);
     const apo_solve_opts *o = opts ? opts : &def;
     if (o->hit_track) return fail(APO_EINVAL, "apo_solve_batch_host takes no hit_track (device output)");
+    if (o->final_level || o->n_final || o->trace_count || o->trace_keys || o->trace_votes)
+        return fail(APO_EINVAL, "apo_solve_batch_host takes no device traces or per-event outputs");
+    Layout L = layout(g, n_events, o);
+    const size_t need = L.end + apo_host_extra_bytes(n_events, n_hits);
+    if (!ws || ws_bytes < need) return fail(APO_ENOMEM, "workspace too small: %zu < %zu", ws_bytes, need);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     size_t off = L.end;
     int32_t *d_off = at<int32_t>(ws, off); off += align256(sizeof(int32_t) * (size_t)(n_events + 1));

@@ -6,6 +6,8 @@
 // waits only for the next free slot.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -24,10 +26,13 @@ namespace {
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
+using Clock = std::chrono::steady_clock;
+
 struct Req {
     uint64_t id;
     std::vector<int32_t> wid;
     std::vector<double> drift;
+    Clock::time_point t_submit;   // when apo_serve_submit accepted it
 };
 
 struct Result {
@@ -52,6 +57,7 @@ struct Slot {
     apo_track *h_tr = nullptr;
     unsigned *h_status = nullptr;     // the workspace's status word, copied back per batch
     std::vector<uint64_t> ids;
+    std::vector<Clock::time_point> t_submit;
     bool busy = false;
 };
 
@@ -68,6 +74,7 @@ struct apo_server {
     std::deque<Result> done;
     long long submitted = 0, finished = 0;
     int batches = 0, busy_now = 0, max_busy = 0;
+    std::vector<double> latency_ms;   // per finished event: accepted -> batch seen complete
     bool stop = false;
     int error = APO_OK;
     std::string msg;
@@ -107,6 +114,7 @@ int launch_slot(apo_server *sv, Slot &s) {
     const int B = sv->o.batch_events, mt = sv->o.solve.max_tracks;
     int n = 0, off = 0;
     s.ids.clear();
+    s.t_submit.clear();
     s.h_off[0] = 0;
     while (n < B && !sv->pending.empty()) {
         Req &r = sv->pending.front();
@@ -115,6 +123,7 @@ int launch_slot(apo_server *sv, Slot &s) {
         off += (int)r.wid.size();
         s.h_off[++n] = off;
         s.ids.push_back(r.id);
+        s.t_submit.push_back(r.t_submit);
         sv->pending.pop_front();
     }
     if (n == 0) return APO_OK;
@@ -165,7 +174,9 @@ void worker_loop(apo_server *sv) {
                 sv->cv_done.notify_all();
                 continue;
             }
+            const Clock::time_point now = Clock::now();
             for (size_t i = 0; i < s.ids.size(); i++) {
+                sv->latency_ms.push_back(std::chrono::duration<double, std::milli>(now - s.t_submit[i]).count());
                 Result r;
                 r.id = s.ids[i];
                 r.n_tracks = s.h_nt[i];
@@ -232,7 +243,8 @@ int apo_serve_create(const apo_geometry *g, const apo_serve_opts *opts, apo_serv
         return fail_msg(APO_EINVAL, "batch_events, max_slots and max_pending must be >= 1");
     if (o.solve.max_tracks < 1 || o.solve.max_tracks > APO_MAX_TRACKS)
         return fail_msg(APO_EINVAL, "solve.max_tracks out of range");
-    if (o.solve.hit_track || o.solve.trace_keys || o.solve.trace_votes)
+    if (o.solve.hit_track || o.solve.trace_keys || o.solve.trace_votes || o.solve.trace_count ||
+        o.solve.final_level || o.solve.n_final)
         return fail_msg(APO_EINVAL, "the server takes no per-batch device outputs (hit_track, trace)");
     int gdev = -1;
     geometry_device_tables(g, &gdev);
@@ -295,6 +307,7 @@ int apo_serve_submit(apo_server *sv, const int32_t *wire_id, const double *drift
     r.id = request_id;
     r.wid.assign(wire_id, wire_id + n_hits);
     r.drift.assign(drift, drift + n_hits);
+    r.t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         if (sv->error != APO_OK) return fail_msg(sv->error, sv->msg.c_str());
@@ -343,6 +356,27 @@ int apo_serve_stats(const apo_server *sv, int32_t *batches, int32_t *max_busy_sl
     std::lock_guard<std::mutex> lk(m->mu);
     if (batches) *batches = m->batches;
     if (max_busy_slots) *max_busy_slots = m->max_busy;
+    return APO_OK;
+}
+
+int apo_serve_latency(const apo_server *sv, double *p50_ms, double *p99_ms, int64_t *n_events) {
+    if (!sv) return fail_msg(APO_EINVAL, "server is NULL");
+    apo_server *m = const_cast<apo_server *>(sv);
+    std::vector<double> v;
+    {
+        std::lock_guard<std::mutex> lk(m->mu);
+        v = m->latency_ms;
+    }
+    std::sort(v.begin(), v.end());
+    auto rank = [&](double p) -> double {   // nearest rank: the ceil(p n)-th smallest
+        if (v.empty()) return 0.0;
+        size_t k = (size_t)std::ceil(p * (double)v.size());
+        if (k < 1) k = 1;
+        return v[k - 1];
+    };
+    if (p50_ms) *p50_ms = rank(0.50);
+    if (p99_ms) *p99_ms = rank(0.99);
+    if (n_events) *n_events = (int64_t)v.size();
     return APO_OK;
 }
 

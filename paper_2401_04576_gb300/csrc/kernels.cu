@@ -351,7 +351,9 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
                 if (mir) mirror_hit(h32);
                 Pre<float> p32 = prefix<float>(c32, h32, k);
                 n_pre32++;
-                if (!p32.guard) {
+                if (p32.novote) {
+                    lm = 0;
+                } else if (!p32.guard) {
                     lm = 0;
                     n_tail32 += Bl;
 #pragma unroll 1
@@ -381,6 +383,7 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
             if (mir) mirror_hit(h64);
             Pre<double> p64 = prefix<double>(c, h64, k);
             n_pre64++;
+            if (p64.novote) continue;
             if (p64.guard) {
                 add_votes(all);
                 continue;
@@ -547,15 +550,15 @@ k_vote_cells_mid(DevGeom g, const HitRecD *hd, const int32_t *n_hits, const uint
     if (parents) {
         uint64_t pk = parents[(long long)ev * (n_per_ev / 32) + j / 32];
         int idx[5], b = (int)(j % 32);
-        unpack_key(pk, idx);
+        unpack_key(g, pk, idx);
 #pragma unroll
         for (int a = 0; a < 5; a++) idx[a] = 2 * idx[a] + ((b >> a) & 1);
-        key = pack_key(idx);
+        key = pack_key(g, idx);
     } else {
         key = keys[(long long)ev * n_per_ev + j];
     }
     int idx[5];
-    unpack_key(key, idx);
+    unpack_key(g, key, idx);
     const long long o = (long long)ev * n_per_ev + j;
     bool valid = true;
 #pragma unroll
@@ -672,15 +675,21 @@ k_vote_cells(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_h
     if (parents) {
         uint64_t pk = parents[(long long)ev * (n_per_ev / 32) + j / 32];
         int idx[5], b = (int)(j % 32);
-        unpack_key(pk, idx);
+        unpack_key(g, pk, idx);
 #pragma unroll
         for (int a = 0; a < 5; a++) idx[a] = 2 * idx[a] + ((b >> a) & 1);
-        key = pack_key(idx);
-    } else {
+        key = pack_key(g, idx);
+    } else if (keys) {
         key = keys[(long long)ev * n_per_ev + j];
+    } else {   // the level-0 grid in linear order (d0 fastest)
+        int idx[5];
+        long long r = j;
+#pragma unroll
+        for (int a = 0; a < 5; a++) { idx[a] = (int)(r % g.bins[a]); r /= g.bins[a]; }
+        key = pack_key(g, idx);
     }
     int idx[5];
-    unpack_key(key, idx);
+    unpack_key(g, key, idx);
     long long o = (long long)ev * n_per_ev + j;
     bool valid = true;
 #pragma unroll
@@ -717,13 +726,17 @@ template <int MODE>
 __global__ void __launch_bounds__(256)
 k_vote_children(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
                 const uint32_t *active, int level, const uint64_t *parents, int n_par,
-                uint64_t *out_keys, int32_t *out_votes, unsigned *status) {
+                const int32_t *n_valid, uint64_t *out_keys, int32_t *out_votes, unsigned *status) {
     constexpr bool k64 = ModeOf<MODE>::k64, k32 = ModeOf<MODE>::k32;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *h64s = smem;
     unsigned char *h32s = smem + (k64 ? kHitCap * 80 : 0);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (k64 ? kHitCap * 80 : 0) + (k32 ? kHitCap * 80 : 0));
     const int ev = blockIdx.y;
+    // n_valid (may be null): parents 0 .. n_valid[ev] - 1 of the event's n_par slots are
+    // real; a block past them has nothing to do (the condition is uniform in the block)
+    const long long n_here = n_valid ? (long long)n_valid[ev] : (long long)n_par;
+    if ((long long)blockIdx.x * blockDim.x >= n_here * 16) return;
     int nh = n_hits[ev];
     if (nh < 0) nh = 0;
     const unsigned bytes = (unsigned)nh * 80u;
@@ -732,16 +745,16 @@ k_vote_children(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *
     __syncthreads();
     if (!ok) nh = 0;
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= (long long)n_par * 16) return;
+    if (j >= n_here * 16) return;
     const int b = (int)(j % 16);
     int idx[5];
-    unpack_key(parents[(long long)ev * n_par + j / 16], idx);
+    unpack_key(g, parents[(long long)ev * n_par + j / 16], idx);
 #pragma unroll
     for (int a = 0; a < 4; a++) idx[a] = 2 * idx[a] + ((b >> a) & 1);
     const int l0 = 2 * idx[4];                    // tan(lambda) bit 0 / 1 of the pair
     idx[4] = l0;
-    const uint64_t key0 = pack_key(idx);
-    const uint64_t key1 = key0 + (1ULL << 40);
+    const uint64_t key0 = pack_key(g, idx);
+    const uint64_t key1 = key0 + (1ULL << g.key_shift[4]);
     Cell<double> c{edge(g, 0, level, idx[0]), sin_phi0(g, level, idx[1]), cos_phi0(g, level, idx[1]),
                    edge(g, 2, level, idx[2]), edge(g, 3, level, idx[3]), edge(g, 4, level, l0)};
     const IV<double> L1 = edge(g, 4, level, l0 + 1);
@@ -764,7 +777,9 @@ k_vote_children(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *
             Hit<float> h32 = load_hit<float>(h32s + h * 80);
             if (mir) mirror_hit(h32);
             Pre<float> p32 = prefix<float>(c32, h32, k);
-            if (!p32.guard) {
+            if (p32.novote) {
+                lm = 0u;
+            } else if (!p32.guard) {
                 lm = (tail<float>(p32, c32.L, h32, R32, c32.W, k) ? 1u : 0u) |
                      (tail<float>(p32, L1f, h32, R32, c32.W, k) ? 2u : 0u);
             }
@@ -774,6 +789,7 @@ k_vote_children(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *
         Hit<double> h64 = load_hit<double>(h64s + h * 80);
         if (mir) mirror_hit(h64);
         Pre<double> p64 = prefix<double>(c, h64, k);
+        if (p64.novote) continue;
         if (p64.guard) { v0++; v1++; continue; }
         if (ModeOf<MODE>::exact) {
             if ((lm & 1u) && tail_exact(p64, c.L, h64, R, c.W, k)) v0++;
@@ -838,19 +854,20 @@ void launch_vote_keys(const DevGeom &g, int prec, int n_ev, const HitRecD *hd, c
 template <int MODE>
 static void launch_children_mode(const DevGeom &g, int n_ev, const HitRecD *hd, const HitRecF *hf,
                                  const int32_t *n_hits, const uint32_t *active, int level,
-                                 const uint64_t *parents, int n_par, uint64_t *out_keys,
-                                 int32_t *out_votes, cudaStream_t s, int block) {
+                                 const uint64_t *parents, int n_par, const int32_t *n_valid,
+                                 uint64_t *out_keys, int32_t *out_votes, cudaStream_t s, int block) {
     size_t sm = (ModeOf<MODE>::k64 ? kHitCap * 80 : 0) + (ModeOf<MODE>::k32 ? kHitCap * 80 : 0) + 16;
     smem_limit_once(k_vote_children<MODE>, g_attr_children[MODE]);
     dim3 grid((unsigned)(((long long)n_par * 16 + block - 1) / block), n_ev);
     k_vote_children<MODE><<<grid, block, sm, s>>>(g, hd, hf, n_hits, active, level, parents, n_par,
-                                                   out_keys, out_votes, nullptr);
+                                                   n_valid, out_keys, out_votes, nullptr);
 }
 
 void launch_vote_children(const DevGeom &g, int prec, int n_ev, const HitRecD *hd,
                           const HitRecF *hf, const int32_t *n_hits, int child_level,
                           const uint64_t *parents, int n_par, uint64_t *child_keys,
-                          int32_t *child_votes, cudaStream_t s, const uint32_t *active, int block) {
+                          int32_t *child_votes, cudaStream_t s, const uint32_t *active, int block,
+                          const int32_t *n_valid) {
     if (n_ev <= 0 || n_par <= 0) return;
     if (block != 128) block = 256;
     if (prec == APO_F64_MID) {   // children in the order of k_vote_children: 32 per parent
@@ -860,16 +877,16 @@ void launch_vote_children(const DevGeom &g, int prec, int n_ev, const HitRecD *h
     }
     if (prec == APO_F64_EXACT)
         launch_children_mode<kModeF64Exact>(g, n_ev, hd, hf, n_hits, active, child_level, parents, n_par,
-                                            child_keys, child_votes, s, block);
+                                            n_valid, child_keys, child_votes, s, block);
     else if (prec == APO_F32)
         launch_children_mode<kModeF32>(g, n_ev, hd, hf, n_hits, active, child_level, parents, n_par,
-                                       child_keys, child_votes, s, block);
+                                       n_valid, child_keys, child_votes, s, block);
     else if (prec == APO_F64_FILTERED)
         launch_children_mode<kModeF64Filtered>(g, n_ev, hd, hf, n_hits, active, child_level, parents, n_par,
-                                               child_keys, child_votes, s, block);
+                                               n_valid, child_keys, child_votes, s, block);
     else
         launch_children_mode<kModeF64>(g, n_ev, hd, hf, n_hits, active, child_level, parents, n_par,
-                                       child_keys, child_votes, s, block);
+                                       n_valid, child_keys, child_votes, s, block);
 }
 
 // Sets every vote kernel's dynamic shared-memory limit now, outside any stream capture.
@@ -979,7 +996,7 @@ k_select_coarse(DevGeom g, int ev0, const int32_t *votes, const uint32_t *hist, 
                 long long rr = j0 + r;
                 int idx[5];
                 for (int q = 0; q < 5; q++) { idx[q] = (int)(rr % g.bins[q]); rr /= g.bins[q]; }
-                ok_[pos] = pack_key(idx);
+                ok_[pos] = pack_key(g, idx);
                 ov[pos] = v[r];
             }
         }
@@ -1121,7 +1138,7 @@ k_estimate_mask(DevGeom g, const uint64_t *keys, const int32_t *votes, int n_in,
         for (int q = tid; q < cn * 5; q += blockDim.x) {
             const int j = q / 5, a = q - 5 * j;
             int idx[5];
-            unpack_key(s[c0 + j] & kKeyMask, idx);
+            unpack_key(g, s[c0 + j] & kKeyMask, idx);
             IV<double> ed = edge(g, a, level, idx[a]);
             s_cen[q] = __dmul_rn(__dadd_rn(ed.lo, ed.hi), 0.5);
             atomicMin(&s_lo[a], okey(ed.lo));
@@ -1156,7 +1173,7 @@ k_estimate_mask(DevGeom g, const uint64_t *keys, const int32_t *votes, int n_in,
         if (!((act0[i >> 5] >> (i & 31)) & 1u)) continue;
         if (!((act1[i >> 5] >> (i & 31)) & 1u)) continue;   // already masked by another cell
         int idx[5];
-        unpack_key(s[j] & kKeyMask, idx);
+        unpack_key(g, s[j] & kKeyMask, idx);
         Cell<double> c{edge(g, 0, level, idx[0]), sin_phi0(g, level, idx[1]), cos_phi0(g, level, idx[1]),
                        edge(g, 2, level, idx[2]), edge(g, 3, level, idx[3]), edge(g, 4, level, idx[4])};
         Hit<double> h = load_hit<double>(hd + (long long)e * kHitCap + i);
@@ -1221,19 +1238,19 @@ void launch_hist(int n_ev, const int32_t *votes, long long n, uint32_t *hist, cu
 }
 
 // 32 children of each key (level + 1)
-__global__ void k_children(const uint64_t *keys, long long n, uint64_t *out) {
+__global__ void k_children(DevGeom g, const uint64_t *keys, long long n, uint64_t *out) {
     long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n * 32) return;
     int idx[5], b = (int)(j % 32);
-    unpack_key(keys[j / 32], idx);
+    unpack_key(g, keys[j / 32], idx);
 #pragma unroll
     for (int a = 0; a < 5; a++) idx[a] = 2 * idx[a] + ((b >> a) & 1);
-    out[j] = pack_key(idx);
+    out[j] = pack_key(g, idx);
 }
 
-void launch_children(const uint64_t *keys, long long n, uint64_t *out, cudaStream_t s) {
+void launch_children(const DevGeom &g, const uint64_t *keys, long long n, uint64_t *out, cudaStream_t s) {
     if (n <= 0) return;
-    k_children<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(keys, n, out);
+    k_children<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(g, keys, n, out);
 }
 
 }  // namespace apo

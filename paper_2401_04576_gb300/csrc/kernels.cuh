@@ -25,7 +25,9 @@ struct DevGeom {
     long long sincos_off[kMaxLevels + 1];
     const double *sincos_mid;       // (sin, cos) at each phi0 cell's centre, same rows; may be null
     const double *wire[8];          // x0, y0, sin phis, cos phis, tan tau, sphi*t, cphi*t, t^2
-    SeriesConsts k;
+    SeriesConsts k;                 // k.outgoing: set per call from the precision's flag bit
+    int key_shift[5];               // cell key layout: idx_a << key_shift[a], key_bits[a] wide
+    int key_bits[5];
 };
 
 // One hit as staged for the vote kernels: 80 bytes, a multiple of 16 so an event's hits
@@ -80,15 +82,17 @@ template <> __device__ __forceinline__ Hit<float> load_hit<float>(const void *re
     return h;
 }
 
-__device__ __forceinline__ uint64_t pack_key(const int idx[5]) {
+// Cell key: idx_a << key_shift[a]; axis a is key_bits[a] = max(10, ceil(log2(bins_a <<
+// levels))) wide, d0 lowest, so the level-0 linear order (d0 fastest) is the key order.
+__device__ __forceinline__ uint64_t pack_key(const DevGeom &g, const int idx[5]) {
     uint64_t k = 0;
 #pragma unroll
-    for (int a = 0; a < 5; a++) k |= (uint64_t)idx[a] << (10 * a);
+    for (int a = 0; a < 5; a++) k |= (uint64_t)idx[a] << g.key_shift[a];
     return k;
 }
-__device__ __forceinline__ void unpack_key(uint64_t k, int idx[5]) {
+__device__ __forceinline__ void unpack_key(const DevGeom &g, uint64_t k, int idx[5]) {
 #pragma unroll
-    for (int a = 0; a < 5; a++) idx[a] = (int)((k >> (10 * a)) & 1023u);
+    for (int a = 0; a < 5; a++) idx[a] = (int)((k >> g.key_shift[a]) & ((1u << g.key_bits[a]) - 1u));
 }
 
 // Status words written by kernels (bit flags, OR-ed into a device word).
@@ -112,7 +116,7 @@ void launch_vote_children(const DevGeom &g, int prec, int n_ev, const HitRecD *h
                           const HitRecF *hf, const int32_t *n_hits, int child_level,
                           const uint64_t *parents, int n_par, uint64_t *child_keys,
                           int32_t *child_votes, cudaStream_t s, const uint32_t *active = nullptr,
-                          int block = 256);
+                          int block = 256, const int32_t *n_valid = nullptr);
 void init_kernel_attributes();
 void launch_wait_never(long limit, unsigned *status, cudaStream_t s);
 void launch_select_coarse(const DevGeom &g, int ev0, int n_ev, const int32_t *votes,
@@ -128,6 +132,30 @@ void launch_estimate_mask(const DevGeom &g, int n_ev, const uint64_t *keys, cons
                           apo_track *out, int32_t *n_tracks, cudaStream_t s,
                           const int32_t *offsets = nullptr, int32_t *hit_track = nullptr);
 void launch_series_consts(SeriesConsts *dev_out, cudaStream_t s);
+
+// maxset.cu: one level of the max-set schedule for n_ev events (pointers already offset to
+// the first of them).  votes / keys: the level's cells, stride cells per event (keys null:
+// the level-0 grid in linear order, n_coarse per event); count_in (levels >= 1): parents of
+// each event, so 32 x count_in[e] children.  Writes the kept cells to front (max_keep per
+// event) and their number to count_out, or, at the end of an event's search, its track,
+// n_tracks (1 when vmax >= min_votes), final_level and n_final, and sets stop.
+struct MaxsetArgs {
+    int level, levels, max_keep, slack, min_votes;
+    long long n_coarse, stride;
+    const int32_t *votes;
+    const uint64_t *keys;
+    const int32_t *count_in;
+    uint64_t *front;
+    int32_t *count_out, *stop;
+    const int32_t *n_hits;
+    apo_track *tracks;
+    int32_t *n_tracks, *final_level, *n_final;
+    uint64_t *trace_keys;          // may be null: events x (levels + 1) x max_keep
+    int32_t *trace_votes, *trace_count;
+};
+size_t maxset_smem_bytes(const DevGeom &g);
+void launch_maxset_select(const DevGeom &g, int n_ev, const MaxsetArgs &A, cudaStream_t s);
+void init_maxset_attributes();
 double pipe_peak(int precision, int op);   // diag.cu: directed operations per second
 int launch_dops(int op, const double *x, double *out, long long n, cudaStream_t s);   // diag.cu
 int launch_pair_ends(const SeriesConsts &k, int precision, const double *cells, const double *hits,
@@ -138,6 +166,6 @@ int launch_pair_ends(const SeriesConsts &k, int precision, const double *cells, 
 const DevGeom *geometry_device_tables(const apo_geometry *g, int *device);
 void set_last_error(const char *msg);
 void launch_hist(int n_ev, const int32_t *votes, long long n, uint32_t *hist, cudaStream_t s);
-void launch_children(const uint64_t *keys, long long n, uint64_t *out, cudaStream_t s);
+void launch_children(const DevGeom &g, const uint64_t *keys, long long n, uint64_t *out, cudaStream_t s);
 
 }  // namespace apo

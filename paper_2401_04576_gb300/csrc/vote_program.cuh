@@ -20,6 +20,9 @@ namespace apo {
 struct SeriesConsts {
     double d_lo[16], d_hi[16];
     float f_lo[16], f_hi[16];
+    // Not a series constant: 1 applies the direction condition of the program (a hit votes
+    // only where it can lie on the track's outgoing arc); set per call by the host.
+    int outgoing;
 };
 enum { C_ATAN0 = 0 /* 1/(2k+1), k = 0..8 */, C_SIN3 = 9, C_SIN5 = 10, C_SIN7 = 11,
        C_COS4 = 12, C_COS6 = 13, C_REM9 = 14, C_REM8 = 15 };
@@ -106,6 +109,7 @@ __device__ __forceinline__ void sincos_iv(IV<T> d, IV<T> &s, IV<T> &c, const Ser
 // Everything of the program that does not depend on tan(lambda).
 template <typename T> struct Pre {
     bool guard;                       // a divisor reached 0: the pair votes (sound)
+    bool novote;                      // direction condition: the hit is upstream everywhere
     IV<T> G0, psi, N, Ninv, sPA, cPA, rsA, rcA, sin2, Nh, dW, psi_sPA, dW_cPA, inner_e,
           psi_cos2, onepN;
 };
@@ -116,12 +120,16 @@ __device__ __forceinline__ Pre<T> prefix(const Cell<T> &c, const Hit<T> &h, cons
     const IV<T> one{T(1), T(1)};
     Pre<T> p;
     p.guard = false;
+    p.novote = false;
     // wire point in the reference plane z_ref = z0 (Eqs. EQSinter_d,e)
     IV<T> Xw = add(h.x0, mul(c.Z, h.spt));
     IV<T> Yw = sub(h.y0, mul(c.Z, h.cpt));
     // coordinates along the tangent / left normal of the helix at the POCA
     IV<T> wt = add(mul(Xw, c.C0), mul(Yw, c.S0));
     IV<T> wn = sub(mul(Yw, c.C0), mul(Xw, c.S0));
+    // direction: the turning angle psi from the POCA to the hit has the sign of w_t (rho > 0);
+    // a hit with w_t < 0 over the whole cell lies upstream of every helix in it
+    if (k.outgoing && lt0(wt.hi)) { p.novote = true; return p; }
     IV<T> V = sub(wn, c.D);
     // xi = rho (x^Ax - x_c, y^Ax - y_c); |xi| = rho R_i^Ax
     IV<T> Xt = mul_nn(wt, c.W);
@@ -241,6 +249,7 @@ __device__ __forceinline__ bool vote_pair_ends(Cell<T> c, Hit<T> h, const Series
     if (le0(c.W.lo)) { ends[4] = 1; return true; }
     IV<T> R = recip(c.W);
     Pre<T> p = prefix(c, h, k);
+    if (p.novote) { ends[4] = 2; return false; }
     if (p.guard) { ends[4] = 1; return true; }
     return tail<T, 0, true>(p, c.L, h, R, c.W, k, ends);
 }
@@ -252,6 +261,7 @@ __device__ __forceinline__ bool vote_pair(Cell<T> c, Hit<T> h, const SeriesConst
     if (le0(c.W.lo)) return true;
     IV<T> R = recip(c.W);
     Pre<T> p = prefix(c, h, k);
+    if (p.novote) return false;
     if (p.guard) return true;
     return tail(p, c.L, h, R, c.W, k);
 }
@@ -350,6 +360,7 @@ __device__ __forceinline__ bool vote_pair_exact(Cell<double> c, Hit<double> h, c
     if (le0(c.W.lo)) return true;
     const IV<double> R = recip(c.W);
     const Pre<double> p = prefix(c, h, k);
+    if (p.novote) return false;
     if (p.guard) return true;
     return tail_exact(p, c.L, h, R, c.W, k);
 }
