@@ -268,7 +268,7 @@ def truth_recovery(g, level_of, tracks_p, tracks_w, truth) -> dict:
 
 def maxset_leg(w, ev, steps: int, flush, world: int = 1, per_event: int = 32) -> dict:
     """The max-set schedule on the anisotropic grid: events/s of the FP32-bulk form (FP32
-    levels 0-3, FP64 levels 4-5) and of the plain FP64 form (every level FP64), both with
+    levels 0-4, FP64 on the last level) and of the plain FP64 form (every level FP64), both with
     the direction condition; (cell, hit) pairs evaluated per second; the truth recovery of
     each; and the plain FP64 form one event per call (the per-event path: latency and
     events/s)."""
@@ -284,7 +284,7 @@ def maxset_leg(w, ev, steps: int, flush, world: int = 1, per_event: int = 32) ->
     stream = torch.cuda.current_stream()
     out = {"workload": MAXSET["name"], "n_events": ne, "coarse_cells": geom.n_coarse,
            "levels": lv, "max_keep": K}
-    forms = {"fp32_bulk": [apo.F32 | apo.OUTGOING] * 4 + [apo.F64 | apo.OUTGOING] * 2,
+    forms = {"fp32_bulk": [apo.F32 | apo.OUTGOING] * lv + [apo.F64 | apo.OUTGOING],
              "fp64": [apo.F64 | apo.OUTGOING] * (lv + 1)}
     for name, prec in forms.items():
         fl = torch.zeros(ne, dtype=torch.int32, device="cuda")
@@ -312,7 +312,7 @@ def maxset_leg(w, ev, steps: int, flush, world: int = 1, per_event: int = 32) ->
         # cells voted per event: the level-0 grid, then 32 children of every kept cell
         cells = geom.n_coarse + 32.0 * kept.sum(axis=1)
         pairs = float(np.sum(cells * nh))
-        out[name] = {"precision": ("FP32 levels 0-3, FP64 levels 4-5" if name == "fp32_bulk"
+        out[name] = {"precision": ("FP32 levels 0-4, FP64 level 5" if name == "fp32_bulk"
                                    else "FP64 at every level") + ", direction condition",
                      "ms_per_step": t, "events_per_s": ne * world / (t * 1e-3),
                      "pairs_evaluated_per_s": pairs * world / (t * 1e-3),

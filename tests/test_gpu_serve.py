@@ -65,7 +65,9 @@ def test_same_result_alone_and_in_the_mix(setup):
     assert srv.drain(60000) == apo.APO_OK
     mix = _collect(srv, len(evs))
     batches, max_busy = srv.stats()
+    p50, p99, n_lat = srv.latency()      # measured inside the library, every finished event
     srv.close()
+    assert n_lat == 2 * len(evs) and 0.0 < p50 <= p99
     assert len(alone) == len(evs) and len(mix) == len(evs)
     for e in range(len(evs)):
         ta, na = alone[e]
@@ -118,3 +120,22 @@ def test_injected_batch_failure_is_reported(setup):
     tr, nt = apo.solve_batch(geom, apo.DeviceHits.from_events(ev.subset([0])), solve)
     torch.cuda.synchronize()
     assert int(nt.cpu()[0]) >= 0
+
+
+def test_max_set_schedule_through_the_server(setup):
+    """The max-set schedule with the direction condition served: each event's track is
+    the one apo_solve_batch gives for the whole set."""
+    geom, ev, _ = setup
+    lv = geom.levels
+    solve = apo.solve_opts(precision=[apo.F32 | apo.OUTGOING] * (lv - 1) + [apo.F64 | apo.OUTGOING] * 2,
+                           schedule=apo.SCHED_MAXSET, max_keep=4096)
+    tr, nt = apo.solve_batch(geom, apo.DeviceHits.from_events(ev), solve)
+    ref = apo.tracks_to_numpy(tr, ev.n_events)
+    srv = apo.Server(geom, solve, batch_events=4, max_slots=3)
+    for e, (w, d) in enumerate(_events(ev)):
+        assert srv.submit(w, d, e) == apo.APO_OK
+    assert srv.drain(60000) == apo.APO_OK
+    got = _collect(srv, ev.n_events)
+    srv.close()
+    for e in range(ev.n_events):
+        assert np.array_equal(got[e][0].view(np.uint8), ref[e].view(np.uint8)), e
