@@ -146,6 +146,12 @@ typedef struct {
     int32_t cells_filter;    /* 1: the same for the bisected cells of levels >= 1 */
     int32_t cells_block;     /* threads per block of the cell-voting kernel: 128 or 256 */
     int32_t chunk_events;    /* events per level-0 launch (at most the workspace's chunk) */
+    int32_t persistent;      /* 1 (APO_SCHED_TOPK only): one persistent launch for the whole
+                                batch; each block pulls the next event from a device counter
+                                and runs its whole search (every round, tile and level),
+                                instead of one launch per step and level.  Levels must share
+                                their APO_OUTGOING flag and use APO_F64, APO_F32 or
+                                APO_F64_FILTERED; no trace. */
 } apo_tune;
 
 /* Options of apo_solve_batch.  precision[L] selects FP64 or FP32 intervals at level L
@@ -236,7 +242,9 @@ int apo_solve_batch(const apo_geometry *geom, const apo_hits *hits, const apo_so
 
 /* Times apo_solve_batch on `hits` (typically a sample of the batch to come) for every
  * combination of the apo_tune knobs and writes the fastest to *best (its time to *best_ms,
- * may be NULL).  opts: as for apo_solve_batch (its tune and use_graph are ignored).
+ * may be NULL): the launch schedule (per-level launches, or the persistent launch when
+ * the options allow it), the FP32-first filters, the threads per block of the bisected
+ * cells' kernel and the events per level-0 launch.  opts: as for apo_solve_batch (its tune and use_graph are ignored).
  * Workspace as for apo_solve_batch.  Synchronous. */
 int apo_autotune(const apo_geometry *geom, const apo_hits *hits, const apo_solve_opts *opts,
                  void *workspace, size_t workspace_bytes, void *stream, apo_tune *best,

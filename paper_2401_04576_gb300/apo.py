@@ -47,7 +47,8 @@ class ApoHits(C.Structure):
 
 class ApoTune(C.Structure):
     _fields_ = [("coarse_filter", C.c_int32), ("cells_filter", C.c_int32),
-                ("cells_block", C.c_int32), ("chunk_events", C.c_int32)]
+                ("cells_block", C.c_int32), ("chunk_events", C.c_int32),
+                ("persistent", C.c_int32)]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -327,7 +328,14 @@ def autotune(geom: Geometry, hits: DeviceHits, opts: ApoSolveOpts | None = None,
              stream=None):
     """apo_autotune: the fastest execution knobs for this batch (results never change)."""
     o = opts if opts is not None else solve_opts()
-    ws = geom.workspace(hits.n_events, opts=o) if workspace is None else workspace
+    if workspace is None:   # room for every candidate, the persistent launch's scratch included
+        op = ApoSolveOpts.from_buffer_copy(o)
+        op.tune.persistent = 1
+        torch = _torch()
+        ws = torch.empty(max(geom.workspace_bytes(hits.n_events, o),
+                             geom.workspace_bytes(hits.n_events, op)), dtype=torch.uint8, device="cuda")
+    else:
+        ws = workspace
     best = ApoTune()
     ms = C.c_float()
     hc = hits.c()

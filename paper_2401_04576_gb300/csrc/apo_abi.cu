@@ -58,6 +58,7 @@ struct apo_geometry {
     DevGeom dg;
     int device;
     long long n_coarse;
+    int persist_blocks = 0;              // blocks of the persistent launch (all resident)
     std::vector<void *> allocs;
     std::mutex graph_mu;                 // guards the two members below
     std::vector<GraphEntry> graphs;
@@ -69,7 +70,7 @@ namespace {
 // Workspace regions for a batch of n_events.
 struct Layout {
     size_t status, n_hits, hd, hf, votes, hist, fk, fv, ck, cv, mask, done, ntr, tune_tracks;
-    size_t ms_front, ms_count, ms_stop, ms_ck, ms_cv, end;
+    size_t ms_front, ms_count, ms_stop, ms_ck, ms_cv, p_votes, p_hist, p_next, end;
     int chunk, ms_chunk;
 };
 
@@ -107,6 +108,13 @@ Layout layout(const apo_geometry *g, int n_events, const apo_solve_opts *opts = 
     L.tune_tracks = o; o = align256(o + sizeof(apo_track) * (size_t)n_events * APO_MAX_TRACKS);
     L.ms_chunk = 0;
     L.ms_front = L.ms_count = L.ms_stop = L.ms_ck = L.ms_cv = o;
+    L.p_votes = L.p_hist = L.p_next = o;
+    if (opts && opts->schedule == APO_SCHED_TOPK && opts->tune.persistent) {
+        const size_t B = (size_t)(g->persist_blocks > 0 ? g->persist_blocks : 1);
+        L.p_votes = o; o = align256(o + sizeof(int32_t) * B * (size_t)g->n_coarse);
+        L.p_hist = o; o = align256(o + sizeof(uint32_t) * B * kHistBins);
+        L.p_next = o; o = align256(o + sizeof(int32_t));
+    }
     if (opts && opts->schedule == APO_SCHED_MAXSET && opts->max_keep > 0) {
         const size_t K = (size_t)opts->max_keep;
         const int c = maxset_chunk(L, opts->max_keep);
@@ -288,6 +296,7 @@ int apo_geometry_create(const apo_wires *w, const apo_grid *gr, apo_geometry **o
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaMemcpy(&d.k, dk, sizeof(SeriesConsts), cudaMemcpyDeviceToHost);
             d.k.outgoing = 0;
+            g->persist_blocks = persist_blocks(d);
             cudaFree(dk);
         }
         if (e != cudaSuccess) rc = fail(APO_ECUDA, "series constants: %s", cudaGetErrorString(e));
@@ -444,6 +453,17 @@ int validate_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_
             return fail(APO_EINVAL, "APO_SCHED_MAXSET needs sum_a bins[a] << levels <= 16384");
     } else if (o->schedule == APO_SCHED_TOPK) {
         if (key_bits_total(g->dg) > 50) return fail(APO_EINVAL, "APO_SCHED_TOPK needs keys of at most 50 bits");
+        if (o->tune.persistent) {
+            for (int i = 0; i <= lv; i++) {
+                const int p = o->precision[i] & ~APO_OUTGOING;
+                if (p != APO_F64 && p != APO_F32 && p != APO_F64_FILTERED)
+                    return fail(APO_EINVAL, "the persistent launch takes APO_F64, APO_F32 or APO_F64_FILTERED");
+                if ((o->precision[i] & APO_OUTGOING) != (o->precision[0] & APO_OUTGOING))
+                    return fail(APO_EINVAL, "the persistent launch needs one APO_OUTGOING setting for all levels");
+            }
+            if (o->trace_keys || o->trace_votes) return fail(APO_EINVAL, "the persistent launch writes no trace");
+            if (g->dg.topk * 32 > 4096) return fail(APO_EINVAL, "topk too large for the persistent launch");
+        }
         if (o->trace_count || o->final_level || o->n_final)
             return fail(APO_EINVAL, "trace_count / final_level / n_final belong to APO_SCHED_MAXSET");
     } else {
@@ -569,6 +589,41 @@ int enqueue_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_o
     for (int lev = 0; lev <= lv; lev++) gl[lev] = geom_for(g, o->precision[lev]);
     if (o->schedule == APO_SCHED_MAXSET)
         return enqueue_maxset(g, hits, o, gl, prec_at, tracks_out, n_tracks_out, ws, L, s);
+    if (o->tune.persistent) {
+        CU(cudaMemsetAsync(status, 0, 256, s));
+        launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, active, done, status, s,
+                     o->hit_track);
+        if ((rc = check_launch("stage"))) return rc;
+        CU(cudaMemsetAsync(at<int32_t>(ws, L.p_next), 0, sizeof(int32_t), s));
+        PersistArgs A{};
+        A.n_events = ne;
+        A.max_tracks = o->max_tracks;
+        A.min_votes = o->min_votes;
+        A.width = width;
+        auto mode_of = [](int p) {
+            return p == APO_F32 ? kPersistF32 : (p == APO_F64_FILTERED ? kPersistF64Filtered : kPersistF64);
+        };
+        for (int lev = 0; lev <= lv; lev++) A.mode[lev] = mode_of(prec_at(lev));
+        A.hd = hd;
+        A.hf = hf;
+        A.n_hits = nh;
+        A.offsets = hits->offsets;
+        A.active = active;
+        A.done = done;
+        A.next_event = at<int32_t>(ws, L.p_next);
+        A.status = status;
+        A.votes = at<int32_t>(ws, L.p_votes);
+        A.hist = at<uint32_t>(ws, L.p_hist);
+        A.fk = fk;
+        A.fv = fv;
+        A.ck = ck;
+        A.cv = cv;
+        A.tracks = tracks_out;
+        A.n_tracks = ntr;
+        A.hit_track = o->hit_track;
+        launch_solve_persistent(gl[0], g->persist_blocks, A, s);
+        return check_launch("solve_persistent");
+    }
     CU(cudaMemsetAsync(status, 0, 256, s));
     launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, active, done, status, s,
                  o->hit_track);
@@ -697,17 +752,32 @@ int apo_autotune(const apo_geometry *g, const apo_hits *hits, const apo_solve_op
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     const int chunks[2] = {0, L.chunk > 4 ? L.chunk / 4 : 0};
+    // the persistent launch is a candidate when the options allow it (and the workspace
+    // holds its per-block scratch)
+    bool try_persistent = false;
+    {
+        apo_solve_opts op = o;
+        op.tune.persistent = 1;
+        Layout Lp;
+        char keep[sizeof(g_err)];
+        std::memcpy(keep, g_err, sizeof(g_err));
+        try_persistent = validate_solve(g, hits, &op, tt, ws, ws_bytes, Lp) == APO_OK;
+        std::memcpy(g_err, keep, sizeof(g_err));
+    }
+    for (int ps = 0; ps < 2; ps++)
     for (int cf = 0; cf < 2; cf++)
         for (int lf = 0; lf < 2; lf++)
             for (int bs = 0; bs < 2; bs++)
                 for (int ch = 0; ch < 2; ch++) {
                     if (ch == 1 && chunks[1] == 0) continue;
-                    apo_tune t{cf, lf, bs ? 128 : 256, chunks[ch]};
+                    if (ps == 1 && (!try_persistent || bs == 1 || ch == 1)) continue;   // no block / chunk knob
+                    apo_tune t{cf, lf, bs ? 128 : 256, chunks[ch], ps};
                     o.tune = t;
                     float ms = 0.f;
+                    Layout Lt = layout(g, hits->n_events, &o);
                     for (int rep = 0; rep < 2 && rc == APO_OK; rep++) {   // warm-up, then timed
                         if (rep == 1) cudaEventRecord(e0, s);
-                        rc = enqueue_solve(g, hits, &o, tt, nullptr, ws, L, s);
+                        rc = enqueue_solve(g, hits, &o, tt, nullptr, ws, Lt, s);
                         if (rep == 1) cudaEventRecord(e1, s);
                     }
                     if (rc != APO_OK) break;

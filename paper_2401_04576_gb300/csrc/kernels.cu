@@ -20,6 +20,9 @@ __device__ __forceinline__ unsigned smem_u32(const void *p) {
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
@@ -230,22 +233,21 @@ template <int MODE> struct CoarseShape {
     static constexpr int min_blocks = MODE == kModeF32 ? APO_F32_COARSE_MIN_BLOCKS : APO_F64_COARSE_MIN_BLOCKS;
 };
 
+// One block's work: part `part` (of `split`) of the (phi0 bin p, omega bin w) tile of event
+// ev; votes to vo (the event's level-0 votes), the histogram added to hist_e.  Shared by
+// k_vote_coarse (one tile per block) and the persistent batch kernel (tiles in a loop);
+// any block size of at least one warp works (threads past the part's cells idle).
 template <int MODE>
-__global__ void __launch_bounds__(CoarseShape<MODE>::threads, CoarseShape<MODE>::min_blocks)
-k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
-              const uint32_t *active, int32_t *votes, uint32_t *hist, unsigned *status,
-              unsigned long long *ctr) {
+__device__ __forceinline__ void coarse_block(const DevGeom &g, int ev, int split, int part, int p, int w,
+                                             const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
+                                             const uint32_t *active, int32_t *vo, uint32_t *hist_e,
+                                             unsigned *status, unsigned long long *ctr, unsigned char *smem) {
     using S = CoarseSmem<MODE>;
     constexpr bool k64 = S::k64, k32 = S::k32;
-    constexpr int split = CoarseShape<MODE>::split;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int Bd = g.bins[0], Bp = g.bins[1], Bw = g.bins[2], Bz = g.bins[3], Bl = g.bins[4];
+    const int Bd = g.bins[0], Bz = g.bins[3], Bl = g.bins[4];
     const int ntile = Bd * Bz;                    // (d0, z0) cells of one (phi0, omega) tile
     const int per = (ntile + split - 1) / split;  // of them in this block
     const int nthr = blockDim.x;
-    const int e = blockIdx.y, ev = ev0 + e;
-    const int part = blockIdx.x % split, pw = blockIdx.x / split;
-    const int p = pw % Bp, w = pw / Bp;
     const int tid = threadIdx.x;
     const int c0 = part * per, c1 = c0 + per < ntile ? c0 + per : ntile;   // this block's cells
     const bool has_cell = c0 + tid < c1;
@@ -270,6 +272,7 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
     bool ok = stage_to_smem(h64s, hd + (long long)ev * kHitCap, k64 ? bytes : 0u, h32s,
                             hf + (long long)ev * kHitCap, k32 ? bytes : 0u, bar, status);
     __syncthreads();
+    if (tid == 0) mbar_inval(bar);   // the barrier's memory may be set up again by a later call
     if (!ok) nh = 0;
 
     const SeriesConsts &k = g.k;
@@ -400,8 +403,7 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
             add_votes(v64);
         }
     }
-    const long long ncell = (long long)Bd * Bp * Bw * Bz * Bl;
-    int32_t *vo = votes + (long long)e * ncell;
+    const int Bp = g.bins[1], Bw = g.bins[2];
     for (int l = 0; l < Bl && has_cell; l++) {
         int v = 0;
 #pragma unroll
@@ -412,7 +414,7 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
     }
     __syncthreads();
     for (int i = tid; i < kHistBins; i += nthr)
-        if (hist_s[i]) atomicAdd(&hist[(long long)e * kHistBins + i], hist_s[i]);
+        if (hist_s[i]) atomicAdd(&hist_e[i], hist_s[i]);
     if (ctr) {   // work counters (diagnostics): FP64 parent / prefix / tail, -, FP32 ones
         unsigned long long v[6] = {n_par64, n_pre64, n_tail64, n_par32, n_pre32, n_tail32};
         const int slot[6] = {0, 1, 2, 4, 5, 6};
@@ -423,6 +425,22 @@ k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const in
             if ((tid & 31) == 0 && x) atomicAdd(&ctr[slot[i]], x);
         }
     }
+    __syncthreads();   // shared memory is reused by the caller's next step
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(CoarseShape<MODE>::threads, CoarseShape<MODE>::min_blocks)
+k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
+              const uint32_t *active, int32_t *votes, uint32_t *hist, unsigned *status,
+              unsigned long long *ctr) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int split = CoarseShape<MODE>::split;
+    const int e = blockIdx.y;
+    const int part = blockIdx.x % split, pw = blockIdx.x / split;
+    const int p = pw % g.bins[1], w = pw / g.bins[1];
+    const long long ncell = (long long)g.bins[0] * g.bins[1] * g.bins[2] * g.bins[3] * g.bins[4];
+    coarse_block<MODE>(g, ev0 + e, split, part, p, w, hd, hf, n_hits, active, votes + (long long)e * ncell,
+                              hist + (long long)e * kHistBins, status, ctr, smem);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -722,33 +740,19 @@ k_vote_cells(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_h
 // Children of kept cells, two per thread: the children 2 idx + bit of a parent that differ
 // only in the tan(lambda) bit share every tan(lambda)-free step of the program, so one
 // prefix per hit serves both tails (same operations as evaluating them apart).
+// One thread's pair j of an event: children 2 idx + bit of parent j / 16 for the bit pattern
+// b = j % 16 on d0 .. z0, with tan(lambda) bit 0 and 1 (slots 32 (j / 16) + b and + 16 of the
+// event's outputs).  h64s / h32s: the event's hits staged in shared memory; parents_e,
+// out_keys_e, out_votes_e: the event's arrays.
 template <int MODE>
-__global__ void __launch_bounds__(256)
-k_vote_children(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
-                const uint32_t *active, int level, const uint64_t *parents, int n_par,
-                const int32_t *n_valid, uint64_t *out_keys, int32_t *out_votes, unsigned *status) {
+__device__ __forceinline__ void children_pair(const DevGeom &g, const unsigned char *h64s,
+                                              const unsigned char *h32s, int nh, const uint32_t *act,
+                                              int level, const uint64_t *parents_e, long long j,
+                                              uint64_t *out_keys_e, int32_t *out_votes_e) {
     constexpr bool k64 = ModeOf<MODE>::k64, k32 = ModeOf<MODE>::k32;
-    extern __shared__ __align__(16) unsigned char smem[];
-    unsigned char *h64s = smem;
-    unsigned char *h32s = smem + (k64 ? kHitCap * 80 : 0);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (k64 ? kHitCap * 80 : 0) + (k32 ? kHitCap * 80 : 0));
-    const int ev = blockIdx.y;
-    // n_valid (may be null): parents 0 .. n_valid[ev] - 1 of the event's n_par slots are
-    // real; a block past them has nothing to do (the condition is uniform in the block)
-    const long long n_here = n_valid ? (long long)n_valid[ev] : (long long)n_par;
-    if ((long long)blockIdx.x * blockDim.x >= n_here * 16) return;
-    int nh = n_hits[ev];
-    if (nh < 0) nh = 0;
-    const unsigned bytes = (unsigned)nh * 80u;
-    bool ok = stage_to_smem(h64s, hd + (long long)ev * kHitCap, k64 ? bytes : 0u, h32s,
-                            hf + (long long)ev * kHitCap, k32 ? bytes : 0u, bar, status);
-    __syncthreads();
-    if (!ok) nh = 0;
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_here * 16) return;
     const int b = (int)(j % 16);
     int idx[5];
-    unpack_key(g, parents[(long long)ev * n_par + j / 16], idx);
+    unpack_key(g, parents_e[j / 16], idx);
 #pragma unroll
     for (int a = 0; a < 4; a++) idx[a] = 2 * idx[a] + ((b >> a) & 1);
     const int l0 = 2 * idx[4];                    // tan(lambda) bit 0 / 1 of the pair
@@ -767,7 +771,6 @@ k_vote_children(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *
     const IV<double> R = recip(c.W);
     const IV<float> R32 = recip(c32.W);
     const SeriesConsts &k = g.k;
-    const uint32_t *act = active ? active + (long long)ev * 8 : nullptr;
     int v0 = 0, v1 = 0;
     for (int h = 0; h < nh; h++) {
         if (act && !((act[h >> 5] >> (h & 31)) & 1u)) continue;
@@ -800,11 +803,40 @@ k_vote_children(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *
         }
     }
     // output order: child b at 32 j' + b, child b + 16 at 32 j' + b + 16 (j' = parent)
-    const long long o = (long long)ev * n_par * 32 + (j / 16) * 32 + b;
-    out_keys[o] = key0;
-    out_votes[o] = v0;
-    out_keys[o + 16] = key1;
-    out_votes[o + 16] = v1;
+    const long long o = (j / 16) * 32 + b;
+    out_keys_e[o] = key0;
+    out_votes_e[o] = v0;
+    out_keys_e[o + 16] = key1;
+    out_votes_e[o + 16] = v1;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256)
+k_vote_children(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
+                const uint32_t *active, int level, const uint64_t *parents, int n_par,
+                const int32_t *n_valid, uint64_t *out_keys, int32_t *out_votes, unsigned *status) {
+    constexpr bool k64 = ModeOf<MODE>::k64, k32 = ModeOf<MODE>::k32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char *h64s = smem;
+    unsigned char *h32s = smem + (k64 ? kHitCap * 80 : 0);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (k64 ? kHitCap * 80 : 0) + (k32 ? kHitCap * 80 : 0));
+    const int ev = blockIdx.y;
+    // n_valid (may be null): parents 0 .. n_valid[ev] - 1 of the event's n_par slots are
+    // real; a block past them has nothing to do (the condition is uniform in the block)
+    const long long n_here = n_valid ? (long long)n_valid[ev] : (long long)n_par;
+    if ((long long)blockIdx.x * blockDim.x >= n_here * 16) return;
+    int nh = n_hits[ev];
+    if (nh < 0) nh = 0;
+    const unsigned bytes = (unsigned)nh * 80u;
+    bool ok = stage_to_smem(h64s, hd + (long long)ev * kHitCap, k64 ? bytes : 0u, h32s,
+                            hf + (long long)ev * kHitCap, k32 ? bytes : 0u, bar, status);
+    __syncthreads();
+    if (!ok) nh = 0;
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_here * 16) return;
+    children_pair<MODE>(g, h64s, h32s, nh, active ? active + (long long)ev * 8 : nullptr, level,
+                        parents + (long long)ev * n_par, j, out_keys + (long long)ev * n_par * 32,
+                        out_votes + (long long)ev * n_par * 32);
 }
 
 template <int MODE>
@@ -920,18 +952,20 @@ void init_kernel_attributes() {
 constexpr int kSelThreads = 1024;
 constexpr int kSelTile = 4 * kSelThreads;
 
-__global__ void __launch_bounds__(kSelThreads)
-k_select_coarse(DevGeom g, int ev0, const int32_t *votes, const uint32_t *hist, int K,
-                uint64_t *out_keys, int32_t *out_votes) {
+// One event's selection by one block of any multiple-of-32 size (tiles of 4 cells per
+// thread): vo = the event's level-0 votes, hist_e its histogram, ok_ / ov its K outputs.
+__device__ __forceinline__ void select_coarse_block(const DevGeom &g, const int32_t *vo, const uint32_t *hist_e,
+                                                    int K, uint64_t *ok_, int32_t *ov) {
     __shared__ int s_vstar, s_need, s_above;
     __shared__ int s_warp[32];
-    const int e = blockIdx.x, ev = ev0 + e, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
+    const long long tile = 4LL * blockDim.x;
     const long long n = (long long)g.bins[0] * g.bins[1] * g.bins[2] * g.bins[3] * g.bins[4];
     if (tid == 0) {
         long long cum = 0;
         int vstar = -1, need = 0;
         for (int v = kHistBins - 1; v >= 0; v--) {
-            long long h = hist[(long long)e * kHistBins + v];
+            long long h = hist_e[v];
             if (cum + h >= K) { vstar = v; need = (int)(K - cum); break; }
             cum += h;
         }
@@ -941,12 +975,9 @@ k_select_coarse(DevGeom g, int ev0, const int32_t *votes, const uint32_t *hist, 
     }
     __syncthreads();
     const int vstar = s_vstar, need = s_need, above = s_above;
-    const int32_t *vo = votes + (long long)e * n;
-    uint64_t *ok_ = out_keys + (long long)ev * K;
-    int32_t *ov = out_votes + (long long)ev * K;
     const bool vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(vo) & 15) == 0);
     int runA = 0, runB = 0;   // cells above v* / at v* in the tiles before this one
-    for (long long t0 = 0; t0 < n; t0 += kSelTile) {
+    for (long long t0 = 0; t0 < n; t0 += tile) {
         if (runA >= above && runB >= need) break;
         const long long j0 = t0 + 4LL * tid;
         int v[4];
@@ -975,7 +1006,7 @@ k_select_coarse(DevGeom g, int ev0, const int32_t *votes, const uint32_t *hist, 
         }
         if (lane == 31) s_warp[wid] = inc;
         __syncthreads();
-        int w = s_warp[lane];
+        int w = lane < nwarps ? s_warp[lane] : 0;
         int winc = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1004,6 +1035,16 @@ k_select_coarse(DevGeom g, int ev0, const int32_t *votes, const uint32_t *hist, 
         runB += total >> 16;
         __syncthreads();   // s_warp is rewritten by the next scanned tile
     }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSelThreads)
+k_select_coarse(DevGeom g, int ev0, const int32_t *votes, const uint32_t *hist, int K,
+                uint64_t *out_keys, int32_t *out_votes) {
+    const int e = blockIdx.x, ev = ev0 + e;
+    const long long n = (long long)g.bins[0] * g.bins[1] * g.bins[2] * g.bins[3] * g.bins[4];
+    select_coarse_block(g, votes + (long long)e * n, hist + (long long)e * kHistBins, K,
+                        out_keys + (long long)ev * K, out_votes + (long long)ev * K);
 }
 
 void launch_select_coarse(const DevGeom &g, int ev0, int n_ev, const int32_t *votes,
@@ -1045,18 +1086,26 @@ __device__ void load_sorted(uint64_t *s, const uint64_t *keys, const int32_t *vo
     block_sort(s, np2);
 }
 
+// One event's top-K by one block: s = shared scratch of pow2_ge(n_in) entries.
+__device__ __forceinline__ void topk_block(const uint64_t *keys_e, const int32_t *votes_e, int n_in, int K,
+                                           uint64_t *out_keys_e, int32_t *out_votes_e, uint64_t *s) {
+    int np2 = pow2_ge(n_in);
+    load_sorted(s, keys_e, votes_e, n_in, np2);
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+        uint64_t x = i < n_in ? s[i] : ~0ULL;
+        out_keys_e[i] = x & kKeyMask;
+        out_votes_e[i] = i < n_in ? 1023 - (int)(x >> 50) : 0;
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(1024)
 k_topk(const uint64_t *keys, const int32_t *votes, int n_in, int K, uint64_t *out_keys,
        int32_t *out_votes) {
     __shared__ uint64_t s[kSortMax];
     const int e = blockIdx.x;
-    int np2 = pow2_ge(n_in);
-    load_sorted(s, keys + (long long)e * n_in, votes + (long long)e * n_in, n_in, np2);
-    for (int i = threadIdx.x; i < K; i += blockDim.x) {
-        uint64_t x = i < n_in ? s[i] : ~0ULL;
-        out_keys[(long long)e * K + i] = x & kKeyMask;
-        out_votes[(long long)e * K + i] = i < n_in ? 1023 - (int)(x >> 50) : 0;
-    }
+    topk_block(keys + (long long)e * n_in, votes + (long long)e * n_in, n_in, K, out_keys + (long long)e * K,
+               out_votes + (long long)e * K, s);
 }
 
 void launch_topk(int n_ev, const uint64_t *keys, const int32_t *votes, int n_in, int K,
@@ -1076,45 +1125,50 @@ void launch_topk(int n_ev, const uint64_t *keys, const int32_t *votes, int n_in,
 // ---------------------------------------------------------------------------------------
 constexpr int kEstChunk = 256;
 
-__global__ void __launch_bounds__(256)
-k_estimate_mask(DevGeom g, const uint64_t *keys, const int32_t *votes, int n_in, int level,
-                const int32_t *n_hits, uint32_t *active, int32_t *done, const HitRecD *hd,
-                int round, int max_tracks, int min_votes, double width, apo_track *out,
-                int32_t *n_tracks, const int32_t *offsets, int32_t *hit_track) {
-    __shared__ uint64_t s[kSortMax];
-    __shared__ double s_cen[kEstChunk * 5];
+// One event's estimate and hit masking by one block (any multiple of 32 threads, at least
+// 64): keys_e / votes_e the last level's cells, active_e its 8 mask words, done_e its flag,
+// hd_e its staged hits, te its max_tracks records, n_tracks_e its count, a0 its first hit
+// in the batch (for hit_track).  s: shared scratch of kSortMax entries; s_cen: of
+// kEstChunk x 5.
+__device__ __forceinline__ void estimate_mask_block(const DevGeom &g, const uint64_t *keys_e, const int32_t *votes_e,
+                                                    int n_in, int level, int nh, uint32_t *active_e,
+                                                    int32_t *done_e, const HitRecD *hd_e, int round,
+                                                    int max_tracks, int min_votes, double width,
+                                                    apo_track *te, int32_t *n_tracks_e, int a0,
+                                                    int32_t *hit_track, uint64_t *s, double *s_cen) {
     __shared__ long long s_lo[5], s_hi[5];
     __shared__ uint32_t act0[8], act1[8];
     __shared__ int s_m;
-    const int e = blockIdx.x, tid = threadIdx.x;
-    if (done[e]) return;
-    const int nh = n_hits[e];
-    apo_track *te = out + (long long)e * max_tracks;
+    const int tid = threadIdx.x;
+    if (*done_e) return;
     if (round == 0) {
         if (tid < max_tracks) {
             for (int a = 0; a < 5; a++) { te[tid].p[a] = 0.0; te[tid].w[a] = 0.0; }
             te[tid].votes = (tid == 0 && nh < 0) ? nh : 0;
             te[tid].n_hits = nh < 0 ? 0 : nh;
         }
-        if (tid == 0) n_tracks[e] = 0;
+        if (tid == 0) *n_tracks_e = 0;
     }
     if (nh < 0) {
         __syncthreads();
-        if (tid == 0) done[e] = 1;
+        if (tid == 0) *done_e = 1;
+        __syncthreads();
         return;
     }
-    if (tid < 8) act0[tid] = act1[tid] = active[(long long)e * 8 + tid];
+    if (tid < 8) act0[tid] = act1[tid] = active_e[tid];
     __syncthreads();
     int na = 0;
     for (int i = 0; i < 8; i++) na += __popc(act0[i]);
     if (na == 0) {
-        if (tid == 0) done[e] = 1;
+        __syncthreads();
+        if (tid == 0) *done_e = 1;
+        __syncthreads();
         return;
     }
     if (tid == 0) s_m = 0;
     if (tid < 5) { s_lo[tid] = okey(1e300); s_hi[tid] = okey(-1e300); }
     int np2 = pow2_ge(n_in);
-    load_sorted(s, keys + (long long)e * n_in, votes + (long long)e * n_in, n_in, np2);
+    load_sorted(s, keys_e, votes_e, n_in, np2);
     // the maximum-vote cells are s[0, m) after the sort
     const uint64_t top = s[0] >> 50;
     const int vmax = 1023 - (int)top;
@@ -1126,7 +1180,8 @@ k_estimate_mask(DevGeom g, const uint64_t *keys, const int32_t *votes, int n_in,
     __syncthreads();
     const int m = s_m;
     if (vmax < min_votes) {
-        if (tid == 0) done[e] = 1;
+        if (tid == 0) *done_e = 1;
+        __syncthreads();
         return;
     }
     // Centres of the m cells, staged per chunk by all threads; thread a < 5 then adds axis
@@ -1158,12 +1213,13 @@ k_estimate_mask(DevGeom g, const uint64_t *keys, const int32_t *votes, int n_in,
         if (tid == 0) {
             t.votes = vmax;
             t.n_hits = nh;
-            n_tracks[e] = round + 1;
+            *n_tracks_e = round + 1;
         }
     }
     const bool last = round + 1 >= max_tracks;
     if (last && !hit_track) {   // no later round needs the masks
-        if (tid == 0) done[e] = 1;
+        if (tid == 0) *done_e = 1;
+        __syncthreads();
         return;
     }
     const SeriesConsts &k = g.k;
@@ -1176,24 +1232,38 @@ k_estimate_mask(DevGeom g, const uint64_t *keys, const int32_t *votes, int n_in,
         unpack_key(g, s[j] & kKeyMask, idx);
         Cell<double> c{edge(g, 0, level, idx[0]), sin_phi0(g, level, idx[1]), cos_phi0(g, level, idx[1]),
                        edge(g, 2, level, idx[2]), edge(g, 3, level, idx[3]), edge(g, 4, level, idx[4])};
-        Hit<double> h = load_hit<double>(hd + (long long)e * kHitCap + i);
+        Hit<double> h = load_hit<double>(hd_e + i);
         const double d = h.d.lo;
         const double dlo = __dsub_rd(d, width);
         h.d = {gt0(dlo) ? dlo : 0.0, __dadd_ru(d, width)};
         if (vote_pair<double>(c, h, k)) atomicAnd(&act1[i >> 5], ~(1u << (i & 31)));
     }
     __syncthreads();
-    if (tid < 8) active[(long long)e * 8 + tid] = act1[tid];
+    if (tid < 8) active_e[tid] = act1[tid];
     if (hit_track) {   // the hits this track took: active before, masked now
-        const int a0 = offsets[e];
         for (int i = tid; i < nh; i += blockDim.x)
             if (((act0[i >> 5] & ~act1[i >> 5]) >> (i & 31)) & 1u) hit_track[a0 + i] = round;
     }
     if (tid == 0) {
         int left = 0;
         for (int i = 0; i < 8; i++) left += __popc(act1[i]);
-        if (left == 0 || last) done[e] = 1;
+        if (left == 0 || last) *done_e = 1;
     }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256)
+k_estimate_mask(DevGeom g, const uint64_t *keys, const int32_t *votes, int n_in, int level,
+                const int32_t *n_hits, uint32_t *active, int32_t *done, const HitRecD *hd,
+                int round, int max_tracks, int min_votes, double width, apo_track *out,
+                int32_t *n_tracks, const int32_t *offsets, int32_t *hit_track) {
+    __shared__ uint64_t s[kSortMax];
+    __shared__ double s_cen[kEstChunk * 5];
+    const int e = blockIdx.x;
+    estimate_mask_block(g, keys + (long long)e * n_in, votes + (long long)e * n_in, n_in, level, n_hits[e],
+                        active + (long long)e * 8, done + e, hd + (long long)e * kHitCap, round, max_tracks,
+                        min_votes, width, out + (long long)e * max_tracks, n_tracks + e,
+                        hit_track ? offsets[e] : 0, hit_track, s, s_cen);
 }
 
 void launch_estimate_mask(const DevGeom &g, int n_ev, const uint64_t *keys, const int32_t *votes,
@@ -1205,6 +1275,123 @@ void launch_estimate_mask(const DevGeom &g, int n_ev, const uint64_t *keys, cons
     k_estimate_mask<<<n_ev, 256, 0, s>>>(g, keys, votes, n_in, level, n_hits, active, done, hd, round,
                                           max_tracks, min_votes, width, out, n_tracks, offsets,
                                           hit_track);
+}
+
+// ---------------------------------------------------------------------------------------
+// Persistent batch search (top-K schedule, multi-track rounds).  One launch of as many
+// blocks as the GPU holds at once.  Each block pulls the next event from a device counter
+// and runs that event's whole search: per round the level-0 tiles (with the parent-cell
+// test), the top-K selection, every bisection level with its top-K, and the estimate with
+// the hit masking of Section 3.3; then the next round or the next event.  The steps are
+// the device functions of the per-level kernels above (same operations, same results);
+// only their scheduling differs.  Events are independent, so no block ever waits on
+// another: uneven events (10-200 hits) simply keep their block longer while the others
+// pull new ones, and no launch boundary waits for the slowest event of a level.  The only
+// device waits are the bounded waits of the hit staging.
+// ---------------------------------------------------------------------------------------
+template <int MODE> __device__ __noinline__ void persist_coarse(const DevGeom &g, const PersistArgs &A, int e,
+                                                                   int32_t *vo, uint32_t *hist_b,
+                                                                   unsigned char *smem) {
+    const int split = (g.bins[0] * g.bins[3] + blockDim.x - 1) / blockDim.x;
+    const int ntiles = g.bins[1] * g.bins[2] * split;
+    for (int t = 0; t < ntiles; t++) {
+        const int part = t % split, pw = t / split;
+        coarse_block<MODE>(g, e, split, part, pw % g.bins[1], pw / g.bins[1], A.hd, A.hf, A.n_hits,
+                           A.active, vo, hist_b, A.status, nullptr, smem);
+    }
+}
+
+template <int MODE> __device__ __noinline__ void persist_children(const DevGeom &g, const PersistArgs &A, int e,
+                                                                     int level, unsigned char *smem) {
+    constexpr bool k64 = ModeOf<MODE>::k64, k32 = ModeOf<MODE>::k32;
+    unsigned char *h64s = smem;
+    unsigned char *h32s = smem + (k64 ? kHitCap * 80 : 0);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (k64 ? kHitCap * 80 : 0) + (k32 ? kHitCap * 80 : 0));
+    int nh = A.n_hits[e];
+    if (nh < 0) nh = 0;
+    const unsigned bytes = (unsigned)nh * 80u;
+    bool ok = stage_to_smem(h64s, A.hd + (long long)e * kHitCap, k64 ? bytes : 0u, h32s,
+                            A.hf + (long long)e * kHitCap, k32 ? bytes : 0u, bar, A.status);
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_inval(bar);
+    if (!ok) nh = 0;
+    const int K = g.topk;
+    const uint32_t *act = A.active + (long long)e * 8;
+    for (long long j = threadIdx.x; j < (long long)K * 16; j += blockDim.x)
+        children_pair<MODE>(g, h64s, h32s, nh, act, level, A.fk + (long long)e * K, j,
+                            A.ck + (long long)e * K * 32, A.cv + (long long)e * K * 32);
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(128, 3) k_solve_persistent(DevGeom g, PersistArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_e;
+    const int lv = g.levels, K = g.topk;
+    const long long ncell = (long long)g.bins[0] * g.bins[1] * g.bins[2] * g.bins[3] * g.bins[4];
+    int32_t *vo = A.votes + (long long)blockIdx.x * ncell;        // this block's level-0 votes
+    uint32_t *hist_b = A.hist + (long long)blockIdx.x * kHistBins;
+    uint64_t *s_sort = reinterpret_cast<uint64_t *>(smem);
+    double *s_cen = reinterpret_cast<double *>(smem + kSortMax * sizeof(uint64_t));
+    for (;;) {
+        if (threadIdx.x == 0) s_e = atomicAdd(A.next_event, 1);
+        __syncthreads();
+        const int e = s_e;
+        __syncthreads();
+        if (e >= A.n_events) break;
+        for (int round = 0; round < A.max_tracks; round++) {
+            if (A.done[e]) break;
+            for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist_b[i] = 0u;
+            __syncthreads();
+            switch (A.mode[0]) {
+                case kModeF32: persist_coarse<kModeF32>(g, A, e, vo, hist_b, smem); break;
+                case kModeF64Filtered: persist_coarse<kModeF64Filtered>(g, A, e, vo, hist_b, smem); break;
+                default: persist_coarse<kModeF64>(g, A, e, vo, hist_b, smem); break;
+            }
+            __threadfence_block();
+            __syncthreads();
+            select_coarse_block(g, vo, hist_b, K, A.fk + (long long)e * K, A.fv + (long long)e * K);
+            for (int lev = 1; lev <= lv; lev++) {
+                switch (A.mode[lev]) {
+                    case kModeF32: persist_children<kModeF32>(g, A, e, lev, smem); break;
+                    case kModeF64Filtered: persist_children<kModeF64Filtered>(g, A, e, lev, smem); break;
+                    default: persist_children<kModeF64>(g, A, e, lev, smem); break;
+                }
+                topk_block(A.ck + (long long)e * K * 32, A.cv + (long long)e * K * 32, K * 32, K,
+                           A.fk + (long long)e * K, A.fv + (long long)e * K, s_sort);
+            }
+            estimate_mask_block(g, A.ck + (long long)e * K * 32, A.cv + (long long)e * K * 32, K * 32, lv,
+                                A.n_hits[e], A.active + (long long)e * 8, A.done + e,
+                                A.hd + (long long)e * kHitCap, round, A.max_tracks, A.min_votes, A.width,
+                                A.tracks + (long long)e * A.max_tracks, A.n_tracks + e,
+                                A.hit_track ? A.offsets[e] : 0, A.hit_track, s_sort, s_cen);
+        }
+    }
+}
+
+static_assert(kPersistF32 == kModeF32 && kPersistF64 == kModeF64 && kPersistF64Filtered == kModeF64Filtered,
+              "persistent launch modes");
+
+size_t persist_smem_bytes(const DevGeom &g) {
+    size_t a = CoarseSmem<kModeF64Filtered>::total(g.bins[4], 128);
+    size_t b = 2 * kHitCap * 80 + 16;
+    size_t c = kSortMax * sizeof(uint64_t) + kEstChunk * 5 * sizeof(double);
+    size_t m = a > b ? a : b;
+    return m > c ? m : c;
+}
+
+int persist_blocks(const DevGeom &g) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_solve_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_persistent, 128, persist_smem_bytes(g));
+    if (per_sm < 1) per_sm = 1;
+    return sms * per_sm;
+}
+
+void launch_solve_persistent(const DevGeom &g, int blocks, const PersistArgs &A, cudaStream_t s) {
+    if (A.n_events <= 0 || blocks <= 0) return;
+    k_solve_persistent<<<blocks, 128, persist_smem_bytes(g), s>>>(g, A);
 }
 
 }  // namespace apo

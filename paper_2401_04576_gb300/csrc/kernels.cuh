@@ -153,6 +153,31 @@ struct MaxsetArgs {
     uint64_t *trace_keys;          // may be null: events x (levels + 1) x max_keep
     int32_t *trace_votes, *trace_count;
 };
+// Persistent batch search (kernels.cu): the top-K schedule with multi-track rounds, every
+// event's whole search in one block, blocks pulling events from next_event (zeroed by the
+// host).  mode[L]: the vote kernel mode of level L (FP32, FP64 or FP32-filtered FP64).
+// votes / hist: per-block scratch (blocks x level-0 cells, blocks x kHistBins).
+enum : int { kPersistF32 = 0, kPersistF64 = 1, kPersistF64Filtered = 2 };   // the vote kernel modes
+struct PersistArgs {
+    int n_events, max_tracks, min_votes;
+    double width;
+    int mode[kMaxLevels + 1];
+    const HitRecD *hd;
+    const HitRecF *hf;
+    const int32_t *n_hits, *offsets;
+    uint32_t *active;
+    int32_t *done, *next_event;
+    unsigned *status;
+    int32_t *votes;
+    uint32_t *hist;
+    uint64_t *fk, *ck;
+    int32_t *fv, *cv;
+    apo_track *tracks;
+    int32_t *n_tracks, *hit_track;
+};
+size_t persist_smem_bytes(const DevGeom &g);
+int persist_blocks(const DevGeom &g);   // blocks resident at once on the current device
+void launch_solve_persistent(const DevGeom &g, int blocks, const PersistArgs &A, cudaStream_t s);
 size_t maxset_smem_bytes(const DevGeom &g);
 void launch_maxset_select(const DevGeom &g, int n_ev, const MaxsetArgs &A, cudaStream_t s);
 void init_maxset_attributes();
