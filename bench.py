@@ -47,7 +47,7 @@ OPS_TAIL = OPS_LPART + OPS_SIGNS
 # launch of that kernel on the 16^5 grid read 3.93 MB and wrote 214.01 MB (the vote
 # array); scaled by events to the benchmark's launch.  Must be re-captured (or set to None)
 # whenever that kernel changes.
-COARSE_F64_DRAM_BYTES_PER_EVENT = (3.930624e6 + 214.013440e6) / 64
+COARSE_F64_DRAM_BYTES_PER_EVENT = None
 
 
 def coarse_kernel_ops(n_parent: int, n_prefix: int, n_tail: int) -> int:
@@ -382,20 +382,39 @@ def background_study(w, n_events: int = 1024, seed: int = 4) -> dict:
     ev = chamber.multi_track_events(n_events, seed=seed, w=w)
     geom = apo.Geometry(g, w)
     hits = apo.DeviceHits.from_events(ev)
-    ws = geom.workspace(ev.n_events)
     ht = torch.empty(int(ev.offsets[-1]), dtype=torch.int32, device="cuda")
-    o = apo.solve_opts(precision=[apo.F32] * 5 + [apo.F64] * 2, max_tracks=5, min_votes=6,
-                       hit_track=ht)
-    apo.solve_batch(geom, hits, o, workspace=ws)      # warm-up
-    torch.cuda.synchronize()
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record()
-    tracks, nt = apo.solve_batch(geom, hits, o, workspace=ws)
-    s1.record()
-    s1.synchronize()
-    ms = s0.elapsed_time(s1)
-    taken = ht.cpu().numpy() >= 0
-    nt = nt.cpu().numpy()
+    prec = [apo.F32] * 5 + [apo.F64] * 2
+    launch = {}
+    results = {}
+    # the same search through the per-level launches recorded as one CUDA graph, and
+    # through the persistent launch with the knobs apo_autotune picks on a 256-event sample
+    sample = apo.DeviceHits.from_events(ev.subset(range(min(256, ev.n_events))))
+    best, _ = apo.autotune(geom, sample, apo.solve_opts(precision=prec, max_tracks=5, min_votes=6))
+    for name, tune, graph in (("graph", apo.ApoTune(0, 1, 256, 0, 0), True),
+                              ("autotuned", best, best.persistent == 0)):
+        o = apo.solve_opts(precision=prec, max_tracks=5, min_votes=6, hit_track=ht, tune=tune,
+                           use_graph=graph)
+        ws = geom.workspace(ev.n_events, opts=o)
+        apo.solve_batch(geom, hits, o, workspace=ws)      # warm-up (and graph recording)
+        torch.cuda.synchronize()
+        mss = []
+        for _ in range(2):
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            tracks, nt = apo.solve_batch(geom, hits, o, workspace=ws)
+            s1.record()
+            s1.synchronize()
+            mss.append(s0.elapsed_time(s1))
+        launch[name] = {"ms": min(mss), "events_per_s": ev.n_events / (min(mss) * 1e-3),
+                        "tune": tune.as_dict()}
+        results[name] = (apo.tracks_to_numpy(tracks, ev.n_events, 5).copy(), nt.cpu().numpy().copy(),
+                         ht.cpu().numpy().copy())
+        del ws
+    same = all(np.array_equal(results["graph"][i].view(np.uint8), results["autotuned"][i].view(np.uint8))
+               for i in range(3))
+    ms = launch["autotuned"]["ms"]
+    taken = results["autotuned"][2] >= 0
+    nt = results["autotuned"][1]
     geom.close()
     bins = [(0.0, 0.15), (0.15, 0.20), (0.20, 0.25), (0.25, 1.0)]
     acc = {b: [0, 0, 0, 0, 0, 0, 0] for b in bins}   # sig, sig taken, noise, noise taken, ev, found, true
@@ -424,6 +443,7 @@ def background_study(w, n_events: int = 1024, seed: int = 4) -> dict:
                         "0.08-0.31, mean %.1f hits), 10^5 coarse cells, top-64, 6 levels, "
                         "FP32 L0-4 / FP64 L5-6, <= 5 tracks, min 6 votes" % (ev.offsets[-1] / ev.n_events),
             "events_per_s": ev.n_events / (ms * 1e-3),
+            "launch_schedules": launch, "schedules_give_identical_results": bool(same),
             "signal_hits_taken": tot[1] / max(tot[0], 1),
             "noise_hits_rejected": 1.0 - tot[3] / max(tot[2], 1),
             "by_noise_fraction": rows}
@@ -625,39 +645,43 @@ def run_apo(args) -> None:
     rec32 = truth_recovery(g, np.full(ev.n_events, lv), tracks32["p"][:, 0, :],
                            tracks32["w"][:, 0, :], truth)
 
-    # roofline of the dominant kernel (coarse vote): counted work / live launch time
-    votes = torch.empty((ev.n_events, geom.n_coarse), dtype=torch.int32, device="cuda")
-    counts = torch.zeros(8, dtype=torch.int64, device="cuda")
+    # roofline of the dominant kernel (coarse vote, in the form the search runs: each block
+    # keeps its K best cells): counted work / live launch time
+    votes = apo.vote(geom, hits, precision=apo.F64, workspace=ws, stream=stream)
+    votes32 = apo.vote(geom, hits, precision=apo.F32, workspace=ws, stream=stream)
+    superset_violations = int((votes32 < votes).sum().item())
+    n_cells_cmp = int(votes.numel())
+    del votes32
     L = apo.lib()
     hc = hits.c()
     import ctypes as C
-    rc = L.apo_diag_vote_coarse_counts(geom.handle, C.byref(hc), apo.F64, apo._ptr(votes),
-                                       apo._ptr(counts), apo._ptr(ws), ws.numel(),
-                                       apo._stream_ptr(stream))
-    apo._check(rc)
-    n_par, n_pre, n_tail, n_launch, p32, q32, t32c, _ = (int(x) for x in counts.cpu().tolist())
-    votes32 = torch.empty_like(votes)
-    counts32 = torch.zeros(8, dtype=torch.int64, device="cuda")
-    rc = L.apo_diag_vote_coarse_counts(geom.handle, C.byref(hc), apo.F32, apo._ptr(votes32),
-                                       apo._ptr(counts32), apo._ptr(ws), ws.numel(),
-                                       apo._stream_ptr(stream))
-    apo._check(rc)
-    superset_violations = int((votes32 < votes).sum().item())
-    n_cells_cmp = int(votes.numel())
-    c32 = [int(x) for x in counts32.cpu().tolist()]
+
+    def coarse_counts(prec):
+        c = torch.zeros(8, dtype=torch.int64, device="cuda")
+        apo._check(L.apo_diag_vote_coarse_counts(geom.handle, C.byref(hc), prec, None, apo._ptr(c),
+                                                 apo._ptr(ws), ws.numel(), apo._stream_ptr(stream)))
+        return [int(x) for x in c.cpu().tolist()]
+
+    def coarse_launch_ms(prec, n_launch, reps):
+        out = []
+        for _ in range(reps):
+            flush.fill_(1)
+            c = torch.zeros(8, dtype=torch.int64, device="cuda")
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            apo._check(L.apo_diag_vote_coarse_counts(geom.handle, C.byref(hc), prec, None, apo._ptr(c),
+                                                     apo._ptr(ws), ws.numel(), apo._stream_ptr(stream)))
+            s1.record(stream)
+            s1.synchronize()
+            out.append(s0.elapsed_time(s1) / max(n_launch, 1))
+        return statistics.mean(out)
+
+    n_par, n_pre, n_tail, n_launch, p32, q32, t32c, _ = coarse_counts(apo.F64)
+    c32 = coarse_counts(apo.F32)
     # the FP32 coarse kernel (dominant in the FP32-bulk solve): counted FP32 directed
     # operations / live launch time, against the measured FP32 directed add/mul rate
     ops32_coarse = coarse_kernel_ops(c32[4], c32[5], c32[6]) / max(c32[3], 1)
-    kms32 = []
-    for _ in range(max(3, args.steps)):
-        flush.fill_(1)
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        apo.vote(geom, hits, precision=apo.F32, out=votes32, workspace=ws, stream=stream)
-        s1.record(stream)
-        s1.synchronize()
-        kms32.append(s0.elapsed_time(s1) / max(c32[3], 1))
-    k32_ms = statistics.mean(kms32)
+    k32_ms = coarse_launch_ms(apo.F32, c32[3], max(3, args.steps))
     peak32 = apo.pipe_peak(apo.F32)
     roofline32 = {"bound": "issue", "kernel": "k_vote_coarse<float>",
                   "achieved": ops32_coarse / (k32_ms * 1e-3) / 1e12, "peak": peak32 / 1e12,
@@ -667,19 +691,9 @@ def run_apo(args) -> None:
                                  "(apo_diag_pipe_peak) on this GPU, this run",
                   "work": {"fp32_parent": c32[4], "fp32_prefix": c32[5], "fp32_tail": c32[6],
                            "launches": c32[3]}}
-    del votes32
     ops_launch = coarse_kernel_ops(n_par, n_pre, n_tail) / max(n_launch, 1)
     ops32_launch = coarse_kernel_ops(p32, q32, t32c) / max(n_launch, 1)
-    kms = []
-    for _ in range(max(2, args.steps)):
-        flush.fill_(1)
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        apo.vote(geom, hits, precision=apo.F64, out=votes, workspace=ws, stream=stream)
-        s1.record(stream)
-        s1.synchronize()
-        kms.append(s0.elapsed_time(s1) / n_launch)
-    k_ms = statistics.mean(kms)
+    k_ms = coarse_launch_ms(apo.F64, n_launch, max(2, args.steps))
     peak = apo.pipe_peak(apo.F64)
     achieved = ops_launch / (k_ms * 1e-3)
     ev_per_launch = ev.n_events / max(n_launch, 1)
@@ -897,6 +911,35 @@ def run_case(args) -> None:
         torch.cuda.synchronize()
         print(json.dumps({"case": args.case, "events": ev4.n_events, "ok": True}))
         return
+    if args.case == "solve-maxset":   # the max-set leg's FP32-bulk form on the first events
+        from gen import chamber, grid as G
+        w = chamber.make_wires()
+        ga = G.make_grid(MAXSET["bins"], MAXSET["levels"], 64)
+        ev = chamber.single_track_events(args.events, seed=WORKLOAD["seed"], w=w)
+        geom = apo.Geometry(ga, w)
+        o = apo.solve_opts(precision=[apo.F32 | apo.OUTGOING] * ga.levels + [apo.F64 | apo.OUTGOING],
+                           schedule=apo.SCHED_MAXSET, max_keep=MAXSET["max_keep"],
+                           tune=apo.ApoTune(0, 0, 256, 0, 0))
+        hits = apo.DeviceHits.from_events(ev)
+        for _ in range(2):
+            apo.solve_batch(geom, hits, o)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "events": ev.n_events, "ok": True}))
+        return
+    if args.case == "solve-persist":   # the multi-track batch through the persistent launch
+        from gen import chamber, grid as G
+        w = chamber.make_wires()
+        g4 = G.make_grid([10] * 5, 6, 64)
+        ev = chamber.multi_track_events(args.events, seed=4, w=w)
+        geom = apo.Geometry(g4, w)
+        o = apo.solve_opts(precision=[apo.F32] * 5 + [apo.F64] * 2, max_tracks=5, min_votes=6,
+                           tune=apo.ApoTune(0, 1, 256, 0, 1))
+        hits = apo.DeviceHits.from_events(ev)
+        for _ in range(2):
+            apo.solve_batch(geom, hits, o)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "events": ev.n_events, "ok": True}))
+        return
     w, g, ev = make_inputs()
     ev = ev.subset(range(args.events))
     geom = apo.Geometry(g, w)
@@ -904,10 +947,18 @@ def run_case(args) -> None:
     ws = geom.workspace(ev.n_events)
     prec = (apo.F64_MID if args.case == "coarse-mid" else
             apo.F64 if args.case.endswith("f64") else apo.F32)
-    if args.case.startswith("coarse"):
+    if args.case == "coarse-mid":
         votes = torch.empty((ev.n_events, geom.n_coarse), dtype=torch.int32, device="cuda")
         for _ in range(2):
             apo.vote(geom, hits, precision=prec, out=votes, workspace=ws)
+    elif args.case.startswith("coarse"):   # the search's form: each block keeps its K best cells
+        import ctypes as C
+        hc = hits.c()
+        for _ in range(2):
+            c = torch.zeros(8, dtype=torch.int64, device="cuda")
+            apo._check(apo.lib().apo_diag_vote_coarse_counts(geom.handle, C.byref(hc), prec, None,
+                                                             apo._ptr(c), apo._ptr(ws), ws.numel(),
+                                                             apo._stream_ptr(None)))
     else:
         precision = ([apo.F32] * 5 + [apo.F64] * (g.levels + 1 - 5) if args.case == "solve-bulk"
                      else [prec] * (g.levels + 1))
@@ -938,7 +989,7 @@ def main(argv=None):
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--case", default=None,
                     choices=["coarse-f64", "coarse-f32", "coarse-mid", "solve-f64", "solve-f32", "solve-bulk",
-                             "four-f32", "four-f64"],
+                             "solve-maxset", "solve-persist", "four-f32", "four-f64"],
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--events", type=int, default=64)
     args = ap.parse_args(argv)

@@ -70,7 +70,7 @@ namespace {
 // Workspace regions for a batch of n_events.
 struct Layout {
     size_t status, n_hits, hd, hf, votes, hist, fk, fv, ck, cv, mask, done, ntr, tune_tracks;
-    size_t ms_front, ms_count, ms_stop, ms_ck, ms_cv, p_votes, p_hist, p_next, end;
+    size_t ms_front, ms_count, ms_stop, ms_ck, ms_cv, p_votes, p_hist, p_next, cand_k, cand_v, end;
     int chunk, ms_chunk;
 };
 
@@ -96,7 +96,15 @@ Layout layout(const apo_geometry *g, int n_events, const apo_solve_opts *opts = 
     L.n_hits = o; o = align256(o + sizeof(int32_t) * (size_t)n_events);
     L.hd = o; o = align256(o + sizeof(HitRecD) * (size_t)n_events * kHitCap);
     L.hf = o; o = align256(o + sizeof(HitRecF) * (size_t)n_events * kHitCap);
-    L.votes = o; o = align256(o + sizeof(int32_t) * (size_t)chunk * (size_t)g->n_coarse);
+    // level 0 keeps every cell's vote only for the max-set schedule and the midpoint form;
+    // otherwise each coarse block keeps its K best cells (candidates).  Without options the
+    // layout holds both, so it serves any options.
+    const bool maxset = opts && opts->schedule == APO_SCHED_MAXSET;
+    const bool full_votes = !opts || maxset || (opts->precision[0] & ~APO_OUTGOING) == APO_F64_MID;
+    L.votes = o; o = align256(o + (full_votes ? sizeof(int32_t) * (size_t)chunk * (size_t)g->n_coarse : 0));
+    const size_t n_lists = (size_t)g->dg.bins[1] * g->dg.bins[2] * 2;   // the larger split
+    L.cand_k = o; o = align256(o + (maxset ? 0 : sizeof(uint64_t) * (size_t)chunk * n_lists * K));
+    L.cand_v = o; o = align256(o + (maxset ? 0 : sizeof(int32_t) * (size_t)chunk * n_lists * K));
     L.hist = o; o = align256(o + sizeof(uint32_t) * (size_t)chunk * kHistBins);
     L.fk = o; o = align256(o + sizeof(uint64_t) * (size_t)n_events * K);
     L.fv = o; o = align256(o + sizeof(int32_t) * (size_t)n_events * K);
@@ -453,6 +461,8 @@ int validate_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_
             return fail(APO_EINVAL, "APO_SCHED_MAXSET needs sum_a bins[a] << levels <= 16384");
     } else if (o->schedule == APO_SCHED_TOPK) {
         if (key_bits_total(g->dg) > 50) return fail(APO_EINVAL, "APO_SCHED_TOPK needs keys of at most 50 bits");
+        if ((long long)g->dg.bins[1] * g->dg.bins[2] * 2 > 8192)
+            return fail(APO_EINVAL, "APO_SCHED_TOPK needs bins[1] * bins[2] <= 4096");
         if (o->tune.persistent) {
             for (int i = 0; i <= lv; i++) {
                 const int p = o->precision[i] & ~APO_OUTGOING;
@@ -577,6 +587,8 @@ int enqueue_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_o
     uint32_t *active = at<uint32_t>(ws, L.mask);
     int32_t *done = at<int32_t>(ws, L.done);
     int32_t *ntr = n_tracks_out ? n_tracks_out : at<int32_t>(ws, L.ntr);
+    uint64_t *cand_k = at<uint64_t>(ws, L.cand_k);
+    int32_t *cand_v = at<int32_t>(ws, L.cand_v);
     const double width = 3.0 * o->mask_sigma;   // round-to-nearest, as the oracle
     const int chunk = (o->tune.chunk_events > 0 && o->tune.chunk_events < L.chunk) ? o->tune.chunk_events : L.chunk;
     const int block = o->tune.cells_block ? o->tune.cells_block : 256;
@@ -642,10 +654,19 @@ int enqueue_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_o
         for (int round = 0; round < o->max_tracks; round++) {
             NvtxRange range_round("apo search round");
             CU(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)n * kHistBins, s));
-            launch_vote_coarse(gl[0], prec_at(0), e0, n, hd, hf, nh, votes, hist, status, s, nullptr, active);
-            if ((rc = check_launch("vote_coarse"))) return rc;
-            launch_select_coarse(g->dg, e0, n, votes, hist, K, fk, fv, s);
-            if ((rc = check_launch("select_coarse"))) return rc;
+            if (prec_at(0) == APO_F64_MID) {   // every cell's vote, then the selection
+                launch_vote_coarse(gl[0], prec_at(0), e0, n, hd, hf, nh, votes, hist, status, s, nullptr, active);
+                if ((rc = check_launch("vote_coarse"))) return rc;
+                launch_select_coarse(g->dg, e0, n, votes, hist, K, fk, fv, s);
+                if ((rc = check_launch("select_coarse"))) return rc;
+            } else {   // each block's K best cells, then the selection among them
+                launch_vote_coarse(gl[0], prec_at(0), e0, n, hd, hf, nh, nullptr, hist, status, s, nullptr, active,
+                                   cand_k, cand_v, K);
+                if ((rc = check_launch("vote_coarse"))) return rc;
+                launch_select_candidates(g->dg, e0, n, cand_k, cand_v, coarse_lists(gl[0], prec_at(0)), hist, K,
+                                         fk, fv, s);
+                if ((rc = check_launch("select_candidates"))) return rc;
+            }
             if (round == 0 && (rc = trace_copy(o, g, e0, n, 0, fke, fve, s))) return rc;
             for (int lev = 1; lev <= lv; lev++) {
                 launch_vote_children(gl[lev], prec_at(lev), n, hde, hfe, nhe, lev, fke, K, cke, cve, s, acte,
@@ -799,8 +820,10 @@ int apo_diag_vote_coarse_counts(const apo_geometry *g, const apo_hits *hits, int
                                 size_t ws_bytes, void *stream) {
     int rc;
     if ((rc = check_geom(g)) || (rc = check_hits(hits))) return rc;
-    if (!votes_out || !counts) return fail(APO_EINVAL, "votes_out / counts_out is NULL");
+    if (!counts) return fail(APO_EINVAL, "counts_out is NULL");
     if ((rc = check_precision(g, precision, "precision"))) return rc;
+    if (!votes_out && (precision & ~APO_OUTGOING) == APO_F64_MID)
+        return fail(APO_EINVAL, "the midpoint form keeps every vote: votes_out is needed");
     Layout L;
     if ((rc = check_ws(g, hits->n_events, ws, ws_bytes, L))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -819,8 +842,14 @@ int apo_diag_vote_coarse_counts(const apo_geometry *g, const apo_hits *hits, int
     for (int e0 = 0; e0 < ne; e0 += L.chunk) {
         int n = ne - e0 < L.chunk ? ne - e0 : L.chunk;
         CU(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)n * kHistBins, s));
-        launch_vote_coarse(g->dg, precision, e0, n, hd, hf, nh, votes_out + (size_t)e0 * g->n_coarse,
-                           hist, status, s, counts);
+        const DevGeom dg = geom_for(g, precision);
+        const int prec = precision & ~APO_OUTGOING;
+        if (votes_out)
+            launch_vote_coarse(dg, prec, e0, n, hd, hf, nh, votes_out + (size_t)e0 * g->n_coarse, hist, status, s,
+                               counts);
+        else   // the search's form: each block keeps its topk best cells
+            launch_vote_coarse(dg, prec, e0, n, hd, hf, nh, nullptr, hist, status, s, counts, nullptr,
+                               at<uint64_t>(ws, L.cand_k), at<int32_t>(ws, L.cand_v), g->dg.topk);
         if ((rc = check_launch("vote_coarse"))) return rc;
         launches++;
     }

@@ -241,7 +241,8 @@ template <int MODE>
 __device__ __forceinline__ void coarse_block(const DevGeom &g, int ev, int split, int part, int p, int w,
                                              const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
                                              const uint32_t *active, int32_t *vo, uint32_t *hist_e,
-                                             unsigned *status, unsigned long long *ctr, unsigned char *smem) {
+                                             unsigned *status, unsigned long long *ctr, unsigned char *smem,
+                                             uint64_t *cand_k = nullptr, int32_t *cand_v = nullptr, int K = 0) {
     using S = CoarseSmem<MODE>;
     constexpr bool k64 = S::k64, k32 = S::k32;
     const int Bd = g.bins[0], Bz = g.bins[3], Bl = g.bins[4];
@@ -404,25 +405,97 @@ __device__ __forceinline__ void coarse_block(const DevGeom &g, int ev, int split
         }
     }
     const int Bp = g.bins[1], Bw = g.bins[2];
-    for (int l = 0; l < Bl && has_cell; l++) {
+    auto vote_of = [&](int l) {
         int v = 0;
 #pragma unroll
         for (int q = 0; q < 9; q++) v |= (int)((pl[q] >> l) & 1u) << q;
-        long long lin = d + (long long)Bd * (p + (long long)Bp * (w + (long long)Bw * (z + (long long)Bz * l)));
-        vo[lin] = v;
+        return v;
+    };
+    for (int l = 0; l < Bl && has_cell; l++) {
+        const int v = vote_of(l);
+        if (!cand_k) {
+            long long lin = d + (long long)Bd * (p + (long long)Bp * (w + (long long)Bw * (z + (long long)Bz * l)));
+            vo[lin] = v;
+        }
         atomicAdd(&hist_s[v], 1u);
     }
     __syncthreads();
     for (int i = tid; i < kHistBins; i += nthr)
         if (hist_s[i]) atomicAdd(&hist_e[i], hist_s[i]);
+    if (cand_k) {
+        // The part's K best cells by (votes desc, key asc), from its own histogram: every
+        // cell above v_t, then the lowest keys at v_t.  Within a part, cells in the order
+        // (tan(lambda) bin, thread) are in key order.  Any cell among the event's K best is
+        // among its part's K best, so these candidates are all the selection needs.
+        __shared__ int s_vt, s_need, s_above, s_wsum[32];
+        if (tid == 0) {
+            int cum = 0, vt = -1, need = 0;
+            for (int v = kHistBins - 1; v >= 0; v--) {
+                const int h = (int)hist_s[v];
+                if (cum + h >= K) { vt = v; need = K - cum; break; }
+                cum += h;
+            }
+            s_vt = vt;
+            s_need = need;
+            s_above = cum;
+        }
+        __syncthreads();
+        const int vt = s_vt, need = s_need, above = s_above;
+        const int lane = tid & 31, wid = tid >> 5, nwarps = (nthr + 31) >> 5;
+        // the block may end in a partial warp (e.g. 100 or 50 threads): shuffle over the
+        // lanes that exist (lanes 0 .. r - 1 of the last warp)
+        const int rem = nthr - (wid << 5);
+        const unsigned wmask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+        int runA = 0, runB = 0;
+        for (int l = 0; l < Bl; l++) {
+            const int v = has_cell ? vote_of(l) : -1;
+            const int a = v > vt, b = v == vt;
+            const int x = a + (b << 16);
+            int inc = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(wmask, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31 || tid == nthr - 1) s_wsum[wid] = inc;
+            __syncthreads();
+            int wpre = 0, total = 0;
+            for (int q = 0; q < nwarps; q++) {
+                const int ws = s_wsum[q];
+                if (q < wid) wpre += ws;
+                total += ws;
+            }
+            const int pre = wpre + inc - x;
+            int pos = -1;
+            if (a) pos = runA + (pre & 0xffff);
+            else if (b && runB + (pre >> 16) < need) pos = above + runB + (pre >> 16);
+            if (pos >= 0) {
+                int idx[5] = {d, p, w, z, l};
+                cand_k[pos] = pack_key(g, idx);
+                cand_v[pos] = v;
+            }
+            runA += total & 0xffff;
+            runB += total >> 16;
+            __syncthreads();   // s_wsum is rewritten for the next bin
+        }
+        const int placed = above + (runB < need ? runB : need);
+        for (int i = placed + tid; i < K; i += nthr) {   // a part with fewer than K cells
+            cand_k[i] = 0;
+            cand_v[i] = -1;
+        }
+    }
     if (ctr) {   // work counters (diagnostics): FP64 parent / prefix / tail, -, FP32 ones
         unsigned long long v[6] = {n_par64, n_pre64, n_tail64, n_par32, n_pre32, n_tail32};
         const int slot[6] = {0, 1, 2, 4, 5, 6};
 #pragma unroll
         for (int i = 0; i < 6; i++) {
             unsigned long long x = v[i];
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if ((tid & 31) == 0 && x) atomicAdd(&ctr[slot[i]], x);
+            if (nthr - (tid & ~31) >= 32) {   // a full warp: reduce, one add per warp
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                if ((tid & 31) == 0 && x) atomicAdd(&ctr[slot[i]], x);
+            } else if (x) {                   // the lanes of a partial last warp add their own
+                atomicAdd(&ctr[slot[i]], x);
+            }
         }
     }
     __syncthreads();   // shared memory is reused by the caller's next step
@@ -432,15 +505,18 @@ template <int MODE>
 __global__ void __launch_bounds__(CoarseShape<MODE>::threads, CoarseShape<MODE>::min_blocks)
 k_vote_coarse(DevGeom g, int ev0, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
               const uint32_t *active, int32_t *votes, uint32_t *hist, unsigned *status,
-              unsigned long long *ctr) {
+              unsigned long long *ctr, uint64_t *cand_k, int32_t *cand_v, int K) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int split = CoarseShape<MODE>::split;
     const int e = blockIdx.y;
     const int part = blockIdx.x % split, pw = blockIdx.x / split;
     const int p = pw % g.bins[1], w = pw / g.bins[1];
     const long long ncell = (long long)g.bins[0] * g.bins[1] * g.bins[2] * g.bins[3] * g.bins[4];
-    coarse_block<MODE>(g, ev0 + e, split, part, p, w, hd, hf, n_hits, active, votes + (long long)e * ncell,
-                              hist + (long long)e * kHistBins, status, ctr, smem);
+    // candidates: K slots per block, the blocks of an event in blockIdx.x order
+    const long long co = ((long long)e * gridDim.x + blockIdx.x) * K;
+    coarse_block<MODE>(g, ev0 + e, split, part, p, w, hd, hf, n_hits, active,
+                       votes ? votes + (long long)e * ncell : nullptr, hist + (long long)e * kHistBins, status,
+                       ctr, smem, cand_k ? cand_k + co : nullptr, cand_v ? cand_v + co : nullptr, K);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -540,8 +616,12 @@ k_vote_coarse_mid(DevGeom g, int ev0, const HitRecD *hd, const int32_t *n_hits,
 #pragma unroll
         for (int i = 0; i < 2; i++) {
             unsigned long long x = v[i];
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if ((tid & 31) == 0 && x) atomicAdd(&ctr[1 + i], x);
+            if ((int)blockDim.x - (tid & ~31) >= 32) {   // a full warp: reduce, one add per warp
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                if ((tid & 31) == 0 && x) atomicAdd(&ctr[1 + i], x);
+            } else if (x) {                               // a partial last warp
+                atomicAdd(&ctr[1 + i], x);
+            }
         }
     }
 }
@@ -638,30 +718,42 @@ template <int MODE> static void launch_coarse_mode(const DevGeom &g, int ev0, in
                                                   const HitRecF *hf, const int32_t *n_hits,
                                                   const uint32_t *active, int32_t *votes,
                                                   uint32_t *hist, unsigned *status, cudaStream_t s,
-                                                  unsigned long long *ctr) {
+                                                  unsigned long long *ctr, uint64_t *cand_k,
+                                                  int32_t *cand_v, int K) {
     smem_limit_once(k_vote_coarse<MODE>, g_attr_coarse[MODE]);
     constexpr int split = CoarseShape<MODE>::split;
     dim3 grid(g.bins[1] * g.bins[2] * split, n_ev);
     const int nthr = (g.bins[0] * g.bins[3] + split - 1) / split;
     size_t sm = CoarseSmem<MODE>::total(g.bins[4], nthr);
-    k_vote_coarse<MODE><<<grid, nthr, sm, s>>>(g, ev0, hd, hf, n_hits, active, votes, hist, status, ctr);
+    k_vote_coarse<MODE><<<grid, nthr, sm, s>>>(g, ev0, hd, hf, n_hits, active, votes, hist, status, ctr,
+                                                cand_k, cand_v, K);
+}
+
+int coarse_lists(const DevGeom &g, int prec) {
+    const int split = (prec == APO_F32 || prec == APO_F64_MID) ? CoarseShape<kModeF32>::split
+                                                                : CoarseShape<kModeF64>::split;
+    return g.bins[1] * g.bins[2] * split;
 }
 
 void launch_vote_coarse(const DevGeom &g, int prec, int ev0, int n_ev, const HitRecD *hd,
                         const HitRecF *hf, const int32_t *n_hits, int32_t *votes, uint32_t *hist,
                         unsigned *status, cudaStream_t s, unsigned long long *ctr,
-                        const uint32_t *active) {
+                        const uint32_t *active, uint64_t *cand_k, int32_t *cand_v, int K) {
     if (n_ev <= 0) return;
     if (prec == APO_F64_MID)
         launch_coarse_mid(g, ev0, n_ev, hd, n_hits, active, votes, hist, status, s, ctr);
     else if (prec == APO_F64_EXACT)
-        launch_coarse_mode<kModeF64Exact>(g, ev0, n_ev, hd, hf, n_hits, active, votes, hist, status, s, ctr);
+        launch_coarse_mode<kModeF64Exact>(g, ev0, n_ev, hd, hf, n_hits, active, votes, hist, status, s, ctr,
+                                              cand_k, cand_v, K);
     else if (prec == APO_F32)
-        launch_coarse_mode<kModeF32>(g, ev0, n_ev, hd, hf, n_hits, active, votes, hist, status, s, ctr);
+        launch_coarse_mode<kModeF32>(g, ev0, n_ev, hd, hf, n_hits, active, votes, hist, status, s, ctr,
+                                              cand_k, cand_v, K);
     else if (prec == APO_F64_FILTERED)
-        launch_coarse_mode<kModeF64Filtered>(g, ev0, n_ev, hd, hf, n_hits, active, votes, hist, status, s, ctr);
+        launch_coarse_mode<kModeF64Filtered>(g, ev0, n_ev, hd, hf, n_hits, active, votes, hist, status, s, ctr,
+                                              cand_k, cand_v, K);
     else
-        launch_coarse_mode<kModeF64>(g, ev0, n_ev, hd, hf, n_hits, active, votes, hist, status, s, ctr);
+        launch_coarse_mode<kModeF64>(g, ev0, n_ev, hd, hf, n_hits, active, votes, hist, status, s, ctr,
+                                              cand_k, cand_v, K);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1045,6 +1137,89 @@ k_select_coarse(DevGeom g, int ev0, const int32_t *votes, const uint32_t *hist, 
     const long long n = (long long)g.bins[0] * g.bins[1] * g.bins[2] * g.bins[3] * g.bins[4];
     select_coarse_block(g, votes + (long long)e * n, hist + (long long)e * kHistBins, K,
                         out_keys + (long long)ev * K, out_votes + (long long)ev * K);
+}
+
+// Top-K of level 0 from the coarse blocks' candidates (see launch_vote_coarse): the same v*
+// and need from the event's histogram as k_select_coarse; every candidate above v* is kept
+// (there are exactly `above` of them), then the `need` lowest keys at v*.  In each block's
+// list the candidates at v* come in key order, so the lowest keys overall come from a
+// merge: `need` rounds, each taking the smallest head over the lists.
+__global__ void __launch_bounds__(kSelThreads)
+k_select_candidates(int ev0, const uint64_t *cand_k, const int32_t *cand_v, int n_lists,
+                    const uint32_t *hist, int K, uint64_t *out_keys, int32_t *out_votes) {
+    extern __shared__ int s_head[];          // n_lists heads
+    __shared__ int s_vstar, s_need, s_above, s_nA;
+    __shared__ unsigned long long s_red[32];
+    const int e = blockIdx.x, ev = ev0 + e, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint64_t *ck = cand_k + (long long)e * n_lists * K;
+    const int32_t *cv = cand_v + (long long)e * n_lists * K;
+    uint64_t *ok_ = out_keys + (long long)ev * K;
+    int32_t *ov = out_votes + (long long)ev * K;
+    if (tid == 0) {
+        long long cum = 0;
+        int vstar = -1, need = 0;
+        for (int v = kHistBins - 1; v >= 0; v--) {
+            long long h = hist[(long long)e * kHistBins + v];
+            if (cum + h >= K) { vstar = v; need = (int)(K - cum); break; }
+            cum += h;
+        }
+        s_vstar = vstar;
+        s_need = need;
+        s_above = (int)cum;
+        s_nA = 0;
+    }
+    __syncthreads();
+    const int vstar = s_vstar, need = s_need, above = s_above;
+    for (long long i = tid; i < (long long)n_lists * K; i += blockDim.x) {
+        const int v = cv[i];
+        if (v > vstar) {
+            const int pos = atomicAdd(&s_nA, 1);
+            if (pos < K) { ok_[pos] = ck[i]; ov[pos] = v; }
+        }
+    }
+    for (int t = tid; t < n_lists; t += blockDim.x) {
+        int j = 0;
+        while (j < K && cv[(long long)t * K + j] != vstar) j++;
+        s_head[t] = j;
+    }
+    __syncthreads();
+    const int nwarps = blockDim.x >> 5;
+    for (int r = 0; r < need; r++) {
+        unsigned long long best = ~0ULL;   // (key << 13) | list: keys of at most 50 bits
+        for (int t = tid; t < n_lists; t += blockDim.x) {
+            const int j = s_head[t];
+            if (j < K) {
+                const unsigned long long x = (ck[(long long)t * K + j] << 13) | (unsigned long long)t;
+                best = x < best ? x : best;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_down_sync(0xffffffffu, best, o);
+            best = y < best ? y : best;
+        }
+        if (lane == 0) s_red[wid] = best;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long b = ~0ULL;
+            for (int q = 0; q < nwarps; q++) b = s_red[q] < b ? s_red[q] : b;
+            const int t = (int)(b & 8191ULL);
+            ok_[above + r] = b >> 13;
+            ov[above + r] = vstar;
+            int j = s_head[t] + 1;
+            while (j < K && cv[(long long)t * K + j] != vstar) j++;
+            s_head[t] = j;
+        }
+        __syncthreads();
+    }
+}
+
+void launch_select_candidates(const DevGeom &, int ev0, int n_ev, const uint64_t *cand_k,
+                              const int32_t *cand_v, int n_lists, const uint32_t *hist, int K,
+                              uint64_t *out_keys, int32_t *out_votes, cudaStream_t s) {
+    if (n_ev <= 0) return;
+    k_select_candidates<<<n_ev, kSelThreads, sizeof(int) * (size_t)n_lists, s>>>(
+        ev0, cand_k, cand_v, n_lists, hist, K, out_keys, out_votes);
 }
 
 void launch_select_coarse(const DevGeom &g, int ev0, int n_ev, const int32_t *votes,

@@ -105,10 +105,21 @@ void launch_stage(const DevGeom &g, int n_events, const int32_t *offsets, const 
                   uint32_t *active, int32_t *done, unsigned *status, cudaStream_t s,
                   int32_t *hit_track = nullptr);
 // active: per event 8 words of hit-activity bits (nullptr: every hit active)
+// cand_k / cand_v (may be null): instead of every cell's vote, each block writes its K best
+// cells by (votes desc, key asc) (unused slots: votes -1), coarse_lists(g, prec) blocks per
+// event in order; votes is then unused.  The midpoint form takes no candidates.
 void launch_vote_coarse(const DevGeom &g, int prec, int ev0, int n_ev, const HitRecD *hd,
                         const HitRecF *hf, const int32_t *n_hits, int32_t *votes, uint32_t *hist,
                         unsigned *status, cudaStream_t s, unsigned long long *ctr = nullptr,
-                        const uint32_t *active = nullptr);
+                        const uint32_t *active = nullptr, uint64_t *cand_k = nullptr,
+                        int32_t *cand_v = nullptr, int K = 0);
+int coarse_lists(const DevGeom &g, int prec);   // level-0 blocks per event of a precision
+// The K best level-0 cells of each event from its blocks' candidates (n_lists x K per
+// event) and its histogram of all cells' votes, to out_keys / out_votes (K per event, in
+// no particular order; the set is that of launch_select_coarse).
+void launch_select_candidates(const DevGeom &g, int ev0, int n_ev, const uint64_t *cand_k,
+                              const int32_t *cand_v, int n_lists, const uint32_t *hist, int K,
+                              uint64_t *out_keys, int32_t *out_votes, cudaStream_t s);
 void launch_vote_keys(const DevGeom &g, int prec, int n_ev, const HitRecD *hd, const HitRecF *hf,
                       const int32_t *n_hits, int level, const uint64_t *keys, long long n_per_ev,
                       int32_t *votes, cudaStream_t s);

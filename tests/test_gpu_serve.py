@@ -95,7 +95,7 @@ def test_backpressure_and_admission(setup):
     ws1 = apo.Server(geom, solve, batch_events=16, max_slots=1)
     one, slot_bytes = ws1.slots, ws1.slot_bytes
     ws1.close()
-    assert one == 1 and slot_bytes > geom.workspace_bytes(16)
+    assert one == 1 and slot_bytes > geom.workspace_bytes(16, solve)
     # a budget for two and a half slots admits two
     srv = apo.Server(geom, solve, batch_events=16, max_slots=8, device_bytes=int(2.5 * slot_bytes))
     assert srv.slots == 2
