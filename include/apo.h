@@ -146,6 +146,10 @@ typedef struct {
     int32_t cells_filter;    /* 1: the same for the bisected cells of levels >= 1 */
     int32_t cells_block;     /* threads per block of the cell-voting kernel: 128 or 256 */
     int32_t chunk_events;    /* events per level-0 launch (at most the workspace's chunk) */
+    int32_t coarse_full;     /* 1 (APO_SCHED_TOPK): level 0 writes every cell's vote and selects
+                                from them, instead of each block keeping its topk best cells
+                                (more workspace, fewer instructions per block); the same
+                                kept set either way */
     int32_t persistent;      /* 1 (APO_SCHED_TOPK only): one persistent launch for the whole
                                 batch; each block pulls the next event from a device counter
                                 and runs its whole search (every round, tile and level),
@@ -213,7 +217,10 @@ int apo_workspace_bytes(const apo_geometry *geom, int32_t n_events, const apo_so
  * one vote per hit when either drift sign passes).  cell_keys: device, n_events x
  * n_cells_per_event keys; NULL = the full level-0 grid in linear order (d0 fastest,
  * tanl slowest; then level must be 0 and n_cells_per_event = apo_coarse_cells).
- * votes_out: device int32, n_events x n_cells_per_event. */
+ * votes_out: device int32, n_events x n_cells_per_event.  The call only queues work: a
+ * device wait that ran out of its poll limit (the votes of that launch are then untrusted)
+ * shows in the workspace's status word; read it with apo_workspace_status (apo_diag.h)
+ * after the work, as apo_solve_batch_host and the server do. */
 int apo_vote(const apo_geometry *geom, const apo_hits *hits, const uint64_t *cell_keys,
              int64_t n_cells_per_event, int32_t level, int32_t precision, int32_t *votes_out,
              void *workspace, size_t workspace_bytes, void *stream);
@@ -221,7 +228,9 @@ int apo_vote(const apo_geometry *geom, const apo_hits *hits, const uint64_t *cel
 /* One coarse-to-fine step: per event, keeps the topk cells of (keys_in, votes_in) by
  * (votes descending, key ascending) and writes them to kept_keys / kept_votes (device,
  * n_events x topk, may be NULL) and their 32 children each (level + 1) to children_out
- * (device, n_events x topk x 32).  keys_in NULL = the full level-0 grid in linear order. */
+ * (device, n_events x topk x 32).  keys_in NULL = the full level-0 grid in linear order.
+ * Needs keys of at most 50 bits.  As for apo_vote, check apo_workspace_status after the
+ * work. */
 int apo_refine(const apo_geometry *geom, const apo_hits *hits, const uint64_t *keys_in,
                const int32_t *votes_in, int64_t n_in_per_event, int32_t level,
                uint64_t *kept_keys, int32_t *kept_votes, uint64_t *children_out,

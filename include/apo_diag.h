@@ -15,7 +15,8 @@ extern "C" {
 
 /* apo_vote on the full level-0 grid that also counts the work the coarse kernel does
  * (votes_out NULL: the form apo_solve_batch runs, each coarse block keeping only its topk
- * best cells in the workspace, instead of writing every vote):
+ * best cells in the workspace, instead of writing every vote; counts_out NULL: no counting,
+ * the kernel exactly as the search runs it):
  * counts_out (device, 8 x uint64, zeroed by the call) receives FP64 parent-cell
  * evaluations, FP64 per-(cell, hit) prefix evaluations, FP64 tan(lambda) tail evaluations,
  * the number of coarse-kernel launches, then the same three FP32 counts.  For APO_F64_MID

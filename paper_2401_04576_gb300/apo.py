@@ -48,7 +48,7 @@ class ApoHits(C.Structure):
 class ApoTune(C.Structure):
     _fields_ = [("coarse_filter", C.c_int32), ("cells_filter", C.c_int32),
                 ("cells_block", C.c_int32), ("chunk_events", C.c_int32),
-                ("persistent", C.c_int32)]
+                ("coarse_full", C.c_int32), ("persistent", C.c_int32)]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -331,9 +331,11 @@ def autotune(geom: Geometry, hits: DeviceHits, opts: ApoSolveOpts | None = None,
     if workspace is None:   # room for every candidate, the persistent launch's scratch included
         op = ApoSolveOpts.from_buffer_copy(o)
         op.tune.persistent = 1
+        of = ApoSolveOpts.from_buffer_copy(o)
+        of.tune.coarse_full = 1
         torch = _torch()
-        ws = torch.empty(max(geom.workspace_bytes(hits.n_events, o),
-                             geom.workspace_bytes(hits.n_events, op)), dtype=torch.uint8, device="cuda")
+        ws = torch.empty(max(geom.workspace_bytes(hits.n_events, x) for x in (o, op, of)),
+                         dtype=torch.uint8, device="cuda")
     else:
         ws = workspace
     best = ApoTune()

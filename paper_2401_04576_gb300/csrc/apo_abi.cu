@@ -100,7 +100,8 @@ Layout layout(const apo_geometry *g, int n_events, const apo_solve_opts *opts = 
     // otherwise each coarse block keeps its K best cells (candidates).  Without options the
     // layout holds both, so it serves any options.
     const bool maxset = opts && opts->schedule == APO_SCHED_MAXSET;
-    const bool full_votes = !opts || maxset || (opts->precision[0] & ~APO_OUTGOING) == APO_F64_MID;
+    const bool full_votes = !opts || maxset || (opts->precision[0] & ~APO_OUTGOING) == APO_F64_MID ||
+                            opts->tune.coarse_full;
     L.votes = o; o = align256(o + (full_votes ? sizeof(int32_t) * (size_t)chunk * (size_t)g->n_coarse : 0));
     const size_t n_lists = (size_t)g->dg.bins[1] * g->dg.bins[2] * 2;   // the larger split
     L.cand_k = o; o = align256(o + (maxset ? 0 : sizeof(uint64_t) * (size_t)chunk * n_lists * K));
@@ -654,7 +655,7 @@ int enqueue_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_o
         for (int round = 0; round < o->max_tracks; round++) {
             NvtxRange range_round("apo search round");
             CU(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (size_t)n * kHistBins, s));
-            if (prec_at(0) == APO_F64_MID) {   // every cell's vote, then the selection
+            if (prec_at(0) == APO_F64_MID || o->tune.coarse_full) {   // every cell's vote, then the selection
                 launch_vote_coarse(gl[0], prec_at(0), e0, n, hd, hf, nh, votes, hist, status, s, nullptr, active);
                 if ((rc = check_launch("vote_coarse"))) return rc;
                 launch_select_coarse(g->dg, e0, n, votes, hist, K, fk, fv, s);
@@ -785,15 +786,18 @@ int apo_autotune(const apo_geometry *g, const apo_hits *hits, const apo_solve_op
         try_persistent = validate_solve(g, hits, &op, tt, ws, ws_bytes, Lp) == APO_OK;
         std::memcpy(g_err, keep, sizeof(g_err));
     }
+    for (int full = 0; full < 2; full++)
     for (int ps = 0; ps < 2; ps++)
     for (int cf = 0; cf < 2; cf++)
         for (int lf = 0; lf < 2; lf++)
             for (int bs = 0; bs < 2; bs++)
                 for (int ch = 0; ch < 2; ch++) {
                     if (ch == 1 && chunks[1] == 0) continue;
-                    if (ps == 1 && (!try_persistent || bs == 1 || ch == 1)) continue;   // no block / chunk knob
-                    apo_tune t{cf, lf, bs ? 128 : 256, chunks[ch], ps};
+                    if (ps == 1 && (!try_persistent || bs == 1 || ch == 1 || full == 1)) continue;
+                    if (full == 1 && o.schedule != APO_SCHED_TOPK) continue;
+                    apo_tune t{cf, lf, bs ? 128 : 256, chunks[ch], full, ps};
                     o.tune = t;
+                    if (layout(g, hits->n_events, &o).end > ws_bytes) continue;   // needs more workspace
                     float ms = 0.f;
                     Layout Lt = layout(g, hits->n_events, &o);
                     for (int rep = 0; rep < 2 && rc == APO_OK; rep++) {   // warm-up, then timed
@@ -820,7 +824,6 @@ int apo_diag_vote_coarse_counts(const apo_geometry *g, const apo_hits *hits, int
                                 size_t ws_bytes, void *stream) {
     int rc;
     if ((rc = check_geom(g)) || (rc = check_hits(hits))) return rc;
-    if (!counts) return fail(APO_EINVAL, "counts_out is NULL");
     if ((rc = check_precision(g, precision, "precision"))) return rc;
     if (!votes_out && (precision & ~APO_OUTGOING) == APO_F64_MID)
         return fail(APO_EINVAL, "the midpoint form keeps every vote: votes_out is needed");
@@ -828,7 +831,7 @@ int apo_diag_vote_coarse_counts(const apo_geometry *g, const apo_hits *hits, int
     if ((rc = check_ws(g, hits->n_events, ws, ws_bytes, L))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int ne = hits->n_events;
-    CU(cudaMemsetAsync(counts, 0, 8 * sizeof(unsigned long long), s));
+    if (counts) CU(cudaMemsetAsync(counts, 0, 8 * sizeof(unsigned long long), s));
     if (ne == 0) return APO_OK;
     unsigned *status = at<unsigned>(ws, L.status);
     int32_t *nh = at<int32_t>(ws, L.n_hits);
@@ -853,7 +856,7 @@ int apo_diag_vote_coarse_counts(const apo_geometry *g, const apo_hits *hits, int
         if ((rc = check_launch("vote_coarse"))) return rc;
         launches++;
     }
-    CU(cudaMemcpyAsync(counts + 3, &launches, sizeof(launches), cudaMemcpyHostToDevice, s));
+    if (counts) CU(cudaMemcpyAsync(counts + 3, &launches, sizeof(launches), cudaMemcpyHostToDevice, s));
     CU(cudaStreamSynchronize(s));
     return APO_OK;
 }

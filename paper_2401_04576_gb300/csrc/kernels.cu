@@ -427,57 +427,105 @@ __device__ __forceinline__ void coarse_block(const DevGeom &g, int ev, int split
         // cell above v_t, then the lowest keys at v_t.  Within a part, cells in the order
         // (tan(lambda) bin, thread) are in key order.  Any cell among the event's K best is
         // among its part's K best, so these candidates are all the selection needs.
-        __shared__ int s_vt, s_need, s_above, s_wsum[32];
-        if (tid == 0) {
-            int cum = 0, vt = -1, need = 0;
-            for (int v = kHistBins - 1; v >= 0; v--) {
-                const int h = (int)hist_s[v];
-                if (cum + h >= K) { vt = v; need = K - cum; break; }
-                cum += h;
+        __shared__ int s_vt, s_need, s_above;
+        // warp 0 (its cw lanes: a block may have fewer than 32 threads): suffix sums of the
+        // histogram from the top, cw bins a step
+        const int cw = nthr < 32 ? nthr : 32;
+        if (tid < cw) {
+            const unsigned m0 = cw == 32 ? 0xffffffffu : ((1u << cw) - 1u);
+            int cum = 0;
+            bool found = false;
+            for (int top = kHistBins - 1; top >= 0 && !found; top -= cw) {
+                const int v = top - tid;
+                const int h = v >= 0 ? (int)hist_s[v] : 0;
+                int inc = h;   // cells with votes in [v, top]
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(m0, inc, o);
+                    if (tid >= o) inc += y;
+                }
+                const unsigned hit = __ballot_sync(m0, v >= 0 && cum + inc >= K);
+                if (hit) {   // the first bin from the top where the count reaches K
+                    const int b = __ffs(hit) - 1;
+                    const int incb = __shfl_sync(m0, inc, b), hb = __shfl_sync(m0, h, b);
+                    if (tid == 0) {
+                        s_vt = top - b;
+                        s_above = cum + incb - hb;
+                        s_need = K - (cum + incb - hb);
+                    }
+                    found = true;
+                } else {
+                    cum += __shfl_sync(m0, inc, cw - 1);
+                }
             }
-            s_vt = vt;
-            s_need = need;
-            s_above = cum;
+            if (!found && tid == 0) {   // fewer than K cells in the part
+                s_vt = -1;
+                s_above = cum;
+                s_need = 0;
+            }
         }
         __syncthreads();
         const int vt = s_vt, need = s_need, above = s_above;
         const int lane = tid & 31, wid = tid >> 5, nwarps = (nthr + 31) >> 5;
-        // the block may end in a partial warp (e.g. 100 or 50 threads): shuffle over the
+        // the block may end in a partial warp (e.g. 100 or 50 threads): ballots over the
         // lanes that exist (lanes 0 .. r - 1 of the last warp)
         const int rem = nthr - (wid << 5);
         const unsigned wmask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
-        int runA = 0, runB = 0;
+        const unsigned lt = (1u << lane) - 1u;
+        // Ranks in key order ((tan(lambda) bin, thread) order): per bin and warp, counts of
+        // cells above v_t / at v_t from ballots; exclusive prefixes over warps, then over
+        // bins; a cell's rank is its bin's base + its warp's prefix + its lane's prefix.
+        __shared__ int s_wa[8][32], s_wb[8][32], s_ba[33], s_bb[33];
         for (int l = 0; l < Bl; l++) {
             const int v = has_cell ? vote_of(l) : -1;
-            const int a = v > vt, b = v == vt;
-            const int x = a + (b << 16);
-            int inc = x;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(wmask, inc, o);
-                if (lane >= o) inc += y;
-            }
-            if (lane == 31 || tid == nthr - 1) s_wsum[wid] = inc;
-            __syncthreads();
-            int wpre = 0, total = 0;
+            const unsigned ma = __ballot_sync(wmask, v > vt), mb = __ballot_sync(wmask, v == vt);
+            if (lane == 0) { s_wa[wid][l] = __popc(ma); s_wb[wid][l] = __popc(mb); }
+        }
+        __syncthreads();
+        if (tid < Bl) {   // exclusive prefix over warps, bin by bin
+            int ra = 0, rb = 0;
             for (int q = 0; q < nwarps; q++) {
-                const int ws = s_wsum[q];
-                if (q < wid) wpre += ws;
-                total += ws;
+                const int xa = s_wa[q][tid], xb = s_wb[q][tid];
+                s_wa[q][tid] = ra;
+                s_wb[q][tid] = rb;
+                ra += xa;
+                rb += xb;
             }
-            const int pre = wpre + inc - x;
+            s_ba[tid] = ra;   // the bin's totals, turned into bases below
+            s_bb[tid] = rb;
+        }
+        __syncthreads();
+        if (tid == 0) {   // exclusive prefix over bins
+            int ra = 0, rb = 0;
+            for (int l = 0; l < Bl; l++) {
+                const int xa = s_ba[l], xb = s_bb[l];
+                s_ba[l] = ra;
+                s_bb[l] = rb;
+                ra += xa;
+                rb += xb;
+            }
+            s_ba[Bl] = ra;
+            s_bb[Bl] = rb;
+        }
+        __syncthreads();
+        for (int l = 0; l < Bl; l++) {
+            const int v = has_cell ? vote_of(l) : -1;
+            const bool a = v > vt, b = v == vt;
+            const unsigned ma = __ballot_sync(wmask, a), mb = __ballot_sync(wmask, b);
             int pos = -1;
-            if (a) pos = runA + (pre & 0xffff);
-            else if (b && runB + (pre >> 16) < need) pos = above + runB + (pre >> 16);
-            if (pos >= 0) {
+            if (a) {
+                pos = s_ba[l] + s_wa[wid][l] + __popc(ma & lt);
+            } else if (b) {
+                const int rb = s_bb[l] + s_wb[wid][l] + __popc(mb & lt);
+                if (rb < need) pos = above + rb;
+            }
+            if (pos >= 0 && pos < K) {   // always below K when the counts agree; never past it
                 int idx[5] = {d, p, w, z, l};
                 cand_k[pos] = pack_key(g, idx);
                 cand_v[pos] = v;
             }
-            runA += total & 0xffff;
-            runB += total >> 16;
-            __syncthreads();   // s_wsum is rewritten for the next bin
         }
+        const int runB = s_bb[Bl];
         const int placed = above + (runB < need ? runB : need);
         for (int i = placed + tid; i < K; i += nthr) {   // a part with fewer than K cells
             cand_k[i] = 0;
@@ -902,8 +950,10 @@ __device__ __forceinline__ void children_pair(const DevGeom &g, const unsigned c
     out_votes_e[o + 16] = v1;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(256)
+// NT: threads per block, 256 or 128; the 128-thread form asks for three resident blocks
+// per SM (12 warps), which the FP64 modes' register count otherwise limits to 8 warps.
+template <int MODE, int NT>
+__global__ void __launch_bounds__(NT, NT == 128 ? 3 : 1)
 k_vote_children(DevGeom g, const HitRecD *hd, const HitRecF *hf, const int32_t *n_hits,
                 const uint32_t *active, int level, const uint64_t *parents, int n_par,
                 const int32_t *n_valid, uint64_t *out_keys, int32_t *out_votes, unsigned *status) {
@@ -981,10 +1031,14 @@ static void launch_children_mode(const DevGeom &g, int n_ev, const HitRecD *hd, 
                                  const uint64_t *parents, int n_par, const int32_t *n_valid,
                                  uint64_t *out_keys, int32_t *out_votes, cudaStream_t s, int block) {
     size_t sm = (ModeOf<MODE>::k64 ? kHitCap * 80 : 0) + (ModeOf<MODE>::k32 ? kHitCap * 80 : 0) + 16;
-    smem_limit_once(k_vote_children<MODE>, g_attr_children[MODE]);
     dim3 grid((unsigned)(((long long)n_par * 16 + block - 1) / block), n_ev);
-    k_vote_children<MODE><<<grid, block, sm, s>>>(g, hd, hf, n_hits, active, level, parents, n_par,
-                                                   n_valid, out_keys, out_votes, nullptr);
+    if (block == 128) {
+        k_vote_children<MODE, 128><<<grid, 128, sm, s>>>(g, hd, hf, n_hits, active, level, parents, n_par,
+                                                         n_valid, out_keys, out_votes, nullptr);
+    } else {
+        k_vote_children<MODE, 256><<<grid, 256, sm, s>>>(g, hd, hf, n_hits, active, level, parents, n_par,
+                                                         n_valid, out_keys, out_votes, nullptr);
+    }
 }
 
 void launch_vote_children(const DevGeom &g, int prec, int n_ev, const HitRecD *hd,
@@ -1022,12 +1076,16 @@ void init_kernel_attributes() {
     cudaFuncSetAttribute(k_vote_cells<kModeF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_vote_cells<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_vote_cells<kModeF64Filtered>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_vote_children<kModeF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_vote_children<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_vote_children<kModeF64Filtered>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_children<kModeF32, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_children<kModeF32, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_children<kModeF64, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_children<kModeF64, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_children<kModeF64Filtered, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_children<kModeF64Filtered, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_vote_coarse<kModeF64Exact>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_vote_cells<kModeF64Exact>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_vote_children<kModeF64Exact>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_children<kModeF64Exact, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_vote_children<kModeF64Exact, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     for (int i = 0; i < 4; i++) g_attr_coarse[i] = g_attr_cells[i] = g_attr_children[i] = true;
 }
 

@@ -164,6 +164,22 @@ def test_full_size_batch_sampled_events(wires, grid2, ev2):
         np.testing.assert_array_equal(got, ref)
 
 
+def test_full_size_fp32_bulk_batch_sampled_events(wires, grid2, ev2):
+    """The precision form at full size (1024 events, 16^5, K = 64, 6 levels; FP32 intervals
+    on the coarse grid and levels 1-4, FP64 on levels 5-6) in the benchmark's launch
+    configuration; three sampled events recomputed whole by the oracle in the same
+    precisions (every kept set and the estimate)."""
+    geom = apo.Geometry(grid2, wires)
+    precision = [apo.F32] * 5 + [apo.F64] * 2
+    tracks, nt, tk, tv = _trace(geom, _hits(ev2), grid2, precision)
+    tab = O.Tables(grid2, wires)
+    for e in (3, 600, 1020):
+        a, b = ev2.offsets[e], ev2.offsets[e + 1]
+        r = O.solve_event(tab, ev2.wire_id[a:b], ev2.drift[a:b], [1] * 5 + [0] * 2)
+        _compare_event(r, tracks[e, 0], tk[e], tv[e], grid2)
+    assert np.all(nt == 1)
+
+
 def test_fp32_votes_contain_fp64_votes(wires, grid2, ev2):
     """Full-grid votes of 8 config-2 events: FP32 >= FP64 cell by cell, and the filtered
     and unfiltered FP64 kernels agree exactly."""
@@ -318,8 +334,9 @@ def test_graph_replay_and_tuning_knobs_do_not_change_results(wires):
         for lf in (0, 1):
             for bs in (128, 256):
                 for ch in (0, 7):
-                    t, n = run(tune=apo.ApoTune(cf, lf, bs, ch))
-                    assert np.array_equal(t, ref_t) and np.array_equal(n, ref_n), (cf, lf, bs, ch)
+                    for full in (0, 1):   # level 0: block candidates or every vote
+                        t, n = run(tune=apo.ApoTune(cf, lf, bs, ch, full))
+                        assert np.array_equal(t, ref_t) and np.array_equal(n, ref_n), (cf, lf, bs, ch, full)
     o = apo.solve_opts(precision=prec, max_tracks=4, min_votes=6, use_graph=True)
     tracks = torch.zeros(ev.n_events * 4 * apo.TRACK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     ntr = torch.zeros(ev.n_events, dtype=torch.int32, device="cuda")

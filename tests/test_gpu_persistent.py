@@ -25,7 +25,7 @@ def wires():
 def _solve(geom, ev, prec, persistent, cells_filter=1, **kw):
     ne = ev.n_events
     ht = torch.full((max(int(ev.offsets[-1]), 1),), -5, dtype=torch.int32, device="cuda")
-    o = apo.solve_opts(precision=prec, hit_track=ht, tune=apo.ApoTune(0, cells_filter, 256, 0, persistent), **kw)
+    o = apo.solve_opts(precision=prec, hit_track=ht, tune=apo.ApoTune(0, cells_filter, 256, 0, persistent=persistent), **kw)
     tr, nt = apo.solve_batch(geom, apo.DeviceHits.from_events(ev), o)
     torch.cuda.synchronize()
     mt = int(o.max_tracks)
