@@ -639,13 +639,16 @@ def run_apo(args) -> None:
     nh = np.diff(ev.offsets)
     geom = apo.Geometry(g, w)
     hits = apo.DeviceHits.from_events(ev)
-    ws = geom.workspace(ev.n_events)
     lv = g.levels
     opts64 = apo.solve_opts(precision=[apo.F64] * (lv + 1))
     # the precision form: knobs from apo_autotune on a 256-event sample (results unchanged)
     tune32, _ = apo.autotune(geom, apo.DeviceHits.from_events(ev.subset(range(256))),
                              apo.solve_opts(precision=[apo.F32] * 5 + [apo.F64] * (lv + 1 - 5)))
     opts32 = apo.solve_opts(precision=[apo.F32] * 5 + [apo.F64] * (lv + 1 - 5), tune=tune32)
+    # one workspace for both forms: the larger of their layouts (the tuned chunk size and
+    # vote form decide the FP32-bulk one)
+    ws = torch.empty(max(geom.workspace_bytes(ev.n_events), geom.workspace_bytes(ev.n_events, opts32)),
+                     dtype=torch.uint8, device="cuda")
     tracks = torch.zeros(ev.n_events * apo.TRACK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     ntr = torch.zeros(ev.n_events, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2

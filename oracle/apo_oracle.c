@@ -396,12 +396,13 @@ static void estimate_groups(const or_grid *g, int level, const uint64_t *keys, c
  * OR_OUTGOING).  Outputs: p, werr, *best_votes = vmax, *final_level, *n_final = the size of
  * the final vmax group; trace (may be NULL): per level L <= final level, trace_count[L]
  * cells kept (0 at the final level) and their keys / votes in ascending key order at
- * trace_keys / trace_votes + L * max_keep. */
-int or_solve_event_maxset(const or_grid *g, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
+ * trace_keys / trace_votes + L * max_keep.  The final level's cells and votes are handed
+ * back in *fin_keys / *fin_votes (*fin_n of them; the caller frees them). */
+static void maxset_search(const or_grid *g, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
                           const double *drift, const int32_t *prec, int32_t max_keep, int32_t slack,
                           double p[5], double werr[5], int32_t *best_votes, int32_t *final_level,
                           int64_t *n_final, int32_t *trace_count, uint64_t *trace_keys,
-                          int32_t *trace_votes) {
+                          int32_t *trace_votes, uint64_t **fin_keys, int32_t **fin_votes, int64_t *fin_n) {
     int64_t n = 1;
     for (int a = 0; a < 5; a++) n *= g->bins[a];
     uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
@@ -454,8 +455,23 @@ int or_solve_event_maxset(const or_grid *g, const or_wires *w, int32_t n_hits, c
         free(fk);
         or_vote_cells(g, w, n_hits, wire_id, drift, L + 1, prec[L + 1], keys, n, votes);
     }
-    free(keys);
-    free(votes);
+    *fin_keys = keys;
+    *fin_votes = votes;
+    *fin_n = n;
+}
+
+int or_solve_event_maxset(const or_grid *g, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
+                          const double *drift, const int32_t *prec, int32_t max_keep, int32_t slack,
+                          double p[5], double werr[5], int32_t *best_votes, int32_t *final_level,
+                          int64_t *n_final, int32_t *trace_count, uint64_t *trace_keys,
+                          int32_t *trace_votes) {
+    uint64_t *fk;
+    int32_t *fv;
+    int64_t fn;
+    maxset_search(g, w, n_hits, wire_id, drift, prec, max_keep, slack, p, werr, best_votes, final_level,
+                  n_final, trace_count, trace_keys, trace_votes, &fk, &fv, &fn);
+    free(fk);
+    free(fv);
     return 0;
 }
 
@@ -551,6 +567,98 @@ int or_solve_event_multi(const or_grid *g, const or_wires *w, int32_t n_hits, co
         for (int32_t i = 0; i < n_hits; i++) if (tk[i]) hit_track[i] = t;
     }
     free(wa); free(da); free(ia); free(lk); free(lv); free(mk); free(act); free(tk);
+    return 0;
+}
+
+/* Vote of one hit for one cell (key at `level`) under precision code prec, as
+ * or_vote_cells counts it.  Must run under FE_DOWNWARD. */
+static int cell_hit_vote(const or_grid *g, const or_wires *w, int32_t level, int32_t prec, uint64_t key,
+                         int32_t wire, double drift) {
+    int32_t idx[5];
+    double c[12], h[9];
+    key_to_idx(g, key, idx);
+    cell_intervals(g, level, idx, c);
+    hit_constants(w, wire, drift, h);
+    return vote_pair(c, h, prec, NULL);
+}
+
+/* Multi-track extraction with the max-set search (Section 3.3's hit finding applied to
+ * several tracks, as or_solve_event_multi).  Round t searches the hits no earlier track
+ * took; if none is left, or the final vmax is below min_votes, the extraction stops.
+ * Otherwise the final vmax group can hold the cells of several tracks (tracks with equal
+ * hit counts tie), so the round takes one of them: the seed is the group's lowest key, S
+ * the searched hits that vote for it (vmax of them, at the final level's precision), and
+ * the track's cells are the group's cells that every hit of S votes for (each has vmax
+ * votes, so its voting hits are exactly S).  Track t is the estimate over those cells (p,
+ * werr as or_solve_event_maxset, votes = vmax, final level, n_final = their number); it
+ * takes the hits of S and every other hit still active that votes (FP64) for at least one
+ * of its cells with the drift widened to [max(d - 3 sigma, 0), d + 3 sigma] (direction
+ * condition as the final level's precision code).  Up to max_tracks rounds.
+ * hit_track[i]: the track that took hit i, or -1. */
+int or_solve_event_maxset_multi(const or_grid *g, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
+                                const double *drift, const int32_t *prec, int32_t max_keep, int32_t slack,
+                                int32_t max_tracks, int32_t min_votes, double mask_sigma, double *p,
+                                double *werr, int32_t *votes, int32_t *final_level, int64_t *n_final,
+                                int32_t *n_found, int32_t *hit_track) {
+    const double width = 3.0 * mask_sigma;
+    size_t nb = (size_t)(n_hits > 0 ? n_hits : 1);
+    int32_t *wa = (int32_t *)malloc(sizeof(int32_t) * nb);
+    double *da = (double *)malloc(sizeof(double) * nb);
+    int32_t *ia = (int32_t *)malloc(sizeof(int32_t) * nb);
+    uint8_t *sv = (uint8_t *)malloc(nb);
+    uint8_t *act = (uint8_t *)malloc(nb);
+    uint8_t *tk = (uint8_t *)malloc(nb);
+    for (int32_t i = 0; i < n_hits; i++) hit_track[i] = -1;
+    *n_found = 0;
+    for (int32_t t = 0; t < max_tracks; t++) {
+        int32_t na = 0;
+        for (int32_t i = 0; i < n_hits; i++)
+            if (hit_track[i] < 0) { wa[na] = wire_id[i]; da[na] = drift[i]; ia[na] = i; na++; }
+        if (na == 0) break;
+        int32_t best = 0, fl = 0;
+        int64_t nf = 0, fn = 0;
+        uint64_t *fk;
+        int32_t *fv;
+        double pt[5], wt[5];
+        maxset_search(g, w, na, wa, da, prec, max_keep, slack, pt, wt, &best, &fl, &nf, NULL, NULL, NULL,
+                      &fk, &fv, &fn);
+        if (best < min_votes) { free(fk); free(fv); break; }
+        /* the final vmax group and its lowest key */
+        int64_t m = 0;
+        for (int64_t j = 0; j < fn; j++)
+            if (fv[j] == best) fk[m++] = fk[j];
+        uint64_t seed = fk[0];
+        for (int64_t j = 1; j < m; j++) if (fk[j] < seed) seed = fk[j];
+        int old = fegetround();
+        fesetround(FE_DOWNWARD);
+        for (int32_t q = 0; q < na; q++) sv[q] = (uint8_t)cell_hit_vote(g, w, fl, prec[fl], seed, wa[q], da[q]);
+        /* the track's cells: the group's cells that every hit of S votes for (in place) */
+        int64_t mc = 0;
+        for (int64_t j = 0; j < m; j++) {
+            int ok = 1;
+            for (int32_t q = 0; q < na && ok; q++)
+                if (sv[q] && !cell_hit_vote(g, w, fl, prec[fl], fk[j], wa[q], da[q])) ok = 0;
+            if (ok) fk[mc++] = fk[j];
+        }
+        fesetround(old);
+        for (int64_t j = 0; j < mc; j++) fv[j] = best;
+        estimate_groups(g, fl, fk, fv, mc, best, pt, wt, &nf);
+        for (int a = 0; a < 5; a++) { p[5 * t + a] = pt[a]; werr[5 * t + a] = wt[a]; }
+        votes[t] = best;
+        final_level[t] = fl;
+        n_final[t] = nf;
+        *n_found = t + 1;
+        for (int32_t i = 0; i < n_hits; i++) { act[i] = hit_track[i] < 0; tk[i] = 0; }
+        for (int32_t q = 0; q < na; q++) if (sv[q]) tk[ia[q]] = 1;
+        old = fegetround();
+        fesetround(FE_DOWNWARD);
+        mask_hits(g, w, n_hits, wire_id, drift, act, fl, fk, mc, width, (prec[fl] & OR_OUTGOING) != 0, tk);
+        fesetround(old);
+        for (int32_t i = 0; i < n_hits; i++) if (tk[i]) hit_track[i] = t;
+        free(fk);
+        free(fv);
+    }
+    free(wa); free(da); free(ia); free(sv); free(act); free(tk);
     return 0;
 }
 

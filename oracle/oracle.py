@@ -77,6 +77,10 @@ def load(path):
     L.or_solve_event_multi.argtypes = [C.POINTER(OrGrid), C.POINTER(OrWires), C.c_int32, ip, dp,
                                        ip, C.c_int32, C.c_int32, C.c_double, dp, dp, ip, ip, ip]
     L.or_solve_event_multi.restype = C.c_int
+    L.or_solve_event_maxset_multi.argtypes = [C.POINTER(OrGrid), C.POINTER(OrWires), C.c_int32, ip, dp,
+                                              ip, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                              C.c_double, dp, dp, ip, ip, C.POINTER(C.c_int64), ip, ip]
+    L.or_solve_event_maxset_multi.restype = C.c_int
     L.or_mask_hits.argtypes = [C.POINTER(OrGrid), C.POINTER(OrWires), C.c_int32, ip, dp,
                                C.POINTER(C.c_uint8), C.c_int32, up, C.c_int64, C.c_double,
                                C.c_int, C.POINTER(C.c_uint8)]
@@ -330,6 +334,36 @@ def solve_event_multi(tab: Tables, wire_id, drift, max_tracks: int, min_votes: i
     k = int(nf[0])
     return dict(n_tracks=k, p=p.reshape(max_tracks, 5)[:k], w=werr.reshape(max_tracks, 5)[:k],
                 votes=votes[:k], hit_track=ht[:n])
+
+
+def solve_event_maxset_multi(tab: Tables, wire_id, drift, max_keep: int, max_tracks: int,
+                             min_votes: int, slack: int = 0, mask_sigma: float = 150e-6,
+                             prec_per_level=None):
+    """Multi-track extraction with the max-set search (see or_solve_event_maxset_multi).
+    Returns dict with per-track p, w, votes, final_level, n_final, the number of tracks and,
+    per hit, the index of the track that took it (-1: none)."""
+    g = tab.grid
+    prec = np.zeros(g.levels + 1, np.int32) if prec_per_level is None else \
+        np.ascontiguousarray(prec_per_level, np.int32)
+    wid = np.ascontiguousarray(wire_id, np.int32)
+    dr = np.ascontiguousarray(drift, np.float64)
+    n = wid.shape[0]
+    p = np.zeros(5 * max_tracks)
+    werr = np.zeros(5 * max_tracks)
+    votes = np.zeros(max_tracks, np.int32)
+    fl = np.zeros(max_tracks, np.int32)
+    nfin = np.zeros(max_tracks, np.int64)
+    nf = np.zeros(1, np.int32)
+    ht = np.zeros(max(n, 1), np.int32)
+    lib().or_solve_event_maxset_multi(C.byref(tab.cg), C.byref(tab.cw), int(n), _p(wid, C.c_int32),
+                                      _p(dr, C.c_double), _p(prec, C.c_int32), int(max_keep),
+                                      int(slack), int(max_tracks), int(min_votes), float(mask_sigma),
+                                      _p(p, C.c_double), _p(werr, C.c_double), _p(votes, C.c_int32),
+                                      _p(fl, C.c_int32), _p(nfin, C.c_int64), _p(nf, C.c_int32),
+                                      _p(ht, C.c_int32))
+    k = int(nf[0])
+    return dict(n_tracks=k, p=p.reshape(max_tracks, 5)[:k], w=werr.reshape(max_tracks, 5)[:k],
+                votes=votes[:k], final_level=fl[:k], n_final=nfin[:k], hit_track=ht[:n])
 
 
 def mask_hits(tab: Tables, wire_id, drift, level: int, keys, width: float, active=None,
