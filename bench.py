@@ -461,23 +461,45 @@ def background_study(w, n_events: int = 1024, seed: int = 4) -> dict:
                for i in range(3) for k in ("persistent", "autotuned"))
     fastest = min(launch, key=lambda k: launch[k]["ms"])
     ms = launch[fastest]["ms"]
-    taken = results[fastest][2] >= 0
-    nt = results[fastest][1]
+    tracks, nt, hts = results[fastest]
     geom.close()
+    out = {"workload": f"{ev.n_events} multi-track events (1-5 helices, noise fraction "
+                       "0.08-0.31, mean %.1f hits), 10^5 coarse cells, top-64, 6 levels, "
+                       "FP32 L0-4 / FP64 L5-6, <= 5 tracks, min 6 votes" % (ev.offsets[-1] / ev.n_events),
+           "events_per_s": ev.n_events / (ms * 1e-3),
+           "launch_schedules": launch, "schedules_give_identical_results": bool(same)}
+    out.update(multi_track_figures(ev, tracks, nt, hts))
+    out["maxset"] = multi_maxset_leg(w, ev)
+    return out
+
+
+def multi_track_figures(ev, tracks, nt, hit_track) -> dict:
+    """Hit and track figures of a multi-track extraction against the generator's truth: the
+    signal hits taken and noise hits left (overall and per bin of the event's noise
+    fraction), the true tracks whose helix lies in some found track's estimate box (value
+    +- error per axis) per true track, and the found tracks whose box holds no true helix."""
+    taken = hit_track >= 0
     bins = [(0.0, 0.15), (0.15, 0.20), (0.20, 0.25), (0.25, 1.0)]
-    acc = {b: [0, 0, 0, 0, 0, 0, 0] for b in bins}   # sig, sig taken, noise, noise taken, ev, found, true
+    acc = {b: [0, 0, 0, 0, 0, 0, 0, 0] for b in bins}   # sig, sig taken, noise, noise taken, ev, found, true, matched
+    fakes = 0
     for e in range(ev.n_events):
         a, b = int(ev.offsets[e]), int(ev.offsets[e + 1])
         noise = np.array([h is None for h in ev.hit_truth[e]])
         frac = noise.mean()
         key = next(k for k in bins if k[0] <= frac < k[1])
         t = taken[a:b]
+        truth = np.array([tr.params for tr in ev.tracks[e]])
+        matched = np.zeros(len(truth), bool)
+        for k in range(int(nt[e])):
+            ins = np.all(np.abs(tracks[e, k]["p"] - truth) <= tracks[e, k]["w"] * (1 + 1e-12), axis=1)
+            matched |= ins
+            fakes += int(not ins.any())
         x = acc[key]
         x[0] += int((~noise).sum()); x[1] += int((t & ~noise).sum())
         x[2] += int(noise.sum()); x[3] += int((t & noise).sum())
-        x[4] += 1; x[5] += int(nt[e]); x[6] += len(ev.tracks[e])
+        x[4] += 1; x[5] += int(nt[e]); x[6] += len(truth); x[7] += int(matched.sum())
     rows = []
-    tot = np.zeros(7, np.int64)
+    tot = np.zeros(8, np.int64)
     for k in bins:
         x = acc[k]
         tot += np.array(x)
@@ -486,15 +508,50 @@ def background_study(w, n_events: int = 1024, seed: int = 4) -> dict:
                          "signal_hits_taken": x[1] / max(x[0], 1),
                          "noise_hits_rejected": 1.0 - x[3] / max(x[2], 1),
                          "tracks_found_per_event": x[5] / x[4],
-                         "true_tracks_per_event": x[6] / x[4]})
-    return {"workload": f"{ev.n_events} multi-track events (1-5 helices, noise fraction "
-                        "0.08-0.31, mean %.1f hits), 10^5 coarse cells, top-64, 6 levels, "
-                        "FP32 L0-4 / FP64 L5-6, <= 5 tracks, min 6 votes" % (ev.offsets[-1] / ev.n_events),
-            "events_per_s": ev.n_events / (ms * 1e-3),
-            "launch_schedules": launch, "schedules_give_identical_results": bool(same),
-            "signal_hits_taken": tot[1] / max(tot[0], 1),
+                         "true_tracks_per_event": x[6] / x[4],
+                         "true_tracks_in_a_found_box": x[7] / max(x[6], 1)})
+    return {"signal_hits_taken": tot[1] / max(tot[0], 1),
             "noise_hits_rejected": 1.0 - tot[3] / max(tot[2], 1),
+            "tracks_found_per_true_track": tot[5] / max(tot[6], 1),
+            "true_tracks_in_a_found_box": tot[7] / max(tot[6], 1),
+            "found_tracks_holding_no_true_helix": fakes / max(tot[5], 1),
             "by_noise_fraction": rows}
+
+
+def multi_maxset_leg(w, ev) -> dict:
+    """The same multi-track events through the max-set schedule (anisotropic grid, FP32
+    levels 0-4 / FP64 level 5, direction condition, max_keep 32768, slack 2, <= 5 tracks,
+    min 6 votes): each round keeps one hit-set cluster of the final maximum-vote group."""
+    import torch
+    from gen import grid as G
+    from paper_2401_04576_gb300 import apo
+    g = G.make_grid(MAXSET["bins"], MAXSET["levels"], 64)
+    geom = apo.Geometry(g, w)
+    hits = apo.DeviceHits.from_events(ev)
+    ht = torch.empty(int(ev.offsets[-1]), dtype=torch.int32, device="cuda")
+    prec = [apo.F32 | apo.OUTGOING] * MAXSET["levels"] + [apo.F64 | apo.OUTGOING]
+    tune = apo.ApoTune(0, 0, 128, 0)
+    o = apo.solve_opts(precision=prec, schedule=apo.SCHED_MAXSET, max_keep=MAXSET["max_keep"], slack=2,
+                       max_tracks=5, min_votes=6, hit_track=ht, tune=tune)
+    ws = geom.workspace(ev.n_events, opts=o)
+    tracks, nt = apo.solve_batch(geom, hits, o, workspace=ws)      # warm-up
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    tracks, nt = apo.solve_batch(geom, hits, o, tracks=tracks, n_tracks=nt, workspace=ws)
+    s1.record()
+    s1.synchronize()
+    ms = s0.elapsed_time(s1)
+    res = {"workload": "the same events; 2 x 256 x 16 x 2 x 8 coarse cells, max-set schedule "
+                       "(max_keep 32768, slack 2), 5 bisection levels, direction condition; FP32 "
+                       "levels 0-4, FP64 level 5; <= 5 tracks, min 6 votes; one hit-set cluster "
+                       "of the final maximum-vote group per round",
+           "events_per_s": ev.n_events / (ms * 1e-3), "ms": ms, "tune": tune.as_dict()}
+    res.update(multi_track_figures(ev, apo.tracks_to_numpy(tracks, ev.n_events, 5), nt.cpu().numpy(),
+                                   ht.cpu().numpy()))
+    del ws
+    geom.close()
+    return res
 
 
 def paper_search_leg(n_events: int = 512, seed: int = 70, cpu_events: int = 1, n_fp64: int = 64) -> dict:

@@ -180,14 +180,15 @@ typedef struct {
     int32_t schedule;        /* APO_SCHED_TOPK (default) or APO_SCHED_MAXSET */
     int32_t max_keep;        /* APO_SCHED_MAXSET: cells kept per event and level, >= 1 */
     int32_t slack;           /* APO_SCHED_MAXSET: vote groups down to vmax - slack are kept */
-    int32_t *final_level;    /* device, may be NULL (APO_SCHED_MAXSET): per event, the level
-                                whose vmax group gave the estimate */
-    int32_t *n_final;        /* device, may be NULL (APO_SCHED_MAXSET): per event, the size of
-                                that group */
-    int32_t *trace_count;    /* device, may be NULL (APO_SCHED_MAXSET): n_events x (levels + 1)
-                                kept counts; trace_keys / trace_votes are then n_events x
-                                (levels + 1) x max_keep, the kept cells of each level before
-                                the final one (in the order of the level's cells) */
+    int32_t *final_level;    /* device, may be NULL (APO_SCHED_MAXSET): per event and track
+                                (n_events x max_tracks), the level whose vmax group gave the
+                                estimate */
+    int32_t *n_final;        /* device, may be NULL (APO_SCHED_MAXSET): per event and track, the
+                                number of cells the estimate was taken over */
+    int32_t *trace_count;    /* device, may be NULL (APO_SCHED_MAXSET, max_tracks 1): n_events x
+                                (levels + 1) kept counts; trace_keys / trace_votes are then
+                                n_events x (levels + 1) x max_keep, the kept cells of each
+                                level before the final one (in the order of the level's cells) */
 } apo_solve_opts;
 
 /* Fills *opts with: all levels FP64, one track, min_votes 0, mask_sigma 150e-6, no trace,
@@ -242,7 +243,14 @@ int apo_refine(const apo_geometry *geom, const apo_hits *hits, const uint64_t *k
  * drift widened to [d - 3 mask_sigma, d + 3 mask_sigma] is removed (the hit finding of
  * Section 3.3 with a widened box) and the event is searched again.  An event stops at
  * max_tracks tracks, when no hit is left, or when the best final vote count is below
- * min_votes (that search gives no track).  tracks_out: device, n_events x
+ * min_votes (that search gives no track).
+ * With APO_SCHED_MAXSET and max_tracks > 1 the final vmax group of a search can hold the
+ * cells of several tracks (tracks with equal hit counts tie), so each round takes one of
+ * them: the seed is the group's lowest key, S the searched hits that vote for it at the
+ * final level's precision, and the track's cells are the group's cells that every hit of
+ * S votes for.  The estimate is taken over those cells; the track takes S and the hits
+ * that vote for one of them with the widened drift.  With max_tracks 1 the estimate is
+ * over the whole group.  APO_F64_MID levels are refused there.  tracks_out: device, n_events x
  * opts->max_tracks records (unused records zeroed); n_tracks_out: device int32 per event
  * (may be NULL).  No host synchronisation: the call only queues work on the stream. */
 int apo_solve_batch(const apo_geometry *geom, const apo_hits *hits, const apo_solve_opts *opts,

@@ -454,8 +454,14 @@ int validate_solve(const apo_geometry *g, const apo_hits *hits, const apo_solve_
     if (o->tune.chunk_events < 0) return fail(APO_EINVAL, "tune.chunk_events < 0");
     if (!tracks_out && hits->n_events > 0) return fail(APO_EINVAL, "tracks_out is NULL");
     if (o->schedule == APO_SCHED_MAXSET) {
-        if (o->max_tracks != 1) return fail(APO_EINVAL, "APO_SCHED_MAXSET searches one track per event");
-        if (o->hit_track) return fail(APO_EINVAL, "APO_SCHED_MAXSET takes no hit_track");
+        if (o->max_tracks > 1) {
+            if (o->trace_count) return fail(APO_EINVAL, "APO_SCHED_MAXSET with max_tracks > 1 writes no trace");
+            for (int i = 0; i <= lv; i++)
+                if ((o->precision[i] & ~APO_OUTGOING) == APO_F64_MID)
+                    return fail(APO_EINVAL, "APO_SCHED_MAXSET with max_tracks > 1 takes no APO_F64_MID level");
+        } else if (o->hit_track) {
+            return fail(APO_EINVAL, "APO_SCHED_MAXSET takes hit_track only with max_tracks > 1");
+        }
         if (o->max_keep < 1 || o->max_keep > (1 << 20)) return fail(APO_EINVAL, "max_keep must be in [1, 2^20]");
         if (o->slack < 0) return fail(APO_EINVAL, "slack < 0");
         if (maxset_smem_bytes(g->dg) > 64 * 1024)
@@ -497,7 +503,7 @@ int enqueue_maxset(const apo_geometry *g, const apo_hits *hits, const apo_solve_
                    PrecAt prec_at, apo_track *tracks_out, int32_t *n_tracks_out, void *ws, const Layout &L,
                    cudaStream_t s) {
     int rc;
-    const int lv = g->dg.levels, K = o->max_keep, ne = hits->n_events;
+    const int lv = g->dg.levels, K = o->max_keep, ne = hits->n_events, mt = o->max_tracks;
     unsigned *status = at<unsigned>(ws, L.status);
     int32_t *nh = at<int32_t>(ws, L.n_hits);
     HitRecD *hd = at<HitRecD>(ws, L.hd);
@@ -508,13 +514,15 @@ int enqueue_maxset(const apo_geometry *g, const apo_hits *hits, const apo_solve_
     int32_t *stop = at<int32_t>(ws, L.ms_stop);
     uint64_t *ck = at<uint64_t>(ws, L.ms_ck);
     int32_t *cv = at<int32_t>(ws, L.ms_cv);
+    uint32_t *active = at<uint32_t>(ws, L.mask);
+    int32_t *done = at<int32_t>(ws, L.done);
     int32_t *ntr = n_tracks_out ? n_tracks_out : at<int32_t>(ws, L.ntr);
     const int block = o->tune.cells_block ? o->tune.cells_block : 256;
     const int chunk = (o->tune.chunk_events > 0 && o->tune.chunk_events < L.ms_chunk) ? o->tune.chunk_events
                                                                                       : L.ms_chunk;
     CU(cudaMemsetAsync(status, 0, 256, s));
-    launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, at<uint32_t>(ws, L.mask),
-                 at<int32_t>(ws, L.done), status, s);
+    launch_stage(g->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, active, done, status, s,
+                 mt > 1 ? o->hit_track : nullptr);
     if ((rc = check_launch("stage"))) return rc;
     for (int e0 = 0; e0 < ne; e0 += chunk) {
         NvtxRange range_chunk("apo max-set chunk");
@@ -522,7 +530,8 @@ int enqueue_maxset(const apo_geometry *g, const apo_hits *hits, const apo_solve_
         const HitRecD *hde = hd + (size_t)e0 * kHitCap;
         const HitRecF *hfe = hf + (size_t)e0 * kHitCap;
         const int32_t *nhe = nh + e0;
-        CU(cudaMemsetAsync(stop, 0, sizeof(int32_t) * (size_t)n, s));
+        // multi-track rounds search the hits still active; one track per event: every hit
+        uint32_t *act = mt > 1 ? active + (size_t)e0 * 8 : nullptr;
         MaxsetArgs A{};
         A.levels = lv;
         A.max_keep = K;
@@ -533,35 +542,49 @@ int enqueue_maxset(const apo_geometry *g, const apo_hits *hits, const apo_solve_
         A.count_out = count;
         A.stop = stop;
         A.n_hits = nhe;
-        A.tracks = tracks_out + e0;
+        A.tracks = tracks_out + (size_t)e0 * mt;
         A.n_tracks = ntr + e0;
-        A.final_level = o->final_level ? o->final_level + e0 : nullptr;
-        A.n_final = o->n_final ? o->n_final + e0 : nullptr;
+        A.final_level = o->final_level ? o->final_level + (size_t)e0 * mt : nullptr;
+        A.n_final = o->n_final ? o->n_final + (size_t)e0 * mt : nullptr;
         A.trace_keys = o->trace_count && o->trace_keys ? o->trace_keys + (size_t)e0 * (lv + 1) * K : nullptr;
         A.trace_votes = o->trace_count && o->trace_votes ? o->trace_votes + (size_t)e0 * (lv + 1) * K : nullptr;
         A.trace_count = o->trace_count ? o->trace_count + (size_t)e0 * (lv + 1) : nullptr;
+        A.max_tracks = mt;
+        A.width = 3.0 * o->mask_sigma;
+        A.active = act;
+        A.done = mt > 1 ? done + e0 : nullptr;
+        A.hd = hde;
+        A.hf = hfe;
+        A.offsets = hits->offsets + e0;
+        A.hit_track = mt > 1 ? o->hit_track : nullptr;
         if (A.trace_count) CU(cudaMemsetAsync(A.trace_count, 0, sizeof(int32_t) * (size_t)n * (lv + 1), s));
-        // level 0: every cell of the grid, one thread each, in linear (= key) order
-        launch_vote_keys(gl[0], prec_at(0), n, hde, hfe, nhe, 0, nullptr, g->n_coarse, votes, s);
-        if ((rc = check_launch("vote_coarse_cells"))) return rc;
-        A.level = 0;
-        A.votes = votes;
-        A.keys = nullptr;
-        A.count_in = nullptr;
-        A.stride = g->n_coarse;
-        launch_maxset_select(gl[0], n, A, s);
-        if ((rc = check_launch("maxset_select"))) return rc;
-        for (int lev = 1; lev <= lv; lev++) {
-            launch_vote_children(gl[lev], prec_at(lev), n, hde, hfe, nhe, lev, front, K, ck, cv, s, nullptr,
-                                 block, count);
-            if ((rc = check_launch("vote_children"))) return rc;
-            A.level = lev;
-            A.votes = cv;
-            A.keys = ck;
-            A.count_in = count;
-            A.stride = (long long)K * 32;
-            launch_maxset_select(gl[lev], n, A, s);
+        for (int r = 0; r < mt; r++) {
+            A.round = r;
+            CU(cudaMemsetAsync(stop, 0, sizeof(int32_t) * (size_t)n, s));
+            // level 0: every cell of the grid, one thread each, in linear (= key) order
+            launch_vote_keys(gl[0], prec_at(0), n, hde, hfe, nhe, 0, nullptr, g->n_coarse, votes, s, act);
+            if ((rc = check_launch("vote_coarse_cells"))) return rc;
+            A.level = 0;
+            A.prec = prec_at(0) & ~APO_OUTGOING;
+            A.votes = votes;
+            A.keys = nullptr;
+            A.count_in = nullptr;
+            A.stride = g->n_coarse;
+            launch_maxset_select(gl[0], n, A, s);
             if ((rc = check_launch("maxset_select"))) return rc;
+            for (int lev = 1; lev <= lv; lev++) {
+                launch_vote_children(gl[lev], prec_at(lev), n, hde, hfe, nhe, lev, front, K, ck, cv, s, act,
+                                     block, count);
+                if ((rc = check_launch("vote_children"))) return rc;
+                A.level = lev;
+                A.prec = prec_at(lev) & ~APO_OUTGOING;
+                A.votes = cv;
+                A.keys = ck;
+                A.count_in = count;
+                A.stride = (long long)K * 32;
+                launch_maxset_select(gl[lev], n, A, s);
+                if ((rc = check_launch("maxset_select"))) return rc;
+            }
         }
     }
     return APO_OK;

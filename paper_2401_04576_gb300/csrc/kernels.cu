@@ -213,10 +213,14 @@ template <int MODE> struct CoarseSmem {
     __host__ __device__ static size_t total(int Bl, int) { return L32(Bl) + 8 * Bl + 16; }
 };
 
-// Resident 256-thread blocks per SM asked of the compiler for the FP32 coarse kernel (it
-// caps registers at 64K / (256 x this)); the FP64 kernels are bound by the FP64 pipe.
+// The FP32 coarse kernel splits each tile's (d0, z0) cells over APO_F32_COARSE_SPLIT
+// blocks, and asks the compiler for APO_F32_COARSE_MIN_BLOCKS resident blocks per SM (it
+// caps registers at 64K / (threads x this)); the FP64 kernels are bound by the FP64 pipe.
+#ifndef APO_F32_COARSE_SPLIT
+#define APO_F32_COARSE_SPLIT 1
+#endif
 #ifndef APO_F32_COARSE_MIN_BLOCKS
-#define APO_F32_COARSE_MIN_BLOCKS 3
+#define APO_F32_COARSE_MIN_BLOCKS (3 * APO_F32_COARSE_SPLIT)
 #endif
 // The FP64 modes split each (phi0, omega) tile's (d0, z0) cells over APO_F64_COARSE_SPLIT
 // blocks (consecutive ranges of the d0-fastest index): smaller blocks with the same register
@@ -228,7 +232,7 @@ template <int MODE> struct CoarseSmem {
 #define APO_F64_COARSE_MIN_BLOCKS (APO_F64_COARSE_SPLIT == 1 ? 1 : 3)
 #endif
 template <int MODE> struct CoarseShape {
-    static constexpr int split = MODE == kModeF32 ? 1 : APO_F64_COARSE_SPLIT;
+    static constexpr int split = MODE == kModeF32 ? APO_F32_COARSE_SPLIT : APO_F64_COARSE_SPLIT;
     static constexpr int threads = 256 / split;
     static constexpr int min_blocks = MODE == kModeF32 ? APO_F32_COARSE_MIN_BLOCKS : APO_F64_COARSE_MIN_BLOCKS;
 };
@@ -360,17 +364,26 @@ __device__ __forceinline__ void coarse_block(const DevGeom &g, int ev, int split
                 } else if (!p32.guard) {
                     lm = 0;
                     n_tail32 += Bl;
+                    // sign of the wire's stereo tangent (0: unknown)
+                    const int tsg = h32.t.lo >= 0.f ? 1 : (h32.t.hi <= 0.f ? -1 : 0);
 #pragma unroll 1
                     for (int l = 0; l < Bl; l++) {
                         const IV<float> Ll = L32[l];
                         bool tv;
                         if (MODE == kModeF32) {
-                            // the block's threads share the bin: a uniform branch on L's sign
-                            // (in the filtered FP64 mode the three FP32 tails cost more code
-                            // than they save)
-                            tv = Ll.lo >= 0.f ? tail<float, 1>(p32, Ll, h32, R32, c32.W, k)
-                               : Ll.hi <= 0.f ? tail<float, -1>(p32, Ll, h32, R32, c32.W, k)
-                                              : tail<float, 0>(p32, Ll, h32, R32, c32.W, k);
+                            // The block's threads share the bin and the hit: uniform branches
+                            // on the signs of L and t.  A bin with L <= 0 is evaluated
+                            // reflected, (L, t) -> (-L, -t), which gives the same vote, so the
+                            // tail always sees L >= 0 and a known sign of t.  (In the filtered
+                            // FP64 mode the extra FP32 tails cost more code than they save.)
+                            const bool lpos = Ll.lo >= 0.f, lneg = Ll.hi <= 0.f;
+                            const int ts = lpos ? tsg : (lneg ? -tsg : 0);
+                            Hit<float> hr = h32;
+                            if (!lpos) hr.t = neg(h32.t);
+                            const IV<float> Lr = lpos ? Ll : neg(Ll);
+                            tv = ts > 0 ? tail<float, 1, false, 1>(p32, Lr, hr, R32, c32.W, k)
+                               : ts < 0 ? tail<float, 1, false, -1>(p32, Lr, hr, R32, c32.W, k)
+                                        : tail<float, 0>(p32, Ll, h32, R32, c32.W, k);
                         } else {
                             tv = tail<float>(p32, Ll, h32, R32, c32.W, k);
                         }
@@ -1019,9 +1032,9 @@ static void launch_cells(const DevGeom &g, int prec, int n_ev, const HitRecD *hd
 
 void launch_vote_keys(const DevGeom &g, int prec, int n_ev, const HitRecD *hd, const HitRecF *hf,
                       const int32_t *n_hits, int level, const uint64_t *keys, long long n_per_ev,
-                      int32_t *votes, cudaStream_t s) {
+                      int32_t *votes, cudaStream_t s, const uint32_t *active) {
     if (n_ev <= 0 || n_per_ev <= 0) return;
-    launch_cells(g, prec, n_ev, hd, hf, n_hits, nullptr, level, keys, nullptr, n_per_ev, nullptr, votes,
+    launch_cells(g, prec, n_ev, hd, hf, n_hits, active, level, keys, nullptr, n_per_ev, nullptr, votes,
                  nullptr, s);
 }
 

@@ -122,7 +122,7 @@ void launch_select_candidates(const DevGeom &g, int ev0, int n_ev, const uint64_
                               uint64_t *out_keys, int32_t *out_votes, cudaStream_t s);
 void launch_vote_keys(const DevGeom &g, int prec, int n_ev, const HitRecD *hd, const HitRecF *hf,
                       const int32_t *n_hits, int level, const uint64_t *keys, long long n_per_ev,
-                      int32_t *votes, cudaStream_t s);
+                      int32_t *votes, cudaStream_t s, const uint32_t *active = nullptr);
 void launch_vote_children(const DevGeom &g, int prec, int n_ev, const HitRecD *hd,
                           const HitRecF *hf, const int32_t *n_hits, int child_level,
                           const uint64_t *parents, int n_par, uint64_t *child_keys,
@@ -153,16 +153,27 @@ void launch_series_consts(SeriesConsts *dev_out, cudaStream_t s);
 struct MaxsetArgs {
     int level, levels, max_keep, slack, min_votes;
     long long n_coarse, stride;
-    const int32_t *votes;
+    int32_t *votes;                // the level's votes (the multi-track step marks cells in it)
     const uint64_t *keys;
     const int32_t *count_in;
     uint64_t *front;
     int32_t *count_out, *stop;
     const int32_t *n_hits;
-    apo_track *tracks;
-    int32_t *n_tracks, *final_level, *n_final;
+    apo_track *tracks;             // events x max_tracks
+    int32_t *n_tracks, *final_level, *n_final;   // the last two: events x max_tracks
     uint64_t *trace_keys;          // may be null: events x (levels + 1) x max_keep
     int32_t *trace_votes, *trace_count;
+    // multi-track extraction (max_tracks > 1): round, the level's precision code (no flag),
+    // 3 sigma, the events' active-hit words, done flags, staged hits, batch offsets of the
+    // events' first hits and the hit_track output (may be null)
+    int max_tracks, round, prec;
+    double width;
+    uint32_t *active;
+    int32_t *done;
+    const HitRecD *hd;
+    const HitRecF *hf;
+    const int32_t *offsets;
+    int32_t *hit_track;
 };
 // Persistent batch search (kernels.cu): the top-K schedule with multi-track rounds, every
 // event's whole search in one block, blocks pulling events from next_event (zeroed by the

@@ -9,6 +9,15 @@
 // vmax group's cell indices, from which one warp per axis sums count x centre in ascending
 // index order: the mean of the group's cell centres with a summation order fixed by the
 // indices, so the result does not depend on the order the cells arrive in.
+//
+// Multi-track extraction (max_tracks > 1, one search per round on the hits still active):
+// the final vmax group can hold several tracks' cells (tracks with equal hit counts tie),
+// so a round keeps one of them.  The seed is the group's lowest key, S the active hits
+// that vote for it at the level's precision, and the track's cells are the group's cells
+// that every hit of S votes for (each has vmax votes, so its voting hits are exactly S);
+// they are marked in the vote array.  The estimate is taken over them as above; the track
+// takes S and every active hit that votes (FP64) for one of them with its drift widened
+// by 3 sigma (Section 3.3's hit finding), which leave the active set.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -35,6 +44,27 @@ __device__ __forceinline__ void cell_index(const DevGeom &g, const uint64_t *key
 
 __device__ __forceinline__ int clamp_votes(int v) { return v < 0 ? 0 : (v > kHitCap ? kHitCap : v); }
 
+constexpr int32_t kTrackCell = -2;   // a vote-array mark: a cell of the round's track
+
+__device__ __forceinline__ Cell<double> cell_at(const DevGeom &g, int level, const int idx[5]) {
+    return Cell<double>{edge(g, 0, level, idx[0]), sin_phi0(g, level, idx[1]), cos_phi0(g, level, idx[1]),
+                        edge(g, 2, level, idx[2]), edge(g, 3, level, idx[3]), edge(g, 4, level, idx[4])};
+}
+
+// The vote of staged hit i for a cell at the level's precision code, as the voting
+// kernels count it (FP32 cells are the FP64 edges rounded outward; the FP32-filtered mode
+// votes as FP64).
+__device__ __forceinline__ bool vote_at(const DevGeom &g, int prec, const Cell<double> &c, const HitRecD *hd,
+                                        const HitRecF *hf, int i) {
+    if (prec == APO_F32) {
+        Cell<float> c32{to_prec<float>(c.D), to_prec<float>(c.S0), to_prec<float>(c.C0), to_prec<float>(c.W),
+                        to_prec<float>(c.Z), to_prec<float>(c.L)};
+        return vote_pair<float>(c32, load_hit<float>(hf + i), g.k);
+    }
+    if (prec == APO_F64_EXACT) return vote_pair_exact(c, load_hit<double>(hd + i), g.k);
+    return vote_pair<double>(c, load_hit<double>(hd + i), g.k);
+}
+
 __global__ void __launch_bounds__(kMsThreads)
 k_maxset_select(DevGeom g, MaxsetArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -44,20 +74,33 @@ k_maxset_select(DevGeom g, MaxsetArgs A) {
     __shared__ int s_T, s_final, s_vmax, s_kept;
     const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (A.stop[e]) return;
-    const int nh = A.n_hits[e];
-    apo_track &t = A.tracks[e];
-    if (A.level == 0) {
-        if (tid < 5) { t.p[tid] = 0.0; t.w[tid] = 0.0; }
+    const int mt = A.max_tracks;
+    if (A.done && A.done[e]) {   // a later round of an event whose extraction has ended
         if (tid == 0) {
-            t.votes = nh < 0 ? nh : 0;
-            t.n_hits = nh < 0 ? 0 : nh;
-            A.n_tracks[e] = 0;
+            A.stop[e] = 1;
+            A.count_out[e] = 0;
         }
+        return;
+    }
+    const int nh = A.n_hits[e];
+    apo_track *te = A.tracks + (long long)e * mt;
+    apo_track &t = te[A.round];
+    if (A.level == 0 && A.round == 0) {
+        for (int q = tid; q < 5 * mt; q += kMsThreads) {
+            te[q / 5].p[q % 5] = 0.0;
+            te[q / 5].w[q % 5] = 0.0;
+        }
+        if (tid < mt) {
+            te[tid].votes = (tid == 0 && nh < 0) ? nh : 0;
+            te[tid].n_hits = nh < 0 ? 0 : nh;
+        }
+        if (tid == 0) A.n_tracks[e] = 0;
         if (nh < 0) {   // malformed event: no search
             if (tid == 0) {
                 A.stop[e] = 1;
                 A.count_out[e] = 0;
-                if (A.final_level) A.final_level[e] = 0;
+                if (A.final_level) A.final_level[(long long)e * mt] = 0;
+                if (A.done) A.done[e] = 1;
             }
             return;
         }
@@ -90,22 +133,83 @@ k_maxset_select(DevGeom g, MaxsetArgs A) {
     __syncthreads();
     const int T = s_T, vmax = s_vmax, kept = s_kept;
     if (s_final) {
-        // ---- estimate over the vmax group ----
+        const bool multi = mt > 1;
+        __shared__ unsigned long long s_seed;
+        __shared__ uint32_t s_act[8], s_S[8], s_take[8];
+        __shared__ int s_mc;
+        if (multi && vmax < A.min_votes) {   // no track this round: the extraction ends
+            if (tid < 8) A.active[(long long)e * 8 + tid] = 0u;   // later rounds vote no hit
+            if (tid == 0) {
+                A.stop[e] = 1;
+                A.count_out[e] = 0;
+                A.done[e] = 1;
+            }
+            return;
+        }
+        // ---- estimate over the vmax group (multi-track: over the round's track cells) ----
         const int sh = g.levels - A.level;
         int off[6];
         off[0] = 0;
 #pragma unroll
         for (int a = 0; a < 5; a++) off[a + 1] = off[a] + (g.bins[a] << A.level);
         for (int i = tid; i < off[5]; i += kMsThreads) cnt[i] = 0;
-        __syncthreads();
+        const HitRecD *hde = multi ? A.hd + (long long)e * kHitCap : nullptr;
+        const HitRecF *hfe = multi ? A.hf + (long long)e * kHitCap : nullptr;
+        if (multi) {
+            if (tid == 0) { s_seed = ~0ull; s_mc = 0; }
+            if (tid < 8) { s_act[tid] = A.active[(long long)e * 8 + tid]; s_S[tid] = 0u; }
+            __syncthreads();
+            // the seed: the group's lowest key
+            unsigned long long kmin = ~0ull;
+            for (long long j = tid; j < n; j += kMsThreads) {
+                if (clamp_votes(vo[j]) != vmax) continue;
+                int idx[5];
+                cell_index(g, ke, j, idx);
+                const unsigned long long key = pack_key(g, idx);
+                kmin = key < kmin ? key : kmin;
+            }
+            atomicMin(&s_seed, kmin);
+            __syncthreads();
+            // S: the active hits that vote for it, one hit per thread
+            {
+                int idx[5];
+                unpack_key(g, s_seed, idx);
+                const Cell<double> cs = cell_at(g, A.level, idx);
+                for (int i = tid; i < nh; i += kMsThreads)
+                    if (((s_act[i >> 5] >> (i & 31)) & 1u) && vote_at(g, A.prec, cs, hde, hfe, i))
+                        atomicOr(&s_S[i >> 5], 1u << (i & 31));
+            }
+            __syncthreads();
+        } else {
+            __syncthreads();
+        }
+        int *vw = A.votes + (long long)e * A.stride;
+        int mc_local = 0;
         for (long long j = tid; j < n; j += kMsThreads) {
             if (clamp_votes(vo[j]) != vmax) continue;
             int idx[5];
             cell_index(g, ke, j, idx);
+            if (multi) {   // a cell of the track when every hit of S votes for it
+                const Cell<double> c = cell_at(g, A.level, idx);
+                bool ok = true;
+                for (int w8 = 0; w8 < 8 && ok; w8++) {
+                    uint32_t m = s_S[w8];
+                    while (m && ok) {
+                        const int i = w8 * 32 + __ffs(m) - 1;
+                        m &= m - 1;
+                        ok = vote_at(g, A.prec, c, hde, hfe, i);
+                    }
+                }
+                if (!ok) continue;
+                vw[j] = kTrackCell;
+                mc_local++;
+            }
 #pragma unroll
             for (int a = 0; a < 5; a++) atomicAdd(&cnt[off[a] + idx[a]], 1u);
         }
+        if (multi && mc_local) atomicAdd(&s_mc, mc_local);
         __syncthreads();
+        const int m_est = multi ? s_mc : kept;
         if (wid < 5) {
             const int a = wid, nb = off[a + 1] - off[a];
             const uint32_t *ca = cnt + off[a];
@@ -128,20 +232,60 @@ k_maxset_select(DevGeom g, MaxsetArgs A) {
                 }
             }
             if (lane == 0 && vmax >= A.min_votes) {
-                t.p[a] = __ddiv_rn(sum, (double)kept);
+                t.p[a] = __ddiv_rn(sum, (double)m_est);
                 t.w[a] = __dmul_rn(__dsub_rn(hi_max, lo_min), 0.5);
             }
         }
+        const long long fo = (long long)e * mt + A.round;
         if (tid == 0) {
             if (vmax >= A.min_votes) {
                 t.votes = vmax;
-                A.n_tracks[e] = 1;
+                A.n_tracks[e] = A.round + 1;
             }
             A.stop[e] = 1;
             A.count_out[e] = 0;
-            if (A.final_level) A.final_level[e] = A.level;
-            if (A.n_final) A.n_final[e] = kept;
+            if (A.final_level) A.final_level[fo] = A.level;
+            if (A.n_final) A.n_final[fo] = m_est;
         }
+        if (!multi) return;
+        // ---- hit finding: S and the active hits voting (FP64, drift +- 3 sigma) for a track cell ----
+        if (tid < 8) s_take[tid] = s_S[tid];
+        __syncthreads();
+        for (long long j = tid; j < n; j += kMsThreads) {
+            if (vw[j] != kTrackCell) continue;
+            int idx[5];
+            cell_index(g, ke, j, idx);
+            const Cell<double> c = cell_at(g, A.level, idx);
+            for (int i = 0; i < nh; i++) {
+                const uint32_t bit = 1u << (i & 31);
+                if (!(s_act[i >> 5] & bit) || (s_take[i >> 5] & bit)) continue;
+                Hit<double> h = load_hit<double>(hde + i);
+                const double d = h.d.lo;
+                const double dlo = __dsub_rd(d, A.width);
+                h.d = {gt0(dlo) ? dlo : 0.0, __dadd_ru(d, A.width)};
+                if (vote_pair<double>(c, h, g.k)) atomicOr(&s_take[i >> 5], bit);
+            }
+        }
+        __syncthreads();
+        __shared__ int s_left;
+        if (tid == 0) s_left = 0;
+        __syncthreads();
+        if (tid < 8) {
+            const uint32_t took = s_act[tid] & s_take[tid], left = s_act[tid] & ~s_take[tid];
+            A.active[(long long)e * 8 + tid] = left;
+            if (left) atomicOr(&s_left, 1);
+            if (A.hit_track) {
+                const int a0 = A.offsets[e];
+                uint32_t m = took;
+                while (m) {
+                    const int i = tid * 32 + __ffs(m) - 1;
+                    m &= m - 1;
+                    A.hit_track[a0 + i] = A.round;
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && (!s_left || A.round + 1 >= mt)) A.done[e] = 1;
         return;
     }
     // ---- order-preserving compaction of {votes >= T} ----

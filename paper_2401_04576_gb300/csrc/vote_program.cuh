@@ -86,12 +86,13 @@ template <typename T> __device__ __forceinline__ IV<T> atan_iv(IV<T> x, const Se
 
 // sin and cos over an interval d with |d| <= 1 (d is the small stereo correction of the
 // phase): sin d = d (1 - d^2/6) + [-1, 1] |d|^5/5!, cos d = 1 - d^2/2 + [-1, 1] |d|^4/4!
-// (Taylor with Lagrange remainders); [-1, 1] when |d| > 1.
+// (Taylor with Lagrange remainders); [-1, 1] when |d| > 1.  Returns whether |d| <= 1, in
+// which case c >= 1 - 1/2 - 1/24 > 0.
 template <typename T>
-__device__ __forceinline__ void sincos_iv(IV<T> d, IV<T> &s, IV<T> &c, const SeriesConsts &k) {
+__device__ __forceinline__ bool sincos_iv(IV<T> d, IV<T> &s, IV<T> &c, const SeriesConsts &k) {
     const IV<T> one{T(1), T(1)};
     T m = mag(d);
-    if (!le(m, T(1))) { s = {T(-1), T(1)}; c = {T(-1), T(1)}; return; }
+    if (!le(m, T(1))) { s = {T(-1), T(1)}; c = {T(-1), T(1)}; return false; }
     IV<T> y = sqr(d);
     IV<T> S = sub(one, mul_pp(y, cst<T>(k, C_SIN3)));
     T m2 = ru_mul(m, m), m4 = ru_mul(m2, m2);
@@ -99,6 +100,7 @@ __device__ __forceinline__ void sincos_iv(IV<T> d, IV<T> &s, IV<T> &c, const Ser
     IV<T> cv = add(sub(one, half(y)), pm(ru_mul(m4, cst<T>(k, C_COS4).hi)));
     s = clamp1(sv);
     c = clamp1(cv);
+    return true;
 }
 
 // Products use mul_nn (second operand >= 0) or mul_pp (both >= 0) where the program's
@@ -180,14 +182,46 @@ template <int LS, typename T> __device__ __forceinline__ IV<T> lsqr(IV<T> L) {
     if (LS < 0) return {rd_mul(L.hi, L.hi), ru_mul(L.lo, L.lo)};
     return sqr(L);
 }
+// a b when both signs are known (SA, SB = 1 for >= 0, -1 for <= 0): one product per end
+// point, the one the sign cases of the general product pick.
+template <int SA, int SB, typename T> __device__ __forceinline__ IV<T> mul_ss(IV<T> a, IV<T> b) {
+    static_assert(SA != 0 && SB != 0, "signs must be known");
+    if (SA > 0 && SB > 0) return {rd_mul(a.lo, b.lo), ru_mul(a.hi, b.hi)};
+    if (SA > 0 && SB < 0) return {rd_mul(a.hi, b.lo), ru_mul(a.lo, b.hi)};
+    if (SA < 0 && SB > 0) return {rd_mul(a.lo, b.hi), ru_mul(a.hi, b.lo)};
+    return {rd_mul(a.hi, b.hi), ru_mul(a.lo, b.lo)};
+}
+// a t for the stereo tangent t of the hit's wire when its sign is known (TS as LS)
+template <int TS, typename T> __device__ __forceinline__ IV<T> tmul(IV<T> a, IV<T> t) {
+    if (TS > 0) return mul_nn(a, t);
+    if (TS < 0) return mul_np(a, t);
+    return mul(a, t);
+}
+// square of an interval whose sign is known (S as LS)
+template <int S, typename T> __device__ __forceinline__ IV<T> sqr_s(IV<T> a) {
+    if (S > 0) return {rd_mul(a.lo, a.lo), ru_mul(a.hi, a.hi)};
+    if (S < 0) return {rd_mul(a.hi, a.hi), ru_mul(a.lo, a.lo)};
+    return sqr(a);
+}
 
 // The tan(lambda)-dependent rest: Phi (ApproxPhi_a), u_d (normudi), z^St (EQSinter_c),
 // c^tau and the radicand of Eq. (defdiAX_b); returns the vote (either drift sign).  LS: the
-// sign of L when the caller knows it (see lmul).  OUT: also store the evaluated intervals
-// in ends (see vote_pair_ends); the voting kernels use OUT = false.
-template <typename T, int LS = 0, bool OUT = false>
+// sign of L when the caller knows it (see lmul); TS: that of the wire's stereo tangent h.t
+// (see tmul), which needs LS known too.  OUT: also store the evaluated intervals in ends
+// (see vote_pair_ends); the voting kernels use OUT = false.
+//
+// Sign-known forms give the same end points as the general ones, so every instantiation
+// returns the same vote.  The program is also unchanged, bit for bit, under the reflection
+// z -> -z of the cell and the wire ((L, t) -> (-L, -t); z^St and c^tau change sign, every
+// other quantity keeps its end points, because an interval product with both operands
+// negated has the same four end-point products and one with a single operand negated is
+// the exact negation): a caller may evaluate (-L, -t) in place of (L, t) to reach a known
+// sign of L.
+template <typename T, int LS = 0, bool OUT = false, int TS = 0>
 __device__ __forceinline__ bool tail(const Pre<T> &p, IV<T> L, const Hit<T> &h, IV<T> R, IV<T> W,
                                      const SeriesConsts &k, double *ends = nullptr) {
+    static_assert(TS == 0 || LS != 0, "a known sign of t needs a known sign of L");
+    constexpr int LT = LS * TS;   // the sign of L t when both are known
     const IV<T> one{T(1), T(1)};
     IV<T> L2 = lsqr<LS>(L);
     IV<T> P1e = neg(mul_nn(lmul<LS>(p.psi_sPA, L), p.Ninv));
@@ -197,27 +231,36 @@ __device__ __forceinline__ bool tail(const Pre<T> &p, IV<T> L, const Hit<T> &h, 
                               p.dW),
                        p.Nh);
     // delta = Phi - Phi^Ax, parts even / odd in the drift sign
-    IV<T> de = add(mul(P1e, h.t), mul_nn(P2e, h.t2));
-    IV<T> dod = add(mul(P1o, h.t), mul_nn(P2o, h.t2));
+    IV<T> de = add(tmul<TS>(P1e, h.t), mul_nn(P2e, h.t2));
+    IV<T> dod = add(tmul<TS>(P1o, h.t), mul_nn(P2o, h.t2));
     IV<T> dP = add(de, dod);
     IV<T> dM = sub(de, dod);
     if (OUT) { ends[5] = dP.lo; ends[6] = dP.hi; ends[7] = dM.lo; ends[8] = dM.hi; }
-    IV<T> sd, cd;
-    sincos_iv(hull(dP, dM), sd, cd, k);
-    IV<T> sP = clamp1(add(mul(p.sPA, cd), mul(p.cPA, sd)));
-    IV<T> cP = clamp1(sub(mul(p.cPA, cd), mul(p.sPA, sd)));
+    IV<T> sd, cd, sP, cP;
+    const bool small = sincos_iv(hull(dP, dM), sd, cd, k);
+    if (sizeof(T) == 4 && small) {   // FP32: cos(delta) > 0 (FP64 keeps its sign cases)
+        sP = clamp1(add(mul_nn(p.sPA, cd), mul(p.cPA, sd)));
+        cP = clamp1(sub(mul_nn(p.cPA, cd), mul(p.sPA, sd)));
+    } else {
+        sP = clamp1(add(mul(p.sPA, cd), mul(p.cPA, sd)));
+        cP = clamp1(sub(mul(p.cPA, cd), mul(p.sPA, sd)));
+    }
     // u_d^2 (Eq. normudi)
-    IV<T> u2 = add(add(add(one, mul(scale2(h.t), lmul<LS>(sP, L))), mul_pp(L2, h.t2)), mul_pp(sqr(cP), h.t2));
+    IV<T> tLsP = TS != 0 ? tmul<TS>(lmul<LS>(sP, L), scale2(h.t)) : mul(scale2(h.t), lmul<LS>(sP, L));
+    IV<T> u2 = add(add(add(one, tLsP), mul_pp(L2, h.t2)), mul_pp(sqr(cP), h.t2));
     if (le0(u2.lo)) {
         if (OUT) ends[4] = 1;
         return true;
     }
     IV<T> Q = mul_pp(h.d, recip(sqrti(u2)));
-    IV<T> Qct = mul_nn(mul(cP, h.t), Q);
-    IV<T> LQ = mul_nn(L, Q);
-    IV<T> LQrsA = mul(LQ, p.rsA);
-    IV<T> a2 = mul_pp(W, sqr(Q));
-    IV<T> a5 = mul_pp(W, sqr(mul(LQ, h.t)));
+    IV<T> Qct = mul_nn(tmul<TS>(cP, h.t), Q);
+    IV<T> LQ = LS > 0 ? mul_pp(L, Q) : mul_nn(L, Q);                  // Q >= 0
+    IV<T> LQrsA = LS > 0 ? mul_nn(p.rsA, LQ) : LS < 0 ? mul_np(p.rsA, LQ) : mul(LQ, p.rsA);
+    IV<T> a2 = mul_pp(W, sqr_s<1>(Q));
+    IV<T> LQt;
+    if constexpr (LT != 0) LQt = mul_ss<LS, TS>(LQ, h.t);
+    else LQt = mul(LQ, h.t);
+    IV<T> a5 = mul_pp(W, sqr_s<LT>(LQt));
     IV<T> t2x = scale2(h.t);
     bool vote = false;
 #pragma unroll
@@ -227,8 +270,8 @@ __device__ __forceinline__ bool tail(const Pre<T> &p, IV<T> L, const Hit<T> &h, 
         IV<T> zS = sg == 0 ? sub(lmul<LS>(sp, L), Qct) : add(lmul<LS>(sp, L), Qct);   // z^St - z_ref
         IV<T> rct = sg == 0 ? sub(mul(zS, p.rcA), LQrsA) : add(mul(zS, p.rcA), LQrsA);
         IV<T> a1 = sg == 0 ? scale2(Q) : neg(scale2(Q));
-        IV<T> a3 = mul(t2x, rct);
-        IV<T> a4 = mul_pp(W, sqr(mul(zS, h.t)));
+        IV<T> a3 = TS != 0 ? tmul<TS>(rct, t2x) : mul(t2x, rct);
+        IV<T> a4 = mul_pp(W, sqr(tmul<TS>(zS, h.t)));
         IV<T> Arad = sub(sub(sub(add(a1, a2), a3), a4), a5);
         IV<T> G = sub(p.G0, Arad);
         if (OUT) { ends[2 * sg] = G.lo; ends[2 * sg + 1] = G.hi; }

@@ -200,3 +200,102 @@ def test_maxset_full_batch_sampled(wires):
     truth = np.array([tr[0].params for tr in ev.tracks])
     inside = np.all(np.abs(t["p"] - truth) <= t["w"], axis=1)
     assert inside.mean() >= 0.95, inside.mean()
+
+
+def _tied_event(w, rng):
+    """Two noiseless tracks with equal hit counts on disjoint wires (phi0 >= 1 rad apart)."""
+    while True:
+        a, b = chamber.draw_track(rng), chamber.draw_track(rng)
+        ha, hb = chamber.simulate_track(a, w, None), chamber.simulate_track(b, w, None)
+        dphi = abs((a.params[1] - b.params[1] + np.pi) % (2 * np.pi) - np.pi)
+        if len(ha) == len(hb) >= 8 and dphi > 1.0 and not ({h.wire for h in ha} & {h.wire for h in hb}):
+            items = sorted([(h.wire, h.drift) for h in ha + hb])
+            return [i[0] for i in items], [i[1] for i in items]
+
+
+def _multi_batch(w, n_multi, seed):
+    ev = chamber.multi_track_events(n_multi, seed=seed, w=w)
+    wid, dr, off = list(ev.wire_id), list(ev.drift), list(ev.offsets)
+    rng = np.random.default_rng(seed)
+    for _ in range(2):   # two events of two tied tracks
+        a, b = _tied_event(w, rng)
+        wid += a
+        dr += b
+        off.append(off[-1] + len(a))
+    return chamber.Events(offsets=np.array(off, np.int32), wire_id=np.array(wid, np.int32),
+                          drift=np.array(dr))
+
+
+def _multi_opts(prec, keep, slack, mt, ne, nhits, **kw):
+    fl = torch.full((ne * mt,), -7, dtype=torch.int32, device="cuda")
+    nf = torch.full((ne * mt,), -7, dtype=torch.int32, device="cuda")
+    ht = torch.full((max(nhits, 1),), -5, dtype=torch.int32, device="cuda")
+    o = apo.solve_opts(precision=prec, schedule=apo.SCHED_MAXSET, max_keep=keep, slack=slack,
+                       max_tracks=mt, min_votes=6, final_level=fl, n_final=nf, hit_track=ht, **kw)
+    return o, (fl, nf, ht)
+
+
+def _check_multi(tab, ev, events, tracks, nt, outs, prec, keep, slack, mt):
+    fl, nf, ht = (x.cpu().numpy() for x in outs)
+    t = apo.tracks_to_numpy(tracks, ev.n_events, mt)
+    nt = nt.cpu().numpy()
+    oprec = [(1 if (p & ~OUT) == apo.F32 else 0) | (O.OUTGOING if p & OUT else 0) for p in prec]
+    n_found = 0
+    for e in events:
+        a, b = ev.offsets[e], ev.offsets[e + 1]
+        r = O.solve_event_maxset_multi(tab, ev.wire_id[a:b], ev.drift[a:b], keep, mt, 6, slack=slack,
+                                       prec_per_level=oprec)
+        assert nt[e] == r["n_tracks"], (e, nt[e], r["n_tracks"])
+        for k in range(r["n_tracks"]):
+            assert t[e, k]["votes"] == r["votes"][k], (e, k)
+            assert fl[e * mt + k] == r["final_level"][k] and nf[e * mt + k] == r["n_final"][k], (e, k)
+            assert np.array_equal(t[e, k]["p"], r["p"][k]) and np.array_equal(t[e, k]["w"], r["w"][k]), (e, k)
+        np.testing.assert_array_equal(ht[a:b], r["hit_track"])
+        n_found += r["n_tracks"]
+    return n_found
+
+
+@pytest.mark.parametrize("tune", [apo.ApoTune(0, 1, 256, 0), apo.ApoTune(0, 0, 128, 3)])
+def test_maxset_multi_track_bit_exact(wires, tune):
+    """Multi-track rounds (one hit-set cluster of the final group per round): tracks, final
+    levels, cluster sizes and every hit's track equal to the oracle, on config-4-like
+    events and on two events of two tied noiseless tracks, which must come out as two."""
+    g = G.make_grid([2, 64, 8, 2, 4], 3, 64)
+    tab = O.Tables(g, wires)
+    geom = apo.Geometry(g, wires)
+    ev = _multi_batch(wires, 6, 96)
+    prec = [apo.F32 | OUT, apo.F32 | OUT, apo.F64 | OUT, apo.F64 | OUT]
+    mt = 4
+    o, outs = _multi_opts(prec, 3000, 2, mt, ev.n_events, int(ev.offsets[-1]), tune=tune)
+    tracks, nt = apo.solve_batch(geom, _hits(ev), o)
+    torch.cuda.synchronize()
+    assert _check_multi(tab, ev, range(ev.n_events), tracks, nt, outs, prec, 3000, 2, mt) >= 8
+    assert np.all(nt.cpu().numpy()[-2:] == 2)
+
+
+def test_maxset_multi_track_config4_sampled(wires):
+    """The multi-track workload in the benchmark's form: config-4 events (1-5 tracks, 10-30 %
+    noise), the 2 x 256 x 16 x 2 x 8 grid, 5 levels, FP32 levels 0-3 / FP64 4-5 with the
+    direction condition, max_keep 32768, slack 2, up to 5 tracks, min 6 votes; 256 events,
+    the two with the fewest hits recomputed whole by the oracle; most true tracks found."""
+    g = G.make_grid([2, 256, 16, 2, 8], 5, 64)
+    tab = O.Tables(g, wires)
+    geom = apo.Geometry(g, wires)
+    ev = chamber.multi_track_events(256, seed=4, w=wires)
+    prec = [apo.F32 | OUT] * 4 + [apo.F64 | OUT] * 2
+    o, outs = _multi_opts(prec, 32768, 2, 5, ev.n_events, int(ev.offsets[-1]))
+    tracks, nt = apo.solve_batch(geom, _hits(ev), o)
+    torch.cuda.synchronize()
+    small = np.argsort(np.diff(ev.offsets), kind="stable")[:2]
+    _check_multi(tab, ev, small, tracks, nt, outs, prec, 32768, 2, 5)
+    t = apo.tracks_to_numpy(tracks, ev.n_events, 5)
+    nt = nt.cpu().numpy()
+    found = true = 0
+    for e in range(ev.n_events):
+        truth = np.array([tr.params for tr in ev.tracks[e]])
+        true += len(truth)
+        hit = np.zeros(len(truth), bool)
+        for k in range(nt[e]):
+            hit |= np.all(np.abs(t[e, k]["p"] - truth) <= t[e, k]["w"], axis=1)
+        found += int(hit.sum())
+    assert found >= 0.6 * true, (found, true)
