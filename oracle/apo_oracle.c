@@ -737,6 +737,7 @@ typedef struct {
     int32_t n[3][4];          /* voxels per axis per iteration */
     int32_t precision;        /* 0: FP64, 1: FP32 */
     int32_t n_iter;           /* 1 .. 3 */
+    int32_t per_sign;         /* 1: iteration 3 searches each sign around its own estimate */
 } or4_opts;
 
 typedef struct {
@@ -860,24 +861,22 @@ void or4_vote_grid(const or4_opts *o, const or4_grid *g, const double ref[2], co
     }
 }
 
-/* Values and errors of one iteration (Section 3.3: the centres and sizes of the maximum-
- * vote voxels): the sign whose accumulator has the larger maximum (ties: tan(lambda) > 0);
- * over its m maximum-vote voxels, value_a = lo_a + w_a (S_a / m + 1/2) with S_a the sum of
- * their indices on axis a (exact integers), error_a = w_a (i_max - i_min + 1) / 2. */
-static void v4_estimate(const or4_grid *g, const int32_t *votes, or4_iter *it) {
+/* Values and errors over the maximum-vote voxels of one sign's accumulator (s = 0 for
+ * tan(lambda) > 0), Section 3.3: over its m maximum-vote voxels, value_a = lo_a + w_a (S_a / m
+ * + 1/2) with S_a the sum of their indices on axis a (exact integers), error_a = w_a (i_max -
+ * i_min + 1) / 2. */
+static void v4_estimate_sign(const or4_grid *g, const int32_t *votes, int s, or4_iter *it) {
     const int64_t nvox = (int64_t)g->n[0] * g->n[1] * g->n[2] * g->n[3];
-    int32_t vm[2] = {0, 0};
-    for (int s = 0; s < 2; s++)
-        for (int64_t j = 0; j < nvox; j++)
-            if (votes[s * nvox + j] > vm[s]) vm[s] = votes[s * nvox + j];
-    const int s = vm[0] >= vm[1] ? 0 : 1;
+    int32_t vm = 0;
+    for (int64_t j = 0; j < nvox; j++)
+        if (votes[s * nvox + j] > vm) vm = votes[s * nvox + j];
     it->sign = s == 0 ? 1 : -1;
-    it->vmax = vm[s];
+    it->vmax = vm;
     int64_t m = 0, S[4] = {0, 0, 0, 0};
     int32_t imin[4], imax[4];
     for (int a = 0; a < 4; a++) { imin[a] = g->n[a]; imax[a] = -1; }
     for (int64_t j = 0; j < nvox; j++) {
-        if (votes[s * nvox + j] != vm[s]) continue;
+        if (votes[s * nvox + j] != vm) continue;
         int32_t idx[4];
         int64_t r = j;
         for (int a = 0; a < 4; a++) { idx[a] = (int32_t)(r % g->n[a]); r /= g->n[a]; }
@@ -894,6 +893,21 @@ static void v4_estimate(const or4_grid *g, const int32_t *votes, or4_iter *it) {
         it->value[a] = g->lo[a] + g->w[a] * (mu + 0.5);
         it->err[a] = (g->w[a] * (double)(imax[a] + 1 - imin[a])) * 0.5;
     }
+}
+
+static int32_t v4_vmax_sign(const or4_grid *g, const int32_t *votes, int s) {
+    const int64_t nvox = (int64_t)g->n[0] * g->n[1] * g->n[2] * g->n[3];
+    int32_t vm = 0;
+    for (int64_t j = 0; j < nvox; j++)
+        if (votes[s * nvox + j] > vm) vm = votes[s * nvox + j];
+    return vm;
+}
+
+/* Values and errors of one iteration: the sign whose accumulator has the larger maximum
+ * (the paper's choice of the tan(lambda) sign; ties: tan(lambda) > 0), estimated as above. */
+static void v4_estimate(const or4_grid *g, const int32_t *votes, or4_iter *it) {
+    const int s = v4_vmax_sign(g, votes, 0) >= v4_vmax_sign(g, votes, 1) ? 0 : 1;
+    v4_estimate_sign(g, votes, s, it);
 }
 
 /* exported for the pins: the disk pre-filter of one voxel (x_c, y_c, R lo / hi) */
@@ -995,35 +1009,79 @@ static double v4_move_z0(const or4_opts *o, const or4_iter *it, const double a[2
  * voxels, the reference point moved to the selected hit nearest to the found circle and
  * only the selected hits; iteration 3 on the box centred on iteration 2's values (z0 moved
  * to the new reference point) with the finest voxels.  Hit finding after each iteration
- * looks at every hit.  out: n_iter records; sel_out (may be NULL): the last selection. */
+ * looks at every hit.  With o->per_sign, iteration 3 reads "the value determined by the
+ * previous step" per accumulator: each tan(lambda) sign takes the estimate of its own
+ * accumulator of iteration 2, its hit finding, reference point and centred box, and votes
+ * on that box with its own selected hits; the sign with the larger maximum then gives the
+ * result as before.  out: n_iter records; sel_out (may be NULL): the last selection. */
 int or4_solve_event(const or4_opts *o, const or_wires *w, int32_t n_hits, const int32_t *wire_id,
                     const double *drift, or4_iter *out, uint8_t *sel_out) {
     int old = fegetround();
     fesetround(FE_TONEAREST);
-    uint8_t *act = (uint8_t *)malloc((size_t)(n_hits > 0 ? n_hits : 1));
-    uint8_t *sel = (uint8_t *)malloc((size_t)(n_hits > 0 ? n_hits : 1));
+    size_t nb = (size_t)(n_hits > 0 ? n_hits : 1);
+    uint8_t *act = (uint8_t *)malloc(nb);
+    uint8_t *sel = (uint8_t *)malloc(nb);
     for (int32_t i = 0; i < n_hits; i++) act[i] = 1;
     double ref[2] = {0.0, 0.0};
     or4_grid g;
+    int32_t *prev_votes = NULL;   /* iteration 2's accumulators (per-sign iteration 3) */
+    or4_grid prev_g;
+    double prev_ref[2] = {0.0, 0.0};
     for (int k = 0; k < o->n_iter && k < 3; k++) {
         for (int a = 0; a < 4; a++) { g.w[a] = o->w[k][a]; g.n[a] = o->n[k][a]; }
-        if (k < 2) {
-            for (int a = 0; a < 4; a++) g.lo[a] = o->glo[a];
-        } else {
-            double ref_n[2] = {ref[0], ref[1]};
-            v4_new_ref(&out[k - 1], w, n_hits, wire_id, sel, ref_n);
-            double c[4] = {out[k - 1].value[0], out[k - 1].value[1], out[k - 1].value[2],
-                           v4_move_z0(o, &out[k - 1], ref, ref_n)};
-            ref[0] = ref_n[0]; ref[1] = ref_n[1];
-            for (int a = 0; a < 4; a++) g.lo[a] = c[a] - ((double)g.n[a] * g.w[a]) * 0.5;
-        }
-        if (k == 1) v4_new_ref(&out[0], w, n_hits, wire_id, sel, ref);
         const int64_t nvox = (int64_t)g.n[0] * g.n[1] * g.n[2] * g.n[3];
-        int32_t *votes = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * nvox));
-        or4_vote_grid(o, &g, ref, w, n_hits, wire_id, drift, act, votes);
-        fesetround(FE_TONEAREST);
-        v4_estimate(&g, votes, &out[k]);
-        free(votes);
+        if (k == 2 && o->per_sign) {
+            or4_grid gs[2];
+            int32_t *vs[2];
+            double rs[2][2];
+            uint8_t *ss[2];
+            for (int s = 0; s < 2; s++) {
+                or4_iter es;
+                v4_estimate_sign(&prev_g, prev_votes, s, &es);
+                ss[s] = (uint8_t *)malloc(nb);
+                v4_find_hits(o, &es, prev_ref, w, n_hits, wire_id, drift, ss[s]);
+                fesetround(FE_TONEAREST);
+                double ref_n[2] = {prev_ref[0], prev_ref[1]};
+                v4_new_ref(&es, w, n_hits, wire_id, ss[s], ref_n);
+                double c[4] = {es.value[0], es.value[1], es.value[2], v4_move_z0(o, &es, prev_ref, ref_n)};
+                gs[s] = g;
+                for (int a = 0; a < 4; a++) gs[s].lo[a] = c[a] - ((double)g.n[a] * g.w[a]) * 0.5;
+                rs[s][0] = ref_n[0];
+                rs[s][1] = ref_n[1];
+                vs[s] = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * nvox));
+                or4_vote_grid(o, &gs[s], rs[s], w, n_hits, wire_id, drift, ss[s], vs[s]);
+                fesetround(FE_TONEAREST);
+            }
+            const int sc = v4_vmax_sign(&gs[0], vs[0], 0) >= v4_vmax_sign(&gs[1], vs[1], 1) ? 0 : 1;
+            v4_estimate_sign(&gs[sc], vs[sc], sc, &out[k]);
+            ref[0] = rs[sc][0];
+            ref[1] = rs[sc][1];
+            for (int s = 0; s < 2; s++) { free(vs[s]); free(ss[s]); }
+        } else {
+            if (k < 2) {
+                for (int a = 0; a < 4; a++) g.lo[a] = o->glo[a];
+            } else {
+                double ref_n[2] = {ref[0], ref[1]};
+                v4_new_ref(&out[k - 1], w, n_hits, wire_id, sel, ref_n);
+                double c[4] = {out[k - 1].value[0], out[k - 1].value[1], out[k - 1].value[2],
+                               v4_move_z0(o, &out[k - 1], ref, ref_n)};
+                ref[0] = ref_n[0]; ref[1] = ref_n[1];
+                for (int a = 0; a < 4; a++) g.lo[a] = c[a] - ((double)g.n[a] * g.w[a]) * 0.5;
+            }
+            if (k == 1) v4_new_ref(&out[0], w, n_hits, wire_id, sel, ref);
+            int32_t *votes = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * nvox));
+            or4_vote_grid(o, &g, ref, w, n_hits, wire_id, drift, act, votes);
+            fesetround(FE_TONEAREST);
+            v4_estimate(&g, votes, &out[k]);
+            if (k == 1 && o->per_sign) {
+                prev_votes = votes;
+                prev_g = g;
+                prev_ref[0] = ref[0];
+                prev_ref[1] = ref[1];
+            } else {
+                free(votes);
+            }
+        }
         out[k].ref[0] = ref[0];
         out[k].ref[1] = ref[1];
         out[k].n_sel = v4_find_hits(o, &out[k], ref, w, n_hits, wire_id, drift, sel);
@@ -1031,6 +1089,7 @@ int or4_solve_event(const or4_opts *o, const or_wires *w, int32_t n_hits, const 
         for (int32_t i = 0; i < n_hits; i++) act[i] = sel[i];
     }
     if (sel_out) memcpy(sel_out, sel, (size_t)n_hits);
+    free(prev_votes);
     free(act);
     free(sel);
     fesetround(old);

@@ -35,7 +35,7 @@ class Or4Opts(C.Structure):
     _fields_ = [("p_gev", C.c_double), ("b_tesla", C.c_double), ("disk_radius", C.c_double),
                 ("hit_factor", C.c_double), ("glo", C.c_double * 4),
                 ("w", (C.c_double * 4) * 3), ("n", (C.c_int32 * 4) * 3),
-                ("precision", C.c_int32), ("n_iter", C.c_int32)]
+                ("precision", C.c_int32), ("n_iter", C.c_int32), ("per_sign", C.c_int32)]
 
 
 class Or4Iter(C.Structure):
@@ -386,7 +386,7 @@ def mask_hits(tab: Tables, wire_id, drift, level: int, keys, width: float, activ
 # The paper's own 4-D search (x_c, y_c, R, z0; Sections 3.1-3.3, Table tabGridDef)
 # ---------------------------------------------------------------------------------------- #
 def four_opts(p_gev=0.105, b_tesla=1.0, disk_radius=0.10, hit_factor=5.0, glo=None, w=None,
-              n=None, precision=0, n_iter=3) -> Or4Opts:
+              n=None, precision=0, n_iter=3, per_sign=1) -> Or4Opts:
     """Defaults: Table tabGridDef read in metres with z0 centred on the chamber middle:
     iterations 1 and 2 on x_c, y_c in [-0.45, 0.45], R in [0.225, 0.375], z0 in [-0.75, 0.75]
     with voxels 18 x 18 x 3.75 x 75 mm and 10 x 10 x 3.75 x 75 mm; iteration 3 on the
@@ -403,7 +403,7 @@ def four_opts(p_gev=0.105, b_tesla=1.0, disk_radius=0.10, hit_factor=5.0, glo=No
         for a in range(4):
             o.w[k][a] = w[k][a]
             o.n[k][a] = n[k][a]
-    o.precision, o.n_iter = precision, n_iter
+    o.precision, o.n_iter, o.per_sign = precision, n_iter, per_sign
     return o
 
 

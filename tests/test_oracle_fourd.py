@@ -188,3 +188,29 @@ def test_four_three_iterations_recover_electrons(wires, events, tab):
         assert abs(last["value"][3] - comet.z_at_point(tr, *last["ref"])) < 0.03
         assert last["sign"] == (1 if tr.tanl > 0 else -1)
         assert sel.sum() >= 0.8 * (b - a)
+
+
+def test_four_iteration_three_per_sign(wires, tab):
+    """Iteration 3 per tan(lambda) sign (each sign's accumulator of iteration 2 gives its
+    own estimate, hit finding, reference point and box).  Iterations 1 and 2 are those of
+    the single-box search; on a steep electron whose iteration 2 chose the wrong sign
+    (event 56 of the benchmark's batch) the single box centred on that estimate ends with
+    the wrong sign, 0.5 m off in z0, while the per-sign search ends with the right sign,
+    within 1 mm (x_c, y_c, R) and 10 mm (z0) of the generated helix."""
+    ev = comet.events(57, seed=70, w=wires)
+    a, b = ev.offsets[56], ev.offsets[57]
+    tr = ev.tracks[56][0]
+    xc, yc, R = comet.helix_centre(tr)
+    sgn = 1 if tr.tanl > 0 else -1
+    one, _ = O.four_solve_event(O.four_opts(per_sign=0), tab, ev.wire_id[a:b], ev.drift[a:b])
+    ps, _ = O.four_solve_event(O.four_opts(per_sign=1), tab, ev.wire_id[a:b], ev.drift[a:b])
+    for k in (0, 1):
+        for f in ("value", "err", "ref"):
+            assert np.array_equal(one[k][f], ps[k][f])
+        assert one[k]["sign"] == ps[k]["sign"] and one[k]["n_sel"] == ps[k]["n_sel"]
+    assert one[1]["sign"] != sgn and one[2]["sign"] != sgn
+    assert abs(one[2]["value"][3] - comet.z_at_point(tr, *one[2]["ref"])) > 0.3
+    last = ps[2]
+    assert last["sign"] == sgn
+    assert np.all(np.abs(last["value"][:3] - [xc, yc, R]) < 1e-3)
+    assert abs(last["value"][3] - comet.z_at_point(tr, *last["ref"])) < 1e-2
