@@ -469,7 +469,9 @@ def background_study(w, n_events: int = 1024, seed: int = 4) -> dict:
            "events_per_s": ev.n_events / (ms * 1e-3),
            "launch_schedules": launch, "schedules_give_identical_results": bool(same)}
     out.update(multi_track_figures(ev, tracks, nt, hts))
-    out["maxset"] = multi_maxset_leg(w, ev)
+    # the max-set extraction on the first 512 of the events (it runs about 5x longer per
+    # event than the top-K one)
+    out["maxset"] = multi_maxset_leg(w, ev.subset(range(min(512, ev.n_events))))
     return out
 
 
@@ -578,10 +580,11 @@ def paper_search_leg(n_events: int = 512, seed: int = 70, cpu_events: int = 1, n
                              "wrong_sign_fraction": [0.166, 0.047, 0.0],
                              "within_1mm_10mm": 0.997}}
     ev_all, hits_all = ev, hits
-    for prec, name in ((apo.F64, "fp64"), (apo.F32, "fp32")):
+    # iteration 3 per tan(lambda) sign (the default), and FP32 on iteration 2's box alone
+    for prec, name, ps in ((apo.F64, "fp64", 1), (apo.F32, "fp32", 1), (apo.F32, "fp32_one_box", 0)):
         ev = ev_all.subset(range(min(n_fp64, ev_all.n_events))) if prec == apo.F64 else ev_all
         hits = apo.DeviceHits.from_events(ev) if prec == apo.F64 else hits_all
-        o = apo.four_opts(precision=prec)
+        o = apo.four_opts(precision=prec, per_sign=ps)
         ws = ch.workspace(ev.n_events, o)
         out, sel = apo.solve4(ch, hits, o, workspace=ws)
         torch.cuda.synchronize()
@@ -612,7 +615,8 @@ def paper_search_leg(n_events: int = 512, seed: int = 70, cpu_events: int = 1, n
                                                            (np.abs(d[:, 3]) < 1e-2)))})
         t = min(ms)
         res[name] = {"ms_per_track": t / ev.n_events, "tracks_per_s": ev.n_events / (t * 1e-3),
-                     "batch_ms": t, "tracks": ev.n_events, "iterations": iters}
+                     "batch_ms": t, "tracks": ev.n_events, "iteration_3": "per sign" if ps else
+                     "both signs on iteration 2's box", "iterations": iters}
     ch.close()
     ev = ev_all
     if cpu_events > 0:
@@ -773,13 +777,15 @@ def run_apo(args) -> None:
                                                  apo._ptr(ws), ws.numel(), apo._stream_ptr(stream)))
         return [int(x) for x in c.cpu().tolist()]
 
-    def coarse_launch_ms(prec, n_launch, reps):
+    def coarse_launch_ms(prec, n_launch, reps, full=None):
+        # full: a vote array for the full-vote form; None: each block keeps its K best cells
         out = []
         for _ in range(reps):
             flush.fill_(1)
             s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             s0.record(stream)
-            apo._check(L.apo_diag_vote_coarse_counts(geom.handle, C.byref(hc), prec, None, None,
+            apo._check(L.apo_diag_vote_coarse_counts(geom.handle, C.byref(hc), prec,
+                                                     None if full is None else apo._ptr(full), None,
                                                      apo._ptr(ws), ws.numel(), apo._stream_ptr(stream)))
             s1.record(stream)
             s1.synchronize()
@@ -791,9 +797,12 @@ def run_apo(args) -> None:
     # the FP32 coarse kernel (dominant in the FP32-bulk solve): counted FP32 directed
     # operations / live launch time, against the measured FP32 directed add/mul rate
     ops32_coarse = coarse_kernel_ops(c32[4], c32[5], c32[6]) / max(c32[3], 1)
-    k32_ms = coarse_launch_ms(apo.F32, c32[3], max(3, args.steps))
+    # in the form the tuned FP32-bulk step runs (full votes or per-block candidates)
+    full32 = bool(tune32.coarse_full)
+    k32_ms = coarse_launch_ms(apo.F32, c32[3], max(3, args.steps), full=votes if full32 else None)
     peak32 = apo.pipe_peak(apo.F32)
     roofline32 = {"bound": "issue", "kernel": "k_vote_coarse<float>",
+                  "form": "full votes" if full32 else "per-block K best cells",
                   "achieved": ops32_coarse / (k32_ms * 1e-3) / 1e12, "peak": peak32 / 1e12,
                   "unit": "TFLOP/s", "frac": ops32_coarse / (k32_ms * 1e-3) / peak32,
                   "launch_ms": k32_ms, "ops_per_launch": ops32_coarse,
@@ -1018,15 +1027,20 @@ def run_case(args) -> None:
         torch.cuda.synchronize()
         print(json.dumps({"case": args.case, "events": ev4.n_events, "ok": True}))
         return
-    if args.case == "solve-maxset":   # the max-set leg's FP32-bulk form on the first events
+    if args.case in ("solve-maxset", "solve-maxset-multi"):
+        # the max-set leg's FP32-bulk form on the first events (single-track events, or the
+        # multi-track events of the background study with up to 5 tracks)
         from gen import chamber, grid as G
         w = chamber.make_wires()
         ga = G.make_grid(MAXSET["bins"], MAXSET["levels"], 64)
-        ev = chamber.single_track_events(args.events, seed=WORKLOAD["seed"], w=w)
+        multi = args.case == "solve-maxset-multi"
+        ev = (chamber.multi_track_events(args.events, seed=4, w=w) if multi else
+              chamber.single_track_events(args.events, seed=WORKLOAD["seed"], w=w))
         geom = apo.Geometry(ga, w)
         o = apo.solve_opts(precision=[apo.F32 | apo.OUTGOING] * ga.levels + [apo.F64 | apo.OUTGOING],
                            schedule=apo.SCHED_MAXSET, max_keep=MAXSET["max_keep"],
-                           tune=apo.ApoTune(0, 0, 128, 0, 0))
+                           tune=apo.ApoTune(0, 0, 128, 0, 0), slack=2 if multi else 0,
+                           max_tracks=5 if multi else 1, min_votes=6 if multi else 0)
         hits = apo.DeviceHits.from_events(ev)
         for _ in range(2):
             apo.solve_batch(geom, hits, o)
@@ -1058,11 +1072,14 @@ def run_case(args) -> None:
         votes = torch.empty((ev.n_events, geom.n_coarse), dtype=torch.int32, device="cuda")
         for _ in range(2):
             apo.vote(geom, hits, precision=prec, out=votes, workspace=ws)
-    elif args.case.startswith("coarse"):   # the search's form: each block keeps its K best cells
+    elif args.case.startswith("coarse"):   # each block keeps its K best cells, or (-full) every vote
         import ctypes as C
         hc = hits.c()
+        full = (torch.empty((ev.n_events, geom.n_coarse), dtype=torch.int32, device="cuda")
+                if args.case.endswith("-full") else None)
         for _ in range(2):
-            apo._check(apo.lib().apo_diag_vote_coarse_counts(geom.handle, C.byref(hc), prec, None,
+            apo._check(apo.lib().apo_diag_vote_coarse_counts(geom.handle, C.byref(hc), prec,
+                                                             None if full is None else apo._ptr(full),
                                                              None, apo._ptr(ws), ws.numel(),
                                                              apo._stream_ptr(None)))
     else:
@@ -1094,8 +1111,9 @@ def main(argv=None):
                     help="events of the multi-track background study")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--case", default=None,
-                    choices=["coarse-f64", "coarse-f32", "coarse-mid", "solve-f64", "solve-f32", "solve-bulk",
-                             "solve-maxset", "solve-persist", "four-f32", "four-f64"],
+                    choices=["coarse-f64", "coarse-f32", "coarse-f32-full", "coarse-mid", "solve-f64",
+                             "solve-f32", "solve-bulk", "solve-maxset", "solve-maxset-multi", "solve-persist",
+                             "four-f32", "four-f64"],
                     help="run one small profiling case instead of the benchmark")
     ap.add_argument("--events", type=int, default=64)
     args = ap.parse_args(argv)

@@ -49,6 +49,11 @@ typedef struct {
     int32_t n[3][4];
     int32_t precision;
     int32_t n_iter;
+    int32_t per_sign;      /* 1 (default): with three iterations, iteration 3 searches each
+                              tan(lambda) sign around its own accumulator's estimate of
+                              iteration 2 (its own hit finding, reference point, z0 carry
+                              and box), then keeps the sign with the larger maximum; 0: both
+                              signs on the box of iteration 2's chosen sign */
 } apo4_opts;
 
 /* One iteration's result for one event.  value / err: x_c, y_c, R, z0 (z0 at ref); ref:
@@ -66,7 +71,7 @@ typedef struct {
 } apo4_iter;
 
 /* Table tabGridDef in metres with z0 centred on the chamber middle, p = 0.105 GeV/c,
- * B = 1 T, disk radius 0.1 m, hit factor 5, FP64, three iterations. */
+ * B = 1 T, disk radius 0.1 m, hit factor 5, FP64, three iterations, per_sign 1. */
 void apo4_opts_default(apo4_opts *opts);
 
 /* Uploads the wire table (as for apo_geometry_create). */

@@ -68,7 +68,7 @@ class Apo4Opts(C.Structure):
     _fields_ = [("p_gev", C.c_double), ("b_tesla", C.c_double), ("disk_radius", C.c_double),
                 ("hit_factor", C.c_double), ("glo", C.c_double * 4),
                 ("w", (C.c_double * 4) * 3), ("n", (C.c_int32 * 4) * 3),
-                ("precision", C.c_int32), ("n_iter", C.c_int32)]
+                ("precision", C.c_int32), ("n_iter", C.c_int32), ("per_sign", C.c_int32)]
 
 
 APO4_ITER_DTYPE = np.dtype([("value", "<f8", (4,)), ("err", "<f8", (4,)), ("ref", "<f8", (2,)),
@@ -537,12 +537,12 @@ class Server:
 # ---------------------------------------------------------------------------------------- #
 # The paper's own 4-D search (include/apo4.h)
 # ---------------------------------------------------------------------------------------- #
-def four_opts(precision: int = F64, n_iter: int = 3, **kw) -> Apo4Opts:
+def four_opts(precision: int = F64, n_iter: int = 3, per_sign: int = 1, **kw) -> Apo4Opts:
     """apo4_opts_default (Table tabGridDef in metres) with overrides: p_gev, b_tesla,
     disk_radius, hit_factor, glo (4), w (3 x 4), n (3 x 4)."""
     o = Apo4Opts()
     lib().apo4_opts_default(C.byref(o))
-    o.precision, o.n_iter = int(precision), int(n_iter)
+    o.precision, o.n_iter, o.per_sign = int(precision), int(n_iter), int(per_sign)
     for k in ("p_gev", "b_tesla", "disk_radius", "hit_factor"):
         if k in kw:
             setattr(o, k, float(kw[k]))

@@ -58,7 +58,7 @@ struct Stats4 {
 };
 
 struct Layout4 {
-    size_t status, nh, hd, hf, active, done, lo, ref, vmax, stats, votes, end;
+    size_t status, nh, hd, hf, active, done, lo, ref, vmax, stats, lo2, ref2, active2, stats2, votes, end;
     int chunk;
     long long max_nvox;
 };
@@ -86,6 +86,11 @@ Layout4 layout4(const apo4_opts *o, int ne) {
     L.ref = off; off += al256(sizeof(double) * n * 2);
     L.vmax = off; off += al256(sizeof(int32_t) * n * 2);
     L.stats = off; off += al256(sizeof(Stats4) * n);
+    // per-sign state of iteration 3 (sign-major: sign s of event e at s n + e)
+    L.lo2 = off; off += al256(sizeof(double) * 2 * n * 4);
+    L.ref2 = off; off += al256(sizeof(double) * 2 * n * 2);
+    L.active2 = off; off += al256(sizeof(uint32_t) * 2 * n * 8);
+    L.stats2 = off; off += al256(sizeof(Stats4) * 2 * n);
     L.votes = off; off += al256(sizeof(int32_t) * 2 * (size_t)mv * (size_t)L.chunk);
     L.end = off;
     return L;
@@ -96,6 +101,7 @@ int check_opts(const apo4_opts *o) {
     if (o->n_iter < 1 || o->n_iter > 3) return fail4(APO_EINVAL, "n_iter must be 1..3");
     if (o->precision != APO_F64 && o->precision != APO_F32)
         return fail4(APO_EINVAL, "precision must be APO_F64 or APO_F32");
+    if (o->per_sign != 0 && o->per_sign != 1) return fail4(APO_EINVAL, "per_sign must be 0 or 1");
     if (!(o->p_gev > 0) || !(o->b_tesla > 0) || !(o->disk_radius >= 0) || !(o->hit_factor >= 0))
         return fail4(APO_EINVAL, "p_gev, b_tesla > 0 and disk_radius, hit_factor >= 0 required");
     for (int k = 0; k < o->n_iter; k++) {
@@ -191,7 +197,7 @@ __device__ __forceinline__ Col4<T> column4(const Iter4 &it, const double *le, co
 template <typename T>
 __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 3 : 5)
 k4_vote(Iter4 it, int ev0, const int32_t *n_hits, const HitRecD *hd, const uint32_t *active,
-        const double *lo, const double *ref, int32_t *votes, int32_t *vmax) {
+        const double *lo, const double *ref, int32_t *votes, int32_t *vmax, int sign_only) {
     __shared__ HitP<T> s_h[kHitCap];
     __shared__ HitI<T> s_w[kHitCap];
     __shared__ T s_zc[32];
@@ -230,7 +236,8 @@ k4_vote(Iter4 it, int ev0, const int32_t *n_hits, const HitRecD *hd, const uint3
             s_col[atomicAdd(&s_np, 1)] = (short)k;
         } else {
             for (int s = 0; s < 2; s++)
-                for (int iz = 0; iz < nz; iz++) vo[(long long)s * it.nvox + col + it.ncol * iz] = 0;
+                if (sign_only < 0 || s == sign_only)
+                    for (int iz = 0; iz < nz; iz++) vo[(long long)s * it.nvox + col + it.ncol * iz] = 0;
         }
     }
     __syncthreads();
@@ -260,13 +267,14 @@ k4_vote(Iter4 it, int ev0, const int32_t *n_hits, const HitRecD *hd, const uint3
                 const Pre4<T> pre = prefix4<T>(c.m, s_zc[iz], h);
                 if (pre.guard) { b0 |= 1u << iz; b1 |= 1u << iz; continue; }
                 const IV<T> A2 = a2_4<T>(c.X, c.Y, s_z[iz], wi);
-                if (pair4<T>(c.m, pre, 1, h, A2, c.Rv)) b0 |= 1u << iz;
-                if (pair4<T>(c.m, pre, -1, h, A2, c.Rv)) b1 |= 1u << iz;
+                if (sign_only != 1 && pair4<T>(c.m, pre, 1, h, A2, c.Rv)) b0 |= 1u << iz;
+                if (sign_only != 0 && pair4<T>(c.m, pre, -1, h, A2, c.Rv)) b1 |= 1u << iz;
             }
             add_votes(0, b0);
             add_votes(1, b1);
         }
-        for (int s = 0; s < 2; s++)
+        for (int s = 0; s < 2; s++) {
+            if (sign_only >= 0 && s != sign_only) continue;
             for (int iz = 0; iz < nz; iz++) {
                 int v = 0;
 #pragma unroll
@@ -274,6 +282,7 @@ k4_vote(Iter4 it, int ev0, const int32_t *n_hits, const HitRecD *hd, const uint3
                 vo[(long long)s * it.nvox + col + it.ncol * iz] = v;
                 mx[s] = v > mx[s] ? v : mx[s];
             }
+        }
     }
     if (mx[0] > 0) atomicMax(&s_vmax[0], mx[0]);
     if (mx[1] > 0) atomicMax(&s_vmax[1], mx[1]);
@@ -281,9 +290,10 @@ k4_vote(Iter4 it, int ev0, const int32_t *n_hits, const HitRecD *hd, const uint3
     if (tid < 2 && s_vmax[tid] > 0) atomicMax(&vmax[(long long)e * 2 + tid], s_vmax[tid]);
 }
 
-// Statistics of the maximum-vote voxels of the accumulator with the larger maximum.
+// Statistics of the maximum-vote voxels of the accumulator with the larger maximum (force
+// >= 0: of that sign's accumulator).
 __global__ void __launch_bounds__(256)
-k4_stats(Iter4 it, int ev0, const int32_t *votes, const int32_t *vmax, Stats4 *st) {
+k4_stats(Iter4 it, int ev0, const int32_t *votes, const int32_t *vmax, Stats4 *st, int force) {
     __shared__ unsigned long long s_cnt, s_sum[4];
     __shared__ int s_mn[4], s_mx[4];
     const int el = blockIdx.y, e = ev0 + el, tid = threadIdx.x;
@@ -292,7 +302,7 @@ k4_stats(Iter4 it, int ev0, const int32_t *votes, const int32_t *vmax, Stats4 *s
         for (int a = 0; a < 4; a++) { s_sum[a] = 0; s_mn[a] = 1 << 30; s_mx[a] = -1; }
     }
     __syncthreads();
-    const int s = vmax[(long long)e * 2] >= vmax[(long long)e * 2 + 1] ? 0 : 1;
+    const int s = force >= 0 ? force : (vmax[(long long)e * 2] >= vmax[(long long)e * 2 + 1] ? 0 : 1);
     const int vm = vmax[(long long)e * 2 + s];
     const int32_t *vo = votes + ((long long)el * 2 + s) * it.nvox;
     unsigned long long cnt = 0, sum[4] = {0, 0, 0, 0};
@@ -358,7 +368,7 @@ __global__ void k4_reset_stats(int n, Stats4 *st, int32_t *vmax) {
     Stats4 &g = st[e];
     g.cnt = 0;
     for (int a = 0; a < 4; a++) { g.sum[a] = 0; g.mn[a] = 1 << 30; g.mx[a] = -1; }
-    vmax[2 * e] = vmax[2 * e + 1] = 0;
+    if (vmax) vmax[2 * e] = vmax[2 * e + 1] = 0;
 }
 
 // Iteration 1 state: the global corner and the origin as reference point.
@@ -371,23 +381,37 @@ __global__ void k4_init(int n, double g0, double g1, double g2, double g3, doubl
 
 // Estimate, hit finding, and the next iteration's reference point and grid corner.
 // One block per event.  k: this iteration; nxt (null after the last): the next one's
-// shape; glo: the global corner.
+// shape; glo: the global corner.  Per-sign iteration 3 (lo2 / ref2 / active2: sign-major
+// state of ne events):
+//   force = s >= 0 (after iteration 2): the estimate of sign s's accumulator (st holds its
+//     statistics), its hit finding into active2, its next reference point and corner into
+//     ref2 / lo2; no record, no selection;
+//   force < 0 with lo2 set (iteration 3): this iteration's corner and reference point are
+//     those of the chosen sign in lo2 / ref2.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k4_finish(Iter4 it, int k, int n_iter, bool has_next, Iter4 nxt, double g0, double g1, double g2, double g3,
           const int32_t *offsets, const int32_t *n_hits, const HitRecD *hd, const int32_t *vmax,
-          const Stats4 *st, double *lo, double *ref, uint32_t *active, apo4_iter *out, uint8_t *selected) {
+          const Stats4 *st, double *lo, double *ref, uint32_t *active, apo4_iter *out, uint8_t *selected,
+          int force, int ne, double *lo2, double *ref2, uint32_t *active2) {
     __shared__ double s_val[4], s_err[4];
     __shared__ int s_sign, s_cnt;
     __shared__ uint32_t s_act[8];
+    __shared__ apo4_iter s_rec;   // the record of a forced-sign pass (not stored)
     const int e = blockIdx.x, tid = threadIdx.x;
     const int nh_raw = n_hits[e];
     const int nh = nh_raw < 0 ? 0 : nh_raw;
-    apo4_iter &o = out[(long long)e * n_iter + k];
-    double *le = lo + (long long)e * 4;
-    double *rf = ref + (long long)e * 2;
+    const int sc = force >= 0 ? force : (vmax[2 * e] >= vmax[2 * e + 1] ? 0 : 1);
+    const long long es = (long long)sc * ne + e;   // sign-major index
+    apo4_iter &o = force >= 0 ? s_rec : out[(long long)e * n_iter + k];
+    const double *le = (force < 0 && lo2) ? lo2 + es * 4 : lo + (long long)e * 4;
+    const double *rf = (force < 0 && lo2) ? ref2 + es * 2 : ref + (long long)e * 2;
+    double *le_out = force >= 0 ? lo2 + es * 4 : lo + (long long)e * 4;
+    double *rf_out = force >= 0 ? ref2 + es * 2 : ref + (long long)e * 2;
+    uint32_t *act_out = force >= 0 ? active2 + es * 8 : active + (long long)e * 8;
+    if (force >= 0) selected = nullptr;
     if (tid == 0) {
-        const int s = vmax[2 * e] >= vmax[2 * e + 1] ? 0 : 1;
+        const int s = sc;
         const Stats4 g = st[e];
         const double m = (double)g.cnt;
         for (int a = 0; a < 4; a++) {
@@ -437,7 +461,7 @@ k4_finish(Iter4 it, int k, int n_iter, bool has_next, Iter4 nxt, double g0, doub
     if (selected && !has_next && nh_raw < 0 && a0 >= 0 && nseg >= 0 && nseg <= kHitCap)
         for (int i = tid; i < nseg; i += blockDim.x) selected[a0 + i] = 0;
     __syncthreads();
-    if (tid < 8) active[(long long)e * 8 + tid] = s_act[tid];
+    if (tid < 8) act_out[tid] = s_act[tid];
     if (tid != 0) return;
     o.n_sel = s_cnt;
     if (!has_next) return;
@@ -451,7 +475,7 @@ k4_finish(Iter4 it, int k, int n_iter, bool has_next, Iter4 nxt, double g0, doub
         if (dist < best) { best = dist; r0 = r.v[0]; r1 = r.v[1]; }
     }
     if (k + 1 == 1) {
-        le[0] = g0; le[1] = g1; le[2] = g2; le[3] = g3;
+        le_out[0] = g0; le_out[1] = g1; le_out[2] = g2; le_out[3] = g3;
     } else {
         // z0 moved from the old reference point to the new one: z0 + tan(lambda) R dpsi,
         // dpsi the difference of their phases from the direction of the origin
@@ -472,10 +496,10 @@ k4_finish(Iter4 it, int k, int n_iter, bool has_next, Iter4 nxt, double g0, doub
         const double c3 = __dadd_rn(s_val[3], __dmul_rn(L, __dmul_rn(R, dpsi)));
         const double cc[4] = {s_val[0], s_val[1], s_val[2], c3};
         for (int a = 0; a < 4; a++)
-            le[a] = __dsub_rn(cc[a], __dmul_rn(__dmul_rn((double)nxt.n[a], nxt.w[a]), 0.5));
+            le_out[a] = __dsub_rn(cc[a], __dmul_rn(__dmul_rn((double)nxt.n[a], nxt.w[a]), 0.5));
     }
-    rf[0] = r0;
-    rf[1] = r1;
+    rf_out[0] = r0;
+    rf_out[1] = r1;
 }
 
 }  // namespace apo
@@ -485,16 +509,27 @@ namespace {
 template <typename T>
 void launch_vote4(const Iter4 &it, int ev0, int n, const int32_t *nh, const HitRecD *hd,
                   const uint32_t *active, const double *lo, const double *ref, int32_t *votes,
-                  int32_t *vmax, cudaStream_t s) {
+                  int32_t *vmax, cudaStream_t s, int sign_only = -1) {
     dim3 grid((unsigned)((it.ncol + kTile4 - 1) / kTile4), n);
-    k4_vote<T><<<grid, 128, 0, s>>>(it, ev0, nh, hd, active, lo, ref, votes, vmax);
+    k4_vote<T><<<grid, 128, 0, s>>>(it, ev0, nh, hd, active, lo, ref, votes, vmax, sign_only);
 }
 
 void launch_stats4(const Iter4 &it, int ev0, int n, const int32_t *votes, const int32_t *vmax,
-                   Stats4 *st, cudaStream_t s) {
+                   Stats4 *st, cudaStream_t s, int force = -1) {
     long long b = (it.nvox + 256LL * 8 - 1) / (256LL * 8);
     dim3 grid((unsigned)(b < 1 ? 1 : (b > 1024 ? 1024 : b)), n);
-    k4_stats<<<grid, 256, 0, s>>>(it, ev0, votes, vmax, st);
+    k4_stats<<<grid, 256, 0, s>>>(it, ev0, votes, vmax, st, force);
+}
+
+template <typename T>
+void launch_finish4(const Iter4 &it, int k, const apo4_opts *o, bool has_next, const Iter4 &nxt,
+                    const apo_hits *hits, const int32_t *nh, const HitRecD *hd, const int32_t *vmax,
+                    const Stats4 *st, double *lo, double *ref, uint32_t *active, apo4_iter *out,
+                    uint8_t *selected, int force, int ne, double *lo2, double *ref2, uint32_t *active2,
+                    cudaStream_t s) {
+    k4_finish<T><<<ne, 256, 0, s>>>(it, k, o->n_iter, has_next, nxt, o->glo[0], o->glo[1], o->glo[2], o->glo[3],
+                                    hits->offsets, nh, hd, vmax, st, lo, ref, active, out, selected, force, ne,
+                                    lo2, ref2, active2);
 }
 
 int check_hits4(const apo_hits *h) {
@@ -543,6 +578,7 @@ void apo4_opts_default(apo4_opts *o) {
         for (int a = 0; a < 4; a++) { o->w[k][a] = w[k][a]; o->n[k][a] = n[k][a]; }
     o->precision = APO_F64;
     o->n_iter = 3;
+    o->per_sign = 1;
 }
 
 int apo4_chamber_create(const apo_wires *w, apo4_chamber **out) {
@@ -608,7 +644,15 @@ int apo4_solve_batch(const apo4_chamber *c, const apo_hits *hits, const apo4_opt
     double *ref = at4<double>(ws, L.ref);
     int32_t *vmax = at4<int32_t>(ws, L.vmax);
     Stats4 *st = at4<Stats4>(ws, L.stats);
+    double *lo2 = at4<double>(ws, L.lo2);
+    double *ref2 = at4<double>(ws, L.ref2);
+    uint32_t *active2 = at4<uint32_t>(ws, L.active2);
+    Stats4 *st2 = at4<Stats4>(ws, L.stats2);
     int32_t *votes = at4<int32_t>(ws, L.votes);
+    // per-sign iteration 3: after iteration 2 each sign's accumulator gets its own estimate,
+    // hit finding, reference point and box; iteration 3 votes sign s on box s
+    const bool ps = o->per_sign && o->n_iter == 3;
+    const bool f32 = o->precision == APO_F32;
     CU4(cudaMemsetAsync(status, 0, 256, s));
     launch_stage(c->dg, ne, hits->offsets, hits->wire_id, hits->drift, hd, hf, nh, active, done, status, s);
     k4_init<<<(ne + 127) / 128, 128, 0, s>>>(ne, o->glo[0], o->glo[1], o->glo[2], o->glo[3], lo, ref);
@@ -617,21 +661,37 @@ int apo4_solve_batch(const apo4_chamber *c, const apo_hits *hits, const apo4_opt
         const Iter4 it = iter4(o, k);
         const bool has_next = k + 1 < o->n_iter;
         const Iter4 nxt = has_next ? iter4(o, k + 1) : it;
+        const bool split_stats = ps && k == 1, split_vote = ps && k == 2;
         k4_reset_stats<<<(ne + 127) / 128, 128, 0, s>>>(ne, st, vmax);
+        if (split_stats) k4_reset_stats<<<(2 * ne + 127) / 128, 128, 0, s>>>(2 * ne, st2, nullptr);
         for (int e0 = 0; e0 < ne; e0 += L.chunk) {
             const int n = ne - e0 < L.chunk ? ne - e0 : L.chunk;
-            if (o->precision == APO_F32) launch_vote4<float>(it, e0, n, nh, hd, active, lo, ref, votes, vmax, s);
-            else launch_vote4<double>(it, e0, n, nh, hd, active, lo, ref, votes, vmax, s);
+            for (int sg = split_vote ? 0 : -1; sg < (split_vote ? 2 : 0); sg++) {
+                const uint32_t *ac = sg < 0 ? active : active2 + (size_t)sg * ne * 8;
+                const double *lc = sg < 0 ? lo : lo2 + (size_t)sg * ne * 4;
+                const double *rc = sg < 0 ? ref : ref2 + (size_t)sg * ne * 2;
+                if (f32) launch_vote4<float>(it, e0, n, nh, hd, ac, lc, rc, votes, vmax, s, sg);
+                else launch_vote4<double>(it, e0, n, nh, hd, ac, lc, rc, votes, vmax, s, sg);
+            }
             launch_stats4(it, e0, n, votes, vmax, st, s);
+            if (split_stats)
+                for (int sg = 0; sg < 2; sg++) launch_stats4(it, e0, n, votes, vmax, st2 + (size_t)sg * ne, s, sg);
         }
-        if (o->precision == APO_F32)
-            k4_finish<float><<<ne, 256, 0, s>>>(it, k, o->n_iter, has_next, nxt, o->glo[0], o->glo[1], o->glo[2],
-                                                o->glo[3], hits->offsets, nh, hd, vmax, st, lo, ref, active, out,
-                                                selected);
+        if (split_stats)   // before the chosen sign's pass, which moves lo / ref on
+            for (int sg = 0; sg < 2; sg++) {
+                if (f32)
+                    launch_finish4<float>(it, k, o, has_next, nxt, hits, nh, hd, vmax, st2 + (size_t)sg * ne, lo, ref,
+                                          active, out, nullptr, sg, ne, lo2, ref2, active2, s);
+                else
+                    launch_finish4<double>(it, k, o, has_next, nxt, hits, nh, hd, vmax, st2 + (size_t)sg * ne, lo,
+                                           ref, active, out, nullptr, sg, ne, lo2, ref2, active2, s);
+            }
+        if (f32)
+            launch_finish4<float>(it, k, o, has_next, nxt, hits, nh, hd, vmax, st, lo, ref, active, out, selected, -1,
+                                  ne, split_vote ? lo2 : nullptr, split_vote ? ref2 : nullptr, active2, s);
         else
-            k4_finish<double><<<ne, 256, 0, s>>>(it, k, o->n_iter, has_next, nxt, o->glo[0], o->glo[1], o->glo[2],
-                                                 o->glo[3], hits->offsets, nh, hd, vmax, st, lo, ref, active, out,
-                                                 selected);
+            launch_finish4<double>(it, k, o, has_next, nxt, hits, nh, hd, vmax, st, lo, ref, active, out, selected,
+                                   -1, ne, split_vote ? lo2 : nullptr, split_vote ? ref2 : nullptr, active2, s);
         CU4(cudaGetLastError());
     }
     return APO_OK;

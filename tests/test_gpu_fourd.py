@@ -100,14 +100,14 @@ def test_four_vote_tiles_without_disk_columns(wires, tab, ch, prec):
     assert got[0].max() == 0 and got[1].max() > 0
 
 
-@pytest.mark.parametrize("prec", [apo.F64, apo.F32])
-def test_four_solve_reduced_grids_bit_exact(wires, tab, ch, prec):
+@pytest.mark.parametrize("prec,per_sign", [(apo.F64, 1), (apo.F32, 1), (apo.F64, 0), (apo.F32, 0)])
+def test_four_solve_reduced_grids_bit_exact(wires, tab, ch, prec, per_sign):
     ev = comet.events(5, seed=62, w=wires)
-    opts = apo.four_opts(precision=prec, w=RW, n=RN)
+    opts = apo.four_opts(precision=prec, w=RW, n=RN, per_sign=per_sign)
     out, sel = apo.solve4(ch, _hits(ev), opts)
     got = apo.iters4_to_numpy(out, ev.n_events, 3)
     sel = sel.cpu().numpy()
-    oo = O.four_opts(w=RW, n=RN, precision=0 if prec == apo.F64 else 1)
+    oo = O.four_opts(w=RW, n=RN, precision=0 if prec == apo.F64 else 1, per_sign=per_sign)
     for e in range(ev.n_events):
         a, b = ev.offsets[e], ev.offsets[e + 1]
         its, rsel = O.four_solve_event(oo, tab, ev.wire_id[a:b], ev.drift[a:b])
@@ -151,3 +151,32 @@ def test_four_malformed_event(wires, ch):
     assert all(got[1, k]["vmax"] == apo.APO_EINVAL and got[1, k]["n_sel"] == 0 for k in range(3))
     assert not sel[ev.offsets[1]:ev.offsets[2]].any()
     assert got[0, 2]["vmax"] > 0 and got[2, 2]["vmax"] > 0
+
+
+@pytest.mark.parametrize("prec", [apo.F64, apo.F32])
+def test_four_per_sign_iteration_three(wires, tab, ch, prec):
+    """Steep tracks whose iteration 2 picks the wrong tan(lambda) sign or a box 20-50 mm off
+    (events 2, 41 and 56 of the benchmark's batch): with iteration 3 per sign the search is
+    bit-exact against the oracle and ends within 1 mm (x_c, y_c, R) and 10 mm (z0) of the
+    generated helix; on iteration 2's box alone it does not."""
+    ev = comet.events(57, seed=70, w=wires).subset([2, 41, 56])
+    res = {}
+    for ps in (1, 0):
+        out, sel = apo.solve4(ch, _hits(ev), apo.four_opts(precision=prec, per_sign=ps))
+        res[ps] = (apo.iters4_to_numpy(out, ev.n_events, 3), sel.cpu().numpy())
+    got, sel = res[1]
+    oo = O.four_opts(precision=0 if prec == apo.F64 else 1, per_sign=1)
+    n_ok = {0: 0, 1: 0}
+    for e in range(ev.n_events):
+        a, b = ev.offsets[e], ev.offsets[e + 1]
+        its, rsel = O.four_solve_event(oo, tab, ev.wire_id[a:b], ev.drift[a:b])
+        for k in range(3):
+            _compare(got[e, k], its[k], e, k)
+        assert np.array_equal(sel[a:b].astype(bool), rsel), e
+        tr = ev.tracks[e][0]
+        xc, yc, R = comet.helix_centre(tr)
+        for ps in (0, 1):
+            r = res[ps][0][e, 2]
+            d = np.abs(r["value"] - [xc, yc, R, comet.z_at_point(tr, *r["ref"])])
+            n_ok[ps] += bool(np.all(d[:3] < 1e-3) and d[3] < 1e-2)
+    assert n_ok[1] == 3 and n_ok[0] < 3, n_ok
