@@ -44,10 +44,10 @@ OPS_TAIL = OPS_LPART + OPS_SIGNS
 
 # DRAM bytes (read + write) of one k_vote_coarse<FP64> launch per event: an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, --clock-control none) of one 64-event
-# launch of that kernel on the 16^5 grid read 3.93 MB and wrote 214.01 MB (the vote
-# array); scaled by events to the benchmark's launch.  Must be re-captured (or set to None)
-# whenever that kernel changes.
-COARSE_F64_DRAM_BYTES_PER_EVENT = None
+# launch of that kernel on the 16^5 grid, in the search's form (each block keeps its K
+# best cells), read 496,384 B and wrote 0 B; scaled by events to the benchmark's launch.
+# Must be re-captured (or set to None) whenever that kernel changes.
+COARSE_F64_DRAM_BYTES_PER_EVENT = 496384 / 64
 
 
 def coarse_kernel_ops(n_parent: int, n_prefix: int, n_tail: int) -> int:
@@ -952,6 +952,11 @@ def run_apo(args) -> None:
         "config": {"workload": WORKLOAD["name"], "n_events": ev.n_events,
                    "coarse_cells": geom.n_coarse, "topk": g.topk, "levels": lv,
                    "hits_per_event_mean": float(nh.mean()),
+                   "hits_per_event_reading": "the configuration's hit rule (closest approach "
+                                             "under half a cell) gives about one wire per "
+                                             "layer of the 10-layer chamber, so ~10 hits, not "
+                                             "the ~20 its text estimates; tracks with fewer "
+                                             "than 6 hits are redrawn",
                    "l2": "flushed between timed steps (256 MiB write)"},
         "events_per_s": ev.n_events * world / (t_step * 1e-3),
         "pairs": {"decided_per_step": pairs,
