@@ -70,7 +70,8 @@ namespace {
 // Workspace regions for a batch of n_events.
 struct Layout {
     size_t status, n_hits, hd, hf, votes, hist, fk, fv, ck, cv, mask, done, ntr, tune_tracks;
-    size_t ms_front, ms_count, ms_stop, ms_ck, ms_cv, p_votes, p_hist, p_next, cand_k, cand_v, end;
+    size_t ms_front, ms_count, ms_stop, ms_ck, ms_cv, ms_ts, ms_tcnt, p_votes, p_hist, p_next, cand_k, cand_v,
+        end;
     int chunk, ms_chunk;
 };
 
@@ -116,7 +117,7 @@ Layout layout(const apo_geometry *g, int n_events, const apo_solve_opts *opts = 
     L.ntr = o; o = align256(o + sizeof(int32_t) * (size_t)n_events);
     L.tune_tracks = o; o = align256(o + sizeof(apo_track) * (size_t)n_events * APO_MAX_TRACKS);
     L.ms_chunk = 0;
-    L.ms_front = L.ms_count = L.ms_stop = L.ms_ck = L.ms_cv = o;
+    L.ms_front = L.ms_count = L.ms_stop = L.ms_ck = L.ms_cv = L.ms_ts = L.ms_tcnt = o;
     L.p_votes = L.p_hist = L.p_next = o;
     if (opts && opts->schedule == APO_SCHED_TOPK && opts->tune.persistent) {
         const size_t B = (size_t)(g->persist_blocks > 0 ? g->persist_blocks : 1);
@@ -133,6 +134,10 @@ Layout layout(const apo_geometry *g, int n_events, const apo_solve_opts *opts = 
         L.ms_stop = o; o = align256(o + sizeof(int32_t) * (size_t)c);
         L.ms_ck = o; o = align256(o + sizeof(uint64_t) * (size_t)c * K * 32);
         L.ms_cv = o; o = align256(o + sizeof(int32_t) * (size_t)c * K * 32);
+        if (opts->max_tracks > 1) {   // the multi-track rounds' track step
+            L.ms_ts = o; o = align256(o + sizeof(TrackStep) * (size_t)c);
+            L.ms_tcnt = o; o = align256(o + maxset_smem_bytes(g->dg) * (size_t)c);
+        }
     }
     L.end = o;
     return L;
@@ -557,6 +562,13 @@ int enqueue_maxset(const apo_geometry *g, const apo_hits *hits, const apo_solve_
         A.hf = hfe;
         A.offsets = hits->offsets + e0;
         A.hit_track = mt > 1 ? o->hit_track : nullptr;
+        A.ts = mt > 1 ? at<TrackStep>(ws, L.ms_ts) : nullptr;
+        A.tcnt = mt > 1 ? at<uint32_t>(ws, L.ms_tcnt) : nullptr;
+        A.cnt_stride = (int)(maxset_smem_bytes(g->dg) / sizeof(uint32_t));
+        if (mt > 1) {   // no pending step, counters zero
+            CU(cudaMemsetAsync(A.ts, 0, sizeof(TrackStep) * (size_t)n, s));
+            CU(cudaMemsetAsync(A.tcnt, 0, maxset_smem_bytes(g->dg) * (size_t)n, s));
+        }
         if (A.trace_count) CU(cudaMemsetAsync(A.trace_count, 0, sizeof(int32_t) * (size_t)n * (lv + 1), s));
         for (int r = 0; r < mt; r++) {
             A.round = r;
@@ -572,6 +584,10 @@ int enqueue_maxset(const apo_geometry *g, const apo_hits *hits, const apo_solve_
             A.stride = g->n_coarse;
             launch_maxset_select(gl[0], n, A, s);
             if ((rc = check_launch("maxset_select"))) return rc;
+            if (mt > 1) {
+                launch_track_step(gl[0], n, A, s);
+                if ((rc = check_launch("track_step"))) return rc;
+            }
             for (int lev = 1; lev <= lv; lev++) {
                 launch_vote_children(gl[lev], prec_at(lev), n, hde, hfe, nhe, lev, front, K, ck, cv, s, act,
                                      block, count);
@@ -584,6 +600,10 @@ int enqueue_maxset(const apo_geometry *g, const apo_hits *hits, const apo_solve_
                 A.stride = (long long)K * 32;
                 launch_maxset_select(gl[lev], n, A, s);
                 if ((rc = check_launch("maxset_select"))) return rc;
+                if (mt > 1) {
+                    launch_track_step(gl[lev], n, A, s);
+                    if ((rc = check_launch("track_step"))) return rc;
+                }
             }
         }
     }

@@ -150,6 +150,13 @@ void launch_series_consts(SeriesConsts *dev_out, cudaStream_t s);
 // each event, so 32 x count_in[e] children.  Writes the kept cells to front (max_keep per
 // event) and their number to count_out, or, at the end of an event's search, its track,
 // n_tracks (1 when vmax >= min_votes), final_level and n_final, and sets stop.
+// One event's pending track step: flag (1: its search ended at this level and it has a
+// track), the final vmax, the level's cell count, the track's cell count, S (the seed
+// cell's voting hits) and the hits taken so far.
+struct TrackStep {
+    int32_t flag, vmax, n, mc;
+    uint32_t S[8], take[8];
+};
 struct MaxsetArgs {
     int level, levels, max_keep, slack, min_votes;
     long long n_coarse, stride;
@@ -174,6 +181,12 @@ struct MaxsetArgs {
     const HitRecF *hf;
     const int32_t *offsets;
     int32_t *hit_track;
+    // the round's track step (max_tracks > 1): per event of the chunk, set by the selection
+    // when its search ends, finished by k_track_cells / k_track_finish; per-axis index
+    // counters (cnt_stride each, zero between uses)
+    TrackStep *ts;
+    uint32_t *tcnt;
+    int cnt_stride;
 };
 // Persistent batch search (kernels.cu): the top-K schedule with multi-track rounds, every
 // event's whole search in one block, blocks pulling events from next_event (zeroed by the
@@ -202,6 +215,10 @@ int persist_blocks(const DevGeom &g);   // blocks resident at once on the curren
 void launch_solve_persistent(const DevGeom &g, int blocks, const PersistArgs &A, cudaStream_t s);
 size_t maxset_smem_bytes(const DevGeom &g);
 void launch_maxset_select(const DevGeom &g, int n_ev, const MaxsetArgs &A, cudaStream_t s);
+// The multi-track round's track step after each level's selection: the track's cells (every
+// vmax cell that all hits of S vote for) with the hit finding over them, then the estimate
+// and the active-hit update.  Events without a pending step return at once.
+void launch_track_step(const DevGeom &g, int n_ev, const MaxsetArgs &A, cudaStream_t s);
 void init_maxset_attributes();
 double pipe_peak(int precision, int op);   // diag.cu: directed operations per second
 int launch_dops(int op, const double *x, double *out, long long n, cudaStream_t s);   // diag.cu

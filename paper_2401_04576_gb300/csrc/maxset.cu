@@ -44,8 +44,6 @@ __device__ __forceinline__ void cell_index(const DevGeom &g, const uint64_t *key
 
 __device__ __forceinline__ int clamp_votes(int v) { return v < 0 ? 0 : (v > kHitCap ? kHitCap : v); }
 
-constexpr int32_t kTrackCell = -2;   // a vote-array mark: a cell of the round's track
-
 __device__ __forceinline__ Cell<double> cell_at(const DevGeom &g, int level, const int idx[5]) {
     return Cell<double>{edge(g, 0, level, idx[0]), sin_phi0(g, level, idx[1]), cos_phi0(g, level, idx[1]),
                         edge(g, 2, level, idx[2]), edge(g, 3, level, idx[3]), edge(g, 4, level, idx[4])};
@@ -63,6 +61,41 @@ __device__ __forceinline__ bool vote_at(const DevGeom &g, int prec, const Cell<d
     }
     if (prec == APO_F64_EXACT) return vote_pair_exact(c, load_hit<double>(hd + i), g.k);
     return vote_pair<double>(c, load_hit<double>(hd + i), g.k);
+}
+
+// Estimate from per-axis index counters (off[a] .. off[a + 1] - 1 hold axis a's bins at
+// `level`): warp a < 5 walks axis a's nonzero bins in ascending index order and sums
+// count x centre in round-to-nearest; value = sum / m, error = half the extent of the bins
+// present.  Written when vmax >= min_votes.
+__device__ __forceinline__ void ordered_estimate(const DevGeom &g, int level, int sh, const int off[6],
+                                                 const uint32_t *cnt, int vmax, int m, int min_votes,
+                                                 apo_track &t, int wid, int lane) {
+    (void)level;
+    if (wid >= 5) return;
+    const int a = wid, nb = off[a + 1] - off[a];
+    const uint32_t *ca = cnt + off[a];
+    double sum = 0.0, lo_min = 0.0, hi_max = 0.0;
+    bool first = true;
+    for (int i0 = 0; i0 < nb; i0 += 32) {
+        const int i = i0 + lane;
+        const uint32_t c = i < nb ? ca[i] : 0u;
+        unsigned msk = __ballot_sync(0xffffffffu, c != 0u);
+        while (msk) {   // every lane walks the chunk's nonzero bins in index order
+            const int b = __ffs(msk) - 1;
+            msk &= msk - 1;
+            const int ib = i0 + b;
+            const uint32_t cb = __shfl_sync(0xffffffffu, c, b);
+            const double lo = g.lo_edge[a][(long long)ib << sh];
+            const double hi = g.hi_edge[a][(((long long)ib + 1) << sh) - 1];
+            sum = __dadd_rn(sum, __dmul_rn((double)cb, __dmul_rn(__dadd_rn(lo, hi), 0.5)));
+            if (first) { lo_min = lo; first = false; }
+            hi_max = hi;
+        }
+    }
+    if (lane == 0 && vmax >= min_votes) {
+        t.p[a] = __ddiv_rn(sum, (double)m);
+        t.w[a] = __dmul_rn(__dsub_rn(hi_max, lo_min), 0.5);
+    }
 }
 
 __global__ void __launch_bounds__(kMsThreads)
@@ -133,30 +166,22 @@ k_maxset_select(DevGeom g, MaxsetArgs A) {
     __syncthreads();
     const int T = s_T, vmax = s_vmax, kept = s_kept;
     if (s_final) {
-        const bool multi = mt > 1;
-        __shared__ unsigned long long s_seed;
-        __shared__ uint32_t s_act[8], s_S[8], s_take[8];
-        __shared__ int s_mc;
-        if (multi && vmax < A.min_votes) {   // no track this round: the extraction ends
-            if (tid < 8) A.active[(long long)e * 8 + tid] = 0u;   // later rounds vote no hit
-            if (tid == 0) {
-                A.stop[e] = 1;
-                A.count_out[e] = 0;
-                A.done[e] = 1;
+        if (mt > 1) {
+            // ---- multi-track: the seed and S here; the track step kernels do the rest ----
+            __shared__ unsigned long long s_seed;
+            __shared__ uint32_t s_act[8], s_S[8];
+            if (vmax < A.min_votes) {   // no track this round: the extraction ends
+                if (tid < 8) A.active[(long long)e * 8 + tid] = 0u;   // later rounds vote no hit
+                if (tid == 0) {
+                    A.stop[e] = 1;
+                    A.count_out[e] = 0;
+                    A.done[e] = 1;
+                }
+                return;
             }
-            return;
-        }
-        // ---- estimate over the vmax group (multi-track: over the round's track cells) ----
-        const int sh = g.levels - A.level;
-        int off[6];
-        off[0] = 0;
-#pragma unroll
-        for (int a = 0; a < 5; a++) off[a + 1] = off[a] + (g.bins[a] << A.level);
-        for (int i = tid; i < off[5]; i += kMsThreads) cnt[i] = 0;
-        const HitRecD *hde = multi ? A.hd + (long long)e * kHitCap : nullptr;
-        const HitRecF *hfe = multi ? A.hf + (long long)e * kHitCap : nullptr;
-        if (multi) {
-            if (tid == 0) { s_seed = ~0ull; s_mc = 0; }
+            const HitRecD *hde = A.hd + (long long)e * kHitCap;
+            const HitRecF *hfe = A.hf + (long long)e * kHitCap;
+            if (tid == 0) s_seed = ~0ull;
             if (tid < 8) { s_act[tid] = A.active[(long long)e * 8 + tid]; s_S[tid] = 0u; }
             __syncthreads();
             // the seed: the group's lowest key
@@ -180,63 +205,35 @@ k_maxset_select(DevGeom g, MaxsetArgs A) {
                         atomicOr(&s_S[i >> 5], 1u << (i & 31));
             }
             __syncthreads();
-        } else {
-            __syncthreads();
+            TrackStep &ts = A.ts[e];
+            if (tid < 8) { ts.S[tid] = s_S[tid]; ts.take[tid] = s_S[tid]; }
+            if (tid == 0) {
+                ts.flag = 1;
+                ts.vmax = vmax;
+                ts.n = (int)n;
+                ts.mc = 0;
+                A.stop[e] = 1;
+                A.count_out[e] = 0;
+            }
+            return;
         }
-        int *vw = A.votes + (long long)e * A.stride;
-        int mc_local = 0;
+        // ---- estimate over the vmax group ----
+        const int sh = g.levels - A.level;
+        int off[6];
+        off[0] = 0;
+#pragma unroll
+        for (int a = 0; a < 5; a++) off[a + 1] = off[a] + (g.bins[a] << A.level);
+        for (int i = tid; i < off[5]; i += kMsThreads) cnt[i] = 0;
+        __syncthreads();
         for (long long j = tid; j < n; j += kMsThreads) {
             if (clamp_votes(vo[j]) != vmax) continue;
             int idx[5];
             cell_index(g, ke, j, idx);
-            if (multi) {   // a cell of the track when every hit of S votes for it
-                const Cell<double> c = cell_at(g, A.level, idx);
-                bool ok = true;
-                for (int w8 = 0; w8 < 8 && ok; w8++) {
-                    uint32_t m = s_S[w8];
-                    while (m && ok) {
-                        const int i = w8 * 32 + __ffs(m) - 1;
-                        m &= m - 1;
-                        ok = vote_at(g, A.prec, c, hde, hfe, i);
-                    }
-                }
-                if (!ok) continue;
-                vw[j] = kTrackCell;
-                mc_local++;
-            }
 #pragma unroll
             for (int a = 0; a < 5; a++) atomicAdd(&cnt[off[a] + idx[a]], 1u);
         }
-        if (multi && mc_local) atomicAdd(&s_mc, mc_local);
         __syncthreads();
-        const int m_est = multi ? s_mc : kept;
-        if (wid < 5) {
-            const int a = wid, nb = off[a + 1] - off[a];
-            const uint32_t *ca = cnt + off[a];
-            double sum = 0.0, lo_min = 0.0, hi_max = 0.0;
-            bool first = true;
-            for (int i0 = 0; i0 < nb; i0 += 32) {
-                const int i = i0 + lane;
-                const uint32_t c = i < nb ? ca[i] : 0u;
-                unsigned m = __ballot_sync(0xffffffffu, c != 0u);
-                while (m) {   // every lane walks the chunk's nonzero bins in index order
-                    const int b = __ffs(m) - 1;
-                    m &= m - 1;
-                    const int ib = i0 + b;
-                    const uint32_t cb = __shfl_sync(0xffffffffu, c, b);
-                    const double lo = g.lo_edge[a][(long long)ib << sh];
-                    const double hi = g.hi_edge[a][(((long long)ib + 1) << sh) - 1];
-                    sum = __dadd_rn(sum, __dmul_rn((double)cb, __dmul_rn(__dadd_rn(lo, hi), 0.5)));
-                    if (first) { lo_min = lo; first = false; }
-                    hi_max = hi;
-                }
-            }
-            if (lane == 0 && vmax >= A.min_votes) {
-                t.p[a] = __ddiv_rn(sum, (double)m_est);
-                t.w[a] = __dmul_rn(__dsub_rn(hi_max, lo_min), 0.5);
-            }
-        }
-        const long long fo = (long long)e * mt + A.round;
+        ordered_estimate(g, A.level, sh, off, cnt, vmax, kept, A.min_votes, t, wid, lane);
         if (tid == 0) {
             if (vmax >= A.min_votes) {
                 t.votes = vmax;
@@ -244,48 +241,9 @@ k_maxset_select(DevGeom g, MaxsetArgs A) {
             }
             A.stop[e] = 1;
             A.count_out[e] = 0;
-            if (A.final_level) A.final_level[fo] = A.level;
-            if (A.n_final) A.n_final[fo] = m_est;
+            if (A.final_level) A.final_level[(long long)e * mt + A.round] = A.level;
+            if (A.n_final) A.n_final[(long long)e * mt + A.round] = kept;
         }
-        if (!multi) return;
-        // ---- hit finding: S and the active hits voting (FP64, drift +- 3 sigma) for a track cell ----
-        if (tid < 8) s_take[tid] = s_S[tid];
-        __syncthreads();
-        for (long long j = tid; j < n; j += kMsThreads) {
-            if (vw[j] != kTrackCell) continue;
-            int idx[5];
-            cell_index(g, ke, j, idx);
-            const Cell<double> c = cell_at(g, A.level, idx);
-            for (int i = 0; i < nh; i++) {
-                const uint32_t bit = 1u << (i & 31);
-                if (!(s_act[i >> 5] & bit) || (s_take[i >> 5] & bit)) continue;
-                Hit<double> h = load_hit<double>(hde + i);
-                const double d = h.d.lo;
-                const double dlo = __dsub_rd(d, A.width);
-                h.d = {gt0(dlo) ? dlo : 0.0, __dadd_ru(d, A.width)};
-                if (vote_pair<double>(c, h, g.k)) atomicOr(&s_take[i >> 5], bit);
-            }
-        }
-        __syncthreads();
-        __shared__ int s_left;
-        if (tid == 0) s_left = 0;
-        __syncthreads();
-        if (tid < 8) {
-            const uint32_t took = s_act[tid] & s_take[tid], left = s_act[tid] & ~s_take[tid];
-            A.active[(long long)e * 8 + tid] = left;
-            if (left) atomicOr(&s_left, 1);
-            if (A.hit_track) {
-                const int a0 = A.offsets[e];
-                uint32_t m = took;
-                while (m) {
-                    const int i = tid * 32 + __ffs(m) - 1;
-                    m &= m - 1;
-                    A.hit_track[a0 + i] = A.round;
-                }
-            }
-        }
-        __syncthreads();
-        if (tid == 0 && (!s_left || A.round + 1 >= mt)) A.done[e] = 1;
         return;
     }
     // ---- order-preserving compaction of {votes >= T} ----
@@ -340,6 +298,118 @@ k_maxset_select(DevGeom g, MaxsetArgs A) {
     }
 }
 
+constexpr int kTsThreads = 128;
+constexpr int kTsBlocks = 96;    // blocks per event of the track-cell kernel
+constexpr int kTfThreads = 192;  // the step's end: one warp per axis for the estimate
+
+// The track's cells of every event with a pending step: each vmax cell of the level is
+// tested against the hits of S (at the level's precision, stopping at the first that does
+// not vote); a track cell adds its indices to the event's per-axis counters and takes
+// every active hit not yet taken that votes (FP64) for it with the drift widened by 3 sigma.
+__global__ void __launch_bounds__(kTsThreads, 3)
+k_track_cells(DevGeom g, MaxsetArgs A) {
+    const int e = blockIdx.y, tid = threadIdx.x;
+    TrackStep &ts = A.ts[e];
+    if (!ts.flag) return;
+    __shared__ uint32_t s_S[8], s_act[8];
+    __shared__ int s_mc;
+    if (tid < 8) { s_S[tid] = ts.S[tid]; s_act[tid] = A.active[(long long)e * 8 + tid]; }
+    if (tid == 0) s_mc = 0;
+    __syncthreads();
+    const int vmax = ts.vmax, nh = A.n_hits[e];
+    const long long n = ts.n;
+    const int32_t *vo = A.votes + (long long)e * A.stride;
+    const uint64_t *ke = A.keys ? A.keys + (long long)e * A.stride : nullptr;
+    const HitRecD *hde = A.hd + (long long)e * kHitCap;
+    const HitRecF *hfe = A.hf + (long long)e * kHitCap;
+    uint32_t *cnt = A.tcnt + (long long)e * A.cnt_stride;
+    volatile uint32_t *take = ts.take;
+    int off[6];
+    off[0] = 0;
+#pragma unroll
+    for (int a = 0; a < 5; a++) off[a + 1] = off[a] + (g.bins[a] << A.level);
+    int mc = 0;
+    for (long long j = (long long)blockIdx.x * kTsThreads + tid; j < n; j += (long long)gridDim.x * kTsThreads) {
+        if (clamp_votes(vo[j]) != vmax) continue;
+        int idx[5];
+        cell_index(g, ke, j, idx);
+        const Cell<double> c = cell_at(g, A.level, idx);
+        bool ok = true;
+        for (int w8 = 0; w8 < 8 && ok; w8++) {
+            uint32_t m = s_S[w8];
+            while (m && ok) {
+                const int i = w8 * 32 + __ffs(m) - 1;
+                m &= m - 1;
+                ok = vote_at(g, A.prec, c, hde, hfe, i);
+            }
+        }
+        if (!ok) continue;
+        mc++;
+#pragma unroll
+        for (int a = 0; a < 5; a++) atomicAdd(&cnt[off[a] + idx[a]], 1u);
+        for (int i = 0; i < nh; i++) {
+            const uint32_t bit = 1u << (i & 31);
+            if (!(s_act[i >> 5] & bit) || (take[i >> 5] & bit)) continue;
+            Hit<double> h = load_hit<double>(hde + i);
+            const double d = h.d.lo;
+            const double dlo = __dsub_rd(d, A.width);
+            h.d = {gt0(dlo) ? dlo : 0.0, __dadd_ru(d, A.width)};
+            if (vote_pair<double>(c, h, g.k)) atomicOr(&ts.take[i >> 5], bit);
+        }
+    }
+    if (mc) atomicAdd(&s_mc, mc);
+    __syncthreads();
+    if (tid == 0 && s_mc) atomicAdd(&ts.mc, s_mc);
+}
+
+// The step's end: the estimate over the track's cells (per-axis counters, ordered sums),
+// the record, the active-hit update, hit_track and the done flag; the counters and the
+// flag are cleared for the next use.
+__global__ void __launch_bounds__(kTfThreads)
+k_track_finish(DevGeom g, MaxsetArgs A) {
+    const int e = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    TrackStep &ts = A.ts[e];
+    if (!ts.flag) return;
+    const int mt = A.max_tracks;
+    apo_track &t = A.tracks[(long long)e * mt + A.round];
+    uint32_t *cnt = A.tcnt + (long long)e * A.cnt_stride;
+    const int sh = g.levels - A.level;
+    int off[6];
+    off[0] = 0;
+#pragma unroll
+    for (int a = 0; a < 5; a++) off[a + 1] = off[a] + (g.bins[a] << A.level);
+    const int vmax = ts.vmax, mc = ts.mc;
+    ordered_estimate(g, A.level, sh, off, cnt, vmax, mc, A.min_votes, t, wid, lane);
+    __shared__ int s_left;
+    if (tid == 0) s_left = 0;
+    __syncthreads();
+    for (int i = tid; i < off[5]; i += kTfThreads) cnt[i] = 0u;
+    if (tid < 8) {
+        const uint32_t act = A.active[(long long)e * 8 + tid];
+        const uint32_t took = act & ts.take[tid], left = act & ~ts.take[tid];
+        A.active[(long long)e * 8 + tid] = left;
+        if (left) atomicOr(&s_left, 1);
+        if (A.hit_track) {
+            const int a0 = A.offsets[e];
+            uint32_t m = took;
+            while (m) {
+                const int i = tid * 32 + __ffs(m) - 1;
+                m &= m - 1;
+                A.hit_track[a0 + i] = A.round;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        t.votes = vmax;
+        A.n_tracks[e] = A.round + 1;
+        if (A.final_level) A.final_level[(long long)e * mt + A.round] = A.level;
+        if (A.n_final) A.n_final[(long long)e * mt + A.round] = mc;
+        if (!s_left || A.round + 1 >= mt) A.done[e] = 1;
+        ts.flag = 0;
+    }
+}
+
 }  // namespace
 
 size_t maxset_smem_bytes(const DevGeom &g) {
@@ -355,6 +425,12 @@ void init_maxset_attributes() {
 void launch_maxset_select(const DevGeom &g, int n_ev, const MaxsetArgs &A, cudaStream_t s) {
     if (n_ev <= 0) return;
     k_maxset_select<<<n_ev, kMsThreads, maxset_smem_bytes(g), s>>>(g, A);
+}
+
+void launch_track_step(const DevGeom &g, int n_ev, const MaxsetArgs &A, cudaStream_t s) {
+    if (n_ev <= 0) return;
+    k_track_cells<<<dim3(kTsBlocks, n_ev), kTsThreads, 0, s>>>(g, A);
+    k_track_finish<<<n_ev, kTfThreads, 0, s>>>(g, A);
 }
 
 }  // namespace apo

@@ -58,3 +58,36 @@ def test_reduce_max_over_two_gloo_ranks():
     for p in ps:
         p.join(timeout=60)
     assert out == {0: 2.0, 1: 2.0}
+
+
+def test_multi_track_figures():
+    """The multi-track figures on a hand-made extraction: two events, three true tracks and
+    two noise hits; one found track's box holds a true helix, another holds none."""
+    from paper_2401_04576_gb300.apo import TRACK_DTYPE
+    w = chamber.make_wires()
+    ev = chamber.multi_track_events(2, seed=9, w=w)
+    n_true = [len(t) for t in ev.tracks]
+    tracks = np.zeros((2, 5), TRACK_DTYPE)
+    nt = np.zeros(2, np.int32)
+    # event 0: track 0 centred on the first generated helix (box 1e-6 wide), track 1 far away
+    tracks[0, 0]["p"] = ev.tracks[0][0].params
+    tracks[0, 0]["w"] = 1e-6
+    tracks[0, 1]["p"] = np.array(ev.tracks[0][0].params) + 10.0
+    tracks[0, 1]["w"] = 1e-6
+    nt[0] = 2
+    a, b = ev.offsets[0], ev.offsets[2]
+    ht = np.full(b - a, -1, np.int32)
+    truth0 = ev.hit_truth[0]
+    sig0 = [i for i, h in enumerate(truth0) if h is not None]
+    noise0 = [i for i, h in enumerate(truth0) if h is None]
+    ht[sig0[:3]] = 0                      # three signal hits taken
+    if noise0:
+        ht[noise0[0]] = 1                 # one noise hit taken
+    f = bench.multi_track_figures(ev, tracks, nt, ht)
+    n_sig = sum(h is not None for e in range(2) for h in ev.hit_truth[e])
+    n_noise = sum(h is None for e in range(2) for h in ev.hit_truth[e])
+    assert f["signal_hits_taken"] == pytest.approx(3 / n_sig)
+    assert f["noise_hits_rejected"] == pytest.approx(1 - (1 if noise0 else 0) / max(n_noise, 1))
+    assert f["tracks_found_per_true_track"] == pytest.approx(2 / sum(n_true))
+    assert f["true_tracks_in_a_found_box"] == pytest.approx(1 / sum(n_true))
+    assert f["found_tracks_holding_no_true_helix"] == pytest.approx(0.5)
