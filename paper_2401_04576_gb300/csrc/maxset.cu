@@ -49,18 +49,36 @@ __device__ __forceinline__ Cell<double> cell_at(const DevGeom &g, int level, con
                         edge(g, 2, level, idx[2]), edge(g, 3, level, idx[3]), edge(g, 4, level, idx[4])};
 }
 
+__device__ __forceinline__ Cell<float> cell32(const Cell<double> &c) {
+    return Cell<float>{to_prec<float>(c.D), to_prec<float>(c.S0), to_prec<float>(c.C0), to_prec<float>(c.W),
+                       to_prec<float>(c.Z), to_prec<float>(c.L)};
+}
+
 // The vote of staged hit i for a cell at the level's precision code, as the voting
 // kernels count it (FP32 cells are the FP64 edges rounded outward; the FP32-filtered mode
-// votes as FP64).
+// votes as FP64).  FP64 (expansion) votes are decided by the FP32 program first: its
+// intervals contain the FP64 ones, so an FP32 refusal is an FP64 refusal.
 __device__ __forceinline__ bool vote_at(const DevGeom &g, int prec, const Cell<double> &c, const HitRecD *hd,
                                         const HitRecF *hf, int i) {
-    if (prec == APO_F32) {
-        Cell<float> c32{to_prec<float>(c.D), to_prec<float>(c.S0), to_prec<float>(c.C0), to_prec<float>(c.W),
-                        to_prec<float>(c.Z), to_prec<float>(c.L)};
-        return vote_pair<float>(c32, load_hit<float>(hf + i), g.k);
-    }
+    if (prec == APO_F32) return vote_pair<float>(cell32(c), load_hit<float>(hf + i), g.k);
     if (prec == APO_F64_EXACT) return vote_pair_exact(c, load_hit<double>(hd + i), g.k);
+    if (!vote_pair<float>(cell32(c), load_hit<float>(hf + i), g.k)) return false;
     return vote_pair<double>(c, load_hit<double>(hd + i), g.k);
+}
+
+// The FP64 vote of staged hit i for a cell with its drift widened to [max(rd(d - width),
+// 0), ru(d + width)] (the hit finding), decided by the FP32 program on the outward-rounded
+// FP32 copy of that interval first.
+__device__ __forceinline__ bool vote_widened(const DevGeom &g, const Cell<double> &c, const Cell<float> &c32,
+                                             const HitRecD *hd, const HitRecF *hf, int i, double width) {
+    Hit<double> h = load_hit<double>(hd + i);
+    const double d = h.d.lo;
+    const double dlo = __dsub_rd(d, width);
+    h.d = {gt0(dlo) ? dlo : 0.0, __dadd_ru(d, width)};
+    Hit<float> h32 = load_hit<float>(hf + i);
+    h32.d = {__double2float_rd(h.d.lo), __double2float_ru(h.d.hi)};
+    if (!vote_pair<float>(c32, h32, g.k)) return false;
+    return vote_pair<double>(c, h, g.k);
 }
 
 // Estimate from per-axis index counters (off[a] .. off[a + 1] - 1 hold axis a's bins at
@@ -347,14 +365,11 @@ k_track_cells(DevGeom g, MaxsetArgs A) {
         mc++;
 #pragma unroll
         for (int a = 0; a < 5; a++) atomicAdd(&cnt[off[a] + idx[a]], 1u);
+        const Cell<float> c32 = cell32(c);
         for (int i = 0; i < nh; i++) {
             const uint32_t bit = 1u << (i & 31);
             if (!(s_act[i >> 5] & bit) || (take[i >> 5] & bit)) continue;
-            Hit<double> h = load_hit<double>(hde + i);
-            const double d = h.d.lo;
-            const double dlo = __dsub_rd(d, A.width);
-            h.d = {gt0(dlo) ? dlo : 0.0, __dadd_ru(d, A.width)};
-            if (vote_pair<double>(c, h, g.k)) atomicOr(&ts.take[i >> 5], bit);
+            if (vote_widened(g, c, c32, hde, hfe, i, A.width)) atomicOr(&ts.take[i >> 5], bit);
         }
     }
     if (mc) atomicAdd(&s_mc, mc);
