@@ -138,15 +138,15 @@ template <> __device__ __forceinline__ IV<float> mul<float>(IV<float> a, IV<floa
                     fmaxf(__fmul_ru(a.hi, b.lo), __fmul_ru(a.hi, b.hi)));
     return {l, h};
 }
-// Square: the upper end is the larger square in every case; the lower end is 0 when the
-// interval straddles 0 (then a.lo a.hi < 0, and a negative product stays negative when
-// rounded down) and the smaller square otherwise.  Fewer compares and selects than the
-// three sign cases (the FP32 kernels are bound by the ALU pipe that runs them).
+// Square from the magnitudes: the upper end is ru(m^2) with m = max(-a.lo, a.hi), the
+// larger |end|; the lower end is rd(n^2) with n = max(0, a.lo, -a.hi), which is a.lo for
+// a >= 0, -a.hi for a <= 0 and 0 when a straddles 0.  Rounding is monotone, so these are
+// the three sign cases' end points; two products and three min / max in all (the FP32
+// kernels are issue-bound).
 template <> __device__ __forceinline__ IV<float> sqr<float>(IV<float> a) {
-    float ll = __fmul_rd(a.lo, a.lo), hh = __fmul_rd(a.hi, a.hi);
-    float LL = __fmul_ru(a.lo, a.lo), HH = __fmul_ru(a.hi, a.hi);
-    float l = __fmul_rd(a.lo, a.hi) < 0.f ? 0.f : fminf(ll, hh);
-    return {l, fmaxf(LL, HH)};
+    const float m = fmaxf(-a.lo, a.hi);
+    const float n = fmaxf(0.f, fmaxf(a.lo, -a.hi));
+    return {__fmul_rd(n, n), __fmul_ru(m, m)};
 }
 template <> __device__ __forceinline__ IV<float> divi<float>(IV<float> a, IV<float> b) {
     // b > 0: lo from a.lo, hi from a.hi; b < 0: lo from a.hi, hi from a.lo.  Either way the
