@@ -299,3 +299,46 @@ def test_maxset_multi_track_config4_sampled(wires):
             hit |= np.all(np.abs(t[e, k]["p"] - truth) <= t[e, k]["w"], axis=1)
         found += int(hit.sum())
     assert found >= 0.6 * true, (found, true)
+
+
+def test_maxset_multi_track_edges_chunks_and_graph(wires):
+    """Multi-track rounds with an empty event, a malformed event and an event whose hits
+    cannot reach min_votes in one batch, processed in chunks of 3 events and replayed from
+    a CUDA graph: every other event equal to the oracle, the malformed one flagged with no
+    track, and chunking and replay change nothing."""
+    g = G.make_grid([2, 64, 8, 2, 4], 3, 64)
+    tab = O.Tables(g, wires)
+    geom = apo.Geometry(g, wires)
+    base = chamber.multi_track_events(5, seed=97, w=wires)
+    wid, dr, off = list(base.wire_id), list(base.drift), list(base.offsets)
+    off.append(off[-1])                                   # event 5: no hit
+    few = chamber.single_track_events(1, seed=98, w=wires)
+    wid += list(few.wire_id[:4]); dr += list(few.drift[:4]); off.append(off[-1] + 4)   # event 6: 4 hits
+    bad_at = len(wid)
+    wid += list(few.wire_id); dr += list(few.drift); off.append(off[-1] + len(few.wire_id))  # event 7
+    dr[bad_at + 1] = -2.0                                 # malformed
+    ev = chamber.Events(offsets=np.array(off, np.int32), wire_id=np.array(wid, np.int32), drift=np.array(dr))
+    prec = [apo.F32 | OUT, apo.F32 | OUT, apo.F64 | OUT, apo.F64 | OUT]
+    mt = 3
+    runs = []
+    for tune, graph in ((apo.ApoTune(0, 1, 256, 0), False), (apo.ApoTune(0, 1, 256, 3), False),
+                        (apo.ApoTune(0, 1, 128, 3), True)):
+        o, outs = _multi_opts(prec, 2000, 2, mt, ev.n_events, int(ev.offsets[-1]), tune=tune, use_graph=graph)
+        for _ in range(2 if graph else 1):
+            tracks, nt = apo.solve_batch(geom, _hits(ev), o)
+            torch.cuda.synchronize()
+        runs.append((apo.tracks_to_numpy(tracks, ev.n_events, mt), nt.cpu().numpy(),
+                     [x.cpu().numpy() for x in outs]))
+    for r in runs[1:]:
+        assert np.array_equal(r[0].view(np.uint8), runs[0][0].view(np.uint8))
+        assert np.array_equal(r[1], runs[0][1])
+        for a, b in zip(r[2], runs[0][2]):
+            np.testing.assert_array_equal(a, b)
+    t, nt, (fl, nf, ht) = runs[0]
+    assert t[7, 0]["votes"] == apo.APO_EINVAL and nt[7] == 0
+    assert np.all(ht[off[7]:off[8]] == -1)
+    assert nt[5] == 0 and nt[6] == 0
+    o2, outs2 = _multi_opts(prec, 2000, 2, mt, ev.n_events, int(ev.offsets[-1]), tune=apo.ApoTune(0, 1, 256, 3))
+    tr2, nt2 = apo.solve_batch(geom, _hits(ev), o2)
+    torch.cuda.synchronize()
+    _check_multi(tab, ev, [0, 1, 2, 3, 4, 5, 6], tr2, nt2, outs2, prec, 2000, 2, mt)
