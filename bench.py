@@ -413,7 +413,7 @@ def serving_leg(w, seconds: float) -> dict:
                                     "precision": "FP64 at every level, one event per call"}}
 
 
-def background_study(w, n_events: int = 1024, seed: int = 4) -> dict:
+def background_study(w, n_events: int = 1024, seed: int = 4, n_maxset: int = 512) -> dict:
     """Background-hit rejection of the multi-track hit finding (the study the paper leaves
     for later, Conclusion), on multi-track events with 10-30 % noise occupancy: 10^5 coarse
     cells, top-64, 6 levels, FP32 levels 0-4 / FP64 levels 5-6, up to 5 tracks, min 6 votes.
@@ -469,9 +469,9 @@ def background_study(w, n_events: int = 1024, seed: int = 4) -> dict:
            "events_per_s": ev.n_events / (ms * 1e-3),
            "launch_schedules": launch, "schedules_give_identical_results": bool(same)}
     out.update(multi_track_figures(ev, tracks, nt, hts))
-    # the max-set extraction on the first 512 of the events (it runs about 5x longer per
-    # event than the top-K one)
-    out["maxset"] = multi_maxset_leg(w, ev.subset(range(min(512, ev.n_events))))
+    # the max-set extraction on the first n_maxset of the events (it runs about 130x
+    # longer per event than the top-K one)
+    out["maxset"] = multi_maxset_leg(w, ev.subset(range(min(n_maxset, ev.n_events))))
     return out
 
 
@@ -1010,7 +1010,8 @@ def run_apo(args) -> None:
     if not args.no_maxset:
         line["recovery_maxset"] = maxset_leg(w, ev, max(2, args.steps), flush, world)
     if rank == 0 and not args.no_bg:
-        line["background_rejection"] = background_study(w, n_events=args.bg_events)
+        line["background_rejection"] = background_study(w, n_events=args.bg_events,
+                                                        n_maxset=args.bg_maxset_events)
     if rank == 0 and not args.no_config1:
         line["config1_latency"] = config1_latency(w)
     if rank == 0 and not args.no_paper4d:
@@ -1125,6 +1126,8 @@ def main(argv=None):
     ap.add_argument("--no-config1", action="store_true", help="skip the one-event latency leg")
     ap.add_argument("--bg-events", type=int, default=4096,
                     help="events of the multi-track background study")
+    ap.add_argument("--bg-maxset-events", type=int, default=512,
+                    help="of them, events of its max-set extraction (about 35 events/s)")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--case", default=None,
                     choices=["coarse-f64", "coarse-f32", "coarse-f32-full", "coarse-mid", "solve-f64",
