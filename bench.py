@@ -165,7 +165,7 @@ def make_inputs(seed_offset: int = 0):
     return w, g, ev
 
 
-def serve_sweep(geom, ev, rates, seconds: float, solve, batch_events: int = 64, max_slots: int = 4,
+def serve_sweep(geom, ev, rates, seconds: float, solve, batch_events: int = 64, max_slots: int = 8,
                 max_pending: int = 4096) -> list:
     """Poisson arrivals at each offered rate (events/s) into the continuous-batching server
     (search options `solve`), cycling through the batch's events; per rate: sustained
@@ -401,7 +401,7 @@ def serving_leg(w, seconds: float) -> dict:
             lat.append(1e3 * (time.perf_counter() - t0))
     geom.close()
     return {"workload": "Poisson arrivals of 2048 multi-track events (seed 5; 1-5 helices plus "
-                        "noise, mean %.1f hits) into apo_serve (64-event slots, 4 slots), "
+                        "noise, mean %.1f hits) into apo_serve (64-event slots, 8 slots), "
                         "10^5 coarse cells, top-64, 6 levels, FP32 "
                         "levels 0-4 / FP64 5-6, up to 5 tracks" % (ev.offsets[-1] / ev.n_events),
             "reading": "the config-3 distribution = the uneven multi-track configuration "
@@ -522,7 +522,7 @@ def multi_track_figures(ev, tracks, nt, hit_track) -> dict:
 
 def multi_maxset_leg(w, ev) -> dict:
     """The same multi-track events through the max-set schedule (anisotropic grid, FP32
-    levels 0-4 / FP64 level 5, direction condition, max_keep 32768, slack 4, <= 5 tracks,
+    levels 0-4 / FP64 level 5, direction condition, max_keep 32768, slack 6, <= 5 tracks,
     min 6 votes): each round keeps one hit-set cluster of the final maximum-vote group."""
     import torch
     from gen import grid as G
@@ -533,7 +533,7 @@ def multi_maxset_leg(w, ev) -> dict:
     ht = torch.empty(int(ev.offsets[-1]), dtype=torch.int32, device="cuda")
     prec = [apo.F32 | apo.OUTGOING] * MAXSET["levels"] + [apo.F64 | apo.OUTGOING]
     tune = apo.ApoTune(0, 1, 256, 0)
-    o = apo.solve_opts(precision=prec, schedule=apo.SCHED_MAXSET, max_keep=MAXSET["max_keep"], slack=4,
+    o = apo.solve_opts(precision=prec, schedule=apo.SCHED_MAXSET, max_keep=MAXSET["max_keep"], slack=6,
                        max_tracks=5, min_votes=6, hit_track=ht, tune=tune)
     ws = geom.workspace(ev.n_events, opts=o)
     tracks, nt = apo.solve_batch(geom, hits, o, workspace=ws)      # warm-up
@@ -545,7 +545,7 @@ def multi_maxset_leg(w, ev) -> dict:
     s1.synchronize()
     ms = s0.elapsed_time(s1)
     res = {"workload": "the same events; 2 x 256 x 16 x 2 x 8 coarse cells, max-set schedule "
-                       "(max_keep 32768, slack 4), 5 bisection levels, direction condition; FP32 "
+                       "(max_keep 32768, slack 6), 5 bisection levels, direction condition; FP32 "
                        "levels 0-4, FP64 level 5; <= 5 tracks, min 6 votes; one hit-set cluster "
                        "of the final maximum-vote group per round",
            "events_per_s": ev.n_events / (ms * 1e-3), "ms": ms, "tune": tune.as_dict()}
@@ -1056,7 +1056,7 @@ def run_case(args) -> None:
         geom = apo.Geometry(ga, w)
         o = apo.solve_opts(precision=[apo.F32 | apo.OUTGOING] * ga.levels + [apo.F64 | apo.OUTGOING],
                            schedule=apo.SCHED_MAXSET, max_keep=MAXSET["max_keep"],
-                           tune=apo.ApoTune(0, 0, 128, 0, 0), slack=4 if multi else 0,
+                           tune=apo.ApoTune(0, 0, 128, 0, 0), slack=6 if multi else 0,
                            max_tracks=5 if multi else 1, min_votes=6 if multi else 0)
         hits = apo.DeviceHits.from_events(ev)
         for _ in range(2):
