@@ -14,10 +14,12 @@
 // the final vmax group can hold several tracks' cells (tracks with equal hit counts tie),
 // so a round keeps one of them.  The seed is the group's lowest key, S the active hits
 // that vote for it at the level's precision, and the track's cells are the group's cells
-// that every hit of S votes for (each has vmax votes, so its voting hits are exactly S);
-// they are marked in the vote array.  The estimate is taken over them as above; the track
-// takes S and every active hit that votes (FP64) for one of them with its drift widened
-// by 3 sigma (Section 3.3's hit finding), which leave the active set.
+// that every hit of S votes for (each has vmax votes, so its voting hits are exactly S).
+// The selection finds the seed and S; k_track_cells (many blocks per event) finds the
+// track's cells, counts their indices per axis and runs the hit finding over them;
+// k_track_finish takes the estimate as above.  The track takes S and every active hit
+// that votes (FP64) for one of its cells with the drift widened by 3 sigma (Section 3.3's
+// hit finding); those hits leave the active set.
 #include <cuda_runtime.h>
 
 #include <climits>
