@@ -1002,7 +1002,11 @@ def run_apo(args) -> None:
         line["exact_phase"] = exact
     if not args.no_serve:
         line["serving"] = serving_leg(w, args.serve_seconds)
-        below = [x for x in line["serving"]["loads"] if x["rejected"] == 0 and x["p50_ms"] is not None]
+        # the headline latencies: at the highest offered rate the server sustains (nothing
+        # rejected and at least 90 % of the offered rate completed per second); above it the
+        # figures measure the queue's backlog, not the service
+        below = [x for x in line["serving"]["loads"] if x["rejected"] == 0 and x["p50_ms"] is not None
+                 and x["sustained_per_s"] >= 0.9 * x["offered_per_s"]]
         if below:
             line["p50_ms"] = below[-1]["p50_ms"]
             line["p99_ms"] = below[-1]["p99_ms"]
