@@ -1060,7 +1060,8 @@ def run_case(args) -> None:
         geom = apo.Geometry(ga, w)
         o = apo.solve_opts(precision=[apo.F32 | apo.OUTGOING] * ga.levels + [apo.F64 | apo.OUTGOING],
                            schedule=apo.SCHED_MAXSET, max_keep=MAXSET["max_keep"],
-                           tune=apo.ApoTune(0, 0, 128, 0, 0), slack=6 if multi else 0,
+                           tune=apo.ApoTune(0, 1, 256, 0, 0) if multi else apo.ApoTune(0, 0, 128, 0, 0),
+                           slack=6 if multi else 0,
                            max_tracks=5 if multi else 1, min_votes=6 if multi else 0)
         hits = apo.DeviceHits.from_events(ev)
         for _ in range(2):
