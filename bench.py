@@ -165,6 +165,16 @@ def make_inputs(seed_offset: int = 0):
     return w, g, ev
 
 
+def headline_latency(loads):
+    """The load whose p50 / p99 head the JSON line: the highest offered rate the server
+    sustains (nothing rejected and at least 90 % of the offered rate completed per second);
+    above it the latencies measure the queue's backlog, not the service.  None if no load
+    qualifies."""
+    ok = [x for x in loads if x["rejected"] == 0 and x["p50_ms"] is not None
+          and x["sustained_per_s"] >= 0.9 * x["offered_per_s"]]
+    return max(ok, key=lambda x: x["offered_per_s"]) if ok else None
+
+
 def serve_sweep(geom, ev, rates, seconds: float, solve, batch_events: int = 64, max_slots: int = 8,
                 max_pending: int = 4096) -> list:
     """Poisson arrivals at each offered rate (events/s) into the continuous-batching server
@@ -1002,15 +1012,11 @@ def run_apo(args) -> None:
         line["exact_phase"] = exact
     if not args.no_serve:
         line["serving"] = serving_leg(w, args.serve_seconds)
-        # the headline latencies: at the highest offered rate the server sustains (nothing
-        # rejected and at least 90 % of the offered rate completed per second); above it the
-        # figures measure the queue's backlog, not the service
-        below = [x for x in line["serving"]["loads"] if x["rejected"] == 0 and x["p50_ms"] is not None
-                 and x["sustained_per_s"] >= 0.9 * x["offered_per_s"]]
-        if below:
-            line["p50_ms"] = below[-1]["p50_ms"]
-            line["p99_ms"] = below[-1]["p99_ms"]
-            line["p50_p99_at_offered_per_s"] = below[-1]["offered_per_s"]
+        best = headline_latency(line["serving"]["loads"])
+        if best is not None:
+            line["p50_ms"] = best["p50_ms"]
+            line["p99_ms"] = best["p99_ms"]
+            line["p50_p99_at_offered_per_s"] = best["offered_per_s"]
     if not args.no_maxset:
         line["recovery_maxset"] = maxset_leg(w, ev, max(2, args.steps), flush, world)
     if rank == 0 and not args.no_bg:

@@ -91,3 +91,14 @@ def test_multi_track_figures():
     assert f["tracks_found_per_true_track"] == pytest.approx(2 / sum(n_true))
     assert f["true_tracks_in_a_found_box"] == pytest.approx(1 / sum(n_true))
     assert f["found_tracks_holding_no_true_helix"] == pytest.approx(0.5)
+
+
+def test_headline_latency_is_at_the_highest_sustained_load():
+    loads = [
+        {"offered_per_s": 1000, "rejected": 0, "sustained_per_s": 1030, "p50_ms": 15.0, "p99_ms": 30.0},
+        {"offered_per_s": 2000, "rejected": 0, "sustained_per_s": 1930, "p50_ms": 31.0, "p99_ms": 58.0},
+        {"offered_per_s": 5000, "rejected": 0, "sustained_per_s": 2540, "p50_ms": 590.0, "p99_ms": 999.0},
+        {"offered_per_s": 10000, "rejected": 3000, "sustained_per_s": 2550, "p50_ms": 1100.0, "p99_ms": 1800.0},
+    ]
+    assert bench.headline_latency(loads)["offered_per_s"] == 2000
+    assert bench.headline_latency(loads[2:]) is None
