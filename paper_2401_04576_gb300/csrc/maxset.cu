@@ -320,23 +320,38 @@ k_maxset_select(DevGeom g, MaxsetArgs A) {
 
 constexpr int kTsThreads = 128;
 constexpr int kTsBlocks = 96;    // blocks per event of the track-cell kernel
+constexpr int kTsChunk = 2048;   // cells a block scans per pass
 constexpr int kTfThreads = 192;  // the step's end: one warp per axis for the estimate
 
 // The track's cells of every event with a pending step: each vmax cell of the level is
 // tested against the hits of S (at the level's precision, stopping at the first that does
 // not vote); a track cell adds its indices to the event's per-axis counters and takes
 // every active hit not yet taken that votes (FP64) for it with the drift widened by 3 sigma.
+// Each block scans its cells in chunks of kTsChunk: the chunk's vmax cells are queued in
+// shared memory, the queue is tested one cell per thread, and the hit finding runs over
+// the (track cell, hit) pairs one pair per thread, so that whole warps do the votes.
 __global__ void __launch_bounds__(kTsThreads, 3)
 k_track_cells(DevGeom g, MaxsetArgs A) {
     const int e = blockIdx.y, tid = threadIdx.x;
     TrackStep &ts = A.ts[e];
     if (!ts.flag) return;
-    __shared__ uint32_t s_S[8], s_act[8];
-    __shared__ int s_mc;
-    if (tid < 8) { s_S[tid] = ts.S[tid]; s_act[tid] = A.active[(long long)e * 8 + tid]; }
-    if (tid == 0) s_mc = 0;
+    __shared__ uint32_t s_S[8];
+    __shared__ int s_q[kTsChunk], s_t[kTsChunk];
+    __shared__ unsigned char s_hit[kHitCap];
+    __shared__ int s_mc, s_nq, s_nt, s_na;
+    const int nh = A.n_hits[e];
+    if (tid < 8) s_S[tid] = ts.S[tid];
+    if (tid == 0) {   // the active hits outside S (S is taken already), in index order
+        s_mc = 0;
+        int na = 0;
+        for (int i = 0; i < nh; i++) {
+            const uint32_t bit = 1u << (i & 31);
+            if ((A.active[(long long)e * 8 + (i >> 5)] & bit) && !(ts.S[i >> 5] & bit)) s_hit[na++] = (unsigned char)i;
+        }
+        s_na = na;
+    }
     __syncthreads();
-    const int vmax = ts.vmax, nh = A.n_hits[e];
+    const int vmax = ts.vmax, na = s_na;
     const long long n = ts.n;
     const int32_t *vo = A.votes + (long long)e * A.stride;
     const uint64_t *ke = A.keys ? A.keys + (long long)e * A.stride : nullptr;
@@ -349,30 +364,49 @@ k_track_cells(DevGeom g, MaxsetArgs A) {
 #pragma unroll
     for (int a = 0; a < 5; a++) off[a + 1] = off[a] + (g.bins[a] << A.level);
     int mc = 0;
-    for (long long j = (long long)blockIdx.x * kTsThreads + tid; j < n; j += (long long)gridDim.x * kTsThreads) {
-        if (clamp_votes(vo[j]) != vmax) continue;
-        int idx[5];
-        cell_index(g, ke, j, idx);
-        const Cell<double> c = cell_at(g, A.level, idx);
-        bool ok = true;
-        for (int w8 = 0; w8 < 8 && ok; w8++) {
-            uint32_t m = s_S[w8];
-            while (m && ok) {
-                const int i = w8 * 32 + __ffs(m) - 1;
-                m &= m - 1;
-                ok = vote_at(g, A.prec, c, hde, hfe, i);
+    for (long long base = (long long)blockIdx.x * kTsChunk; base < n; base += (long long)gridDim.x * kTsChunk) {
+        if (tid == 0) { s_nq = 0; s_nt = 0; }
+        __syncthreads();
+        // the chunk's vmax cells
+        for (int k = tid; k < kTsChunk; k += kTsThreads) {
+            const long long j = base + k;
+            if (j < n && clamp_votes(vo[j]) == vmax) s_q[atomicAdd(&s_nq, 1)] = k;
+        }
+        __syncthreads();
+        // the cluster test, one queued cell per thread
+        const int nq = s_nq;
+        for (int q = tid; q < nq; q += kTsThreads) {
+            int idx[5];
+            cell_index(g, ke, base + s_q[q], idx);
+            const Cell<double> c = cell_at(g, A.level, idx);
+            bool ok = true;
+            for (int w8 = 0; w8 < 8 && ok; w8++) {
+                uint32_t m = s_S[w8];
+                while (m && ok) {
+                    const int i = w8 * 32 + __ffs(m) - 1;
+                    m &= m - 1;
+                    ok = vote_at(g, A.prec, c, hde, hfe, i);
+                }
             }
-        }
-        if (!ok) continue;
-        mc++;
+            if (!ok) continue;
+            s_t[atomicAdd(&s_nt, 1)] = s_q[q];
+            mc++;
 #pragma unroll
-        for (int a = 0; a < 5; a++) atomicAdd(&cnt[off[a] + idx[a]], 1u);
-        const Cell<float> c32 = cell32(c);
-        for (int i = 0; i < nh; i++) {
-            const uint32_t bit = 1u << (i & 31);
-            if (!(s_act[i >> 5] & bit) || (take[i >> 5] & bit)) continue;
-            if (vote_widened(g, c, c32, hde, hfe, i, A.width)) atomicOr(&ts.take[i >> 5], bit);
+            for (int a = 0; a < 5; a++) atomicAdd(&cnt[off[a] + idx[a]], 1u);
         }
+        __syncthreads();
+        // the hit finding over (track cell, listed hit) pairs, one pair per thread
+        const long long np = (long long)s_nt * na;
+        for (long long pr = tid; pr < np; pr += kTsThreads) {
+            const int q = (int)(pr / na), i = s_hit[pr % na];
+            const uint32_t bit = 1u << (i & 31);
+            if (take[i >> 5] & bit) continue;
+            int idx[5];
+            cell_index(g, ke, base + s_t[q], idx);
+            const Cell<double> c = cell_at(g, A.level, idx);
+            if (vote_widened(g, c, cell32(c), hde, hfe, i, A.width)) atomicOr(&ts.take[i >> 5], bit);
+        }
+        __syncthreads();   // the queues are refilled by the next chunk
     }
     if (mc) atomicAdd(&s_mc, mc);
     __syncthreads();
