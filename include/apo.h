@@ -176,7 +176,9 @@ typedef struct {
     int32_t *hit_track;      /* device, may be NULL: for every hit of the batch (CSR order of
                                 apo_hits) the track whose final maximum-vote cells took it in
                                 the hit finding of Section 3.3 (0-based), or -1 if none did.
-                                apo_solve_batch_host and the server require NULL. */
+                                With APO_SCHED_MAXSET it needs max_tracks > 1 (each round's
+                                track cells, see apo_solve_batch).  apo_solve_batch_host and
+                                the server require NULL. */
     int32_t schedule;        /* APO_SCHED_TOPK (default) or APO_SCHED_MAXSET */
     int32_t max_keep;        /* APO_SCHED_MAXSET: cells kept per event and level, >= 1 */
     int32_t slack;           /* APO_SCHED_MAXSET: vote groups down to vmax - slack are kept */
